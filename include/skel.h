@@ -1,0 +1,243 @@
+/*
+ * skel.h — C-ABI of the GB300 skeletonized fast multipole apply.
+ *
+ * The library evaluates u_i = sum_{j != i} G(x_i, x_j) q_j (Section 1,
+ * Eq. (1)) for the Laplace kernels of Eq. (2) and the 3D low-frequency
+ * Helmholtz kernel of Eq. (5) (normalised as e^{i kappa r} / (4 pi r)) with
+ * the strong recursive skeletonization FMM of the paper:
+ *   - skel_build: adaptive 2:1-balanced tree and neighbor lists (Section 3.1)
+ *     and the proxy-surface interpolative decompositions of Algorithm 1
+ *     (Section 2.1), computed on the host in FP64 / complex128 and uploaded
+ *     to the GPU once;
+ *   - skel_apply: Algorithm 2 (upward pass, ifo / ifs / tfo translations,
+ *     level-1 sum, downward pass) in hand-written sm_103a CUDA kernels.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns SKEL_OK (0) or a negative SKEL_ERR_* code; no
+ *     C++ exception crosses this boundary. skel_last_error() gives a
+ *     message for the last failure on the calling thread.
+ *   - Points are host FP64, row-major n x dim, and are copied.
+ *   - Charges q and potentials u are n x nrhs with each right-hand side
+ *     contiguous (column-major, user point order). FP64 precision uses
+ *     double (complex128 as interleaved (re, im) for Helmholtz); FP32 and
+ *     FP32_TC use float (complex64).
+ *   - A handle owns all host and device memory of its plan. One handle may be
+ *     used by one apply at a time (it owns the apply's workspace).
+ */
+#ifndef SKEL_H
+#define SKEL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define SKEL_OK            0
+#define SKEL_ERR_ARG      (-1)  /* invalid argument (null, size, range, layout) */
+#define SKEL_ERR_OOM      (-2)  /* host or device allocation failed            */
+#define SKEL_ERR_CUDA     (-3)  /* a CUDA runtime call failed                  */
+#define SKEL_ERR_TIMEOUT  (-4)  /* a bounded device wait gave up               */
+#define SKEL_ERR_NUMERIC  (-5)  /* non-finite input                            */
+#define SKEL_ERR_STATE    (-6)  /* handle not in the right state (e.g. host-only plan) */
+
+/* ---- kernels (Eq. (2), Eq. (5)) ----------------------------------------- */
+#define SKEL_LAPLACE_2D    0    /* G = -log|x-y| / (2 pi)          */
+#define SKEL_LAPLACE_3D    1    /* G = 1 / (4 pi |x-y|)            */
+#define SKEL_HELMHOLTZ_3D  2    /* G = e^{i kappa r} / (4 pi r)    */
+
+/* ---- apply precisions ------------------------------------------------- */
+#define SKEL_FP64     0   /* FP64 arithmetic, double charges/potentials            */
+#define SKEL_FP32     1   /* FP32 arithmetic on the CUDA cores, float in/out       */
+#define SKEL_FP32_TC  2   /* FP32 kernel evaluation, tensor-core contractions over
+                             right-hand sides (3-pass TF32 split, FP32 accumulate) */
+
+typedef struct skel_plan* skel_handle;
+
+typedef struct {
+    int    kind;    /* SKEL_LAPLACE_2D | SKEL_LAPLACE_3D | SKEL_HELMHOLTZ_3D */
+    double kappa;   /* wavenumber, Helmholtz only                             */
+} skel_kernel;
+
+typedef struct {
+    int proxy_p;      /* proxy Chebyshev nodes per box edge; 0 = default (2D: 32, 3D: 12) */
+    int nrhs_max;     /* largest nrhs any later apply will use; 0 = 32                   */
+    int host_only;    /* 1 = build the plan on the host only; apply returns SKEL_ERR_STATE */
+    int num_threads;  /* host threads used by the build; 0 = all                          */
+} skel_options;
+
+typedef struct {
+    int64_t n_points;
+    int     dim;
+    int     n_levels;        /* L: deepest level (root = level 0)                     */
+    int64_t n_boxes;         /* including the root                                     */
+    int64_t n_leaves;
+    int     k_max;           /* largest skeleton rank on levels >= 2                   */
+    int64_t n_index;         /* sum over boxes of |I_B|                                */
+    int64_t n_T;             /* sum over boxes of k_B (|I_B| - k_B) (T entries)        */
+    int64_t n_colleague, n_coarse, n_fine;   /* neighbor-list entries                  */
+    int64_t pairs_direct;    /* kernel evaluations per apply between touching leaves   */
+    int64_t pairs_far;       /* kernel evaluations per apply on all other translations */
+    int64_t n_work_items;    /* near-field work items of the device plan               */
+    double  t_tree;          /* seconds: tree + balance + neighbor lists               */
+    double  t_skel;          /* seconds: Algorithm 1 (all IDs)                         */
+    double  t_upload;        /* seconds: device plan construction and upload           */
+    int64_t device_bytes;    /* device memory held by the plan (all precisions)       */
+} skel_stats;
+
+/*
+ * skel_build — tree, neighbor lists and Algorithm 1 on the host, then upload.
+ *   points     host, n x dim row-major FP64, copied; must be finite
+ *   n, dim     n >= 1; dim = 2 for SKEL_LAPLACE_2D, 3 otherwise
+ *   k          kernel (kappa >= 0 for Helmholtz)
+ *   tol        ID tolerance, 0 < tol < 1 (rank rule |R_kk| > tol |R_00|)
+ *   leaf_size  b >= 1: boxes with more than b points are split (Section 3.1)
+ *   opts       may be NULL (defaults)
+ *   out        receives the handle; untouched on error
+ * The upload goes to the CUDA device that is current on the calling thread.
+ * Errors: SKEL_ERR_ARG, SKEL_ERR_NUMERIC (non-finite point), SKEL_ERR_OOM,
+ * SKEL_ERR_CUDA.
+ */
+int skel_build(const double* points, int64_t n, int dim, skel_kernel k,
+               double tol, int leaf_size, const skel_options* opts,
+               skel_handle* out);
+
+/*
+ * skel_apply — u = A~ q by Algorithm 2 on the GPU.
+ *   q, u       n x nrhs (see conventions); device pointers (the common case:
+ *              asynchronous on `stream`, no allocation, CUDA-graph
+ *              capturable) or host pointers (then staged through device
+ *              buffers that the handle allocates on first use, and the call
+ *              synchronises `stream` before returning). q and u must not
+ *              overlap; u is overwritten.
+ *   nrhs       1 <= nrhs <= opts.nrhs_max
+ *   precision  SKEL_FP64 | SKEL_FP32 | SKEL_FP32_TC
+ *   stream     a cudaStream_t, or NULL for the legacy default stream
+ * Errors: SKEL_ERR_ARG, SKEL_ERR_STATE (host-only plan), SKEL_ERR_CUDA,
+ * SKEL_ERR_OOM (host staging only).
+ */
+int skel_apply(skel_handle h, const void* q, void* u, int nrhs, int precision,
+               void* stream);
+
+/*
+ * skel_apply_transpose — qbar = A~^T ubar (plain transpose, no conjugation).
+ * Same arguments and rules as skel_apply. For the real Laplace kernels A~
+ * is symmetric and this equals skel_apply; for Helmholtz it runs Algorithm 2
+ * with every interpolation matrix T replaced by conj(T) (the kernel blocks
+ * are complex-symmetric and the neighbor relations symmetric).
+ */
+int skel_apply_transpose(skel_handle h, const void* ubar, void* qbar, int nrhs,
+                         int precision, void* stream);
+
+/* skel_free — release the handle and all its memory; NULL is a no-op. */
+void skel_free(skel_handle h);
+
+/* skel_info — sizes, ranks, work counts and build timings of a plan. */
+int skel_info(skel_handle h, skel_stats* s);
+
+/*
+ * skel_last_error — message of the last failed call on this thread (or an
+ * empty string). The pointer stays valid until the next call on the thread.
+ */
+const char* skel_last_error(void);
+
+/*
+ * ---- plan exchange ----------------------------------------------------
+ * A plan is the tree plus one ID per box, in this flat format (boxes in
+ * (level, Morton key) order, children by child index sum_d bit_d 2^d):
+ *   level[b], coord[b*dim + d]   box level and integer cell coordinates
+ *   parent[b]                    parent box, -1 for the root
+ *   is_leaf[b]                   1 for leaves
+ *   idx[idx_ptr[b] ..]           I_B as user point indices in slot order
+ *                                (leaf: ascending; tree box: the children's
+ *                                skeletons concatenated in child order)
+ *   piv[idx_ptr[b] ..]           positions within I_B: the first k[b] are the
+ *                                skeleton S_B in pivot order, then R_B
+ *   T[T_ptr[b] ..]               k_b x (|I_B| - k_b), column-major; complex
+ *                                plans store interleaved (re, im) pairs and
+ *                                T_ptr counts complex entries
+ * The root (level 0) has an empty index set unless it is the only box.
+ */
+typedef struct {
+    int64_t n_boxes;
+    int64_t n_index;
+    int64_t n_T;          /* entries (complex entries count once)      */
+    int     dim;
+    int     is_complex;
+    double  center[3];    /* root box centre (dim entries used)        */
+    double  side;         /* root box side                             */
+} skel_plan_dims;
+
+/* skel_plan_get_dims — sizes needed to export a plan. */
+int skel_plan_get_dims(skel_handle h, skel_plan_dims* d);
+
+/*
+ * skel_plan_export — copy the plan into caller-owned host arrays sized by
+ * skel_plan_get_dims (level, parent, is_leaf, k: n_boxes; coord:
+ * n_boxes*dim; idx_ptr, T_ptr: n_boxes+1; idx, piv: n_index; T: n_T, doubled
+ * for complex). Any pointer may be NULL to skip that array.
+ */
+int skel_plan_export(skel_handle h, int32_t* level, int32_t* coord,
+                     int64_t* parent, int8_t* is_leaf, int64_t* idx_ptr,
+                     int64_t* idx, int64_t* piv, int32_t* k, int64_t* T_ptr,
+                     double* T);
+
+/*
+ * skel_plan_import — build a handle from an externally computed plan in the
+ * format above (for example the IDs of another implementation of Algorithm
+ * 1) instead of running the library's own tree and ID. The library checks
+ * the plan's consistency (box order, parents, slot structure of every index
+ * set, permutations), derives the neighbor lists itself and uploads.
+ *   points, n, dim, k   as for skel_build
+ *   center, side        root box (dim entries of center)
+ * Errors: SKEL_ERR_ARG for any inconsistency, plus those of skel_build.
+ */
+int skel_plan_import(const double* points, int64_t n, int dim, skel_kernel k,
+                     const double* center, double side, int64_t n_boxes,
+                     const int32_t* level, const int32_t* coord,
+                     const int64_t* parent, const int8_t* is_leaf,
+                     const int64_t* idx_ptr, const int64_t* idx,
+                     const int64_t* piv, const int32_t* kk,
+                     const int64_t* T_ptr, const double* T,
+                     const skel_options* opts, skel_handle* out);
+
+/*
+ * skel_neighbors_export — one neighbor relation in CSR form.
+ *   which   0 = colleagues (same level, touching, self included),
+ *           1 = coarse neighbors (leaves one level up touching the box),
+ *           2 = fine neighbors (boxes one level down touching a leaf)
+ *   ptr     n_boxes + 1 entries (always filled)
+ *   list    ptr[n_boxes] entries, or NULL to query the size only
+ */
+int skel_neighbors_export(skel_handle h, int which, int64_t* ptr, int64_t* list);
+
+/*
+ * ---- phase timing -------------------------------------------------------
+ * skel_set_profiling(h, m) makes each of the next m applies record CUDA
+ * events on its stream at the boundaries of its six phases: permutation in,
+ * upward pass, translations (the near-field kernel), reduction of partial
+ * sums, downward pass, permutation out (seven event records per apply and
+ * nothing else; the events are created here, not in the apply). m = 0 turns
+ * it off. skel_last_timings waits for the captured applies and returns each
+ * phase's duration summed over them, in milliseconds, with the number of
+ * kernels they launched and the number of applies captured.
+ */
+typedef struct {
+    double ms[6];          /* permute_in, upward, translations, reduce, downward, permute_out */
+    int    launches;       /* kernels launched by the captured applies                        */
+    int    n_applies;      /* applies captured                                                */
+} skel_timings;
+
+/* skel_set_profiling — capture the next max_applies applies (0 = off, <= 100000). */
+int skel_set_profiling(skel_handle h, int max_applies);
+
+/* skel_last_timings — summed phase durations of the captured applies;
+ * SKEL_ERR_STATE if profiling is off. */
+int skel_last_timings(skel_handle h, skel_timings* t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKEL_H */

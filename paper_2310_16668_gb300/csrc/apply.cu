@@ -1,0 +1,303 @@
+// Algorithm 2 (FMM apply) on the GPU: CUDA-core kernels in FP64 and FP32.
+//
+// One apply, all on one stream:
+//   permute_in            q (user order)  -> leaf entries of Q
+//   up_kernel, l = L..2   qhat_S = q_S + T q_R, written into the parent's slot
+//   near_kernel           every translation (ifo / ifs / tfo / level-1 sum,
+//                         subtractions folded in as slot masks, see layout.cpp)
+//                         into per-work-item partial sums
+//   reduce_kernel         partial sums -> U (deterministic order)
+//   down_kernel, l = 2..L uhat_S = U[parent slot]; u_S += uhat; u_R += T^* uhat
+//   permute_out           leaf entries of U -> u (user order)
+//
+// The near field is the hot loop: a warp owns 32 targets (one per lane, in
+// registers) and streams the sources of its task range through a per-warp
+// shared-memory tile, every lane reading the same source (a broadcast).
+// Tasks between touching leaves (TASK_ADJ) hold the only close pairs: in FP32
+// they difference coordinates split into hi + lo floats, so a pair at
+// distance r keeps ~1e-7 relative accuracy however small r is, and they test
+// r^2 > 0 (the zero diagonal); every other task has pairs at least one small
+// box apart and uses the hi part alone.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "device.h"
+#include "skel_kernels.cuh"
+
+namespace skel {
+
+#define CUDA_CHECK(x)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (x);                                                           \
+        if (e_ != cudaSuccess)                                                          \
+            throw Error(-3, std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #x); \
+    } while (0)
+
+struct DeviceBuffers {
+    void* X = nullptr;       // Real4 per entry: (x, y, z, 0); FP32: hi part
+    void* Xlo = nullptr;     // FP32 only: lo part
+    void* T = nullptr;       // Real or complex
+    void* Q = nullptr;       // n_tot * nrhs_max
+    void* U = nullptr;
+    void* partial = nullptr; // n_items * 32 * nrhs_max
+};
+
+namespace {
+
+template <class T>
+T* dalloc(size_t n, int64_t& bytes) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(-2, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    bytes += (int64_t)(n * sizeof(T));
+    return (T*)p;
+}
+
+template <class T>
+T* upload(const std::vector<T>& v, int64_t& bytes) {
+    T* p = dalloc<T>(v.size(), bytes);
+    if (!v.empty()) CUDA_CHECK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+}
+
+template <class Real>
+void make_buffers(DevicePlan* dp, const Layout& lay, DeviceBuffers* b) {
+    using V = typename RealT<Real>::V4;
+    const int64_t nt = lay.n_tot;
+    const int w = dp->cplx ? 2 : 1;
+    std::vector<V> xh(nt), xl(nt);
+    for (int64_t e = 0; e < nt; ++e) {
+        double x[4] = {lay.X[e * 4], lay.X[e * 4 + 1], lay.X[e * 4 + 2], 0.0};
+        Real h[4], l[4];
+        for (int d = 0; d < 4; ++d) {
+            h[d] = (Real)x[d];
+            l[d] = (Real)(x[d] - (double)h[d]);
+        }
+        xh[e] = V{h[0], h[1], h[2], h[3]};
+        xl[e] = V{l[0], l[1], l[2], l[3]};
+    }
+    b->X = upload(xh, dp->bytes);
+    if (sizeof(Real) == 4) b->Xlo = upload(xl, dp->bytes);
+    std::vector<Real> tr(lay.T.size());
+    for (size_t i = 0; i < lay.T.size(); ++i) tr[i] = (Real)lay.T[i];
+    b->T = upload(tr, dp->bytes);
+    b->Q = dalloc<Real>((size_t)nt * dp->nrhs_max * w, dp->bytes);
+    b->U = dalloc<Real>((size_t)nt * dp->nrhs_max * w, dp->bytes);
+    b->partial = dalloc<Real>((size_t)dp->n_items * kChunk * dp->nrhs_max * w, dp->bytes);
+}
+
+void free_buffers(DeviceBuffers* b) {
+    if (!b) return;
+    cudaFree(b->X);
+    cudaFree(b->Xlo);
+    cudaFree(b->T);
+    cudaFree(b->Q);
+    cudaFree(b->U);
+    cudaFree(b->partial);
+    delete b;
+}
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+inline void mark(DevicePlan* dp, int i, cudaStream_t st) {
+    if (dp->prof_count < dp->prof_cap)
+        CUDA_CHECK(cudaEventRecord((cudaEvent_t)dp->events[dp->prof_count * 7 + i], st));
+}
+
+template <class Real, bool CPLX>
+void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrhs, bool transpose,
+               cudaStream_t st) {
+    int launches = 0;
+    using S = typename Scal<Real, CPLX>::T;
+    S* Q = (S*)b->Q;
+    S* U = (S*)b->U;
+    const S* T = (const S*)b->T;
+    S* part = (S*)b->partial;
+    const int64_t N = dp->N;
+    // 1. permute in
+    mark(dp, 0, st);
+    {
+        ++launches;
+        const int64_t n = N * nrhs;
+        permute_in<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->perm_entry, dp->perm_point, (const S*)q,
+                                                        Q, N, nrhs);
+        CUDA_CHECK(cudaGetLastError());
+    }
+    // 2. upward pass, levels L .. 2
+    mark(dp, 1, st);
+    for (int l = dp->L; l >= 2; --l) {
+        const int64_t b0 = dp->up_level_ptr[l], b1 = dp->up_level_ptr[l + 1];
+        if (b1 > b0) {
+            ++launches;
+            up_kernel<S><<<(unsigned)(b1 - b0), 128, 0, st>>>(dp->up + b0, dp->pos, T, Q, nrhs, transpose);
+            CUDA_CHECK(cudaGetLastError());
+        }
+    }
+    // 3. near field
+    mark(dp, 2, st);
+    if (dp->n_items > 0) {
+        NearArgs<Real, CPLX> a;
+        a.items = dp->items;
+        a.n_items = dp->n_items;
+        a.box_off = dp->box_off;
+        a.box_n = dp->box_n;
+        a.box_nslot = dp->box_nslot;
+        a.slot_start = dp->slot_start;
+        a.task_src = dp->task_src;
+        a.task_mask = dp->task_mask;
+        a.task_flags = dp->task_flags;
+        a.X = (const typename RealT<Real>::V4*)b->X;
+        a.Xlo = (const typename RealT<Real>::V4*)b->Xlo;
+        a.Q = Q;
+        a.partial = part;
+        a.nrhs = nrhs;
+        a.kappa = (Real)dp->kappa;
+        const unsigned grid = ceil_div(dp->n_items, kNearWarps);
+        launches += launch_near<Real, CPLX>(dp->kind, a, nrhs, grid, st);
+        CUDA_CHECK(cudaGetLastError());
+        mark(dp, 3, st);
+        ++launches;
+        const int64_t n = dp->n_chunks * kChunk * nrhs;
+        reduce_kernel<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->chunk_box, dp->chunk_t0, dp->chunk_item_ptr,
+                                                           dp->chunk_items, dp->box_off, dp->box_n, part, U,
+                                                           nrhs, dp->n_chunks);
+        CUDA_CHECK(cudaGetLastError());
+    }
+    else {
+        mark(dp, 3, st);
+    }
+    // 4. downward pass, levels 2 .. L
+    mark(dp, 4, st);
+    for (int l = 2; l <= dp->L; ++l) {
+        const int64_t b0 = dp->up_level_ptr[l], b1 = dp->up_level_ptr[l + 1];
+        if (b1 > b0) {
+            ++launches;
+            down_kernel<S><<<(unsigned)(b1 - b0), 256, 0, st>>>(dp->up + b0, dp->pos, T, U, nrhs, transpose);
+            CUDA_CHECK(cudaGetLastError());
+        }
+    }
+    // 5. permute out
+    mark(dp, 5, st);
+    {
+        ++launches;
+        const int64_t n = N * nrhs;
+        permute_out<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->perm_entry, dp->perm_point, U, (S*)u, N, nrhs);
+        CUDA_CHECK(cudaGetLastError());
+    }
+    mark(dp, 6, st);
+    if (dp->prof_count < dp->prof_cap) dp->prof_launches[dp->prof_count++] = launches;
+}
+
+}  // namespace
+
+DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
+    DevicePlan* dp = new DevicePlan();
+    try {
+        CUDA_CHECK(cudaGetDevice(&dp->device));
+        dp->dim = p.tree.dim;
+        dp->kind = p.kind;
+        dp->kappa = p.kappa;
+        dp->cplx = p.kind == 2;
+        dp->N = p.tree.n;
+        dp->n_tot = lay.n_tot;
+        dp->nrhs_max = nrhs_max;
+        dp->top = lay.top;
+        dp->L = p.tree.L;
+        dp->box_off = upload(lay.box_off, dp->bytes);
+        dp->box_n = upload(lay.box_n, dp->bytes);
+        dp->box_nslot = upload(lay.box_nslot, dp->bytes);
+        dp->slot_start = upload(lay.slot_start, dp->bytes);
+        dp->pos = upload(lay.pos, dp->bytes);
+        dp->perm_entry = upload(lay.perm_entry, dp->bytes);
+        dp->perm_point = upload(lay.perm_point, dp->bytes);
+        dp->up = upload(lay.up, dp->bytes);
+        dp->up_level_ptr = lay.up_level_ptr;
+        dp->task_src = upload(lay.task_src, dp->bytes);
+        dp->task_mask = upload(lay.task_mask, dp->bytes);
+        dp->task_flags = upload(lay.task_flags, dp->bytes);
+        dp->items = upload(lay.items, dp->bytes);
+        dp->n_items = (int64_t)lay.items.size();
+        dp->chunk_box = upload(lay.chunk_box, dp->bytes);
+        dp->chunk_t0 = upload(lay.chunk_t0, dp->bytes);
+        dp->chunk_item_ptr = upload(lay.chunk_item_ptr, dp->bytes);
+        dp->chunk_items = upload(lay.chunk_items, dp->bytes);
+        dp->n_chunks = (int64_t)lay.chunk_box.size();
+        dp->p64 = new DeviceBuffers();
+        make_buffers<double>(dp, lay, dp->p64);
+        dp->p32 = new DeviceBuffers();
+        make_buffers<float>(dp, lay, dp->p32);
+        CUDA_CHECK(cudaDeviceSynchronize());
+    } catch (...) {
+        device_plan_destroy(dp);
+        throw;
+    }
+    return dp;
+}
+
+void device_plan_destroy(DevicePlan* dp) {
+    if (!dp) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(dp->device);
+    void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->perm_entry,
+                    dp->perm_point, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
+                    dp->chunk_box, dp->chunk_t0, dp->chunk_item_ptr, dp->chunk_items, dp->stage_in,
+                    dp->stage_out};
+    for (void* p : ptrs) cudaFree(p);
+    for (void* e : dp->events)
+        if (e) cudaEventDestroy((cudaEvent_t)e);
+    free_buffers(dp->p64);
+    free_buffers(dp->p32);
+    cudaSetDevice(cur);
+    delete dp;
+}
+
+void device_set_profiling(DevicePlan* dp, int max_applies) {
+    if (max_applies < 0 || max_applies > 100000) throw Error(-1, "max_applies out of range");
+    while ((int)dp->events.size() < 7 * max_applies) {
+        cudaEvent_t e;
+        CUDA_CHECK(cudaEventCreate(&e));
+        dp->events.push_back((void*)e);
+    }
+    dp->prof_cap = max_applies;
+    dp->prof_count = 0;
+    dp->prof_launches.assign(max_applies, 0);
+}
+
+void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_applies) {
+    if (dp->prof_cap == 0) throw Error(-6, "profiling is not enabled");
+    for (int i = 0; i < 6; ++i) ms6[i] = 0;
+    *launches = 0;
+    for (int a = 0; a < dp->prof_count; ++a) {
+        CUDA_CHECK(cudaEventSynchronize((cudaEvent_t)dp->events[a * 7 + 6]));
+        for (int i = 0; i < 6; ++i) {
+            float ms = 0;
+            CUDA_CHECK(cudaEventElapsedTime(&ms, (cudaEvent_t)dp->events[a * 7 + i],
+                                            (cudaEvent_t)dp->events[a * 7 + i + 1]));
+            ms6[i] += ms;
+        }
+        *launches += dp->prof_launches[a];
+    }
+    *n_applies = dp->prof_count;
+}
+
+void device_apply(DevicePlan* dp, const void* q, void* u, int nrhs, int precision, bool transpose,
+                  void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == 0) {
+        if (dp->cplx) run_apply<double, true>(dp, dp->p64, q, u, nrhs, transpose, st);
+        else run_apply<double, false>(dp, dp->p64, q, u, nrhs, transpose, st);
+    } else {
+        if (dp->cplx) run_apply<float, true>(dp, dp->p32, q, u, nrhs, transpose, st);
+        else run_apply<float, false>(dp, dp->p32, q, u, nrhs, transpose, st);
+    }
+}
+
+}  // namespace skel

@@ -1,0 +1,455 @@
+// extern "C" entry points of skel.h. Every call catches all exceptions and
+// turns them into SKEL_ERR_* codes plus a thread-local message.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "../../include/skel.h"
+#include "device.h"
+#include "host.h"
+
+using skel::Error;
+
+struct skel_plan {
+    skel::Plan plan;
+    skel::DevicePlan* dev = nullptr;
+    int nrhs_max = 32;
+    bool host_only = false;
+    double t_upload = 0;
+    int64_t n_items = 0, pairs_direct = 0, pairs_far = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+double now() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+template <class F>
+int guarded(F&& f) {
+    try {
+        g_err.clear();
+        f();
+        return SKEL_OK;
+    } catch (const Error& e) {
+        return fail(e.code, e.what());
+    } catch (const std::bad_alloc&) {
+        return fail(SKEL_ERR_OOM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(SKEL_ERR_ARG, e.what());
+    } catch (...) {
+        return fail(SKEL_ERR_ARG, "unknown error");
+    }
+}
+
+void check_kernel(skel_kernel k, int dim) {
+    if (k.kind != SKEL_LAPLACE_2D && k.kind != SKEL_LAPLACE_3D && k.kind != SKEL_HELMHOLTZ_3D)
+        throw Error(SKEL_ERR_ARG, "unknown kernel kind");
+    if ((k.kind == SKEL_LAPLACE_2D) != (dim == 2) || (dim != 2 && dim != 3))
+        throw Error(SKEL_ERR_ARG, "dim does not match the kernel (2D Laplace: dim 2, others: dim 3)");
+    if (k.kind == SKEL_HELMHOLTZ_3D && !(std::isfinite(k.kappa) && k.kappa >= 0))
+        throw Error(SKEL_ERR_ARG, "kappa must be finite and >= 0");
+}
+
+void check_points(const double* pts, int64_t n, int dim) {
+    if (!pts) throw Error(SKEL_ERR_ARG, "points is NULL");
+    if (n < 1) throw Error(SKEL_ERR_ARG, "n must be >= 1");
+    if (n > ((int64_t)1 << 31) - 1) throw Error(SKEL_ERR_ARG, "n too large");
+    for (int64_t i = 0; i < n * dim; ++i)
+        if (!std::isfinite(pts[i])) throw Error(SKEL_ERR_NUMERIC, "non-finite point coordinate");
+}
+
+void finalize(skel_plan* h, const skel_options* opts) {
+    h->nrhs_max = (opts && opts->nrhs_max > 0) ? opts->nrhs_max : 32;
+    if (h->nrhs_max > 1024) throw Error(SKEL_ERR_ARG, "nrhs_max too large");
+    h->host_only = opts && opts->host_only;
+    double t0 = now();
+    skel::Layout lay;
+    skel::build_layout(h->plan, lay);
+    h->n_items = (int64_t)lay.items.size();
+    h->pairs_direct = lay.pairs_direct;
+    h->pairs_far = lay.pairs_far;
+    if (!h->host_only) h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max);
+    h->t_upload = now() - t0;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int do_apply(skel_handle h, const void* q, void* u, int nrhs, int precision, void* stream, bool transpose) {
+    return guarded([&] {
+        if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");
+        if (!q || !u) throw Error(SKEL_ERR_ARG, "q or u is NULL");
+        if (h->host_only || !h->dev) throw Error(SKEL_ERR_STATE, "plan was built host-only");
+        if (nrhs < 1 || nrhs > h->nrhs_max) throw Error(SKEL_ERR_ARG, "nrhs out of range [1, nrhs_max]");
+        if (precision != SKEL_FP64 && precision != SKEL_FP32 && precision != SKEL_FP32_TC)
+            throw Error(SKEL_ERR_ARG, "unknown precision");
+        skel::DevicePlan* dp = h->dev;
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != dp->device) throw Error(SKEL_ERR_STATE, "current CUDA device differs from the plan's device");
+        const size_t elem = (precision == SKEL_FP64 ? 8 : 4) * (dp->cplx ? 2 : 1);
+        const size_t bytes = elem * (size_t)dp->N * nrhs;
+        if (q == u || ((const char*)q < (const char*)u + bytes && (const char*)u < (const char*)q + bytes))
+            throw Error(SKEL_ERR_ARG, "q and u overlap");
+        const bool qd = is_device_ptr(q), ud = is_device_ptr(u);
+        cudaStream_t st = (cudaStream_t)stream;
+        const void* qq = q;
+        void* uu = u;
+        if (!qd || !ud) {
+            if (dp->stage_bytes < bytes) {
+                cudaFree(dp->stage_in);
+                cudaFree(dp->stage_out);
+                dp->stage_in = dp->stage_out = nullptr;
+                dp->stage_bytes = 0;
+                if (cudaMalloc(&dp->stage_in, bytes) != cudaSuccess || cudaMalloc(&dp->stage_out, bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    throw Error(SKEL_ERR_OOM, "staging allocation failed");
+                }
+                dp->stage_bytes = bytes;
+            }
+            if (!qd) {
+                if (cudaMemcpyAsync(dp->stage_in, q, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                    throw Error(SKEL_ERR_CUDA, "host-to-device copy failed");
+                qq = dp->stage_in;
+            }
+            if (!ud) uu = dp->stage_out;
+        }
+        skel::device_apply(dp, qq, uu, nrhs, precision, transpose, stream);
+        if (!ud) {
+            if (cudaMemcpyAsync(u, uu, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                throw Error(SKEL_ERR_CUDA, "device-to-host copy failed");
+        }
+        if (!qd || !ud) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) throw Error(SKEL_ERR_CUDA, std::string("apply: ") + cudaGetErrorString(e));
+        }
+    });
+}
+
+}  // namespace
+
+extern "C" {
+
+int skel_build(const double* points, int64_t n, int dim, skel_kernel k, double tol, int leaf_size,
+               const skel_options* opts, skel_handle* out) {
+    return guarded([&] {
+        if (!out) throw Error(SKEL_ERR_ARG, "out is NULL");
+        check_kernel(k, dim);
+        check_points(points, n, dim);
+        if (!(tol > 0 && tol < 1)) throw Error(SKEL_ERR_ARG, "tol must be in (0, 1)");
+        if (leaf_size < 1) throw Error(SKEL_ERR_ARG, "leaf_size must be >= 1");
+        skel_plan* h = new skel_plan();
+        try {
+            skel::Plan& P = h->plan;
+            P.kind = k.kind;
+            P.kappa = k.kappa;
+            P.tol = tol;
+            P.leaf_size = leaf_size;
+            P.proxy_p = (opts && opts->proxy_p > 0) ? opts->proxy_p : (dim == 2 ? 32 : 12);
+            P.pts.assign(points, points + n * dim);
+            double t0 = now();
+            std::vector<std::vector<int64_t>> leaf_points;
+            skel::build_tree(points, n, dim, leaf_size, P.tree, leaf_points);
+            double t1 = now();
+            skel::build_skeletons(P, leaf_points, opts ? opts->num_threads : 0);
+            P.t_tree = t1 - t0;
+            P.t_skel = now() - t1;
+            finalize(h, opts);
+        } catch (...) {
+            if (h->dev) skel::device_plan_destroy(h->dev);
+            delete h;
+            throw;
+        }
+        *out = h;
+    });
+}
+
+int skel_apply(skel_handle h, const void* q, void* u, int nrhs, int precision, void* stream) {
+    return do_apply(h, q, u, nrhs, precision, stream, false);
+}
+
+int skel_apply_transpose(skel_handle h, const void* ubar, void* qbar, int nrhs, int precision, void* stream) {
+    return do_apply(h, ubar, qbar, nrhs, precision, stream, true);
+}
+
+void skel_free(skel_handle h) {
+    if (!h) return;
+    skel::device_plan_destroy(h->dev);
+    delete h;
+}
+
+int skel_info(skel_handle h, skel_stats* s) {
+    return guarded([&] {
+        if (!h || !s) throw Error(SKEL_ERR_ARG, "NULL argument");
+        const skel::Plan& P = h->plan;
+        const skel::Tree& t = P.tree;
+        std::memset(s, 0, sizeof(*s));
+        s->n_points = t.n;
+        s->dim = t.dim;
+        s->n_levels = t.L;
+        s->n_boxes = t.nb;
+        for (int64_t b = 0; b < t.nb; ++b) {
+            s->n_leaves += t.is_leaf[b];
+            if (t.level[b] >= 2) s->k_max = std::max(s->k_max, (int)P.sk.k[b]);
+        }
+        s->n_index = P.sk.idx_ptr[t.nb];
+        s->n_T = P.sk.T_ptr[t.nb];
+        s->n_colleague = (int64_t)t.coll.size();
+        s->n_coarse = (int64_t)t.coarse.size();
+        s->n_fine = (int64_t)t.fine.size();
+        s->pairs_direct = h->pairs_direct;
+        s->pairs_far = h->pairs_far;
+        s->n_work_items = h->n_items;
+        s->t_tree = P.t_tree;
+        s->t_skel = P.t_skel;
+        s->t_upload = h->t_upload;
+        s->device_bytes = h->dev ? h->dev->bytes : 0;
+    });
+}
+
+const char* skel_last_error(void) { return g_err.c_str(); }
+
+int skel_plan_get_dims(skel_handle h, skel_plan_dims* d) {
+    return guarded([&] {
+        if (!h || !d) throw Error(SKEL_ERR_ARG, "NULL argument");
+        const skel::Plan& P = h->plan;
+        std::memset(d, 0, sizeof(*d));
+        d->n_boxes = P.tree.nb;
+        d->n_index = P.sk.idx_ptr[P.tree.nb];
+        d->n_T = P.sk.T_ptr[P.tree.nb];
+        d->dim = P.tree.dim;
+        d->is_complex = P.sk.cplx ? 1 : 0;
+        for (int i = 0; i < P.tree.dim; ++i) d->center[i] = P.tree.center[i];
+        d->side = P.tree.side;
+    });
+}
+
+int skel_plan_export(skel_handle h, int32_t* level, int32_t* coord, int64_t* parent, int8_t* is_leaf,
+                     int64_t* idx_ptr, int64_t* idx, int64_t* piv, int32_t* k, int64_t* T_ptr, double* T) {
+    return guarded([&] {
+        if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");
+        const skel::Plan& P = h->plan;
+        const skel::Tree& t = P.tree;
+        const int64_t nb = t.nb;
+        if (level) std::copy(t.level.begin(), t.level.end(), level);
+        if (coord) for (int64_t i = 0; i < nb * t.dim; ++i) coord[i] = (int32_t)t.coord[i];
+        if (parent) std::copy(t.parent.begin(), t.parent.end(), parent);
+        if (is_leaf) std::copy(t.is_leaf.begin(), t.is_leaf.end(), is_leaf);
+        if (idx_ptr) std::copy(P.sk.idx_ptr.begin(), P.sk.idx_ptr.end(), idx_ptr);
+        if (idx) std::copy(P.sk.idx.begin(), P.sk.idx.end(), idx);
+        if (piv) std::copy(P.sk.piv.begin(), P.sk.piv.end(), piv);
+        if (k) std::copy(P.sk.k.begin(), P.sk.k.end(), k);
+        if (T_ptr) std::copy(P.sk.T_ptr.begin(), P.sk.T_ptr.end(), T_ptr);
+        if (T) std::copy(P.sk.T.begin(), P.sk.T.end(), T);
+    });
+}
+
+int skel_plan_import(const double* points, int64_t n, int dim, skel_kernel kern, const double* center,
+                     double side, int64_t nb, const int32_t* level, const int32_t* coord,
+                     const int64_t* parent, const int8_t* is_leaf, const int64_t* idx_ptr,
+                     const int64_t* idx, const int64_t* piv, const int32_t* kk, const int64_t* T_ptr,
+                     const double* T, const skel_options* opts, skel_handle* out) {
+    return guarded([&] {
+        if (!out) throw Error(SKEL_ERR_ARG, "out is NULL");
+        check_kernel(kern, dim);
+        check_points(points, n, dim);
+        if (!center || !level || !coord || !parent || !is_leaf || !idx_ptr || !idx || !piv || !kk || !T_ptr ||
+            (!T && T_ptr[nb] > 0))
+            throw Error(SKEL_ERR_ARG, "NULL plan array");
+        if (!(side > 0) || !std::isfinite(side) || nb < 1) throw Error(SKEL_ERR_ARG, "bad root box or box count");
+        const int D = skel::max_depth(dim);
+        skel_plan* h = new skel_plan();
+        try {
+            skel::Plan& P = h->plan;
+            P.kind = kern.kind;
+            P.kappa = kern.kappa;
+            P.pts.assign(points, points + n * dim);
+            skel::Tree& t = P.tree;
+            t.dim = dim;
+            t.n = n;
+            t.side = side;
+            for (int d = 0; d < dim; ++d) {
+                t.center[d] = center[d];
+                t.corner[d] = center[d] - side * 0.5;
+            }
+            t.nb = nb;
+            t.level.assign(level, level + nb);
+            t.coord.resize(nb * dim);
+            for (int64_t i = 0; i < nb * dim; ++i) t.coord[i] = coord[i];
+            t.parent.assign(parent, parent + nb);
+            t.is_leaf.assign(is_leaf, is_leaf + nb);
+            // structural checks
+            if (t.level[0] != 0 || t.parent[0] != -1) throw Error(SKEL_ERR_ARG, "box 0 must be the root");
+            std::vector<int64_t> nchild(nb, 0);
+            for (int64_t b = 1; b < nb; ++b) {
+                const int l = t.level[b];
+                if (l < 1 || l > D || l < t.level[b - 1]) throw Error(SKEL_ERR_ARG, "boxes not sorted by level");
+                const int64_t p = t.parent[b];
+                if (p < 0 || p >= b || t.level[p] != l - 1) throw Error(SKEL_ERR_ARG, "bad parent");
+                for (int d = 0; d < dim; ++d) {
+                    const int64_t c = t.coord[b * dim + d];
+                    if (c < 0 || c >= ((int64_t)1 << l) || (c >> 1) != t.coord[p * dim + d])
+                        throw Error(SKEL_ERR_ARG, "box coordinates inconsistent with parent");
+                }
+                nchild[p]++;
+            }
+            for (int64_t b = 0; b < nb; ++b)
+                if ((nchild[b] == 0) != (t.is_leaf[b] != 0)) throw Error(SKEL_ERR_ARG, "is_leaf inconsistent");
+            skel::finish_tree(t);
+            // box order within a level: strictly increasing Morton key
+            // (finish_tree's lookup would silently merge duplicates)
+            for (int64_t b = 1; b < nb; ++b) {
+                if (t.level[b] != t.level[b - 1]) continue;
+                auto key = [&](int64_t x) {
+                    uint64_t kk2 = 0;
+                    for (int bit = 0; bit < (dim == 2 ? 32 : 21); ++bit)
+                        for (int d = 0; d < dim; ++d)
+                            kk2 |= (uint64_t)((t.coord[x * dim + d] >> bit) & 1) << (bit * dim + d);
+                    return kk2;
+                };
+                if (!(key(b - 1) < key(b))) throw Error(SKEL_ERR_ARG, "boxes not in Morton order");
+            }
+            // 2:1 balance: no leaf touches a box two or more levels finer
+            for (int64_t b = 0; b < nb; ++b) {
+                if (!t.is_leaf[b]) continue;
+                for (int64_t q = t.coll_ptr[b]; q < t.coll_ptr[b + 1]; ++q) {
+                    const int64_t c = t.coll[q];
+                    if (c == b || t.is_leaf[c]) continue;
+                    for (int64_t r = t.child_ptr[c]; r < t.child_ptr[c + 1]; ++r) {
+                        const int64_t ch = t.child[r];
+                        if (t.is_leaf[ch]) continue;
+                        for (int64_t s = t.child_ptr[ch]; s < t.child_ptr[ch + 1]; ++s) {
+                            const int64_t g = t.child[s];
+                            if (skel::touches(t.level[b], &t.coord[b * dim], t.level[g], &t.coord[g * dim], dim))
+                                throw Error(SKEL_ERR_ARG, "plan is not 2:1 balanced");
+                        }
+                    }
+                }
+            }
+            // index sets and IDs
+            skel::Skel& sk = P.sk;
+            sk.cplx = kern.kind == SKEL_HELMHOLTZ_3D;
+            sk.idx_ptr.assign(idx_ptr, idx_ptr + nb + 1);
+            if (sk.idx_ptr[0] != 0) throw Error(SKEL_ERR_ARG, "idx_ptr[0] != 0");
+            for (int64_t b = 0; b < nb; ++b)
+                if (sk.idx_ptr[b + 1] < sk.idx_ptr[b]) throw Error(SKEL_ERR_ARG, "idx_ptr not monotone");
+            const int64_t ni = sk.idx_ptr[nb];
+            sk.idx.assign(idx, idx + ni);
+            sk.piv.assign(piv, piv + ni);
+            sk.k.assign(kk, kk + nb);
+            sk.T_ptr.assign(T_ptr, T_ptr + nb + 1);
+            const int w = sk.cplx ? 2 : 1;
+            sk.T.assign(T, T + sk.T_ptr[nb] * w);
+            std::vector<char> seen(n, 0);
+            const double scale = std::ldexp(1.0, D);
+            for (int64_t b = 0; b < nb; ++b) {
+                const int64_t nbI = sk.idx_ptr[b + 1] - sk.idx_ptr[b];
+                const int64_t* I = &sk.idx[sk.idx_ptr[b]];
+                if (t.level[b] == 0 && t.L > 0) {
+                    if (nbI != 0) throw Error(SKEL_ERR_ARG, "root must have an empty index set");
+                    continue;
+                }
+                if (nbI < 1 || nbI > (int64_t)1 << 30) throw Error(SKEL_ERR_ARG, "empty index set");
+                if (sk.k[b] < 1 || sk.k[b] > nbI) throw Error(SKEL_ERR_ARG, "k out of range");
+                if (sk.T_ptr[b + 1] - sk.T_ptr[b] != (int64_t)sk.k[b] * (nbI - sk.k[b]))
+                    throw Error(SKEL_ERR_ARG, "T size does not match k x |R|");
+                std::vector<char> pv(nbI, 0);
+                for (int64_t i = 0; i < nbI; ++i) {
+                    const int64_t pp = sk.piv[sk.idx_ptr[b] + i];
+                    if (pp < 0 || pp >= nbI || pv[pp]) throw Error(SKEL_ERR_ARG, "piv is not a permutation");
+                    pv[pp] = 1;
+                    if (I[i] < 0 || I[i] >= n) throw Error(SKEL_ERR_ARG, "point index out of range");
+                }
+                if (t.is_leaf[b]) {
+                    const int l = t.level[b];
+                    for (int64_t i = 0; i < nbI; ++i) {
+                        if (seen[I[i]]) throw Error(SKEL_ERR_ARG, "point in two leaves");
+                        seen[I[i]] = 1;
+                        for (int d = 0; d < dim; ++d) {
+                            double tt = (points[I[i] * dim + d] - t.corner[d]) / side;
+                            int64_t v = (int64_t)std::floor(tt * scale);
+                            v = std::min(std::max(v, (int64_t)0), ((int64_t)1 << D) - 1);
+                            if ((v >> (D - l)) != t.coord[b * dim + d])
+                                throw Error(SKEL_ERR_ARG, "point outside its leaf box");
+                        }
+                    }
+                } else {
+                    int64_t o = 0;
+                    for (int64_t q = t.child_ptr[b]; q < t.child_ptr[b + 1]; ++q) {
+                        const int64_t c = t.child[q];
+                        for (int i = 0; i < sk.k[c]; ++i, ++o) {
+                            const int64_t s = sk.idx[sk.idx_ptr[c] + sk.piv[sk.idx_ptr[c] + i]];
+                            if (o >= nbI || I[o] != s)
+                                throw Error(SKEL_ERR_ARG, "tree-box index set is not its children's skeletons");
+                        }
+                    }
+                    if (o != nbI) throw Error(SKEL_ERR_ARG, "tree-box index set is not its children's skeletons");
+                }
+            }
+            for (int64_t i = 0; i < n; ++i)
+                if (!seen[i]) throw Error(SKEL_ERR_ARG, "point in no leaf");
+            finalize(h, opts);
+        } catch (...) {
+            if (h->dev) skel::device_plan_destroy(h->dev);
+            delete h;
+            throw;
+        }
+        *out = h;
+    });
+}
+
+int skel_neighbors_export(skel_handle h, int which, int64_t* ptr, int64_t* list) {
+    return guarded([&] {
+        if (!h || !ptr) throw Error(SKEL_ERR_ARG, "NULL argument");
+        const skel::Tree& t = h->plan.tree;
+        const std::vector<int64_t>* p = nullptr;
+        const std::vector<int64_t>* l = nullptr;
+        if (which == 0) { p = &t.coll_ptr; l = &t.coll; }
+        else if (which == 1) { p = &t.coarse_ptr; l = &t.coarse; }
+        else if (which == 2) { p = &t.fine_ptr; l = &t.fine; }
+        else throw Error(SKEL_ERR_ARG, "which must be 0, 1 or 2");
+        std::copy(p->begin(), p->end(), ptr);
+        if (list) std::copy(l->begin(), l->end(), list);
+    });
+}
+
+int skel_set_profiling(skel_handle h, int max_applies) {
+    return guarded([&] {
+        if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");
+        if (!h->dev) throw Error(SKEL_ERR_STATE, "plan was built host-only");
+        skel::device_set_profiling(h->dev, max_applies);
+    });
+}
+
+int skel_last_timings(skel_handle h, skel_timings* t) {
+    return guarded([&] {
+        if (!h || !t) throw Error(SKEL_ERR_ARG, "NULL argument");
+        if (!h->dev) throw Error(SKEL_ERR_STATE, "plan was built host-only");
+        skel::device_last_timings(h->dev, t->ms, &t->launches, &t->n_applies);
+    });
+}
+
+}  // extern "C"

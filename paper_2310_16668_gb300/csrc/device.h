@@ -1,0 +1,69 @@
+// Device-resident plan and the apply entry points used by the C-ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "host.h"
+
+namespace skel {
+
+struct DeviceBuffers;   // per precision (defined in apply.cu)
+
+struct DevicePlan {
+    int device = 0;
+    int dim = 3, kind = 1;
+    double kappa = 0.0;
+    bool cplx = false;
+    int64_t N = 0, n_tot = 0;
+    int nrhs_max = 32;
+    int top = 1, L = 0;
+    // shared index arrays (device)
+    int64_t* box_off = nullptr;
+    int32_t* box_n = nullptr;
+    int32_t* box_nslot = nullptr;
+    int32_t* slot_start = nullptr;
+    int32_t* pos = nullptr;
+    int64_t* perm_entry = nullptr;
+    int64_t* perm_point = nullptr;
+    UpBox* up = nullptr;
+    std::vector<int64_t> up_level_ptr;     // host copy
+    int64_t* task_src = nullptr;
+    uint64_t* task_mask = nullptr;
+    int32_t* task_flags = nullptr;
+    WorkItem* items = nullptr;
+    int64_t n_items = 0;
+    int64_t* chunk_box = nullptr;
+    int32_t* chunk_t0 = nullptr;
+    int64_t* chunk_item_ptr = nullptr;
+    int64_t* chunk_items = nullptr;
+    int64_t n_chunks = 0;
+    DeviceBuffers* p64 = nullptr;
+    DeviceBuffers* p32 = nullptr;
+    // optional per-phase CUDA events (permute_in, up, near, reduce, down,
+    // permute_out): 7 events for each of up to prof_cap applies
+    std::vector<void*> events;
+    int prof_cap = 0, prof_count = 0;
+    std::vector<int> prof_launches;
+    // host-pointer staging (allocated on first host-pointer call)
+    void* stage_in = nullptr;
+    void* stage_out = nullptr;
+    size_t stage_bytes = 0;
+    int64_t bytes = 0;
+};
+
+// Upload a layout; throws Error on failure.
+DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max);
+void device_plan_destroy(DevicePlan* dp);
+// capture the phases of the next max_applies applies (0 = off)
+void device_set_profiling(DevicePlan* dp, int max_applies);
+// summed milliseconds of the 6 phases over the captured applies (waits for them)
+void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_applies);
+
+// Algorithm 2 on `stream`. q, u: device pointers in user order (n x nrhs,
+// each right-hand side contiguous). transpose: run with conj(T).
+void device_apply(DevicePlan* dp, const void* q, void* u, int nrhs, int precision,
+                  bool transpose, void* stream);
+
+}  // namespace skel

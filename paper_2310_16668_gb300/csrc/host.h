@@ -1,0 +1,126 @@
+// Host-side plan of the skeletonized FMM: tree (Section 3.1), per-box
+// interpolative decompositions (Algorithm 1) and the flattened device layout
+// used by the apply kernels (Algorithm 2).
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace skel {
+
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+inline int max_depth(int dim) { return dim == 2 ? 31 : 21; }
+
+// Balanced adaptive tree. Boxes are numbered by (level, Morton key); the
+// children of a box are listed by child index sum_d bit_d 2^d (x lowest).
+struct Tree {
+    int dim = 3;
+    int64_t n = 0;
+    double center[3] = {0, 0, 0};
+    double corner[3] = {0, 0, 0};
+    double side = 1.0;
+    int L = 0;                       // deepest level
+    int64_t nb = 0;                  // number of boxes
+    std::vector<int32_t> level;      // nb
+    std::vector<int64_t> coord;      // nb * dim
+    std::vector<int64_t> parent;     // nb, -1 for the root
+    std::vector<int8_t> is_leaf;     // nb
+    std::vector<int64_t> child_ptr, child;      // CSR
+    std::vector<int64_t> level_ptr;             // L + 2
+    std::vector<int64_t> coll_ptr, coll;        // colleagues (self included)
+    std::vector<int64_t> coarse_ptr, coarse;    // leaves one level up, touching
+    std::vector<int64_t> fine_ptr, fine;        // boxes one level down, touching (leaves only)
+};
+
+// Per-box IDs; index sets in slot order, piv = positions (S first).
+struct Skel {
+    bool cplx = false;
+    std::vector<int64_t> idx_ptr, idx, piv;
+    std::vector<int32_t> k;
+    std::vector<int64_t> T_ptr;      // in entries (complex entries count once)
+    std::vector<double> T;           // real: 1 double / entry, complex: 2
+};
+
+struct Plan {
+    int kind = 1;
+    double kappa = 0.0;
+    double tol = 0.0;
+    int leaf_size = 0;
+    int proxy_p = 0;
+    std::vector<double> pts;         // n * dim
+    Tree tree;
+    Skel sk;
+    double t_tree = 0, t_skel = 0;
+};
+
+bool touches(int la, const int64_t* ca, int lb, const int64_t* cb, int dim);
+
+// Tree construction from points (root cube, split while > b, prune empty,
+// 2:1 balance between a leaf and every box touching it) and its neighbor lists.
+void build_tree(const double* pts, int64_t n, int dim, int leaf_size, Tree& t,
+                std::vector<std::vector<int64_t>>& leaf_points);
+// Derive children, level ranges and neighbor lists from level/coord/parent/is_leaf.
+void finish_tree(Tree& t);
+
+// Algorithm 1: IDs of all boxes on levels L..2 (level-1 boxes keep S = I_B).
+void build_skeletons(Plan& p, const std::vector<std::vector<int64_t>>& leaf_points,
+                     int nthreads);
+
+// Host kernel values for the proxy matrices.
+std::complex<double> kernel_value(int kind, double kappa, const double* x,
+                                  const double* y, int dim);
+
+// ---- flattened device layout ---------------------------------------------
+constexpr int kMaxSlots = 8;
+constexpr int kChunk = 32;             // targets per warp work item
+enum TaskFlags : int32_t { TASK_ADJ = 1 };
+
+struct UpBox {                          // one box of the upward / downward pass
+    int64_t off;                        // entry offset of I_B
+    int64_t dst;                        // entry offset of S_B inside the parent
+    int64_t T_off;                      // T entries offset
+    int32_t n, k;
+};
+
+struct WorkItem {                       // one warp: 32 targets x a task range
+    int64_t tgt_box;
+    int32_t t0;
+    int32_t task_lo, task_hi;
+    int32_t pad;
+};
+
+struct Layout {
+    int top = 1;
+    int64_t n_tot = 0;
+    std::vector<int64_t> box_off;       // nb, -1 if the box holds no entries
+    std::vector<int32_t> box_n;
+    std::vector<int32_t> box_nslot;
+    std::vector<int32_t> slot_start;    // nb * (kMaxSlots + 1)
+    std::vector<double> X;              // n_tot * 4 (x, y, z, 0)
+    std::vector<int64_t> perm_entry, perm_point;  // leaf entries <-> user points
+    std::vector<int32_t> pos;           // n_tot: piv of the owning box
+    std::vector<UpBox> up;              // boxes of levels >= max(2, top+1)
+    std::vector<int64_t> up_level_ptr;  // up[] ranges, index = level
+    std::vector<double> T;              // all T, column-major per box
+    // near field
+    std::vector<int64_t> task_ptr;      // nb + 1
+    std::vector<int64_t> task_src;
+    std::vector<uint64_t> task_mask;    // bit (c*8 + c'): skip target slot c x source slot c'
+    std::vector<int32_t> task_flags;
+    std::vector<WorkItem> items;        // execution order
+    std::vector<int64_t> chunk_box;     // per target chunk: box
+    std::vector<int32_t> chunk_t0;
+    std::vector<int64_t> chunk_item_ptr, chunk_items;
+    int64_t pairs_direct = 0, pairs_far = 0;
+};
+
+void build_layout(const Plan& p, Layout& lay);
+
+}  // namespace skel

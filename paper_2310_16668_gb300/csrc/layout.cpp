@@ -1,0 +1,228 @@
+// Flattened device layout of Algorithm 2 with the translations regrouped.
+//
+// Entry space: every box B on levels >= top (top = 1, or 0 when the root is
+// the only box) owns a contiguous segment of |I_B| entries in slot order, so
+// a tree box's segment is its children's skeletons back to back. The upward
+// pass writes qhat_{S_c} of child c straight into slot c of its parent's
+// segment (the concatenation of Algorithm 2 is free), and the downward pass
+// reads uhat_{S_c} from the same place.
+//
+// Near field. Algorithm 2 adds u_B += A_{B,B_j} q_{B_j} over colleagues and,
+// one level down, subtracts uhat_{S_c} -= A_{S_c,S_c'} qhat_{S_c'} over
+// colleague children c, c'. Both write the same entries of level l's entry
+// space (uhat_{S_c} lives in slot c of the parent), and qhat_{S_c'} is slot
+// c' of the colleague's segment, so the subtraction cancels exactly the
+// (c, c') block of the addition. The layout therefore evaluates every
+// colleague block once with the touching child pairs masked out (a 64-bit
+// mask per task, bit c*8 + c'). The ifs and tfo subtractions cancel blocks
+// the same way (a child touching a colleague leaf; a colleague's child
+// touching a leaf), and their additions become unmasked tasks between
+// levels. The sums are regrouped, never approximated.
+//
+// Tasks between two touching leaves are flagged TASK_ADJ: only they can hold
+// arbitrarily close (or coincident) pairs.
+#include <algorithm>
+#include <numeric>
+
+#include "host.h"
+
+namespace skel {
+
+namespace {
+constexpr int64_t kItemCost = 2048;   // source entries per warp work item
+}
+
+void build_layout(const Plan& p, Layout& lay) {
+    const Tree& t = p.tree;
+    const Skel& sk = p.sk;
+    const int dim = t.dim;
+    const int64_t nb = t.nb;
+    lay.top = t.L >= 1 ? 1 : 0;
+
+    // ---- entry space ----------------------------------------------------
+    lay.box_off.assign(nb, -1);
+    lay.box_n.assign(nb, 0);
+    lay.box_nslot.assign(nb, 0);
+    lay.slot_start.assign(nb * (kMaxSlots + 1), 0);
+    int64_t off = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        if (t.level[b] < lay.top) continue;
+        const int64_t n = sk.idx_ptr[b + 1] - sk.idx_ptr[b];
+        lay.box_off[b] = off;
+        lay.box_n[b] = (int32_t)n;
+        off += n;
+        int32_t* ss = &lay.slot_start[b * (kMaxSlots + 1)];
+        if (t.is_leaf[b]) {
+            lay.box_nslot[b] = 1;
+            ss[0] = 0;
+            ss[1] = (int32_t)n;
+        } else {
+            int s = 0;
+            int32_t acc = 0;
+            for (int64_t q = t.child_ptr[b]; q < t.child_ptr[b + 1]; ++q, ++s) {
+                ss[s] = acc;
+                acc += sk.k[t.child[q]];
+            }
+            ss[s] = acc;
+            lay.box_nslot[b] = s;
+            if (acc != n) throw Error(-1, "layout: index set is not the children's skeletons");
+        }
+    }
+    lay.n_tot = off;
+    lay.X.assign(lay.n_tot * 4, 0.0);
+    lay.pos.assign(lay.n_tot, 0);
+    lay.perm_entry.clear();
+    lay.perm_point.clear();
+    for (int64_t b = 0; b < nb; ++b) {
+        if (lay.box_off[b] < 0) continue;
+        const int64_t o = lay.box_off[b];
+        for (int64_t i = 0; i < lay.box_n[b]; ++i) {
+            const int64_t pt = sk.idx[sk.idx_ptr[b] + i];
+            for (int d = 0; d < dim; ++d) lay.X[(o + i) * 4 + d] = p.pts[pt * dim + d];
+            lay.pos[o + i] = (int32_t)sk.piv[sk.idx_ptr[b] + i];
+            if (t.is_leaf[b]) {
+                lay.perm_entry.push_back(o + i);
+                lay.perm_point.push_back(pt);
+            }
+        }
+    }
+
+    // ---- upward / downward boxes -----------------------------------------
+    const int lo_up = std::max(2, lay.top + 1);
+    lay.up.clear();
+    lay.up_level_ptr.assign(t.L + 2, 0);
+    for (int l = 0; l <= t.L; ++l) {
+        lay.up_level_ptr[l] = (int64_t)lay.up.size();
+        if (l < lo_up) continue;
+        for (int64_t b = t.level_ptr[l]; b < t.level_ptr[l + 1]; ++b) {
+            const int64_t par = t.parent[b];
+            int s = 0;
+            for (int64_t q = t.child_ptr[par]; q < t.child_ptr[par + 1]; ++q, ++s)
+                if (t.child[q] == b) break;
+            UpBox u;
+            u.off = lay.box_off[b];
+            u.dst = lay.box_off[par] + lay.slot_start[par * (kMaxSlots + 1) + s];
+            u.T_off = sk.T_ptr[b];
+            u.n = lay.box_n[b];
+            u.k = sk.k[b];
+            lay.up.push_back(u);
+        }
+    }
+    lay.up_level_ptr[t.L + 1] = (int64_t)lay.up.size();
+    lay.T = sk.T;
+
+    // ---- near-field tasks ---------------------------------------------------
+    auto child_of = [&](int64_t b, int s) { return t.child[t.child_ptr[b] + s]; };
+    auto C = [&](int64_t b) { return &t.coord[b * dim]; };
+    lay.task_ptr.assign(nb + 1, 0);
+    lay.task_src.clear();
+    lay.task_mask.clear();
+    lay.task_flags.clear();
+    lay.pairs_direct = lay.pairs_far = 0;
+    auto slot_size = [&](int64_t b, int s) {
+        const int32_t* ss = &lay.slot_start[b * (kMaxSlots + 1)];
+        return (int64_t)(ss[s + 1] - ss[s]);
+    };
+    auto add_task = [&](int64_t b, int64_t src, uint64_t mask, int32_t flags) {
+        lay.task_src.push_back(src);
+        lay.task_mask.push_back(mask);
+        lay.task_flags.push_back(flags);
+        for (int i = 0; i < lay.box_nslot[b]; ++i)
+            for (int j = 0; j < lay.box_nslot[src]; ++j)
+                if (!((mask >> (i * 8 + j)) & 1)) {
+                    int64_t pr = slot_size(b, i) * slot_size(src, j);
+                    if (flags & TASK_ADJ) lay.pairs_direct += pr; else lay.pairs_far += pr;
+                }
+    };
+    for (int64_t b = 0; b < nb; ++b) {
+        lay.task_ptr[b] = (int64_t)lay.task_src.size();
+        if (lay.box_off[b] < 0) continue;
+        const int l = t.level[b];
+        const bool bl = t.is_leaf[b];
+        for (int64_t q = t.coll_ptr[b]; q < t.coll_ptr[b + 1]; ++q) {
+            const int64_t bj = t.coll[q];
+            const bool jl = t.is_leaf[bj];
+            uint64_t mask = 0;
+            int32_t flags = 0;
+            if (bl && jl) {
+                flags = TASK_ADJ;
+            } else if (!bl && !jl) {
+                for (int i = 0; i < lay.box_nslot[b]; ++i)
+                    for (int j = 0; j < lay.box_nslot[bj]; ++j) {
+                        const int64_t ci = child_of(b, i), cj = child_of(bj, j);
+                        if (touches(l + 1, C(ci), l + 1, C(cj), dim)) mask |= (uint64_t)1 << (i * 8 + j);
+                    }
+            } else if (!bl && jl) {
+                for (int i = 0; i < lay.box_nslot[b]; ++i)
+                    if (touches(l + 1, C(child_of(b, i)), l, C(bj), dim)) mask |= (uint64_t)1 << (i * 8);
+            } else {
+                for (int j = 0; j < lay.box_nslot[bj]; ++j)
+                    if (touches(l, C(b), l + 1, C(child_of(bj, j)), dim)) mask |= (uint64_t)1 << j;
+            }
+            add_task(b, bj, mask, flags);
+        }
+        if (l > lay.top)
+            for (int64_t q = t.coarse_ptr[b]; q < t.coarse_ptr[b + 1]; ++q)
+                add_task(b, t.coarse[q], 0, bl ? TASK_ADJ : 0);
+        if (bl)
+            for (int64_t q = t.fine_ptr[b]; q < t.fine_ptr[b + 1]; ++q)
+                add_task(b, t.fine[q], 0, t.is_leaf[t.fine[q]] ? TASK_ADJ : 0);
+    }
+    lay.task_ptr[nb] = (int64_t)lay.task_src.size();
+
+    // ---- warp work items: 32 targets x a range of tasks ---------------------
+    struct Tmp { WorkItem it; int64_t cost; int64_t chunk; };
+    std::vector<Tmp> tmp;
+    lay.chunk_box.clear();
+    lay.chunk_t0.clear();
+    for (int64_t b = 0; b < nb; ++b) {
+        if (lay.box_off[b] < 0) continue;
+        const int32_t* ss = &lay.slot_start[b * (kMaxSlots + 1)];
+        for (int32_t t0 = 0; t0 < lay.box_n[b]; t0 += kChunk) {
+            const int64_t chunk = (int64_t)lay.chunk_box.size();
+            lay.chunk_box.push_back(b);
+            lay.chunk_t0.push_back(t0);
+            const int32_t t1 = std::min(t0 + kChunk, lay.box_n[b]);
+            // target slots present in this chunk
+            uint32_t slots = 0;
+            for (int i = 0; i < lay.box_nslot[b]; ++i)
+                if (ss[i] < t1 && ss[i + 1] > t0) slots |= 1u << i;
+            int64_t lo = lay.task_ptr[b], cost = 0;
+            for (int64_t tk = lay.task_ptr[b]; tk < lay.task_ptr[b + 1]; ++tk) {
+                const int64_t src = lay.task_src[tk];
+                int64_t c = 0;
+                for (int j = 0; j < lay.box_nslot[src]; ++j) {
+                    bool any = false;
+                    for (int i = 0; i < lay.box_nslot[b]; ++i)
+                        if (((slots >> i) & 1) && !((lay.task_mask[tk] >> (i * 8 + j)) & 1)) any = true;
+                    if (any) c += slot_size(src, j);
+                }
+                if (cost > 0 && cost + c > kItemCost) {
+                    tmp.push_back({{b, t0, (int32_t)lo, (int32_t)tk, 0}, cost, chunk});
+                    lo = tk;
+                    cost = 0;
+                }
+                cost += c;
+            }
+            tmp.push_back({{b, t0, (int32_t)lo, (int32_t)lay.task_ptr[b + 1], 0}, cost, chunk});
+        }
+    }
+    std::vector<int64_t> order(tmp.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t c) { return tmp[a].cost > tmp[c].cost; });
+    const int64_t nchunk = (int64_t)lay.chunk_box.size();
+    lay.items.resize(tmp.size());
+    lay.chunk_item_ptr.assign(nchunk + 1, 0);
+    for (auto& x : tmp) lay.chunk_item_ptr[x.chunk + 1]++;
+    for (int64_t c = 0; c < nchunk; ++c) lay.chunk_item_ptr[c + 1] += lay.chunk_item_ptr[c];
+    lay.chunk_items.assign(tmp.size(), 0);
+    std::vector<int64_t> fill(lay.chunk_item_ptr.begin(), lay.chunk_item_ptr.end() - 1);
+    for (size_t r = 0; r < order.size(); ++r) {
+        const Tmp& x = tmp[order[r]];
+        lay.items[r] = x.it;
+        lay.chunk_items[fill[x.chunk]++] = (int64_t)r;
+    }
+}
+
+}  // namespace skel
