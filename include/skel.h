@@ -62,7 +62,7 @@ typedef struct {
 
 typedef struct {
     int proxy_p;      /* proxy Chebyshev nodes per box edge; 0 = default (2D: 32, 3D: 12) */
-    int nrhs_max;     /* largest nrhs any later apply will use; 0 = 32                   */
+    int nrhs_max;     /* largest nrhs any later apply will use, <= 256; 0 = 32           */
     int host_only;    /* 1 = build the plan on the host only; apply returns SKEL_ERR_STATE */
     int num_threads;  /* host threads used by the build; 0 = all                          */
 } skel_options;
@@ -235,6 +235,15 @@ int skel_set_profiling(skel_handle h, int max_applies);
 /* skel_last_timings — summed phase durations of the captured applies;
  * SKEL_ERR_STATE if profiling is off. */
 int skel_last_timings(skel_handle h, skel_timings* t);
+
+/*
+ * skel_device_status — the tensor-core apply waits on its own tensor-core
+ * completions with bounded spins. If one ever gives up, the kernel raises a
+ * device status word (and that apply's result is invalid) instead of hanging.
+ * This call waits for the device, returns SKEL_ERR_TIMEOUT if the word was
+ * raised since the last call (else SKEL_OK) and clears it.
+ */
+int skel_device_status(skel_handle h);
 
 #ifdef __cplusplus
 }

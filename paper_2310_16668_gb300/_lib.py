@@ -20,7 +20,8 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_tc": 2}
 # every symbol include/skel.h declares
 SYMBOLS = ("skel_build", "skel_apply", "skel_apply_transpose", "skel_free", "skel_info",
            "skel_last_error", "skel_plan_get_dims", "skel_plan_export", "skel_plan_import",
-           "skel_neighbors_export", "skel_set_profiling", "skel_last_timings")
+           "skel_neighbors_export", "skel_set_profiling", "skel_last_timings",
+           "skel_device_status")
 
 
 class SkelKernel(ctypes.Structure):
@@ -85,6 +86,7 @@ def load() -> ctypes.CDLL:
     lib.skel_neighbors_export.argtypes = [P, I, P, P]
     lib.skel_set_profiling.argtypes = [P, I]
     lib.skel_last_timings.argtypes = [P, ctypes.POINTER(SkelTimings)]
+    lib.skel_device_status.argtypes = [P]
     for name in SYMBOLS:
         if name not in ("skel_free", "skel_last_error"):
             getattr(lib, name).restype = ctypes.c_int

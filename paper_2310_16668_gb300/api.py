@@ -130,6 +130,10 @@ class SkelFMM:
         out["n_applies"] = t.n_applies
         return out
 
+    def device_status(self) -> None:
+        """Raise SkelError(SKEL_ERR_TIMEOUT) if a bounded device wait gave up."""
+        check(self._lib.skel_device_status(self._h))
+
     def apply_into(self, q_cm, u_cm, nrhs: int, precision: str = "fp32_tc", transpose: bool = False,
                    stream=None) -> None:
         """Apply on preallocated column-major buffers (raw data pointers, no copies).

@@ -20,12 +20,14 @@
 // box apart and uses the hi part alone.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
 
 #include "device.h"
 #include "skel_kernels.cuh"
+#include "tc_kernels.cuh"
 
 namespace skel {
 
@@ -39,7 +41,8 @@ namespace skel {
 struct DeviceBuffers {
     void* X = nullptr;       // Real4 per entry: (x, y, z, 0); FP32: hi part
     void* Xlo = nullptr;     // FP32 only: lo part
-    void* T = nullptr;       // Real or complex
+    void* T = nullptr;       // Real or complex, per box k x r column-major
+    void* Tt = nullptr;      // the same blocks transposed (r x k column-major)
     void* Q = nullptr;       // n_tot * nrhs_max
     void* U = nullptr;
     void* partial = nullptr; // n_items * 32 * nrhs_max
@@ -85,12 +88,21 @@ void make_buffers(DevicePlan* dp, const Layout& lay, DeviceBuffers* b) {
     }
     b->X = upload(xh, dp->bytes);
     if (sizeof(Real) == 4) b->Xlo = upload(xl, dp->bytes);
-    std::vector<Real> tr(lay.T.size());
+    std::vector<Real> tr(lay.T.size()), tt(lay.T.size());
     for (size_t i = 0; i < lay.T.size(); ++i) tr[i] = (Real)lay.T[i];
+    for (const UpBox& u : lay.up) {
+        const int k = u.k, r = u.n - u.k;
+        for (int j = 0; j < r; ++j)
+            for (int i = 0; i < k; ++i)
+                for (int c = 0; c < w; ++c)
+                    tt[(u.T_off + j + (int64_t)i * r) * w + c] = tr[(u.T_off + i + (int64_t)j * k) * w + c];
+    }
     b->T = upload(tr, dp->bytes);
+    b->Tt = upload(tt, dp->bytes);
     b->Q = dalloc<Real>((size_t)nt * dp->nrhs_max * w, dp->bytes);
     b->U = dalloc<Real>((size_t)nt * dp->nrhs_max * w, dp->bytes);
-    b->partial = dalloc<Real>((size_t)dp->n_items * kChunk * dp->nrhs_max * w, dp->bytes);
+    const int64_t slots = std::max<int64_t>(dp->n_items, sizeof(Real) == 4 ? dp->tc_n_slots : 0);
+    b->partial = dalloc<Real>((size_t)slots * kChunk * dp->nrhs_max * w, dp->bytes);
 }
 
 void free_buffers(DeviceBuffers* b) {
@@ -98,6 +110,7 @@ void free_buffers(DeviceBuffers* b) {
     cudaFree(b->X);
     cudaFree(b->Xlo);
     cudaFree(b->T);
+    cudaFree(b->Tt);
     cudaFree(b->Q);
     cudaFree(b->U);
     cudaFree(b->partial);
@@ -106,19 +119,107 @@ void free_buffers(DeviceBuffers* b) {
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// right-hand sides per thread of the up / down GEMMs
+template <class S> constexpr int rg_of() { return sizeof(S) == 4 ? 8 : sizeof(S) == 8 ? 4 : 2; }
+
+template <class S, int RG>
+void launch_up_down(bool down, unsigned grid, const UpBox* up, const int32_t* pos, const S* T, S* X, int nrhs,
+                    bool transpose, cudaStream_t st) {
+    const size_t smem = (size_t)kJT * nrhs * sizeof(S);
+    if (down) {
+        if (smem > 48 * 1024)
+            CUDA_CHECK(cudaFuncSetAttribute(down_kernel<S, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        down_kernel<S, RG><<<grid, kUpThreads, smem, st>>>(up, pos, T, X, nrhs, transpose);
+    } else {
+        if (smem > 48 * 1024)
+            CUDA_CHECK(cudaFuncSetAttribute(up_kernel<S, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        up_kernel<S, RG><<<grid, kUpThreads, smem, st>>>(up, pos, T, X, nrhs, transpose);
+    }
+}
+
+template <class S>
+void up_down(bool down, unsigned grid, const UpBox* up, const int32_t* pos, const S* T, S* X, int nrhs,
+             bool transpose, cudaStream_t st) {
+    if (nrhs >= rg_of<S>()) launch_up_down<S, rg_of<S>()>(down, grid, up, pos, T, X, nrhs, transpose, st);
+    else launch_up_down<S, 1>(down, grid, up, pos, T, X, nrhs, transpose, st);
+}
+
 inline void mark(DevicePlan* dp, int i, cudaStream_t st) {
     if (dp->prof_count < dp->prof_cap)
         CUDA_CHECK(cudaEventRecord((cudaEvent_t)dp->events[dp->prof_count * 7 + i], st));
 }
 
 template <class Real, bool CPLX>
-void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrhs, bool transpose,
+NearArgs<Real, CPLX> near_args(DevicePlan* dp, DeviceBuffers* b, const WorkItem* items, int64_t n_items, int nrhs) {
+    NearArgs<Real, CPLX> a;
+    a.items = items;
+    a.n_items = n_items;
+    a.box_off = dp->box_off;
+    a.box_n = dp->box_n;
+    a.box_nslot = dp->box_nslot;
+    a.slot_start = dp->slot_start;
+    a.task_src = dp->task_src;
+    a.task_mask = dp->task_mask;
+    a.task_flags = dp->task_flags;
+    a.X = (const typename RealT<Real>::V4*)b->X;
+    a.Xlo = (const typename RealT<Real>::V4*)b->Xlo;
+    a.Q = (const typename Scal<Real, CPLX>::T*)b->Q;
+    a.partial = (typename Scal<Real, CPLX>::T*)b->partial;
+    a.nrhs = nrhs;
+    a.kappa = (Real)dp->kappa;
+    return a;
+}
+
+// tensor-core translations (real kernels, FP32): CUDA-core items for the
+// small boxes, then one tensor-core pass per 32 right-hand sides
+template <class Real, bool CPLX>
+int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st) {
+    int launches = 0;
+    if (dp->n_mix > 0) {
+        auto a = near_args<Real, CPLX>(dp, b, dp->mix_items, dp->n_mix, nrhs);
+        launches += launch_near<Real, CPLX>(dp->kind, a, nrhs, ceil_div(dp->n_mix, kNearWarps), st);
+        CUDA_CHECK(cudaGetLastError());
+    }
+    TcArgs t;
+    t.items = dp->tc_items;
+    t.tiles = dp->tc_tiles;
+    t.box_off = dp->box_off;
+    t.box_n = dp->box_n;
+    t.box_nslot = dp->box_nslot;
+    t.slot_start = dp->slot_start;
+    t.X = (const float4*)b->X;
+    t.Xlo = (const float4*)b->Xlo;
+    t.Q = (const float*)b->Q;
+    t.partial = (float*)b->partial;
+    t.nrhs = nrhs;
+    t.status = dp->status;
+    static bool attr_set[2] = {false, false};
+    const int kidx = dp->kind == 0 ? 0 : 1;
+    if (!attr_set[kidx]) {
+        if (kidx == 0)
+            CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+        else
+            CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+        attr_set[kidx] = true;
+    }
+    for (int r0 = 0; r0 < nrhs; r0 += kTcN, ++launches) {
+        t.r0 = r0;
+        if (kidx == 0) tc_near_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+        else tc_near_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+        CUDA_CHECK(cudaGetLastError());
+    }
+    return launches;
+}
+
+template <class Real, bool CPLX>
+void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrhs, bool transpose, bool use_tc,
                cudaStream_t st) {
     int launches = 0;
     using S = typename Scal<Real, CPLX>::T;
     S* Q = (S*)b->Q;
     S* U = (S*)b->U;
     const S* T = (const S*)b->T;
+    const S* Tt = (const S*)b->Tt;
     S* part = (S*)b->partial;
     const int64_t N = dp->N;
     // 1. permute in
@@ -136,29 +237,24 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
         const int64_t b0 = dp->up_level_ptr[l], b1 = dp->up_level_ptr[l + 1];
         if (b1 > b0) {
             ++launches;
-            up_kernel<S><<<(unsigned)(b1 - b0), 128, 0, st>>>(dp->up + b0, dp->pos, T, Q, nrhs, transpose);
+            up_down<S>(false, (unsigned)(b1 - b0), dp->up + b0, dp->pos, T, Q, nrhs, transpose, st);
             CUDA_CHECK(cudaGetLastError());
         }
     }
     // 3. near field
     mark(dp, 2, st);
-    if (dp->n_items > 0) {
-        NearArgs<Real, CPLX> a;
-        a.items = dp->items;
-        a.n_items = dp->n_items;
-        a.box_off = dp->box_off;
-        a.box_n = dp->box_n;
-        a.box_nslot = dp->box_nslot;
-        a.slot_start = dp->slot_start;
-        a.task_src = dp->task_src;
-        a.task_mask = dp->task_mask;
-        a.task_flags = dp->task_flags;
-        a.X = (const typename RealT<Real>::V4*)b->X;
-        a.Xlo = (const typename RealT<Real>::V4*)b->Xlo;
-        a.Q = Q;
-        a.partial = part;
-        a.nrhs = nrhs;
-        a.kappa = (Real)dp->kappa;
+    const bool tc = use_tc && !CPLX && sizeof(Real) == 4 && dp->n_tc > 0;
+    if (tc) {
+        launches += run_tc<Real, CPLX>(dp, b, nrhs, st);
+        mark(dp, 3, st);
+        ++launches;
+        const int64_t n = dp->n_chunks * kChunk * nrhs;
+        reduce_kernel<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->chunk_box, dp->chunk_t0, dp->tc_chunk_ptr,
+                                                           dp->tc_chunk_slots, dp->box_off, dp->box_n, part, U,
+                                                           nrhs, dp->n_chunks);
+        CUDA_CHECK(cudaGetLastError());
+    } else if (dp->n_items > 0) {
+        auto a = near_args<Real, CPLX>(dp, b, dp->items, dp->n_items, nrhs);
         const unsigned grid = ceil_div(dp->n_items, kNearWarps);
         launches += launch_near<Real, CPLX>(dp->kind, a, nrhs, grid, st);
         CUDA_CHECK(cudaGetLastError());
@@ -179,7 +275,7 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
         const int64_t b0 = dp->up_level_ptr[l], b1 = dp->up_level_ptr[l + 1];
         if (b1 > b0) {
             ++launches;
-            down_kernel<S><<<(unsigned)(b1 - b0), 256, 0, st>>>(dp->up + b0, dp->pos, T, U, nrhs, transpose);
+            up_down<S>(true, (unsigned)(b1 - b0), dp->up + b0, dp->pos, Tt, U, nrhs, transpose, st);
             CUDA_CHECK(cudaGetLastError());
         }
     }
@@ -229,6 +325,16 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
         dp->chunk_item_ptr = upload(lay.chunk_item_ptr, dp->bytes);
         dp->chunk_items = upload(lay.chunk_items, dp->bytes);
         dp->n_chunks = (int64_t)lay.chunk_box.size();
+        dp->mix_items = upload(lay.mix_items, dp->bytes);
+        dp->n_mix = (int64_t)lay.mix_items.size();
+        dp->tc_tiles = upload(lay.tc_tiles, dp->bytes);
+        dp->tc_items = upload(lay.tc_items, dp->bytes);
+        dp->n_tc = (int64_t)lay.tc_items.size();
+        dp->tc_n_slots = lay.tc_n_slots;
+        dp->tc_chunk_ptr = upload(lay.tc_chunk_ptr, dp->bytes);
+        dp->tc_chunk_slots = upload(lay.tc_chunk_slots, dp->bytes);
+        dp->status = dalloc<int>(1, dp->bytes);
+        CUDA_CHECK(cudaMemset(dp->status, 0, sizeof(int)));
         dp->p64 = new DeviceBuffers();
         make_buffers<double>(dp, lay, dp->p64);
         dp->p32 = new DeviceBuffers();
@@ -249,7 +355,8 @@ void device_plan_destroy(DevicePlan* dp) {
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->perm_entry,
                     dp->perm_point, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->chunk_box, dp->chunk_t0, dp->chunk_item_ptr, dp->chunk_items, dp->stage_in,
-                    dp->stage_out};
+                    dp->stage_out, dp->mix_items, dp->tc_tiles, dp->tc_items, dp->tc_chunk_ptr,
+                    dp->tc_chunk_slots, dp->status};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);
@@ -269,6 +376,14 @@ void device_set_profiling(DevicePlan* dp, int max_applies) {
     dp->prof_cap = max_applies;
     dp->prof_count = 0;
     dp->prof_launches.assign(max_applies, 0);
+}
+
+int device_status(DevicePlan* dp) {
+    int v = 0;
+    CUDA_CHECK(cudaDeviceSynchronize());
+    CUDA_CHECK(cudaMemcpy(&v, dp->status, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_CHECK(cudaMemset(dp->status, 0, sizeof(int)));
+    return v;
 }
 
 void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_applies) {
@@ -291,12 +406,13 @@ void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_appl
 void device_apply(DevicePlan* dp, const void* q, void* u, int nrhs, int precision, bool transpose,
                   void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
+    const bool tc = precision == 2;
     if (precision == 0) {
-        if (dp->cplx) run_apply<double, true>(dp, dp->p64, q, u, nrhs, transpose, st);
-        else run_apply<double, false>(dp, dp->p64, q, u, nrhs, transpose, st);
+        if (dp->cplx) run_apply<double, true>(dp, dp->p64, q, u, nrhs, transpose, false, st);
+        else run_apply<double, false>(dp, dp->p64, q, u, nrhs, transpose, false, st);
     } else {
-        if (dp->cplx) run_apply<float, true>(dp, dp->p32, q, u, nrhs, transpose, st);
-        else run_apply<float, false>(dp, dp->p32, q, u, nrhs, transpose, st);
+        if (dp->cplx) run_apply<float, true>(dp, dp->p32, q, u, nrhs, transpose, tc, st);
+        else run_apply<float, false>(dp, dp->p32, q, u, nrhs, transpose, tc, st);
     }
 }
 

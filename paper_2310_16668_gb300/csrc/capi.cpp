@@ -77,7 +77,7 @@ void check_points(const double* pts, int64_t n, int dim) {
 
 void finalize(skel_plan* h, const skel_options* opts) {
     h->nrhs_max = (opts && opts->nrhs_max > 0) ? opts->nrhs_max : 32;
-    if (h->nrhs_max > 1024) throw Error(SKEL_ERR_ARG, "nrhs_max too large");
+    if (h->nrhs_max > 256) throw Error(SKEL_ERR_ARG, "nrhs_max must be <= 256");
     h->host_only = opts && opts->host_only;
     double t0 = now();
     skel::Layout lay;
@@ -450,6 +450,18 @@ int skel_last_timings(skel_handle h, skel_timings* t) {
         if (!h->dev) throw Error(SKEL_ERR_STATE, "plan was built host-only");
         skel::device_last_timings(h->dev, t->ms, &t->launches, &t->n_applies);
     });
+}
+
+int skel_device_status(skel_handle h) {
+    int code = SKEL_OK;
+    int rc = guarded([&] {
+        if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");
+        if (!h->dev) throw Error(SKEL_ERR_STATE, "plan was built host-only");
+        if (skel::device_status(h->dev) != 0) code = SKEL_ERR_TIMEOUT;
+    });
+    if (rc != SKEL_OK) return rc;
+    if (code != SKEL_OK) return fail(code, "a bounded device wait gave up during an earlier apply");
+    return SKEL_OK;
 }
 
 }  // extern "C"

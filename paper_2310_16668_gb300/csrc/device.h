@@ -39,6 +39,16 @@ struct DevicePlan {
     int64_t* chunk_item_ptr = nullptr;
     int64_t* chunk_items = nullptr;
     int64_t n_chunks = 0;
+    // tensor-core mode
+    WorkItem* mix_items = nullptr;
+    int64_t n_mix = 0;
+    SrcTile* tc_tiles = nullptr;
+    TcItem* tc_items = nullptr;
+    int64_t n_tc = 0;
+    int64_t tc_n_slots = 0;
+    int64_t* tc_chunk_ptr = nullptr;
+    int64_t* tc_chunk_slots = nullptr;
+    int* status = nullptr;                 // device word raised by a bounded wait that gave up
     DeviceBuffers* p64 = nullptr;
     DeviceBuffers* p32 = nullptr;
     // optional per-phase CUDA events (permute_in, up, near, reduce, down,
@@ -58,6 +68,8 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max);
 void device_plan_destroy(DevicePlan* dp);
 // capture the phases of the next max_applies applies (0 = off)
 void device_set_profiling(DevicePlan* dp, int max_applies);
+// read and clear the device status word (synchronizes the device)
+int device_status(DevicePlan* dp);
 // summed milliseconds of the 6 phases over the captured applies (waits for them)
 void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_applies);
 

@@ -96,6 +96,30 @@ struct WorkItem {                       // one warp: 32 targets x a task range
     int32_t pad;
 };
 
+// Tensor-core translations: a CTA owns 128 target rows of one box and streams
+// that box's sources in tiles of 32 (never spanning two tasks).
+constexpr int kTcRows = 128;
+constexpr int kTcK = 32;
+constexpr int kTcMinRows = 96;          // boxes with fewer entries use the CUDA-core kernel
+constexpr int kTcMaxTiles = 96;         // source tiles per tensor-core work item
+
+struct SrcTile {                        // 32 bytes
+    int64_t start;                      // first source entry
+    int16_t cnt;                        // sources (1..32)
+    int8_t nseg;                        // source slots in the tile (1..8)
+    int8_t flags;                       // TASK_ADJ
+    uint8_t seg_end[8];                 // end (exclusive, within the tile) of each slot segment
+    uint8_t seg_mask[8];                // bit c: target slot c skips this segment
+    int32_t pad;
+};
+
+struct TcItem {
+    int64_t box;
+    int32_t r0;                         // first target row (multiple of 128)
+    int32_t tile_lo, tile_hi;           // range of the box's source tiles
+    int32_t slot;                       // first of its 4 partial-sum slots (32 rows each)
+};
+
 struct Layout {
     int top = 1;
     int64_t n_tot = 0;
@@ -114,10 +138,16 @@ struct Layout {
     std::vector<int64_t> task_src;
     std::vector<uint64_t> task_mask;    // bit (c*8 + c'): skip target slot c x source slot c'
     std::vector<int32_t> task_flags;
-    std::vector<WorkItem> items;        // execution order
-    std::vector<int64_t> chunk_box;     // per target chunk: box
+    std::vector<WorkItem> items;        // CUDA-core items for every box (execution order)
+    std::vector<int64_t> chunk_box;     // per 32-row target chunk: box
     std::vector<int32_t> chunk_t0;
-    std::vector<int64_t> chunk_item_ptr, chunk_items;
+    std::vector<int64_t> chunk_item_ptr, chunk_items;   // chunk -> partial slots (CUDA-core mode)
+    // tensor-core mode: CUDA-core items for small boxes, tensor-core items for the rest
+    std::vector<WorkItem> mix_items;
+    std::vector<SrcTile> tc_tiles;
+    std::vector<TcItem> tc_items;
+    std::vector<int64_t> tc_chunk_ptr, tc_chunk_slots;
+    int64_t tc_n_slots = 0;
     int64_t pairs_direct = 0, pairs_far = 0;
 };
 

@@ -171,58 +171,142 @@ void build_layout(const Plan& p, Layout& lay) {
     lay.task_ptr[nb] = (int64_t)lay.task_src.size();
 
     // ---- warp work items: 32 targets x a range of tasks ---------------------
-    struct Tmp { WorkItem it; int64_t cost; int64_t chunk; };
-    std::vector<Tmp> tmp;
+    // chunks: every 32-row slice of every box
     lay.chunk_box.clear();
     lay.chunk_t0.clear();
+    std::vector<int64_t> box_chunk0(nb, -1);
     for (int64_t b = 0; b < nb; ++b) {
         if (lay.box_off[b] < 0) continue;
-        const int32_t* ss = &lay.slot_start[b * (kMaxSlots + 1)];
+        box_chunk0[b] = (int64_t)lay.chunk_box.size();
         for (int32_t t0 = 0; t0 < lay.box_n[b]; t0 += kChunk) {
-            const int64_t chunk = (int64_t)lay.chunk_box.size();
             lay.chunk_box.push_back(b);
             lay.chunk_t0.push_back(t0);
-            const int32_t t1 = std::min(t0 + kChunk, lay.box_n[b]);
-            // target slots present in this chunk
-            uint32_t slots = 0;
-            for (int i = 0; i < lay.box_nslot[b]; ++i)
-                if (ss[i] < t1 && ss[i + 1] > t0) slots |= 1u << i;
-            int64_t lo = lay.task_ptr[b], cost = 0;
-            for (int64_t tk = lay.task_ptr[b]; tk < lay.task_ptr[b + 1]; ++tk) {
-                const int64_t src = lay.task_src[tk];
-                int64_t c = 0;
-                for (int j = 0; j < lay.box_nslot[src]; ++j) {
-                    bool any = false;
-                    for (int i = 0; i < lay.box_nslot[b]; ++i)
-                        if (((slots >> i) & 1) && !((lay.task_mask[tk] >> (i * 8 + j)) & 1)) any = true;
-                    if (any) c += slot_size(src, j);
-                }
-                if (cost > 0 && cost + c > kItemCost) {
-                    tmp.push_back({{b, t0, (int32_t)lo, (int32_t)tk, 0}, cost, chunk});
-                    lo = tk;
-                    cost = 0;
-                }
-                cost += c;
-            }
-            tmp.push_back({{b, t0, (int32_t)lo, (int32_t)lay.task_ptr[b + 1], 0}, cost, chunk});
         }
     }
-    std::vector<int64_t> order(tmp.size());
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int64_t a, int64_t c) { return tmp[a].cost > tmp[c].cost; });
     const int64_t nchunk = (int64_t)lay.chunk_box.size();
-    lay.items.resize(tmp.size());
-    lay.chunk_item_ptr.assign(nchunk + 1, 0);
-    for (auto& x : tmp) lay.chunk_item_ptr[x.chunk + 1]++;
-    for (int64_t c = 0; c < nchunk; ++c) lay.chunk_item_ptr[c + 1] += lay.chunk_item_ptr[c];
-    lay.chunk_items.assign(tmp.size(), 0);
-    std::vector<int64_t> fill(lay.chunk_item_ptr.begin(), lay.chunk_item_ptr.end() - 1);
-    for (size_t r = 0; r < order.size(); ++r) {
-        const Tmp& x = tmp[order[r]];
-        lay.items[r] = x.it;
-        lay.chunk_items[fill[x.chunk]++] = (int64_t)r;
+    struct Tmp { WorkItem it; int64_t cost; int64_t chunk; };
+    auto simt_items = [&](auto use_box, std::vector<WorkItem>& out, std::vector<std::pair<int64_t, int64_t>>& cs,
+                          int64_t slot0) {
+        std::vector<Tmp> tmp;
+        for (int64_t b = 0; b < nb; ++b) {
+            if (lay.box_off[b] < 0 || !use_box(b)) continue;
+            const int32_t* ss = &lay.slot_start[b * (kMaxSlots + 1)];
+            for (int32_t t0 = 0; t0 < lay.box_n[b]; t0 += kChunk) {
+                const int64_t chunk = box_chunk0[b] + t0 / kChunk;
+                const int32_t t1 = std::min(t0 + kChunk, lay.box_n[b]);
+                uint32_t slots = 0;
+                for (int i = 0; i < lay.box_nslot[b]; ++i)
+                    if (ss[i] < t1 && ss[i + 1] > t0) slots |= 1u << i;
+                int64_t lo = lay.task_ptr[b], cost = 0;
+                for (int64_t tk = lay.task_ptr[b]; tk < lay.task_ptr[b + 1]; ++tk) {
+                    const int64_t src = lay.task_src[tk];
+                    int64_t c = 0;
+                    for (int j = 0; j < lay.box_nslot[src]; ++j) {
+                        bool any = false;
+                        for (int i = 0; i < lay.box_nslot[b]; ++i)
+                            if (((slots >> i) & 1) && !((lay.task_mask[tk] >> (i * 8 + j)) & 1)) any = true;
+                        if (any) c += slot_size(src, j);
+                    }
+                    if (cost > 0 && cost + c > kItemCost) {
+                        tmp.push_back({{b, t0, (int32_t)lo, (int32_t)tk, 0}, cost, chunk});
+                        lo = tk;
+                        cost = 0;
+                    }
+                    cost += c;
+                }
+                tmp.push_back({{b, t0, (int32_t)lo, (int32_t)lay.task_ptr[b + 1], 0}, cost, chunk});
+            }
+        }
+        std::vector<int64_t> order(tmp.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int64_t a, int64_t c) { return tmp[a].cost > tmp[c].cost; });
+        out.resize(tmp.size());
+        for (size_t r = 0; r < order.size(); ++r) {
+            out[r] = tmp[order[r]].it;
+            cs.push_back({tmp[order[r]].chunk, slot0 + (int64_t)r});
+        }
+    };
+    auto to_csr = [&](std::vector<std::pair<int64_t, int64_t>>& cs, std::vector<int64_t>& ptr,
+                      std::vector<int64_t>& lst) {
+        std::stable_sort(cs.begin(), cs.end(), [](const std::pair<int64_t, int64_t>& a,
+                                                  const std::pair<int64_t, int64_t>& c) { return a.first < c.first; });
+        ptr.assign(nchunk + 1, 0);
+        for (auto& x : cs) ptr[x.first + 1]++;
+        for (int64_t c = 0; c < nchunk; ++c) ptr[c + 1] += ptr[c];
+        lst.resize(cs.size());
+        for (size_t i = 0; i < cs.size(); ++i) lst[i] = cs[i].second;
+    };
+    {
+        std::vector<std::pair<int64_t, int64_t>> cs;
+        simt_items([](int64_t) { return true; }, lay.items, cs, 0);
+        to_csr(cs, lay.chunk_item_ptr, lay.chunk_items);
     }
+
+    // ---- tensor-core mode --------------------------------------------------------
+    auto is_tc = [&](int64_t b) { return lay.box_n[b] >= kTcMinRows; };
+    std::vector<std::pair<int64_t, int64_t>> cs;
+    simt_items([&](int64_t b) { return !is_tc(b); }, lay.mix_items, cs, 0);
+    int64_t slot = (int64_t)lay.mix_items.size();
+    lay.tc_tiles.clear();
+    lay.tc_items.clear();
+    for (int64_t b = 0; b < nb; ++b) {
+        if (lay.box_off[b] < 0 || !is_tc(b)) continue;
+        const int32_t* ssB = &lay.slot_start[b * (kMaxSlots + 1)];
+        const int64_t tile0 = (int64_t)lay.tc_tiles.size();
+        for (int64_t tk = lay.task_ptr[b]; tk < lay.task_ptr[b + 1]; ++tk) {
+            const int64_t src = lay.task_src[tk];
+            const int32_t* ssS = &lay.slot_start[src * (kMaxSlots + 1)];
+            const int ns = lay.box_nslot[src];
+            // segment masks of the source slots: bit c = target slot c skips it
+            uint8_t smask[kMaxSlots];
+            bool all_skip = true;
+            for (int j = 0; j < ns; ++j) {
+                smask[j] = 0;
+                for (int i = 0; i < lay.box_nslot[b]; ++i)
+                    if ((lay.task_mask[tk] >> (i * 8 + j)) & 1) smask[j] |= (uint8_t)(1u << i);
+                const uint8_t full = (uint8_t)((1u << lay.box_nslot[b]) - 1);
+                if (smask[j] != full) all_skip = false;
+            }
+            if (all_skip) continue;
+            const int32_t n = lay.box_n[src];
+            for (int32_t p0 = 0; p0 < n; p0 += kTcK) {
+                SrcTile st{};
+                st.start = lay.box_off[src] + p0;
+                st.cnt = (int16_t)std::min(kTcK, n - p0);
+                st.flags = (int8_t)lay.task_flags[tk];
+                int nseg = 0;
+                for (int j = 0; j < ns; ++j) {
+                    const int a = std::max(ssS[j] - p0, 0), e = std::min(ssS[j + 1] - p0, (int)st.cnt);
+                    if (e <= a) continue;
+                    st.seg_end[nseg] = (uint8_t)e;
+                    st.seg_mask[nseg] = smask[j];
+                    ++nseg;
+                }
+                st.nseg = (int8_t)nseg;
+                lay.tc_tiles.push_back(st);
+            }
+        }
+        const int64_t tile1 = (int64_t)lay.tc_tiles.size();
+        for (int32_t r0 = 0; r0 < lay.box_n[b]; r0 += kTcRows) {
+            for (int64_t t = tile0; t < tile1 || t == tile0; t += kTcMaxTiles) {
+                TcItem it;
+                it.box = b;
+                it.r0 = r0;
+                it.tile_lo = (int32_t)t;
+                it.tile_hi = (int32_t)std::min(t + kTcMaxTiles, tile1);
+                it.slot = (int32_t)slot;
+                for (int q = 0; q < kTcRows / kChunk; ++q)
+                    if (r0 + q * kChunk < lay.box_n[b]) cs.push_back({box_chunk0[b] + (r0 + q * kChunk) / kChunk, slot + q});
+                slot += kTcRows / kChunk;
+                lay.tc_items.push_back(it);
+                if (tile1 == tile0) break;
+            }
+        }
+        (void)ssB;
+    }
+    lay.tc_n_slots = slot;
+    to_csr(cs, lay.tc_chunk_ptr, lay.tc_chunk_slots);
 }
 
 }  // namespace skel

@@ -67,47 +67,121 @@ __global__ void permute_out(const int64_t* __restrict__ pe, const int64_t* __res
 }
 
 // ---- upward: qhat_S = q_S + T q_R into the parent's slot ---------------------------
-template <class S>
-__global__ void up_kernel(const UpBox* __restrict__ up, const int32_t* __restrict__ pos,
-                          const S* __restrict__ T, S* Q, int nrhs, bool conjT) {
+// One CTA per box, a small GEMM (k x r) x (r x nrhs): rows of q_R are gathered
+// into shared memory 32 at a time; each thread owns up to kOwn (row, group of
+// RG right-hand sides) outputs; T (column-major, k contiguous) is read
+// coalesced across rows.
+constexpr int kUpThreads = 256;
+constexpr int kOwn = 4;
+constexpr int kJT = 32;
+
+template <class S, int RG>
+__global__ void __launch_bounds__(kUpThreads) up_kernel(const UpBox* __restrict__ up, const int32_t* __restrict__ pos,
+                                                        const S* __restrict__ T, S* Q, int nrhs, bool conjT) {
+    extern __shared__ unsigned char smem_raw[];
+    S* qs = reinterpret_cast<S*>(smem_raw);              // kJT x nrhs
     const UpBox u = up[blockIdx.x];
     const int k = u.k, r = u.n - u.k;
-    for (int idx = threadIdx.x; idx < k * nrhs; idx += blockDim.x) {
-        const int i = idx % k, rr = idx / k;
-        S acc = Q[(u.off + pos[u.off + i]) * nrhs + rr];
-        const S* Ti = T + u.T_off + i;
-        for (int j = 0; j < r; ++j) {
-            S tv = Ti[(int64_t)j * k];
-            if (conjT) tv = conj(tv);
-            acc += tv * Q[(u.off + pos[u.off + k + j]) * nrhs + rr];
+    const int ng = (nrhs + RG - 1) / RG;
+    const int total = k * ng;
+    for (int base = 0; base < total; base += kUpThreads * kOwn) {
+        S acc[kOwn][RG];
+#pragma unroll
+        for (int o = 0; o < kOwn; ++o)
+#pragma unroll
+            for (int c = 0; c < RG; ++c) acc[o][c] = zero<S>();
+        for (int j0 = 0; j0 < r; j0 += kJT) {
+            const int jn = min(kJT, r - j0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < jn * nrhs; e += kUpThreads) {
+                const int jj = e / nrhs, c = e % nrhs;
+                qs[e] = Q[(u.off + pos[u.off + k + j0 + jj]) * nrhs + c];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int o = 0; o < kOwn; ++o) {
+                const int task = base + o * kUpThreads + threadIdx.x;
+                if (task >= total) break;
+                const int i = task % k, g = task / k;
+                const S* Ti = T + u.T_off + i + (int64_t)j0 * k;
+                for (int jj = 0; jj < jn; ++jj) {
+                    S tv = Ti[(int64_t)jj * k];
+                    if (conjT) tv = conj(tv);
+#pragma unroll
+                    for (int c = 0; c < RG; ++c)
+                        if (g * RG + c < nrhs) acc[o][c] += tv * qs[jj * nrhs + g * RG + c];
+                }
+            }
         }
-        Q[(u.dst + i) * nrhs + rr] = acc;
+#pragma unroll
+        for (int o = 0; o < kOwn; ++o) {
+            const int task = base + o * kUpThreads + threadIdx.x;
+            if (task >= total) break;
+            const int i = task % k, g = task / k;
+            const int64_t src = (u.off + pos[u.off + i]) * nrhs, dst = (u.dst + i) * nrhs;
+#pragma unroll
+            for (int c = 0; c < RG; ++c) {
+                const int cc = g * RG + c;
+                if (cc < nrhs) Q[dst + cc] = Q[src + cc] + acc[o][c];
+            }
+        }
     }
 }
 
 // ---- downward: uhat = U[parent slot]; u_S += uhat; u_R += T^* uhat -------------------
-template <class S>
-__global__ void down_kernel(const UpBox* __restrict__ up, const int32_t* __restrict__ pos,
-                            const S* __restrict__ T, S* U, int nrhs, bool transpose) {
+// One CTA per box; uhat rows are staged in shared memory 32 at a time and the
+// transposed copy Tt (r x k, column-major: r contiguous) is read coalesced
+// across the output rows j of R.
+template <class S, int RG>
+__global__ void __launch_bounds__(kUpThreads) down_kernel(const UpBox* __restrict__ up, const int32_t* __restrict__ pos,
+                                                          const S* __restrict__ Tt, S* U, int nrhs, bool transpose) {
+    extern __shared__ unsigned char smem_raw[];
+    S* us = reinterpret_cast<S*>(smem_raw);              // kJT x nrhs
     const UpBox u = up[blockIdx.x];
     const int k = u.k, r = u.n - u.k;
-    for (int idx = threadIdx.x; idx < k * nrhs; idx += blockDim.x) {
-        const int i = idx / nrhs, rr = idx % nrhs;
-        U[(u.off + pos[u.off + i]) * nrhs + rr] += U[(u.dst + i) * nrhs + rr];
+    for (int e = threadIdx.x; e < k * nrhs; e += kUpThreads) {
+        const int i = e / nrhs, c = e % nrhs;
+        U[(u.off + pos[u.off + i]) * nrhs + c] += U[(u.dst + i) * nrhs + c];
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int j = warp; j < r; j += nw) {
-        const S* Tj = T + u.T_off + (int64_t)j * k;
-        const int64_t e = u.off + pos[u.off + k + j];
-        for (int rr = 0; rr < nrhs; ++rr) {
-            S s = zero<S>();
-            for (int i = lane; i < k; i += 32) {
-                S tv = Tj[i];
-                if (!transpose) tv = conj(tv);
-                s += tv * U[(u.dst + i) * nrhs + rr];
+    const int ng = (nrhs + RG - 1) / RG;
+    const int total = r * ng;
+    for (int base = 0; base < total; base += kUpThreads * kOwn) {
+        S acc[kOwn][RG];
+#pragma unroll
+        for (int o = 0; o < kOwn; ++o)
+#pragma unroll
+            for (int c = 0; c < RG; ++c) acc[o][c] = zero<S>();
+        for (int i0 = 0; i0 < k; i0 += kJT) {
+            const int in = min(kJT, k - i0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < in * nrhs; e += kUpThreads) us[e] = U[(u.dst + i0) * nrhs + e];
+            __syncthreads();
+#pragma unroll
+            for (int o = 0; o < kOwn; ++o) {
+                const int task = base + o * kUpThreads + threadIdx.x;
+                if (task >= total) break;
+                const int j = task % r, g = task / r;
+                const S* Tj = Tt + u.T_off + j + (int64_t)i0 * r;
+                for (int ii = 0; ii < in; ++ii) {
+                    S tv = Tj[(int64_t)ii * r];
+                    if (!transpose) tv = conj(tv);
+#pragma unroll
+                    for (int c = 0; c < RG; ++c)
+                        if (g * RG + c < nrhs) acc[o][c] += tv * us[ii * nrhs + g * RG + c];
+                }
             }
-            s = warp_sum(s);
-            if (lane == 0) U[e * nrhs + rr] += s;
+        }
+#pragma unroll
+        for (int o = 0; o < kOwn; ++o) {
+            const int task = base + o * kUpThreads + threadIdx.x;
+            if (task >= total) break;
+            const int j = task % r, g = task / r;
+            const int64_t e = (u.off + pos[u.off + k + j]) * nrhs;
+#pragma unroll
+            for (int c = 0; c < RG; ++c) {
+                const int cc = g * RG + c;
+                if (cc < nrhs) U[e + cc] += acc[o][c];
+            }
         }
     }
 }

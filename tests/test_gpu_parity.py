@@ -67,8 +67,30 @@ def test_apply_matches_oracle(oracle_case, nrhs):
     qt = torch.from_numpy(q).cuda()
     u64 = fmm.apply(qt, "fp64").cpu().numpy()
     u32 = fmm.apply(qt, "fp32").cpu().numpy()
+    utc = fmm.apply(qt, "fp32_tc").cpu().numpy()
+    fmm.device_status()
     assert relerr(u64, ref) < 1e-12
     assert relerr(u32, ref) < 1e-5
+    assert relerr(utc, ref) < 1e-5
+
+
+@pytest.mark.parametrize("nrhs,b", [(32, 64), (45, 64), (32, 128)])
+def test_tensor_core_many_rhs(nrhs, b):
+    """Tensor-core translations: 45 right-hand sides = one full and one ragged
+    pass; leaf size 128 puts leaves of 96..128 points (touching-leaf tasks) on
+    the tensor-core path too."""
+    x = W.points_uniform(40000, 3, 31)
+    sk = osk.Skeletons(otree.Tree(x, b), "laplace3d", 1e-6)
+    fmm = SkelFMM.from_plan(x, "laplace3d", oplan.to_exchange(sk), nrhs_max=64)
+    q = W.charges_normal(x.shape[0], nrhs, 32)
+    qt = torch.from_numpy(q).cuda()
+    utc = fmm.apply(qt, "fp32_tc").cpu().numpy()
+    fmm.device_status()
+    u64 = fmm.apply(qt, "fp64").cpu().numpy()
+    for r in range(nrhs):
+        assert relerr(utc[:, r], u64[:, r]) < 1e-5, r
+    for r in (0, nrhs - 1):
+        assert relerr(u64[:, r], oap.skeleton_apply(sk, q[:, r])) < 1e-12
 
 
 def test_transpose_matches_oracle(oracle_case):
@@ -99,6 +121,9 @@ def test_library_build_vs_direct(kind, dim, b, tol):
     assert relerr(u, ref) < 10 * tol
     u32 = fmm.apply(torch.from_numpy(q).cuda(), "fp32").cpu().numpy()
     assert relerr(u32, ref) < 10 * tol + 1e-5
+    utc = fmm.apply(torch.from_numpy(q).cuda(), "fp32_tc").cpu().numpy()
+    fmm.device_status()
+    assert relerr(utc, ref) < 10 * tol + 1e-5
 
 
 @pytest.mark.parametrize("n", [1, 2, 31, 33])
@@ -158,13 +183,16 @@ def test_autograd_helmholtz_backward_vs_dense():
 def test_full_size_laplace3d_sampled():
     wl = W.LAPLACE3D_1M
     x = wl.make_points()
-    q = wl.make_charges(1)[:, 0]
+    qall = wl.make_charges(32)
+    q = np.ascontiguousarray(qall[:, 0])
     fmm = SkelFMM(x, wl.kernel, wl.tol, wl.leaf, nrhs_max=32)
     tg = wl.make_sample()
     ref = direct.direct_sum(wl.kernel, x, q, targets=tg)
     qt = torch.from_numpy(q).cuda()
     u64 = fmm.apply(qt, "fp64").cpu().numpy()[tg]
     u32 = fmm.apply(qt.float(), "fp32").cpu().numpy()[tg]
-    e64, e32 = relerr(u64, ref), relerr(u32, ref)
-    print(f"full size: relerr fp64 {e64:.3e}  fp32 {e32:.3e}  info {fmm.info()}")
-    assert e64 < 10 * wl.tol and e32 < 10 * wl.tol
+    utc = fmm.apply(torch.from_numpy(qall).cuda().float(), "fp32_tc").cpu().numpy()
+    fmm.device_status()
+    e64, e32, etc = relerr(u64, ref), relerr(u32, ref), relerr(utc[tg, 0], ref)
+    print(f"full size: relerr fp64 {e64:.3e}  fp32 {e32:.3e}  fp32_tc {etc:.3e}  info {fmm.info()}")
+    assert e64 < 10 * wl.tol and e32 < 10 * wl.tol and etc < 10 * wl.tol
