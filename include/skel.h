@@ -65,6 +65,8 @@ typedef struct {
     int nrhs_max;     /* largest nrhs any later apply will use, <= 256; 0 = 32           */
     int host_only;    /* 1 = build the plan on the host only; apply returns SKEL_ERR_STATE */
     int num_threads;  /* host threads used by the build; 0 = all                          */
+    int tc_drain;     /* FP32_TC: source tiles (of 32) summed in tensor memory before the
+                         partial sum is added into FP32 registers; 0 = default (1)        */
 } skel_options;
 
 typedef struct {

@@ -192,6 +192,7 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st) {
     t.Q = (const float*)b->Q;
     t.partial = (float*)b->partial;
     t.nrhs = nrhs;
+    t.drain = dp->tc_drain;
     t.status = dp->status;
     static bool attr_set[2] = {false, false};
     const int kidx = dp->kind == 0 ? 0 : 1;

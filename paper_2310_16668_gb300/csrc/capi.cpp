@@ -85,7 +85,12 @@ void finalize(skel_plan* h, const skel_options* opts) {
     h->n_items = (int64_t)lay.items.size();
     h->pairs_direct = lay.pairs_direct;
     h->pairs_far = lay.pairs_far;
-    if (!h->host_only) h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max);
+    const int drain = (opts && opts->tc_drain > 0) ? opts->tc_drain : 1;
+    if (drain > 1 << 20) throw Error(SKEL_ERR_ARG, "tc_drain too large");
+    if (!h->host_only) {
+        h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max);
+        h->dev->tc_drain = drain;
+    }
     h->t_upload = now() - t0;
 }
 

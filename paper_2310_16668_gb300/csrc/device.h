@@ -46,6 +46,7 @@ struct DevicePlan {
     TcItem* tc_items = nullptr;
     int64_t n_tc = 0;
     int64_t tc_n_slots = 0;
+    int tc_drain = 1;                      // tiles per tensor-memory accumulation segment
     int64_t* tc_chunk_ptr = nullptr;
     int64_t* tc_chunk_slots = nullptr;
     int* status = nullptr;                 // device word raised by a bounded wait that gave up

@@ -101,7 +101,7 @@ struct WorkItem {                       // one warp: 32 targets x a task range
 constexpr int kTcRows = 128;
 constexpr int kTcK = 32;
 constexpr int kTcMinRows = 96;          // boxes with fewer entries use the CUDA-core kernel
-constexpr int kTcMaxTiles = 96;         // source tiles per tensor-core work item
+constexpr int kTcMaxTiles = 96;         // source tiles per tensor-core work item (3 KB of descriptors)
 
 struct SrcTile {                        // 32 bytes
     int64_t start;                      // first source entry
@@ -112,6 +112,8 @@ struct SrcTile {                        // 32 bytes
     uint8_t seg_mask[8];                // bit c: target slot c skips this segment
     int32_t pad;
 };
+
+static_assert(sizeof(SrcTile) == 32, "SrcTile is copied as two 16-byte words");
 
 struct TcItem {
     int64_t box;

@@ -16,7 +16,10 @@
 //     FP32 tensor-memory tile, and commits them to the tile buffer's mbarrier.
 // Two buffers let the kernel evaluation of tile t+1 run while the tensor
 // core multiplies tile t. The dropped lo*lo term and the TF32 rounding of the
-// lo parts are below 2^-21 of each product.
+// lo parts are below 2^-21 of each product. The tensor-memory accumulator
+// only ever sums `drain` tiles: two accumulators alternate, and each finished
+// one is added into FP32 registers (round to nearest) while the other fills,
+// so no long accumulation chain runs inside the tensor core.
 //
 // Masks: a source slot that a target slot must skip (the regrouped
 // subtractions of Algorithm 2) gives G = 0 for those rows. Every wait is
@@ -36,12 +39,13 @@ namespace skel {
 constexpr int kTcThreads = 256;
 constexpr int kTcN = 32;                       // right-hand sides per pass (MMA N)
 constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kColD = 0, kColA = 64;      // D [0,32); A_hi[b] at 64+64b, A_lo[b] at 96+64b
+constexpr uint32_t kColD = 0, kColA = 64;      // D0 [0,32), D1 [32,64); A_hi[b] at 64+64b, A_lo[b] at 96+64b
 constexpr int kSmB = 0;                        // B_hi[2][1024] floats, then B_lo[2][1024]
 constexpr int kSmSrc = 16384;                  // src hi [2][32] float4, then lo [2][32]
 constexpr int kSmBar = 18432;                  // mbar[2]
 constexpr int kSmTmem = 18448;
 constexpr int kSmSlots = 18452;
+constexpr int kSmTiles = 18464;                // the item's SrcTile descriptors (<= kTcMaxTiles)
 constexpr int kTcSmemRequest = 100 * 1024;     // at most two CTAs (2 x 256 TMEM columns) per SM
 constexpr int kSpinLimit = 1 << 20;
 
@@ -58,6 +62,7 @@ struct TcArgs {
     float* partial;
     int nrhs;
     int r0;                                    // first right-hand side of this pass
+    int drain;                                 // tiles accumulated in tensor memory before a drain
     int* status;
 };
 
@@ -141,7 +146,7 @@ __device__ __forceinline__ void tc_eval16(const float4* sh, const float4* sl, fl
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_near_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     float* bhi = reinterpret_cast<float*>(sm + kSmB);
     float* blo = bhi + 2 * 1024;
@@ -189,41 +194,103 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_near_kernel(const TcArgs a) 
     const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((128u >> 4) << 24);
 
-    int n_issued = 0;
-    bool ok = true;
-    for (int ti = it.tile_lo; ti < it.tile_hi; ++ti) {
-        const SrcTile st = a.tiles[ti];
+    float acc[kTcN];
+#pragma unroll
+    for (int c = 0; c < kTcN; ++c) acc[c] = 0.f;
+    int drained = 0;                               // segments already added into acc
+    // add the finished accumulator of segment `seg` into acc (warps 0-3)
+    auto drain_seg = [&](int seg) {
+        if (half == 0) {
+            uint32_t v[kTcN];
+            tmem_ld32(tbase + lane_off + kColD + 32u * (seg & 1), v);
+#pragma unroll
+            for (int c = 0; c < kTcN; ++c) acc[c] += __uint_as_float(v[c]);
+        }
+    };
+    // the item's tile descriptors -> shared memory (one coalesced pass)
+    SrcTile* stiles = reinterpret_cast<SrcTile*>(sm + kSmTiles);
+    const int ntiles = it.tile_hi - it.tile_lo;
+    {
+        const int4* src = reinterpret_cast<const int4*>(a.tiles + it.tile_lo);
+        int4* dst = reinterpret_cast<int4*>(stiles);
+        for (int e = tid; e < ntiles * 2; e += kTcThreads) dst[e] = src[e];
+    }
+    __syncthreads();
+    auto needed = [&](int k) {
+        const SrcTile& st = stiles[k];
         uint32_t need = 0;
         for (int s = 0; s < st.nseg; ++s) need |= (~(uint32_t)st.seg_mask[s]) & item_slots;
-        if (need == 0) continue;
+        return need != 0;
+    };
+    auto next_needed = [&](int k) {
+        while (k < ntiles && !needed(k)) ++k;
+        return k;
+    };
+    // register prefetch of one tile: coordinates (threads 0..31) and 4 charges per thread
+    const int pj = tid >> 3, pc0 = (tid & 7) * 4;
+    const bool vec4 = (a.nrhs & 3) == 0;
+    auto prefetch = [&](int k, float4& ph, float4& pl, float* pq) {
+        if (k >= ntiles) return;
+        const SrcTile& st = stiles[k];
+        if (tid < 32) {
+            ph = make_float4(0.f, 0.f, 0.f, 0.f);
+            pl = ph;
+            if (tid < st.cnt) {
+                ph = a.X[st.start + tid];
+                if (st.flags & TASK_ADJ) pl = a.Xlo[st.start + tid];
+            }
+        }
+        const int rr = a.r0 + pc0;
+        const int64_t base = (st.start + pj) * a.nrhs + rr;
+        if (pj < st.cnt && vec4 && rr + 3 < a.nrhs) {
+            const float4 v = *reinterpret_cast<const float4*>(a.Q + base);
+            pq[0] = v.x; pq[1] = v.y; pq[2] = v.z; pq[3] = v.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) pq[c] = (pj < st.cnt && rr + c < a.nrhs) ? a.Q[base + c] : 0.f;
+        }
+    };
+    float4 nh = make_float4(0.f, 0.f, 0.f, 0.f), nl = nh;
+    float nq[4] = {0.f, 0.f, 0.f, 0.f};
+    int cur = next_needed(0);
+    prefetch(cur, nh, nl, nq);
+
+    int n_issued = 0;
+    bool ok = true;
+    while (cur < ntiles) {
+        const SrcTile st = stiles[cur];
+        const float4 ch = nh, cl = nl;
+        float cq[4] = {nq[0], nq[1], nq[2], nq[3]};
+        const int nxt = next_needed(cur + 1);
+        prefetch(nxt, nh, nl, nq);
         const int buf = n_issued & 1, use = n_issued >> 1;
         if (use >= 1) {
             const bool w = mbar_wait(sm_addr(&mbar[buf]), (uint32_t)((use - 1) & 1));
             if (!__syncthreads_and(w)) { ok = false; break; }
+            // tile n_issued - 2 is complete: if it closed a segment, drain it
+            const int done_tile = n_issued - 2;
+            if ((done_tile + 1) % a.drain == 0 && done_tile / a.drain == drained) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                drain_seg(drained);
+                ++drained;
+            }
         }
         const bool adj = (st.flags & TASK_ADJ) != 0;
         // stage source coordinates and the split charge block
         if (tid < 32) {
-            float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-            if (tid < st.cnt) {
-                h = a.X[st.start + tid];
-                if (adj) l = a.Xlo[st.start + tid];
-            }
-            shi[buf * 32 + tid] = h;
-            slo[buf * 32 + tid] = l;
+            shi[buf * 32 + tid] = ch;
+            slo[buf * 32 + tid] = cl;
         }
         {
-            const int j = tid >> 3, c0 = (tid & 7) * 4;
             float* bh = bhi + buf * 1024;
             float* bl = blo + buf * 1024;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const int n = c0 + c, rr = a.r0 + n;
-                const float v = (j < st.cnt && rr < a.nrhs) ? a.Q[(st.start + j) * a.nrhs + rr] : 0.f;
-                const uint32_t h = to_tf32(v);
-                const int w = ((n >> 3) * 1024 + (j >> 2) * 128 + (n & 7) * 16 + (j & 3) * 4) >> 2;
+                const int n = pc0 + c;
+                const uint32_t h = to_tf32(cq[c]);
+                const int w = ((n >> 3) * 1024 + (pj >> 2) * 128 + (n & 7) * 16 + (pj & 3) * 4) >> 2;
                 bh[w] = __uint_as_float(h);
-                bl[w] = __uint_as_float(to_tf32(v - __uint_as_float(h)));
+                bl[w] = __uint_as_float(to_tf32(cq[c] - __uint_as_float(h)));
             }
         }
         __syncthreads();
@@ -258,11 +325,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_near_kernel(const TcArgs a) 
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t bh = sm_addr(bhi + buf * 1024), bl = sm_addr(blo + buf * 1024);
-            const uint32_t d = tbase + kColD;
+            const int seg = n_issued / a.drain;
+            const uint32_t d = tbase + kColD + 32u * (seg & 1);
+            const bool first = (n_issued % a.drain) == 0;
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
                 const uint32_t ahi = tbase + kColA + 64u * buf + 8u * s, alo = ahi + 32u;
-                mma_tf32(d, ahi, smem_desc(bh + 256u * s), idesc, (n_issued > 0 || s > 0) ? 1u : 0u);
+                mma_tf32(d, ahi, smem_desc(bh + 256u * s), idesc, (!first || s > 0) ? 1u : 0u);
                 mma_tf32(d, ahi, smem_desc(bl + 256u * s), idesc, 1u);
                 mma_tf32(d, alo, smem_desc(bh + 256u * s), idesc, 1u);
             }
@@ -270,22 +339,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_near_kernel(const TcArgs a) 
                          :: "r"(sm_addr(&mbar[buf])) : "memory");
         }
         ++n_issued;
+        cur = nxt;
     }
-    float acc[kTcN];
-#pragma unroll
-    for (int c = 0; c < kTcN; ++c) acc[c] = 0.f;
     if (n_issued > 0) {
         const int last = n_issued - 1;
         const bool w = mbar_wait(sm_addr(&mbar[last & 1]), (uint32_t)((last >> 1) & 1));
         const bool all = __syncthreads_and(w);
         if (all && ok) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (half == 0) {
-                uint32_t v[kTcN];
-                tmem_ld32(tbase + lane_off + kColD, v);
-#pragma unroll
-                for (int c = 0; c < kTcN; ++c) acc[c] = __uint_as_float(v[c]);
-            }
+            const int nseg = last / a.drain + 1;
+            for (; drained < nseg; ++drained) drain_seg(drained);
         } else {
             ok = false;
             if (!all) mbar_wait(sm_addr(&mbar[last & 1]), (uint32_t)((last >> 1) & 1));
