@@ -51,7 +51,9 @@ extern "C" {
 #define SKEL_FP64     0   /* FP64 arithmetic, double charges/potentials            */
 #define SKEL_FP32     1   /* FP32 arithmetic on the CUDA cores, float in/out       */
 #define SKEL_FP32_TC  2   /* FP32 kernel evaluation, tensor-core contractions over
-                             right-hand sides (3-pass TF32 split, FP32 accumulate) */
+                             right-hand sides (3-pass TF32 split, FP32 accumulate);
+                             real kernels with nrhs a multiple of 4 — otherwise the
+                             FP32 CUDA-core path runs */
 
 typedef struct skel_plan* skel_handle;
 
@@ -65,8 +67,6 @@ typedef struct {
     int nrhs_max;     /* largest nrhs any later apply will use, <= 256; 0 = 32           */
     int host_only;    /* 1 = build the plan on the host only; apply returns SKEL_ERR_STATE */
     int num_threads;  /* host threads used by the build; 0 = all                          */
-    int tc_drain;     /* FP32_TC: source tiles (of 32) summed in tensor memory before the
-                         partial sum is added into FP32 registers; 0 = default (1)        */
 } skel_options;
 
 typedef struct {

@@ -30,7 +30,7 @@ class SkelKernel(ctypes.Structure):
 
 class SkelOptions(ctypes.Structure):
     _fields_ = [("proxy_p", ctypes.c_int), ("nrhs_max", ctypes.c_int),
-                ("host_only", ctypes.c_int), ("num_threads", ctypes.c_int), ("tc_drain", ctypes.c_int)]
+                ("host_only", ctypes.c_int), ("num_threads", ctypes.c_int)]
 
 
 class SkelStats(ctypes.Structure):

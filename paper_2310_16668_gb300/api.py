@@ -24,8 +24,8 @@ _DTYPES = {("fp64", False): torch.float64, ("fp64", True): torch.complex128,
            ("fp32_tc", False): torch.float32, ("fp32_tc", True): torch.complex64}
 
 
-def _options(proxy_p, nrhs_max, host_only, num_threads, tc_drain=0):
-    return SkelOptions(int(proxy_p), int(nrhs_max), int(bool(host_only)), int(num_threads), int(tc_drain))
+def _options(proxy_p, nrhs_max, host_only, num_threads):
+    return SkelOptions(int(proxy_p), int(nrhs_max), int(bool(host_only)), int(num_threads))
 
 
 class SkelFMM:
@@ -33,7 +33,7 @@ class SkelFMM:
 
     def __init__(self, points, kernel: str = "laplace3d", tol: float = 1e-6, leaf_size: int = 128,
                  kappa: float = 0.0, proxy_p: int = 0, nrhs_max: int = 32, host_only: bool = False,
-                 num_threads: int = 0, tc_drain: int = 0, _handle=None):
+                 num_threads: int = 0, _handle=None):
         self._lib = _lib.load()
         self.kernel = kernel
         self.kappa = float(kappa)
@@ -45,7 +45,7 @@ class SkelFMM:
             pts = np.ascontiguousarray(points, dtype=np.float64)
             n, dim = pts.shape
             h = ctypes.c_void_p()
-            opts = _options(proxy_p, nrhs_max, host_only, num_threads, tc_drain)
+            opts = _options(proxy_p, nrhs_max, host_only, num_threads)
             check(self._lib.skel_build(pts.ctypes.data, n, dim, SkelKernel(_lib.KERNELS[kernel], self.kappa),
                                        float(tol), int(leaf_size), ctypes.byref(opts), ctypes.byref(h)))
             self._h = h
@@ -54,7 +54,7 @@ class SkelFMM:
     # ---- construction from an external plan --------------------------------------
     @classmethod
     def from_plan(cls, points, kernel: str, plan: dict, kappa: float = 0.0, nrhs_max: int = 32,
-                  host_only: bool = False, tc_drain: int = 0):
+                  host_only: bool = False):
         """Handle from a plan in the skel.h exchange format (dict of arrays)."""
         lib = _lib.load()
         pts = np.ascontiguousarray(points, dtype=np.float64)
@@ -75,7 +75,7 @@ class SkelFMM:
         center = np.ascontiguousarray(plan["center"], dtype=np.float64)
         nb = arr["level"].shape[0]
         h = ctypes.c_void_p()
-        opts = _options(0, nrhs_max, host_only, 0, tc_drain)
+        opts = _options(0, nrhs_max, host_only, 0)
         check(lib.skel_plan_import(pts.ctypes.data, n, dim, SkelKernel(_lib.KERNELS[kernel], float(kappa)),
                                    center.ctypes.data, float(plan["side"]), nb,
                                    *[arr[k].ctypes.data for k in ("level", "coord", "parent", "is_leaf",

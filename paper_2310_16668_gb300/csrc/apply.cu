@@ -183,6 +183,7 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st) {
     TcArgs t;
     t.items = dp->tc_items;
     t.tiles = dp->tc_tiles;
+    t.list = dp->tc_list;
     t.box_off = dp->box_off;
     t.box_n = dp->box_n;
     t.box_nslot = dp->box_nslot;
@@ -192,7 +193,6 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st) {
     t.Q = (const float*)b->Q;
     t.partial = (float*)b->partial;
     t.nrhs = nrhs;
-    t.drain = dp->tc_drain;
     t.status = dp->status;
     static bool attr_set[2] = {false, false};
     const int kidx = dp->kind == 0 ? 0 : 1;
@@ -330,6 +330,7 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
         dp->n_mix = (int64_t)lay.mix_items.size();
         dp->tc_tiles = upload(lay.tc_tiles, dp->bytes);
         dp->tc_items = upload(lay.tc_items, dp->bytes);
+        dp->tc_list = upload(lay.tc_list, dp->bytes);
         dp->n_tc = (int64_t)lay.tc_items.size();
         dp->tc_n_slots = lay.tc_n_slots;
         dp->tc_chunk_ptr = upload(lay.tc_chunk_ptr, dp->bytes);
@@ -356,7 +357,7 @@ void device_plan_destroy(DevicePlan* dp) {
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->perm_entry,
                     dp->perm_point, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->chunk_box, dp->chunk_t0, dp->chunk_item_ptr, dp->chunk_items, dp->stage_in,
-                    dp->stage_out, dp->mix_items, dp->tc_tiles, dp->tc_items, dp->tc_chunk_ptr,
+                    dp->stage_out, dp->mix_items, dp->tc_tiles, dp->tc_items, dp->tc_list, dp->tc_chunk_ptr,
                     dp->tc_chunk_slots, dp->status};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
@@ -407,13 +408,22 @@ void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_appl
 void device_apply(DevicePlan* dp, const void* q, void* u, int nrhs, int precision, bool transpose,
                   void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
-    const bool tc = precision == 2;
     if (precision == 0) {
         if (dp->cplx) run_apply<double, true>(dp, dp->p64, q, u, nrhs, transpose, false, st);
         else run_apply<double, false>(dp, dp->p64, q, u, nrhs, transpose, false, st);
+    } else if (dp->cplx) {
+        run_apply<float, true>(dp, dp->p32, q, u, nrhs, transpose, false, st);
+    } else if (precision == 2 && nrhs % 4 == 0) {
+        // tensor-core path: at most kTcMaxRhs right-hand sides per apply
+        const float* qf = (const float*)q;
+        float* uf = (float*)u;
+        for (int c0 = 0; c0 < nrhs; c0 += kTcMaxRhs) {
+            const int nc = std::min(kTcMaxRhs, nrhs - c0);
+            run_apply<float, false>(dp, dp->p32, qf + (int64_t)c0 * dp->N, uf + (int64_t)c0 * dp->N, nc, transpose,
+                                    true, st);
+        }
     } else {
-        if (dp->cplx) run_apply<float, true>(dp, dp->p32, q, u, nrhs, transpose, tc, st);
-        else run_apply<float, false>(dp, dp->p32, q, u, nrhs, transpose, tc, st);
+        run_apply<float, false>(dp, dp->p32, q, u, nrhs, transpose, false, st);
     }
 }
 

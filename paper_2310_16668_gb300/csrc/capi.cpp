@@ -85,12 +85,7 @@ void finalize(skel_plan* h, const skel_options* opts) {
     h->n_items = (int64_t)lay.items.size();
     h->pairs_direct = lay.pairs_direct;
     h->pairs_far = lay.pairs_far;
-    const int drain = (opts && opts->tc_drain > 0) ? opts->tc_drain : 1;
-    if (drain > 1 << 20) throw Error(SKEL_ERR_ARG, "tc_drain too large");
-    if (!h->host_only) {
-        h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max);
-        h->dev->tc_drain = drain;
-    }
+    if (!h->host_only) h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max);
     h->t_upload = now() - t0;
 }
 

@@ -44,9 +44,9 @@ struct DevicePlan {
     int64_t n_mix = 0;
     SrcTile* tc_tiles = nullptr;
     TcItem* tc_items = nullptr;
+    int32_t* tc_list = nullptr;
     int64_t n_tc = 0;
     int64_t tc_n_slots = 0;
-    int tc_drain = 1;                      // tiles per tensor-memory accumulation segment
     int64_t* tc_chunk_ptr = nullptr;
     int64_t* tc_chunk_slots = nullptr;
     int* status = nullptr;                 // device word raised by a bounded wait that gave up

@@ -101,24 +101,21 @@ struct WorkItem {                       // one warp: 32 targets x a task range
 constexpr int kTcRows = 128;
 constexpr int kTcK = 32;
 constexpr int kTcMinRows = 96;          // boxes with fewer entries use the CUDA-core kernel
-constexpr int kTcMaxTiles = 96;         // source tiles per tensor-core work item (3 KB of descriptors)
+constexpr int kTcMaxTiles = 128;        // source tiles per tensor-core work item
 
-struct SrcTile {                        // 32 bytes
+struct SrcTile {                        // 64 bytes; copied into shared memory by the bulk-copy engine
     int64_t start;                      // first source entry
-    int16_t cnt;                        // sources (1..32)
-    int8_t nseg;                        // source slots in the tile (1..8)
-    int8_t flags;                       // TASK_ADJ
-    uint8_t seg_end[8];                 // end (exclusive, within the tile) of each slot segment
-    uint8_t seg_mask[8];                // bit c: target slot c skips this segment
-    int32_t pad;
+    int32_t cnt;                        // sources (1..32)
+    int32_t flags;                      // TASK_ADJ
+    uint32_t keep[kMaxSlots];           // per target slot: bit j = the slot keeps source j
+    int32_t pad[4];
 };
-
-static_assert(sizeof(SrcTile) == 32, "SrcTile is copied as two 16-byte words");
+static_assert(sizeof(SrcTile) == 64, "SrcTile is one 64-byte bulk copy");
 
 struct TcItem {
     int64_t box;
     int32_t r0;                         // first target row (multiple of 128)
-    int32_t tile_lo, tile_hi;           // range of the box's source tiles
+    int32_t list_lo, list_hi;           // range in tc_list (indices of the tiles it needs)
     int32_t slot;                       // first of its 4 partial-sum slots (32 rows each)
 };
 
@@ -147,6 +144,7 @@ struct Layout {
     // tensor-core mode: CUDA-core items for small boxes, tensor-core items for the rest
     std::vector<WorkItem> mix_items;
     std::vector<SrcTile> tc_tiles;
+    std::vector<int32_t> tc_list;
     std::vector<TcItem> tc_items;
     std::vector<int64_t> tc_chunk_ptr, tc_chunk_slots;
     int64_t tc_n_slots = 0;

@@ -249,61 +249,66 @@ void build_layout(const Plan& p, Layout& lay) {
     simt_items([&](int64_t b) { return !is_tc(b); }, lay.mix_items, cs, 0);
     int64_t slot = (int64_t)lay.mix_items.size();
     lay.tc_tiles.clear();
+    lay.tc_list.clear();
     lay.tc_items.clear();
     for (int64_t b = 0; b < nb; ++b) {
         if (lay.box_off[b] < 0 || !is_tc(b)) continue;
-        const int32_t* ssB = &lay.slot_start[b * (kMaxSlots + 1)];
         const int64_t tile0 = (int64_t)lay.tc_tiles.size();
         for (int64_t tk = lay.task_ptr[b]; tk < lay.task_ptr[b + 1]; ++tk) {
             const int64_t src = lay.task_src[tk];
             const int32_t* ssS = &lay.slot_start[src * (kMaxSlots + 1)];
             const int ns = lay.box_nslot[src];
-            // segment masks of the source slots: bit c = target slot c skips it
-            uint8_t smask[kMaxSlots];
-            bool all_skip = true;
-            for (int j = 0; j < ns; ++j) {
-                smask[j] = 0;
-                for (int i = 0; i < lay.box_nslot[b]; ++i)
-                    if ((lay.task_mask[tk] >> (i * 8 + j)) & 1) smask[j] |= (uint8_t)(1u << i);
-                const uint8_t full = (uint8_t)((1u << lay.box_nslot[b]) - 1);
-                if (smask[j] != full) all_skip = false;
-            }
-            if (all_skip) continue;
             const int32_t n = lay.box_n[src];
             for (int32_t p0 = 0; p0 < n; p0 += kTcK) {
                 SrcTile st{};
                 st.start = lay.box_off[src] + p0;
-                st.cnt = (int16_t)std::min(kTcK, n - p0);
-                st.flags = (int8_t)lay.task_flags[tk];
-                int nseg = 0;
+                st.cnt = std::min(kTcK, n - p0);
+                st.flags = lay.task_flags[tk];
                 for (int j = 0; j < ns; ++j) {
-                    const int a = std::max(ssS[j] - p0, 0), e = std::min(ssS[j + 1] - p0, (int)st.cnt);
+                    const int a = std::max(ssS[j] - p0, 0), e = std::min(ssS[j + 1] - p0, st.cnt);
                     if (e <= a) continue;
-                    st.seg_end[nseg] = (uint8_t)e;
-                    st.seg_mask[nseg] = smask[j];
-                    ++nseg;
+                    const uint32_t bits = (uint32_t)(((1ull << e) - 1ull) ^ ((1ull << a) - 1ull));
+                    for (int i = 0; i < lay.box_nslot[b]; ++i)
+                        if (!((lay.task_mask[tk] >> (i * 8 + j)) & 1)) st.keep[i] |= bits;
                 }
-                st.nseg = (int8_t)nseg;
-                lay.tc_tiles.push_back(st);
+                bool any = false;
+                for (int i = 0; i < lay.box_nslot[b]; ++i) any |= st.keep[i] != 0;
+                if (any) lay.tc_tiles.push_back(st);
             }
         }
         const int64_t tile1 = (int64_t)lay.tc_tiles.size();
+        const int32_t* ssB = &lay.slot_start[b * (kMaxSlots + 1)];
         for (int32_t r0 = 0; r0 < lay.box_n[b]; r0 += kTcRows) {
-            for (int64_t t = tile0; t < tile1 || t == tile0; t += kTcMaxTiles) {
+            // target slots present in rows [r0, r0 + 128)
+            const int32_t r1 = std::min(r0 + kTcRows, lay.box_n[b]);
+            uint32_t slots = 0;
+            for (int i = 0; i < lay.box_nslot[b]; ++i)
+                if (ssB[i] < r1 && ssB[i + 1] > r0) slots |= 1u << i;
+            std::vector<int32_t> need;
+            for (int64_t t = tile0; t < tile1; ++t) {
+                bool any = false;
+                for (int i = 0; i < lay.box_nslot[b]; ++i)
+                    if (((slots >> i) & 1) && lay.tc_tiles[t].keep[i]) any = true;
+                if (any) need.push_back((int32_t)t);
+            }
+            size_t p = 0;
+            do {
                 TcItem it;
                 it.box = b;
                 it.r0 = r0;
-                it.tile_lo = (int32_t)t;
-                it.tile_hi = (int32_t)std::min(t + kTcMaxTiles, tile1);
+                it.list_lo = (int32_t)lay.tc_list.size();
+                const size_t q = std::min(p + (size_t)kTcMaxTiles, need.size());
+                lay.tc_list.insert(lay.tc_list.end(), need.begin() + p, need.begin() + q);
+                it.list_hi = (int32_t)lay.tc_list.size();
                 it.slot = (int32_t)slot;
-                for (int q = 0; q < kTcRows / kChunk; ++q)
-                    if (r0 + q * kChunk < lay.box_n[b]) cs.push_back({box_chunk0[b] + (r0 + q * kChunk) / kChunk, slot + q});
+                for (int c = 0; c < kTcRows / kChunk; ++c)
+                    if (r0 + c * kChunk < lay.box_n[b])
+                        cs.push_back({box_chunk0[b] + (r0 + c * kChunk) / kChunk, slot + c});
                 slot += kTcRows / kChunk;
                 lay.tc_items.push_back(it);
-                if (tile1 == tile0) break;
-            }
+                p = q;
+            } while (p < need.size());
         }
-        (void)ssB;
     }
     lay.tc_n_slots = slot;
     to_csr(cs, lay.tc_chunk_ptr, lay.tc_chunk_slots);

@@ -369,15 +369,18 @@ __global__ void __launch_bounds__(kNearWarps * 32) near_kernel(const NearArgs<Re
         if (r0 + r < a.nrhs) a.partial[(item_id * kChunk + lane) * a.nrhs + r0 + r] = scale * acc[r];
 }
 
-// returns the number of launches
+// returns the number of launches; right-hand sides go in passes of 8 (a
+// single 32-wide pass measured slower: its registers and shared memory halve
+// the resident warps)
 template <class Real, int KIND>
 int launch_near_kind(const NearArgs<Real, KIND == 2>& a, int nrhs, unsigned grid, cudaStream_t st) {
     if (nrhs == 1) {
         near_kernel<Real, KIND, 1><<<grid, kNearWarps * 32, 0, st>>>(a, 0);
         return 1;
     }
+    constexpr int RT = 8;
     int n = 0;
-    for (int r0 = 0; r0 < nrhs; r0 += 8, ++n) near_kernel<Real, KIND, 8><<<grid, kNearWarps * 32, 0, st>>>(a, r0);
+    for (int r0 = 0; r0 < nrhs; r0 += RT, ++n) near_kernel<Real, KIND, RT><<<grid, kNearWarps * 32, 0, st>>>(a, r0);
     return n;
 }
 
