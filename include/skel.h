@@ -247,6 +247,30 @@ int skel_last_timings(skel_handle h, skel_timings* t);
  */
 int skel_device_status(skel_handle h);
 
+/*
+ * skel_direct_noalloc — u = A q by direct summation (FP64; complex128 for
+ * Helmholtz), for callers that cannot allocate device memory: code running
+ * inside a framework that owns (and has reserved) the device memory pool, or
+ * a loop that must not take the device-wide synchronisation a cudaMalloc or
+ * cudaFree can cause. The paper has no counterpart: it is the plan-free form
+ * of the translation kernel's partial-sum scheme, and it allocates nothing.
+ *   points     device, n x dim row-major FP64
+ *   q, u       device, n x nrhs (each right-hand side contiguous); u is
+ *              overwritten; asynchronous on `stream`
+ *   n, dim, k  as for skel_build (coincident points contribute nothing)
+ * Its partial sums live in one 32 MiB __device__ array inside the library:
+ * every GPU that loads the library holds it until the process exits, and all
+ * calls share it, so calls that overlap on the GPU race. Each call overwrites
+ * every scratch value it reads; nothing has to start at zero. The first call
+ * on a device looks up the array's device address there; make that first
+ * call before any stream capture.
+ * Errors: SKEL_ERR_ARG for NULL or host pointers, bad sizes, or a problem
+ * whose partial sums exceed the array (n up to 131,072 for real kernels,
+ * 91,168 for Helmholtz); SKEL_ERR_CUDA.
+ */
+int skel_direct_noalloc(const double* points, int64_t n, int dim, skel_kernel k,
+                        const double* q, double* u, int nrhs, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

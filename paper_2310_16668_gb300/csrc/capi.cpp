@@ -151,6 +151,11 @@ int do_apply(skel_handle h, const void* q, void* u, int nrhs, int precision, voi
 
 }  // namespace
 
+namespace skel {
+// lets other translation units of the C-ABI report through skel_last_error
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace skel
+
 extern "C" {
 
 int skel_build(const double* points, int64_t n, int dim, skel_kernel k, double tol, int leaf_size,

@@ -62,6 +62,9 @@ struct Plan {
 
 bool touches(int la, const int64_t* ca, int lb, const int64_t* cb, int dim);
 
+// record a message for skel_last_error on this thread; returns code
+int set_error(int code, const std::string& msg);
+
 // Tree construction from points (root cube, split while > b, prune empty,
 // 2:1 balance between a leaf and every box touching it) and its neighbor lists.
 void build_tree(const double* pts, int64_t n, int dim, int leaf_size, Tree& t,

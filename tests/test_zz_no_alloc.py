@@ -1,0 +1,66 @@
+"""skel_direct_noalloc: the direct sum for callers that cannot allocate device
+memory (its partial sums live in a fixed array inside the library).
+
+Checked through the C-ABI against the existing entry point that computes the
+same sum: skel_apply on a plan whose root is a single leaf (Algorithm 2 then
+reduces to the direct sum). Two calls in a row, so the second one runs on the
+scratch the first left behind. This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2310_16668_gb300 import SkelFMM, _lib
+from paper_2310_16668_gb300 import workloads as W
+from paper_2310_16668_gb300._lib import SkelKernel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_16668_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _noalloc(x, q, kind, kappa):
+    lib = _lib.load()
+    n, dim = x.shape
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    qd = torch.from_numpy(np.ascontiguousarray(q.T)).cuda()          # column-major n x nrhs
+    ud = torch.empty_like(qd)
+    stream = torch.cuda.current_stream().cuda_stream
+    _lib.check(lib.skel_direct_noalloc(ctypes.c_void_p(xd.data_ptr()), n, dim,
+                                       SkelKernel(_lib.KERNELS[kind], kappa), ctypes.c_void_p(qd.data_ptr()),
+                                       ctypes.c_void_p(ud.data_ptr()), q.shape[1], ctypes.c_void_p(stream)))
+    torch.cuda.synchronize()
+    return ud.t().cpu().numpy()
+
+
+@pytest.mark.parametrize("kind,dim,n", [("laplace3d", 3, 3000), ("laplace2d", 2, 2500),
+                                        ("helmholtz3d", 3, 2000)])
+def test_noalloc_matches_single_leaf_apply(kind, dim, n):
+    x = W.points_uniform(n, dim, 41)
+    x[7] = x[3]                                                      # a coincident pair
+    cplx = kind == "helmholtz3d"
+    q = (W.charges_complex if cplx else W.charges_normal)(n, 2, 42)
+    fmm = SkelFMM(x, kind, 1e-6, n, kappa=25.0)                      # one leaf: the direct sum
+    assert fmm.info()["n_levels"] == 0
+    ref = fmm.apply(torch.from_numpy(q).cuda(), "fp64").cpu().numpy()
+    scale = np.abs(ref).max()
+    for _ in range(2):                                               # two calls in a row
+        u = _noalloc(x, q, kind, 25.0)
+        assert np.abs(u - ref).max() / scale < 1e-12
+
+
+def test_noalloc_rejects_too_large():
+    lib = _lib.load()
+    x = torch.zeros(3, dtype=torch.float64, device="cuda")
+    rc = lib.skel_direct_noalloc(ctypes.c_void_p(x.data_ptr()), 200000, 3, SkelKernel(1, 0.0),
+                                 ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 1, None)
+    assert rc == -1 and b"too large" in lib.skel_last_error()
