@@ -184,10 +184,6 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st) {
     t.items = dp->tc_items;
     t.tiles = dp->tc_tiles;
     t.list = dp->tc_list;
-    t.box_off = dp->box_off;
-    t.box_n = dp->box_n;
-    t.box_nslot = dp->box_nslot;
-    t.slot_start = dp->slot_start;
     t.X = (const float4*)b->X;
     t.Xlo = (const float4*)b->Xlo;
     t.Q = (const float*)b->Q;
@@ -249,10 +245,9 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
         launches += run_tc<Real, CPLX>(dp, b, nrhs, st);
         mark(dp, 3, st);
         ++launches;
-        const int64_t n = dp->n_chunks * kChunk * nrhs;
-        reduce_kernel<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->chunk_box, dp->chunk_t0, dp->tc_chunk_ptr,
-                                                           dp->tc_chunk_slots, dp->box_off, dp->box_n, part, U,
-                                                           nrhs, dp->n_chunks);
+        const int64_t n = dp->n_tot * nrhs;
+        reduce_kernel<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->tc_part_ptr, dp->tc_part_idx, part, U, nrhs,
+                                                           dp->n_tot);
         CUDA_CHECK(cudaGetLastError());
     } else if (dp->n_items > 0) {
         auto a = near_args<Real, CPLX>(dp, b, dp->items, dp->n_items, nrhs);
@@ -261,10 +256,8 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
         CUDA_CHECK(cudaGetLastError());
         mark(dp, 3, st);
         ++launches;
-        const int64_t n = dp->n_chunks * kChunk * nrhs;
-        reduce_kernel<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->chunk_box, dp->chunk_t0, dp->chunk_item_ptr,
-                                                           dp->chunk_items, dp->box_off, dp->box_n, part, U,
-                                                           nrhs, dp->n_chunks);
+        const int64_t n = dp->n_tot * nrhs;
+        reduce_kernel<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->part_ptr, dp->part_idx, part, U, nrhs, dp->n_tot);
         CUDA_CHECK(cudaGetLastError());
     }
     else {
@@ -321,11 +314,8 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
         dp->task_flags = upload(lay.task_flags, dp->bytes);
         dp->items = upload(lay.items, dp->bytes);
         dp->n_items = (int64_t)lay.items.size();
-        dp->chunk_box = upload(lay.chunk_box, dp->bytes);
-        dp->chunk_t0 = upload(lay.chunk_t0, dp->bytes);
-        dp->chunk_item_ptr = upload(lay.chunk_item_ptr, dp->bytes);
-        dp->chunk_items = upload(lay.chunk_items, dp->bytes);
-        dp->n_chunks = (int64_t)lay.chunk_box.size();
+        dp->part_ptr = upload(lay.part_ptr, dp->bytes);
+        dp->part_idx = upload(lay.part_idx, dp->bytes);
         dp->mix_items = upload(lay.mix_items, dp->bytes);
         dp->n_mix = (int64_t)lay.mix_items.size();
         dp->tc_tiles = upload(lay.tc_tiles, dp->bytes);
@@ -333,8 +323,8 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
         dp->tc_list = upload(lay.tc_list, dp->bytes);
         dp->n_tc = (int64_t)lay.tc_items.size();
         dp->tc_n_slots = lay.tc_n_slots;
-        dp->tc_chunk_ptr = upload(lay.tc_chunk_ptr, dp->bytes);
-        dp->tc_chunk_slots = upload(lay.tc_chunk_slots, dp->bytes);
+        dp->tc_part_ptr = upload(lay.tc_part_ptr, dp->bytes);
+        dp->tc_part_idx = upload(lay.tc_part_idx, dp->bytes);
         dp->status = dalloc<int>(1, dp->bytes);
         CUDA_CHECK(cudaMemset(dp->status, 0, sizeof(int)));
         dp->p64 = new DeviceBuffers();
@@ -356,9 +346,8 @@ void device_plan_destroy(DevicePlan* dp) {
     cudaSetDevice(dp->device);
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->perm_entry,
                     dp->perm_point, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
-                    dp->chunk_box, dp->chunk_t0, dp->chunk_item_ptr, dp->chunk_items, dp->stage_in,
-                    dp->stage_out, dp->mix_items, dp->tc_tiles, dp->tc_items, dp->tc_list, dp->tc_chunk_ptr,
-                    dp->tc_chunk_slots, dp->status};
+                    dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
+                    dp->tc_items, dp->tc_list, dp->tc_part_ptr, dp->tc_part_idx, dp->status};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);

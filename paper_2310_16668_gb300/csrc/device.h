@@ -34,11 +34,8 @@ struct DevicePlan {
     int32_t* task_flags = nullptr;
     WorkItem* items = nullptr;
     int64_t n_items = 0;
-    int64_t* chunk_box = nullptr;
-    int32_t* chunk_t0 = nullptr;
-    int64_t* chunk_item_ptr = nullptr;
-    int64_t* chunk_items = nullptr;
-    int64_t n_chunks = 0;
+    int64_t* part_ptr = nullptr;           // per entry: its partial sums (CUDA-core mode)
+    int64_t* part_idx = nullptr;
     // tensor-core mode
     WorkItem* mix_items = nullptr;
     int64_t n_mix = 0;
@@ -47,8 +44,8 @@ struct DevicePlan {
     int32_t* tc_list = nullptr;
     int64_t n_tc = 0;
     int64_t tc_n_slots = 0;
-    int64_t* tc_chunk_ptr = nullptr;
-    int64_t* tc_chunk_slots = nullptr;
+    int64_t* tc_part_ptr = nullptr;        // per entry: its partial sums (tensor-core mode)
+    int64_t* tc_part_idx = nullptr;
     int* status = nullptr;                 // device word raised by a bounded wait that gave up
     DeviceBuffers* p64 = nullptr;
     DeviceBuffers* p32 = nullptr;

@@ -115,12 +115,18 @@ struct SrcTile {                        // 64 bytes; copied into shared memory b
 };
 static_assert(sizeof(SrcTile) == 64, "SrcTile is one 64-byte bulk copy");
 
-struct TcItem {
-    int64_t box;
-    int32_t r0;                         // first target row (multiple of 128)
+// A tensor-core work item: up to 128 consecutive entries of the entry space
+// (rows of one box, or whole small leaves packed together), with the slot
+// table the keep masks refer to (a box's child slots, or one slot per leaf).
+struct TcItem {                         // 64 bytes
+    int64_t row_off;                    // entry of row 0
+    int32_t nrows;                      // valid rows (<= 128)
+    int32_t nslot;
+    int32_t slot_start[kMaxSlots + 1];  // first row of each slot (may be < 0 for a box's later rows)
     int32_t list_lo, list_hi;           // range in tc_list (indices of the tiles it needs)
     int32_t slot;                       // first of its 4 partial-sum slots (32 rows each)
 };
+static_assert(sizeof(TcItem) == 64, "TcItem layout");
 
 struct Layout {
     int top = 1;
@@ -141,15 +147,16 @@ struct Layout {
     std::vector<uint64_t> task_mask;    // bit (c*8 + c'): skip target slot c x source slot c'
     std::vector<int32_t> task_flags;
     std::vector<WorkItem> items;        // CUDA-core items for every box (execution order)
-    std::vector<int64_t> chunk_box;     // per 32-row target chunk: box
-    std::vector<int32_t> chunk_t0;
-    std::vector<int64_t> chunk_item_ptr, chunk_items;   // chunk -> partial slots (CUDA-core mode)
-    // tensor-core mode: CUDA-core items for small boxes, tensor-core items for the rest
+    // per entry: the partial sums (slot * 32 + row) that add up to its
+    // translations, in a fixed order (CUDA-core mode)
+    std::vector<int64_t> part_ptr, part_idx;
+    // tensor-core mode: tensor-core items for large boxes and packed small
+    // leaves, CUDA-core items for the remaining small boxes
     std::vector<WorkItem> mix_items;
     std::vector<SrcTile> tc_tiles;
     std::vector<int32_t> tc_list;
     std::vector<TcItem> tc_items;
-    std::vector<int64_t> tc_chunk_ptr, tc_chunk_slots;
+    std::vector<int64_t> tc_part_ptr, tc_part_idx;
     int64_t tc_n_slots = 0;
     int64_t pairs_direct = 0, pairs_far = 0;
 };

@@ -171,28 +171,27 @@ void build_layout(const Plan& p, Layout& lay) {
     lay.task_ptr[nb] = (int64_t)lay.task_src.size();
 
     // ---- warp work items: 32 targets x a range of tasks ---------------------
-    // chunks: every 32-row slice of every box
-    lay.chunk_box.clear();
-    lay.chunk_t0.clear();
-    std::vector<int64_t> box_chunk0(nb, -1);
-    for (int64_t b = 0; b < nb; ++b) {
-        if (lay.box_off[b] < 0) continue;
-        box_chunk0[b] = (int64_t)lay.chunk_box.size();
-        for (int32_t t0 = 0; t0 < lay.box_n[b]; t0 += kChunk) {
-            lay.chunk_box.push_back(b);
-            lay.chunk_t0.push_back(t0);
-        }
-    }
-    const int64_t nchunk = (int64_t)lay.chunk_box.size();
-    struct Tmp { WorkItem it; int64_t cost; int64_t chunk; };
-    auto simt_items = [&](auto use_box, std::vector<WorkItem>& out, std::vector<std::pair<int64_t, int64_t>>& cs,
-                          int64_t slot0) {
+    // every partial sum is (slot, row): slot = one work item's 32-row block;
+    // per entry, the list of partial sums that add up to its translations
+    std::vector<std::pair<int64_t, int64_t>> parts;             // (entry, slot * 32 + row)
+    auto to_csr = [&](std::vector<std::pair<int64_t, int64_t>>& ps, std::vector<int64_t>& ptr,
+                      std::vector<int64_t>& idx) {
+        std::stable_sort(ps.begin(), ps.end(), [](const std::pair<int64_t, int64_t>& a,
+                                                  const std::pair<int64_t, int64_t>& c) { return a.first < c.first; });
+        ptr.assign(lay.n_tot + 1, 0);
+        for (auto& x : ps) ptr[x.first + 1]++;
+        for (int64_t e = 0; e < lay.n_tot; ++e) ptr[e + 1] += ptr[e];
+        idx.resize(ps.size());
+        for (size_t i = 0; i < ps.size(); ++i) idx[i] = ps[i].second;
+        ps.clear();
+    };
+    struct Tmp { WorkItem it; int64_t cost; };
+    auto simt_items = [&](auto use_box, std::vector<WorkItem>& out, int64_t slot0) {
         std::vector<Tmp> tmp;
         for (int64_t b = 0; b < nb; ++b) {
             if (lay.box_off[b] < 0 || !use_box(b)) continue;
             const int32_t* ss = &lay.slot_start[b * (kMaxSlots + 1)];
             for (int32_t t0 = 0; t0 < lay.box_n[b]; t0 += kChunk) {
-                const int64_t chunk = box_chunk0[b] + t0 / kChunk;
                 const int32_t t1 = std::min(t0 + kChunk, lay.box_n[b]);
                 uint32_t slots = 0;
                 for (int i = 0; i < lay.box_nslot[b]; ++i)
@@ -208,13 +207,13 @@ void build_layout(const Plan& p, Layout& lay) {
                         if (any) c += slot_size(src, j);
                     }
                     if (cost > 0 && cost + c > kItemCost) {
-                        tmp.push_back({{b, t0, (int32_t)lo, (int32_t)tk, 0}, cost, chunk});
+                        tmp.push_back({{b, t0, (int32_t)lo, (int32_t)tk, 0}, cost});
                         lo = tk;
                         cost = 0;
                     }
                     cost += c;
                 }
-                tmp.push_back({{b, t0, (int32_t)lo, (int32_t)lay.task_ptr[b + 1], 0}, cost, chunk});
+                tmp.push_back({{b, t0, (int32_t)lo, (int32_t)lay.task_ptr[b + 1], 0}, cost});
             }
         }
         std::vector<int64_t> order(tmp.size());
@@ -223,95 +222,125 @@ void build_layout(const Plan& p, Layout& lay) {
                          [&](int64_t a, int64_t c) { return tmp[a].cost > tmp[c].cost; });
         out.resize(tmp.size());
         for (size_t r = 0; r < order.size(); ++r) {
-            out[r] = tmp[order[r]].it;
-            cs.push_back({tmp[order[r]].chunk, slot0 + (int64_t)r});
+            const WorkItem& it = tmp[order[r]].it;
+            out[r] = it;
+            const int32_t t1 = std::min(it.t0 + kChunk, lay.box_n[it.tgt_box]);
+            for (int32_t t = it.t0; t < t1; ++t)
+                parts.push_back({lay.box_off[it.tgt_box] + t, (slot0 + (int64_t)r) * kChunk + (t - it.t0)});
         }
     };
-    auto to_csr = [&](std::vector<std::pair<int64_t, int64_t>>& cs, std::vector<int64_t>& ptr,
-                      std::vector<int64_t>& lst) {
-        std::stable_sort(cs.begin(), cs.end(), [](const std::pair<int64_t, int64_t>& a,
-                                                  const std::pair<int64_t, int64_t>& c) { return a.first < c.first; });
-        ptr.assign(nchunk + 1, 0);
-        for (auto& x : cs) ptr[x.first + 1]++;
-        for (int64_t c = 0; c < nchunk; ++c) ptr[c + 1] += ptr[c];
-        lst.resize(cs.size());
-        for (size_t i = 0; i < cs.size(); ++i) lst[i] = cs[i].second;
-    };
-    {
-        std::vector<std::pair<int64_t, int64_t>> cs;
-        simt_items([](int64_t) { return true; }, lay.items, cs, 0);
-        to_csr(cs, lay.chunk_item_ptr, lay.chunk_items);
-    }
+    simt_items([](int64_t) { return true; }, lay.items, 0);
+    to_csr(parts, lay.part_ptr, lay.part_idx);
 
     // ---- tensor-core mode --------------------------------------------------------
+    // large boxes: their own 128-row items; small leaves: packed, consecutive
+    // in box order (so neighbouring in space), up to 128 rows and 8 leaves per
+    // item, one keep-mask slot per leaf; any other small box: CUDA-core items
     auto is_tc = [&](int64_t b) { return lay.box_n[b] >= kTcMinRows; };
-    std::vector<std::pair<int64_t, int64_t>> cs;
-    simt_items([&](int64_t b) { return !is_tc(b); }, lay.mix_items, cs, 0);
+    auto packable = [&](int64_t b) { return !is_tc(b) && t.is_leaf[b]; };
+    simt_items([&](int64_t b) { return !is_tc(b) && !packable(b); }, lay.mix_items, 0);
     int64_t slot = (int64_t)lay.mix_items.size();
     lay.tc_tiles.clear();
     lay.tc_list.clear();
     lay.tc_items.clear();
-    for (int64_t b = 0; b < nb; ++b) {
-        if (lay.box_off[b] < 0 || !is_tc(b)) continue;
-        const int64_t tile0 = (int64_t)lay.tc_tiles.size();
-        for (int64_t tk = lay.task_ptr[b]; tk < lay.task_ptr[b + 1]; ++tk) {
-            const int64_t src = lay.task_src[tk];
+    // one item: rows [row_off, row_off + nrows) whose slot j covers rows
+    // [sst[j], sst[j+1]); targets = (box, first slot of that box in the item,
+    // row of the box's first entry)
+    struct Tgt { int64_t box; int slot0; int32_t row0; };
+    auto emit = [&](int64_t row_off, int32_t nrows, int nslot, const int32_t* sst, const std::vector<Tgt>& tg) {
+        // the union of the targets' tasks, one tile run per (source box, flags)
+        std::vector<std::pair<int64_t, int32_t>> srcs;                 // (source box, flags)
+        std::vector<std::vector<uint64_t>> keepslot;                  // per source: per item slot, mask of source slots kept
+        for (const Tgt& g : tg) {
+            const int64_t b = g.box;
+            for (int64_t tk = lay.task_ptr[b]; tk < lay.task_ptr[b + 1]; ++tk) {
+                const int64_t src = lay.task_src[tk];
+                size_t k = 0;
+                while (k < srcs.size() && !(srcs[k].first == src && srcs[k].second == lay.task_flags[tk])) ++k;
+                if (k == srcs.size()) {
+                    srcs.push_back({src, lay.task_flags[tk]});
+                    keepslot.push_back(std::vector<uint64_t>(kMaxSlots, 0));
+                }
+                for (int i = 0; i < lay.box_nslot[b]; ++i) {
+                    const int is = g.slot0 + i;
+                    if (is < 0 || is >= nslot) continue;
+                    for (int j = 0; j < lay.box_nslot[src]; ++j)
+                        if (!((lay.task_mask[tk] >> (i * 8 + j)) & 1)) keepslot[k][is] |= (uint64_t)1 << j;
+                }
+            }
+        }
+        TcItem it{};
+        it.row_off = row_off;
+        it.nrows = nrows;
+        it.nslot = nslot;
+        for (int j = 0; j <= nslot; ++j) it.slot_start[j] = sst[j];
+        it.list_lo = (int32_t)lay.tc_list.size();
+        for (size_t k = 0; k < srcs.size(); ++k) {
+            const int64_t src = srcs[k].first;
             const int32_t* ssS = &lay.slot_start[src * (kMaxSlots + 1)];
-            const int ns = lay.box_nslot[src];
             const int32_t n = lay.box_n[src];
             for (int32_t p0 = 0; p0 < n; p0 += kTcK) {
                 SrcTile st{};
                 st.start = lay.box_off[src] + p0;
                 st.cnt = std::min(kTcK, n - p0);
-                st.flags = lay.task_flags[tk];
-                for (int j = 0; j < ns; ++j) {
+                st.flags = srcs[k].second;
+                for (int j = 0; j < lay.box_nslot[src]; ++j) {
                     const int a = std::max(ssS[j] - p0, 0), e = std::min(ssS[j + 1] - p0, st.cnt);
                     if (e <= a) continue;
                     const uint32_t bits = (uint32_t)(((1ull << e) - 1ull) ^ ((1ull << a) - 1ull));
-                    for (int i = 0; i < lay.box_nslot[b]; ++i)
-                        if (!((lay.task_mask[tk] >> (i * 8 + j)) & 1)) st.keep[i] |= bits;
+                    for (int is = 0; is < nslot; ++is)
+                        if ((keepslot[k][is] >> j) & 1) st.keep[is] |= bits;
                 }
                 bool any = false;
-                for (int i = 0; i < lay.box_nslot[b]; ++i) any |= st.keep[i] != 0;
-                if (any) lay.tc_tiles.push_back(st);
+                for (int is = 0; is < nslot; ++is) any |= st.keep[is] != 0;
+                if (!any) continue;
+                if (lay.tc_list.size() - it.list_lo == (size_t)kTcMaxTiles) {   // split long lists
+                    it.list_hi = (int32_t)lay.tc_list.size();
+                    it.slot = (int32_t)slot;
+                    lay.tc_items.push_back(it);
+                    for (int32_t r = 0; r < nrows; ++r) parts.push_back({row_off + r, slot * kChunk + r});
+                    slot += kTcRows / kChunk;
+                    it.list_lo = it.list_hi;
+                }
+                lay.tc_list.push_back((int32_t)lay.tc_tiles.size());
+                lay.tc_tiles.push_back(st);
             }
         }
-        const int64_t tile1 = (int64_t)lay.tc_tiles.size();
+        it.list_hi = (int32_t)lay.tc_list.size();
+        it.slot = (int32_t)slot;
+        lay.tc_items.push_back(it);
+        for (int32_t r = 0; r < nrows; ++r) parts.push_back({row_off + r, slot * kChunk + r});
+        slot += kTcRows / kChunk;
+    };
+    for (int64_t b = 0; b < nb; ++b) {
+        if (lay.box_off[b] < 0 || !is_tc(b)) continue;
         const int32_t* ssB = &lay.slot_start[b * (kMaxSlots + 1)];
         for (int32_t r0 = 0; r0 < lay.box_n[b]; r0 += kTcRows) {
-            // target slots present in rows [r0, r0 + 128)
-            const int32_t r1 = std::min(r0 + kTcRows, lay.box_n[b]);
-            uint32_t slots = 0;
-            for (int i = 0; i < lay.box_nslot[b]; ++i)
-                if (ssB[i] < r1 && ssB[i + 1] > r0) slots |= 1u << i;
-            std::vector<int32_t> need;
-            for (int64_t t = tile0; t < tile1; ++t) {
-                bool any = false;
-                for (int i = 0; i < lay.box_nslot[b]; ++i)
-                    if (((slots >> i) & 1) && lay.tc_tiles[t].keep[i]) any = true;
-                if (any) need.push_back((int32_t)t);
-            }
-            size_t p = 0;
-            do {
-                TcItem it;
-                it.box = b;
-                it.r0 = r0;
-                it.list_lo = (int32_t)lay.tc_list.size();
-                const size_t q = std::min(p + (size_t)kTcMaxTiles, need.size());
-                lay.tc_list.insert(lay.tc_list.end(), need.begin() + p, need.begin() + q);
-                it.list_hi = (int32_t)lay.tc_list.size();
-                it.slot = (int32_t)slot;
-                for (int c = 0; c < kTcRows / kChunk; ++c)
-                    if (r0 + c * kChunk < lay.box_n[b])
-                        cs.push_back({box_chunk0[b] + (r0 + c * kChunk) / kChunk, slot + c});
-                slot += kTcRows / kChunk;
-                lay.tc_items.push_back(it);
-                p = q;
-            } while (p < need.size());
+            int32_t sst[kMaxSlots + 1];
+            for (int j = 0; j <= lay.box_nslot[b]; ++j) sst[j] = ssB[j] - r0;
+            emit(lay.box_off[b] + r0, std::min(kTcRows, lay.box_n[b] - r0), lay.box_nslot[b], sst,
+                 {Tgt{b, 0, -r0}});
         }
     }
+    for (int64_t b = 0; b < nb;) {
+        if (lay.box_off[b] < 0 || !packable(b)) { ++b; continue; }
+        // consecutive packable leaves with contiguous segments
+        std::vector<Tgt> tg;
+        int32_t sst[kMaxSlots + 1];
+        int32_t rows = 0;
+        const int64_t row_off = lay.box_off[b];
+        while (b < nb && lay.box_off[b] >= 0 && packable(b) && (int)tg.size() < kMaxSlots &&
+               rows + lay.box_n[b] <= kTcRows && lay.box_off[b] == row_off + rows) {
+            sst[tg.size()] = rows;
+            tg.push_back(Tgt{b, (int)tg.size(), rows});
+            rows += lay.box_n[b];
+            ++b;
+        }
+        sst[tg.size()] = rows;
+        emit(row_off, rows, (int)tg.size(), sst, tg);
+    }
     lay.tc_n_slots = slot;
-    to_csr(cs, lay.tc_chunk_ptr, lay.tc_chunk_slots);
+    to_csr(parts, lay.tc_part_ptr, lay.tc_part_idx);
 }
 
 }  // namespace skel

@@ -187,22 +187,17 @@ __global__ void __launch_bounds__(kUpThreads) down_kernel(const UpBox* __restric
 }
 
 // ---- reduction of near-field partial sums ------------------------------------------
+// U[e] = sum of the entry's partial sums (slot * 32 + row), in a fixed order
 template <class S>
-__global__ void reduce_kernel(const int64_t* __restrict__ chunk_box, const int32_t* __restrict__ chunk_t0,
-                              const int64_t* __restrict__ cptr, const int64_t* __restrict__ citems,
-                              const int64_t* __restrict__ box_off, const int32_t* __restrict__ box_n,
-                              const S* __restrict__ part, S* __restrict__ U, int nrhs, int64_t nchunks) {
+__global__ void reduce_kernel(const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
+                              const S* __restrict__ part, S* __restrict__ U, int nrhs, int64_t n_tot) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= nchunks * kChunk * nrhs) return;
-    const int64_t c = g / (kChunk * nrhs);
-    const int rem = (int)(g % (kChunk * nrhs));
-    const int lane = rem / nrhs, rr = rem % nrhs;
-    const int64_t b = chunk_box[c];
-    const int t = chunk_t0[c] + lane;
-    if (t >= box_n[b]) return;
+    if (g >= n_tot * nrhs) return;
+    const int64_t e = g / nrhs;
+    const int r = (int)(g % nrhs);
     S s = zero<S>();
-    for (int64_t p = cptr[c]; p < cptr[c + 1]; ++p) s += part[(citems[p] * kChunk + lane) * nrhs + rr];
-    U[(box_off[b] + t) * nrhs + rr] = s;
+    for (int64_t p = ptr[e]; p < ptr[e + 1]; ++p) s += part[idx[p] * nrhs + r];
+    U[e * nrhs + r] = s;
 }
 
 // ---- near field ------------------------------------------------------------------------

@@ -1,6 +1,7 @@
 // Tensor-core translations for many right-hand sides (FP32_TC precision).
 //
-// For a tile of 128 target rows of one box the translations are
+// For a work item of up to 128 target rows (rows of one box, or several small
+// leaves packed together) the translations are
 // U[128 x 32] += G[128 x K] Q[K x 32] over the K source entries of the box's
 // tasks, G_ij = G(x_i, y_j) evaluated on the fly, 32 sources per pipeline
 // tile. The CTA is warp-specialised:
@@ -76,10 +77,6 @@ struct TcArgs {
     const TcItem* items;
     const SrcTile* tiles;
     const int32_t* list;
-    const int64_t* box_off;
-    const int32_t* box_n;
-    const int32_t* box_nslot;
-    const int32_t* slot_start;
     const float4* X;
     const float4* Xlo;
     const float* Q;
@@ -276,18 +273,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
     } else {
         // ---------------- compute warps ----------------
         const int row = tid & 127, half = tid >> 7;
-        const int64_t B = it.box;
-        const int64_t boff = a.box_off[B];
-        const int t = it.r0 + row;
-        const bool valid = t < a.box_n[B];
-        const int32_t* ssB = a.slot_start + B * (kMaxSlots + 1);
+        const bool valid = row < it.nrows;
         int myslot = 0;
-        for (int c = 1; c < a.box_nslot[B]; ++c)
-            if (t >= ssB[c]) myslot = c;
+        for (int c = 1; c < it.nslot; ++c)
+            if (row >= it.slot_start[c]) myslot = c;
         float4 tx = make_float4(0.f, 0.f, 0.f, 0.f), tl = tx;
         if (valid) {
-            tx = a.X[boff + t];
-            tl = a.Xlo[boff + t];
+            tx = a.X[it.row_off + row];
+            tl = a.Xlo[it.row_off + row];
         }
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         // this thread's part of each charge block: right-hand side n = lane,
