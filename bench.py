@@ -319,19 +319,32 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    # roofline of the dominant kernel: translations (pair evaluations, MUFU-bound)
-    n_near = max(1, phases["launches"] // max(1, phases["n_applies"]) - 2 * (info["n_levels"] - 1) - 3)
+    # roofline of the dominant kernel: the translations (pair evaluations on
+    # the CUDA cores; MUFU rsqrt-bound), one launch per 32 right-hand sides
+    # on the tensor-core path (plus CUDA-core items for small non-leaf boxes)
+    if prec == "fp32_tc":
+        kname = "tc_near_kernel"
+        n_near = -(-nrhs // 32) * (1 + (1 if info["n_mix_items"] > 0 else 0))
+    else:
+        kname = "near_kernel"
+        n_near = 1 if nrhs == 1 else -(-nrhs // 8)
     near_ms_per_launch = phases["translations"] / (phases["n_applies"] * n_near)
     achieved = pairs / (near_ms_per_launch * 1e-3) / 1e9
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = SM_COUNT * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e9
     peaks, peaks_kind = measured_peaks()
-    roof = {"kernel": "near_kernel", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-            "frac": achieved / peak, "traffic": ncu_traffic("near_kernel", prec),
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(kname, prec),
             "peak_basis": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU rsqrt/clk x median SM clock under load "
                           f"({sm_mhz:.0f} MHz)",
             "per_launch_ms": near_ms_per_launch, "launches_per_step": n_near,
             "algorithmic_units": f"{pairs} kernel evaluations per launch (skel_info pairs_direct + pairs_far)"}
+    if prec == "fp32_tc":
+        # the same launch against the tensor pipe: 3 TF32 products of 2*32 flops per evaluation
+        tc_tflops = pairs * 2 * 32 * 3 / (near_ms_per_launch * 1e-3) / 1e12
+        tf32_peak = peaks["bf16_tflops"] * 0.5
+        roof["tensor"] = {"achieved": tc_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc_tflops / tf32_peak,
+                          "peak_basis": f"TF32 = 0.5 x {peaks_kind} bf16 burst ({peaks['bf16_tflops']} TFLOP/s)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -86,6 +86,9 @@ typedef struct {
     double  t_skel;          /* seconds: Algorithm 1 (all IDs)                         */
     double  t_upload;        /* seconds: device plan construction and upload           */
     int64_t device_bytes;    /* device memory held by the plan (all precisions)       */
+    int64_t n_tc_items;      /* FP32_TC: tensor-core work items (128 target rows each) */
+    int64_t n_tc_tiles;      /* FP32_TC: source tiles streamed by them (32 sources)    */
+    int64_t n_mix_items;     /* FP32_TC: CUDA-core items for the remaining small boxes */
 } skel_stats;
 
 /*

@@ -41,7 +41,8 @@ class SkelStats(ctypes.Structure):
                 ("pairs_direct", ctypes.c_int64), ("pairs_far", ctypes.c_int64),
                 ("n_work_items", ctypes.c_int64),
                 ("t_tree", ctypes.c_double), ("t_skel", ctypes.c_double), ("t_upload", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("n_tc_items", ctypes.c_int64),
+                ("n_tc_tiles", ctypes.c_int64), ("n_mix_items", ctypes.c_int64)]
 
 
 class SkelPlanDims(ctypes.Structure):

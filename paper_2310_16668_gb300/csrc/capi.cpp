@@ -26,6 +26,7 @@ struct skel_plan {
     bool host_only = false;
     double t_upload = 0;
     int64_t n_items = 0, pairs_direct = 0, pairs_far = 0;
+    int64_t n_tc_items = 0, n_tc_tiles = 0, n_mix_items = 0;
 };
 
 namespace {
@@ -85,6 +86,9 @@ void finalize(skel_plan* h, const skel_options* opts) {
     h->n_items = (int64_t)lay.items.size();
     h->pairs_direct = lay.pairs_direct;
     h->pairs_far = lay.pairs_far;
+    h->n_tc_items = (int64_t)lay.tc_items.size();
+    h->n_tc_tiles = (int64_t)lay.tc_list.size();
+    h->n_mix_items = (int64_t)lay.mix_items.size();
     if (!h->host_only) h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max);
     h->t_upload = now() - t0;
 }
@@ -232,6 +236,9 @@ int skel_info(skel_handle h, skel_stats* s) {
         s->t_skel = P.t_skel;
         s->t_upload = h->t_upload;
         s->device_bytes = h->dev ? h->dev->bytes : 0;
+        s->n_tc_items = h->n_tc_items;
+        s->n_tc_tiles = h->n_tc_tiles;
+        s->n_mix_items = h->n_mix_items;
     });
 }
 
