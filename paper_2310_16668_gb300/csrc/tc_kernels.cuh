@@ -15,7 +15,9 @@
 //     hi*lo + lo*hi for each of 4 K-steps) and commits them to the stage's
 //     "empty" mbarrier;
 //   * warps 0-7 (compute, two threads per target row, 16 sources each): wait
-//     "full", evaluate the kernel block, split each value into TF32 hi + lo,
+//     "full", lay the source coordinates out per axis, evaluate the kernel
+//     block two sources per paired FP32 instruction (fadd2 / fmul2 / ffma2),
+//     split each value into TF32 hi + lo,
 //     convert the charge block into the B operand (K-major, no swizzle,
 //     8 x 16-byte core matrices: 512 bytes between core matrices along K,
 //     128 bytes between groups of 8 right-hand sides), add the finished
@@ -30,8 +32,9 @@
 // of each product.
 //
 // Masks: a source that a target row's slot must skip (the regrouped
-// subtractions of Algorithm 2) gets G = 0 in that row. Every wait is
-// bounded; on timeout the kernel raises the status word, keeps the protocol
+// subtractions of Algorithm 2) gets G = 0 in that row. Waiting threads sleep
+// in the mbarrier (suspend-time hint) rather than spin, and every wait is
+// bounded by wall time (globaltimer, 2 s); on timeout the kernel raises the status word, keeps the protocol
 // going without hanging, waits (bounded) for its copies and MMAs and always
 // frees its tensor memory.
 #pragma once
@@ -54,12 +57,15 @@ constexpr int kNA = 3;                         // A-operand buffers in tensor me
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kColD = 0;                  // accumulators D0 [0,32), D1 [32,64)
 constexpr uint32_t kColA = 64;                 // A[b]: hi at 64+64b, lo at 96+64b (b < kNA)
-constexpr int kSpinLimit = 1 << 20;
+constexpr uint32_t kSleepNs = 20000;           // suspend hint of one wait attempt
+constexpr uint64_t kWaitLimitNs = 2000000000ull; // a wait gives up after 2 s
 
 struct alignas(128) TcStage {
     SrcTile tile;                              // 64 B
     float4 xh[32];                             // source coordinates (hi)
     float4 xl[32];                             // lo parts (touching-leaf tiles)
+    float sx[32], sy[32], sz[32];              // the same coordinates, one array per axis (hi)
+    float lx[32], ly[32], lz[32];              // lo parts per axis
     float qraw[32 * kTcMaxRhs];                // raw charge rows
     float bhi[32 * 32];                        // B operand, TF32 hi
     float blo[32 * 32];                        // B operand, TF32 lo
@@ -101,10 +107,29 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// the same test, letting the hardware suspend the thread (up to the hint)
+// while the phase is incomplete instead of spinning on issue slots
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(bar), "r"(parity), "r"(kSleepNs) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait: gives up after kWaitLimitNs of wall time
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < kSpinLimit; ++it)
-        if (mbar_try(bar, parity)) return true;
-    return false;
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_sleep(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -164,28 +189,47 @@ template <int KIND> __device__ __forceinline__ float tc_green(float r2) {
     return KIND == 0 ? logf(r2) : rsqrtf(r2);
 }
 
+// TF32 hi part of a finite float, rounded to nearest (ties away from zero):
+// the same value as cvt.rna.tf32.f32 for finite inputs, in two integer ops
+__device__ __forceinline__ uint32_t tf32_hi(float g) { return (__float_as_uint(g) + 0x1000u) & 0xFFFFE000u; }
+
+// 16 sources (j0 .. j0+15) against this thread's target, two sources per
+// paired FP32 instruction. nt / nl hold the negated target coordinates.
 template <int KIND, bool ADJ, bool MASKED>
-__device__ __forceinline__ void tc_eval16(const float4* sh, const float4* sl, float4 tx, float4 tl, uint32_t keep,
+__device__ __forceinline__ void tc_eval16(const TcStage& st, int j0, float4 nt, float4 nl, uint32_t keep,
                                           uint32_t* ghi, uint32_t* glo) {
+    const float2 ntx = make_float2(nt.x, nt.x), nty = make_float2(nt.y, nt.y), ntz = make_float2(nt.z, nt.z);
+    float2 nlx, nly, nlz;
+    if (ADJ) nlx = make_float2(nl.x, nl.x), nly = make_float2(nl.y, nl.y), nlz = make_float2(nl.z, nl.z);
 #pragma unroll
-    for (int jj = 0; jj < 16; ++jj) {
-        const float4 s = sh[jj];
-        float dx = tx.x - s.x, dy = tx.y - s.y, dz = tx.z - s.z;
+    for (int p = 0; p < 8; ++p) {
+        const int j = j0 + 2 * p;
+        float2 dx = __fadd2_rn(*reinterpret_cast<const float2*>(&st.sx[j]), ntx);
+        float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(&st.sy[j]), nty);
+        float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(&st.sz[j]), ntz);
         if (ADJ) {
-            const float4 l = sl[jj];
-            dx += tl.x - l.x;
-            dy += tl.y - l.y;
-            dz += tl.z - l.z;
+            dx = __fadd2_rn(dx, __fadd2_rn(*reinterpret_cast<const float2*>(&st.lx[j]), nlx));
+            dy = __fadd2_rn(dy, __fadd2_rn(*reinterpret_cast<const float2*>(&st.ly[j]), nly));
+            dz = __fadd2_rn(dz, __fadd2_rn(*reinterpret_cast<const float2*>(&st.lz[j]), nlz));
         }
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float g = tc_green<KIND>(r2);
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        float g0 = tc_green<KIND>(r2.x), g1 = tc_green<KIND>(r2.y);
         if (MASKED || ADJ) {
-            const bool on = ((keep >> jj) & 1u) && (!ADJ || r2 > 0.f);
-            g = on ? g : 0.f;
+            const bool on0 = ((keep >> (2 * p)) & 1u) && (!ADJ || r2.x > 0.f);
+            const bool on1 = ((keep >> (2 * p + 1)) & 1u) && (!ADJ || r2.y > 0.f);
+            g0 = on0 ? g0 : 0.f;
+            g1 = on1 ? g1 : 0.f;
         }
-        const uint32_t h = to_tf32(g);
-        ghi[jj] = h;
-        glo[jj] = __float_as_uint(g - __uint_as_float(h));   // the tensor core truncates it to TF32
+        const uint32_t h0 = tf32_hi(g0), h1 = tf32_hi(g1);
+        // lo = g - hi (exact); the tensor core truncates it to TF32
+        const float2 lo = __ffma2_rn(make_float2(__uint_as_float(h0), __uint_as_float(h1)), make_float2(-1.f, -1.f),
+                                     make_float2(g0, g1));
+        ghi[2 * p] = h0;
+        ghi[2 * p + 1] = h1;
+        glo[2 * p] = __float_as_uint(lo.x);
+        glo[2 * p + 1] = __float_as_uint(lo.y);
     }
 }
 
@@ -194,8 +238,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcShared& S = *reinterpret_cast<TcShared*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const TcItem it = a.items[blockIdx.x];
-    const int ntile = it.list_hi - it.list_lo;
+    const TcItem* itp = a.items + blockIdx.x;
+    const int64_t row_off = itp->row_off;
+    const int nrows = itp->nrows, nslot = itp->nslot, list_lo = itp->list_lo, out_slot = itp->slot;
+    const int ntile = itp->list_hi - list_lo;
 
     if (tid == 0) {
         S.slots = 0;
@@ -220,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
     if (warp == kTcCompute / 32) {
         // ---------------- producer (one thread): bulk copies up to kNS tiles ahead ----------------
         if (lane == 0) {
-            const SrcTile* gnext = ntile > 0 ? a.tiles + a.list[it.list_lo] : nullptr;
+            const SrcTile* gnext = ntile > 0 ? a.tiles + a.list[list_lo] : nullptr;
             int64_t n_start = gnext ? gnext->start : 0;
             int n_cnt = gnext ? gnext->cnt : 0, n_flags = gnext ? gnext->flags : 0;
             for (int t = 0; t < ntile; ++t) {
@@ -230,7 +276,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                 const int cnt = n_cnt;
                 const bool adj = (n_flags & TASK_ADJ) != 0;
                 if (t + 1 < ntile) {                         // prefetch the next descriptor
-                    gnext = a.tiles + a.list[it.list_lo + t + 1];
+                    gnext = a.tiles + a.list[list_lo + t + 1];
                     n_start = gnext->start;
                     n_cnt = gnext->cnt;
                     n_flags = gnext->flags;
@@ -273,15 +319,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
     } else {
         // ---------------- compute warps ----------------
         const int row = tid & 127, half = tid >> 7;
-        const bool valid = row < it.nrows;
+        const bool valid = row < nrows;
         int myslot = 0;
-        for (int c = 1; c < it.nslot; ++c)
-            if (row >= it.slot_start[c]) myslot = c;
+        for (int c = 1; c < nslot; ++c)
+            if (row >= itp->slot_start[c]) myslot = c;
         float4 tx = make_float4(0.f, 0.f, 0.f, 0.f), tl = tx;
         if (valid) {
-            tx = a.X[it.row_off + row];
-            tl = a.Xlo[it.row_off + row];
+            tx = a.X[row_off + row];
+            tl = a.Xlo[row_off + row];
         }
+        const float4 nt = make_float4(-tx.x, -tx.y, -tx.z, 0.f), nl = make_float4(-tl.x, -tl.y, -tl.z, 0.f);
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         // this thread's part of each charge block: right-hand side n = lane,
         // sources j = 4*warp .. 4*warp+3 (one 16-byte core-matrix row)
@@ -310,6 +357,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             const int cnt = st.tile.cnt;
             const bool adj = (st.tile.flags & TASK_ADJ) != 0;
             const uint32_t keep = valid ? (st.tile.keep[myslot] >> (16 * half)) & 0xFFFFu : 0u;
+            // coordinates per axis (sources past cnt are never kept)
+            if (tid < 96) {
+                const float4 v = st.xh[tid & 31];
+                const int c = tid >> 5;
+                (c == 0 ? st.sx : c == 1 ? st.sy : st.sz)[tid & 31] = c == 0 ? v.x : c == 1 ? v.y : v.z;
+            } else if (adj && tid < 192) {
+                const float4 v = st.xl[tid & 31];
+                const int c = (tid >> 5) - 3;
+                (c == 0 ? st.lx : c == 1 ? st.ly : st.lz)[tid & 31] = c == 0 ? v.x : c == 1 ? v.y : v.z;
+            }
+            asm volatile("bar.sync 1, %0;" :: "r"(kTcCompute) : "memory");   // compute warps only
             // B operand of this stage (sources beyond cnt are zero)
             {
                 float v[4];
@@ -326,17 +384,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             }
             if (u >= 2) drain(u - 2);                          // frees accumulator (u & 1)
             uint32_t ghi[16], glo[16];
-            const float4* sh = st.xh + 16 * half;
-            const float4* sl = st.xl + 16 * half;
+            const int j0 = 16 * half;
             if (__all_sync(0xffffffffu, keep == 0)) {
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) ghi[jj] = glo[jj] = 0u;
             } else if (adj) {
-                tc_eval16<KIND, true, true>(sh, sl, tx, tl, keep, ghi, glo);
+                tc_eval16<KIND, true, true>(st, j0, nt, nl, keep, ghi, glo);
             } else if (__all_sync(0xffffffffu, keep == 0xFFFFu)) {
-                tc_eval16<KIND, false, false>(sh, sl, tx, tl, keep, ghi, glo);
+                tc_eval16<KIND, false, false>(st, j0, nt, nl, keep, ghi, glo);
             } else {
-                tc_eval16<KIND, false, true>(sh, sl, tx, tl, keep, ghi, glo);
+                tc_eval16<KIND, false, true>(st, j0, nt, nl, keep, ghi, glo);
             }
             // A buffer u % kNA was last read by MMA(u - kNA), complete since drain(u - 2)
             const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + 16u * half;
@@ -350,7 +407,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         for (int m = (ntile >= 2 ? ntile - 2 : 0); m < ntile; ++m) drain(m);
         if (half == 0 && valid) {
             const float scale = (float)green_scale<KIND>();
-            const int64_t base = ((int64_t)(it.slot + (row >> 5)) * kChunk + (row & 31)) * a.nrhs;
+            const int64_t base = ((int64_t)(out_slot + (row >> 5)) * kChunk + (row & 31)) * a.nrhs;
 #pragma unroll
             for (int c = 0; c < kTcN; ++c)
                 if (a.r0 + c < a.nrhs) a.partial[base + a.r0 + c] = scale * acc[c];
