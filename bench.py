@@ -154,6 +154,24 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def replica_seed(base: int, rank: int) -> int:
+    """Seed of rank `rank`'s independent replica (its own point set)."""
+    return base + 17 * rank
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest `value` over all ranks (the job is as slow as its slowest rank)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(n: int, nrhs: int, world: int, ms_step: float) -> float:
+    """Mpts*RHS/s of the whole job: every rank applies its own n x nrhs problem per step."""
+    return n * nrhs * world / (ms_step * 1e-3) / 1e6
+
+
 def oracle_direct_sample(x, q0, targets):
     """The oracle's FP64 direct sum at `targets` (cpu_baseline leg)."""
     from oracle import direct
@@ -218,7 +236,7 @@ def run_ours(args):
     n = args.n or wl.n
     tol = args.tol or wl.tol
     nrhs = args.nrhs
-    seed = wl.seed + 17 * rank          # independent replica per rank
+    seed = replica_seed(wl.seed, rank)  # independent replica per rank
     x = W.points_uniform(n, 3, seed)
     q = W.charges_normal(n, nrhs, seed + 1000)
     threads = max(1, (os.cpu_count() or 1) // max(1, int(os.environ.get("LOCAL_WORLD_SIZE", world))))
@@ -259,11 +277,9 @@ def run_ours(args):
     fmm.set_profiling(0)
     if world > 1:
         dist.barrier()
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+        ms_total = max_over_ranks(ms_total, dist, dev)
     ms_step = ms_total / args.steps
-    value = n * nrhs * world / (ms_step * 1e-3) / 1e6
+    value = whole_job_value(n, nrhs, world, ms_step)
 
     # errors against the oracle's direct sum on sampled targets (RHS 0)
     u_main = uc[0].double().cpu().numpy()
@@ -319,22 +335,27 @@ def run_ours(args):
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / k
         nb = qh.numel() * qh.element_size()
-        e2e = {"value": n * nrhs * world / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": nb,
+        if world > 1:
+            dt = max_over_ranks(dt, dist, dev)
+        e2e = {"value": whole_job_value(n, nrhs, world, dt * 1e3), "unit": UNIT, "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb, "ms_per_step": dt * 1e3}
 
     if rank != 0:
         return 0
-    # roofline of the dominant kernel: the translations (pair evaluations on
-    # the CUDA cores; MUFU rsqrt-bound), one launch per 32 right-hand sides
-    # on the tensor-core path (plus CUDA-core items for small non-leaf boxes)
+    # roofline of the dominant kernel, the main translation kernel (kernel
+    # evaluations; MUFU rsqrt-bound): on the tensor-core path one launch per
+    # 32 right-hand sides over the pairs of the tensor-core items, timed by
+    # the plan's own events on the launching stream (the CUDA-core launch for
+    # the small non-leaf boxes is outside that span)
     if prec == "fp32_tc":
-        kname = "tc_near_kernel"
-        n_near = -(-nrhs // 32) * (1 + (1 if info["n_mix_items"] > 0 else 0))
+        kname, units = "tc_near_kernel", info["pairs_tc"]
+        unit_note = "skel_info pairs_tc: kept kernel evaluations of the tensor-core items"
     else:
-        kname = "near_kernel"
-        n_near = 1 if nrhs == 1 else -(-nrhs // 8)
-    near_ms_per_launch = phases["translations"] / (phases["n_applies"] * n_near)
-    achieved = pairs / (near_ms_per_launch * 1e-3) / 1e9
+        kname, units = "near_kernel", pairs
+        unit_note = "skel_info pairs_direct + pairs_far"
+    n_near = phases["main_launches"] / phases["n_applies"]
+    near_ms_per_launch = phases["main_near"] / phases["main_launches"]
+    achieved = units / (near_ms_per_launch * 1e-3) / 1e9
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = SM_COUNT * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e9
     peaks, peaks_kind = measured_peaks()
@@ -343,12 +364,16 @@ def run_ours(args):
             "peak_basis": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU rsqrt/clk x median SM clock under load "
                           f"({sm_mhz:.0f} MHz)",
             "per_launch_ms": near_ms_per_launch, "launches_per_step": n_near,
-            "algorithmic_units": f"{pairs} kernel evaluations per launch (skel_info pairs_direct + pairs_far)"}
+            "algorithmic_units": f"{units} kernel evaluations per launch ({unit_note})"}
     if prec == "fp32_tc":
-        # the same launch against the tensor pipe: 3 TF32 products of 2*32 flops per evaluation
-        tc_tflops = pairs * 2 * 32 * 3 / (near_ms_per_launch * 1e-3) / 1e12
+        # the same launch against the tensor pipe: algorithmic 2 flops per
+        # evaluation and right-hand side (32 per launch); the pipe issues 3
+        # TF32 products (hi.hi + hi.lo + lo.hi) over full 128 x 32 tiles
+        tc_tflops = units * 2 * 32 / (near_ms_per_launch * 1e-3) / 1e12
+        issued = info["n_tc_tiles"] * 128 * 32 * 32 * 2 * 3 / (near_ms_per_launch * 1e-3) / 1e12
         tf32_peak = peaks["bf16_tflops"] * 0.5
         roof["tensor"] = {"achieved": tc_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc_tflops / tf32_peak,
+                          "issued_tflops": issued,
                           "peak_basis": f"TF32 = 0.5 x {peaks_kind} bf16 burst ({peaks['bf16_tflops']} TFLOP/s)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -363,7 +388,7 @@ def run_ours(args):
         "relerr": out.get("relerr"),
         "comparator_fp64": fp64,
         "phases_ms_per_step": {k: v / phases["n_applies"] for k, v in phases.items()
-                               if k not in ("launches", "n_applies")},
+                               if k not in ("launches", "n_applies", "main_launches")},
         "roofline": roof,
         "peaks_source": peaks_kind,
         "cpu_baseline": out.get("cpu_baseline"),

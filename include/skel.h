@@ -89,6 +89,8 @@ typedef struct {
     int64_t n_tc_items;      /* FP32_TC: tensor-core work items (128 target rows each) */
     int64_t n_tc_tiles;      /* FP32_TC: source tiles streamed by them (32 sources)    */
     int64_t n_mix_items;     /* FP32_TC: CUDA-core items for the remaining small boxes */
+    int64_t pairs_tc;        /* FP32_TC: kernel evaluations (of pairs_direct + pairs_far)
+                                done by the tensor-core items, per 32 right-hand sides */
 } skel_stats;
 
 /*
@@ -222,16 +224,21 @@ int skel_neighbors_export(skel_handle h, int which, int64_t* ptr, int64_t* list)
  * skel_set_profiling(h, m) makes each of the next m applies record CUDA
  * events on its stream at the boundaries of its six phases: permutation in,
  * upward pass, translations (the near-field kernel), reduction of partial
- * sums, downward pass, permutation out (seven event records per apply and
- * nothing else; the events are created here, not in the apply). m = 0 turns
- * it off. skel_last_timings waits for the captured applies and returns each
- * phase's duration summed over them, in milliseconds, with the number of
- * kernels they launched and the number of applies captured.
+ * sums, downward pass, permutation out, plus one where the main translation
+ * kernel starts (eight event records per apply and nothing else; the events
+ * are created here, not in the apply). m = 0 turns it off. skel_last_timings
+ * waits for the captured applies and returns each phase's duration summed
+ * over them, in milliseconds, with the number of kernels they launched and
+ * the number of applies captured. An FP32_TC apply of more than 64
+ * right-hand sides runs in chunks of 64, each captured as one apply.
  */
 typedef struct {
     double ms[6];          /* permute_in, upward, translations, reduce, downward, permute_out */
     int    launches;       /* kernels launched by the captured applies                        */
     int    n_applies;      /* applies captured                                                */
+    double ms_main;        /* the part of ms[2] spent in the main translation kernel: the
+                              tensor-core launches of FP32_TC, else the whole phase          */
+    int    main_launches;  /* launches of that kernel                                         */
 } skel_timings;
 
 /* skel_set_profiling — capture the next max_applies applies (0 = off, <= 100000). */

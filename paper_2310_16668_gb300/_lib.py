@@ -42,7 +42,8 @@ class SkelStats(ctypes.Structure):
                 ("n_work_items", ctypes.c_int64),
                 ("t_tree", ctypes.c_double), ("t_skel", ctypes.c_double), ("t_upload", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("n_tc_items", ctypes.c_int64),
-                ("n_tc_tiles", ctypes.c_int64), ("n_mix_items", ctypes.c_int64)]
+                ("n_tc_tiles", ctypes.c_int64), ("n_mix_items", ctypes.c_int64),
+                ("pairs_tc", ctypes.c_int64)]
 
 
 class SkelPlanDims(ctypes.Structure):
@@ -52,7 +53,8 @@ class SkelPlanDims(ctypes.Structure):
 
 
 class SkelTimings(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int), ("n_applies", ctypes.c_int)]
+    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int), ("n_applies", ctypes.c_int),
+                ("ms_main", ctypes.c_double), ("main_launches", ctypes.c_int)]
 
 
 class SkelError(RuntimeError):

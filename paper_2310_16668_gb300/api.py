@@ -122,12 +122,15 @@ class SkelFMM:
         check(self._lib.skel_set_profiling(self._h, int(max_applies)))
 
     def last_timings(self) -> dict:
-        """Phase durations (ms, summed over the captured applies), launches, applies."""
+        """Phase durations (ms, summed over the captured applies), launches, applies;
+        ``main_near`` / ``main_launches``: the main translation kernel inside ``translations``."""
         t = SkelTimings()
         check(self._lib.skel_last_timings(self._h, ctypes.byref(t)))
         out = {p: t.ms[i] for i, p in enumerate(PHASES)}
         out["launches"] = t.launches
         out["n_applies"] = t.n_applies
+        out["main_near"] = t.ms_main
+        out["main_launches"] = t.main_launches
         return out
 
     def device_status(self) -> None:

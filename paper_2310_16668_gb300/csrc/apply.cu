@@ -119,34 +119,48 @@ void free_buffers(DeviceBuffers* b) {
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
-// right-hand sides per thread of the up / down GEMMs
-template <class S> constexpr int rg_of() { return sizeof(S) == 4 ? 8 : sizeof(S) == 8 ? 4 : 2; }
+// one level of the upward or downward pass
+template <class S>
+void up_down(bool down, const DevicePlan* dp, int l, const S* T, S* X, int nrhs, bool conj_op, cudaStream_t st) {
+    const int64_t b0 = dp->up_level_ptr[l], b1 = dp->up_level_ptr[l + 1];
+    const int nout = down ? dp->up_level_maxr[l] : dp->up_level_maxk[l];
+    const dim3 grid((unsigned)(b1 - b0), std::max(1u, ceil_div(nout, kGT)), ceil_div(nrhs, kGT));
+    if (down) updown_kernel<S, true><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
+    else updown_kernel<S, false><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
+}
 
-template <class S, int RG>
-void launch_up_down(bool down, unsigned grid, const UpBox* up, const int32_t* pos, const S* T, S* X, int nrhs,
-                    bool transpose, cudaStream_t st) {
-    const size_t smem = (size_t)kJT * nrhs * sizeof(S);
-    if (down) {
-        if (smem > 48 * 1024)
-            CUDA_CHECK(cudaFuncSetAttribute(down_kernel<S, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        down_kernel<S, RG><<<grid, kUpThreads, smem, st>>>(up, pos, T, X, nrhs, transpose);
+template <class S>
+void reduce(const int64_t* ptr, const int64_t* idx, const S* part, S* U, int nrhs, int64_t n_tot, cudaStream_t st) {
+    constexpr int W = 16 / sizeof(S);
+    if (W > 1 && nrhs % W == 0) {
+        const int64_t n = n_tot * (nrhs / W);
+        reduce_kernel<S, W><<<ceil_div(n, 256), 256, 0, st>>>(ptr, idx, part, U, nrhs, n_tot);
     } else {
-        if (smem > 48 * 1024)
-            CUDA_CHECK(cudaFuncSetAttribute(up_kernel<S, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        up_kernel<S, RG><<<grid, kUpThreads, smem, st>>>(up, pos, T, X, nrhs, transpose);
+        const int64_t n = n_tot * nrhs;
+        reduce_kernel<S, 1><<<ceil_div(n, 256), 256, 0, st>>>(ptr, idx, part, U, nrhs, n_tot);
     }
 }
 
 template <class S>
-void up_down(bool down, unsigned grid, const UpBox* up, const int32_t* pos, const S* T, S* X, int nrhs,
-             bool transpose, cudaStream_t st) {
-    if (nrhs >= rg_of<S>()) launch_up_down<S, rg_of<S>()>(down, grid, up, pos, T, X, nrhs, transpose, st);
-    else launch_up_down<S, 1>(down, grid, up, pos, T, X, nrhs, transpose, st);
+void permute(bool out, const DevicePlan* dp, const S* src, S* dst, int nrhs, cudaStream_t st) {
+    const int64_t N = dp->N;
+    if (nrhs >= 8) {
+        const dim3 grid(ceil_div(N, kPermTile), ceil_div(nrhs, kPermTile));
+        if (out) permute_out<S><<<grid, kPermThreads, 0, st>>>(dp->eop, src, dst, N, nrhs);
+        else permute_in<S><<<grid, kPermThreads, 0, st>>>(dp->eop, src, dst, N, nrhs);
+    } else {
+        const int64_t n = N * nrhs;
+        if (out) permute_out_narrow<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->eop, src, dst, N, nrhs);
+        else permute_in_narrow<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->eop, src, dst, N, nrhs);
+    }
 }
+
+constexpr int kProfEvents = 8;   // 7 phase boundaries + the start of the main translation kernel
+constexpr int kMainEvent = 7;
 
 inline void mark(DevicePlan* dp, int i, cudaStream_t st) {
     if (dp->prof_count < dp->prof_cap)
-        CUDA_CHECK(cudaEventRecord((cudaEvent_t)dp->events[dp->prof_count * 7 + i], st));
+        CUDA_CHECK(cudaEventRecord((cudaEvent_t)dp->events[dp->prof_count * kProfEvents + i], st));
 }
 
 template <class Real, bool CPLX>
@@ -173,13 +187,14 @@ NearArgs<Real, CPLX> near_args(DevicePlan* dp, DeviceBuffers* b, const WorkItem*
 // tensor-core translations (real kernels, FP32): CUDA-core items for the
 // small boxes, then one tensor-core pass per 32 right-hand sides
 template <class Real, bool CPLX>
-int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st) {
+int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_launches) {
     int launches = 0;
     if (dp->n_mix > 0) {
         auto a = near_args<Real, CPLX>(dp, b, dp->mix_items, dp->n_mix, nrhs);
         launches += launch_near<Real, CPLX>(dp->kind, a, nrhs, ceil_div(dp->n_mix, kNearWarps), st);
         CUDA_CHECK(cudaGetLastError());
     }
+    mark(dp, kMainEvent, st);
     TcArgs t;
     t.items = dp->tc_items;
     t.tiles = dp->tc_tiles;
@@ -199,7 +214,8 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st) {
             CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
         attr_set[kidx] = true;
     }
-    for (int r0 = 0; r0 < nrhs; r0 += kTcN, ++launches) {
+    tc_launches = 0;
+    for (int r0 = 0; r0 < nrhs; r0 += kTcN, ++launches, ++tc_launches) {
         t.r0 = r0;
         if (kidx == 0) tc_near_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
         else tc_near_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
@@ -218,58 +234,54 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
     const S* T = (const S*)b->T;
     const S* Tt = (const S*)b->Tt;
     S* part = (S*)b->partial;
-    const int64_t N = dp->N;
     // 1. permute in
     mark(dp, 0, st);
     {
         ++launches;
-        const int64_t n = N * nrhs;
-        permute_in<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->perm_entry, dp->perm_point, (const S*)q,
-                                                        Q, N, nrhs);
+        permute<S>(false, dp, (const S*)q, Q, nrhs, st);
         CUDA_CHECK(cudaGetLastError());
     }
     // 2. upward pass, levels L .. 2
     mark(dp, 1, st);
     for (int l = dp->L; l >= 2; --l) {
-        const int64_t b0 = dp->up_level_ptr[l], b1 = dp->up_level_ptr[l + 1];
-        if (b1 > b0) {
+        if (dp->up_level_ptr[l + 1] > dp->up_level_ptr[l]) {
             ++launches;
-            up_down<S>(false, (unsigned)(b1 - b0), dp->up + b0, dp->pos, T, Q, nrhs, transpose, st);
+            up_down<S>(false, dp, l, T, Q, nrhs, transpose, st);
             CUDA_CHECK(cudaGetLastError());
         }
     }
     // 3. near field
     mark(dp, 2, st);
     const bool tc = use_tc && !CPLX && sizeof(Real) == 4 && dp->n_tc > 0;
+    int main_launches = 0;
     if (tc) {
-        launches += run_tc<Real, CPLX>(dp, b, nrhs, st);
+        launches += run_tc<Real, CPLX>(dp, b, nrhs, st, main_launches);
         mark(dp, 3, st);
         ++launches;
-        const int64_t n = dp->n_tot * nrhs;
-        reduce_kernel<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->tc_part_ptr, dp->tc_part_idx, part, U, nrhs,
-                                                           dp->n_tot);
+        reduce<S>(dp->tc_part_ptr, dp->tc_part_idx, part, U, nrhs, dp->n_tot, st);
         CUDA_CHECK(cudaGetLastError());
     } else if (dp->n_items > 0) {
         auto a = near_args<Real, CPLX>(dp, b, dp->items, dp->n_items, nrhs);
         const unsigned grid = ceil_div(dp->n_items, kNearWarps);
-        launches += launch_near<Real, CPLX>(dp->kind, a, nrhs, grid, st);
+        mark(dp, kMainEvent, st);
+        main_launches = launch_near<Real, CPLX>(dp->kind, a, nrhs, grid, st);
+        launches += main_launches;
         CUDA_CHECK(cudaGetLastError());
         mark(dp, 3, st);
         ++launches;
-        const int64_t n = dp->n_tot * nrhs;
-        reduce_kernel<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->part_ptr, dp->part_idx, part, U, nrhs, dp->n_tot);
+        reduce<S>(dp->part_ptr, dp->part_idx, part, U, nrhs, dp->n_tot, st);
         CUDA_CHECK(cudaGetLastError());
     }
     else {
+        mark(dp, kMainEvent, st);
         mark(dp, 3, st);
     }
     // 4. downward pass, levels 2 .. L
     mark(dp, 4, st);
     for (int l = 2; l <= dp->L; ++l) {
-        const int64_t b0 = dp->up_level_ptr[l], b1 = dp->up_level_ptr[l + 1];
-        if (b1 > b0) {
+        if (dp->up_level_ptr[l + 1] > dp->up_level_ptr[l]) {
             ++launches;
-            up_down<S>(true, (unsigned)(b1 - b0), dp->up + b0, dp->pos, Tt, U, nrhs, transpose, st);
+            up_down<S>(true, dp, l, Tt, U, nrhs, !transpose, st);
             CUDA_CHECK(cudaGetLastError());
         }
     }
@@ -277,12 +289,14 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
     mark(dp, 5, st);
     {
         ++launches;
-        const int64_t n = N * nrhs;
-        permute_out<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->perm_entry, dp->perm_point, U, (S*)u, N, nrhs);
+        permute<S>(true, dp, U, (S*)u, nrhs, st);
         CUDA_CHECK(cudaGetLastError());
     }
     mark(dp, 6, st);
-    if (dp->prof_count < dp->prof_cap) dp->prof_launches[dp->prof_count++] = launches;
+    if (dp->prof_count < dp->prof_cap) {
+        dp->prof_launches[dp->prof_count] = launches;
+        dp->prof_main_launches[dp->prof_count++] = main_launches;
+    }
 }
 
 }  // namespace
@@ -305,10 +319,23 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
         dp->box_nslot = upload(lay.box_nslot, dp->bytes);
         dp->slot_start = upload(lay.slot_start, dp->bytes);
         dp->pos = upload(lay.pos, dp->bytes);
-        dp->perm_entry = upload(lay.perm_entry, dp->bytes);
-        dp->perm_point = upload(lay.perm_point, dp->bytes);
+        {
+            std::vector<int64_t> eop(dp->N, -1);
+            for (size_t i = 0; i < lay.perm_point.size(); ++i) eop[lay.perm_point[i]] = lay.perm_entry[i];
+            for (int64_t v : eop)
+                if (v < 0) throw Error(-5, "a point has no leaf entry");
+            dp->eop = upload(eop, dp->bytes);
+        }
         dp->up = upload(lay.up, dp->bytes);
         dp->up_level_ptr = lay.up_level_ptr;
+        const int nl = (int)lay.up_level_ptr.size() - 1;
+        dp->up_level_maxk.assign(std::max(nl, 0), 0);
+        dp->up_level_maxr.assign(std::max(nl, 0), 0);
+        for (int l = 0; l < nl; ++l)
+            for (int64_t i = lay.up_level_ptr[l]; i < lay.up_level_ptr[l + 1]; ++i) {
+                dp->up_level_maxk[l] = std::max(dp->up_level_maxk[l], lay.up[i].k);
+                dp->up_level_maxr[l] = std::max(dp->up_level_maxr[l], lay.up[i].n - lay.up[i].k);
+            }
         dp->task_src = upload(lay.task_src, dp->bytes);
         dp->task_mask = upload(lay.task_mask, dp->bytes);
         dp->task_flags = upload(lay.task_flags, dp->bytes);
@@ -344,8 +371,7 @@ void device_plan_destroy(DevicePlan* dp) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(dp->device);
-    void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->perm_entry,
-                    dp->perm_point, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
+    void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
                     dp->tc_items, dp->tc_list, dp->tc_part_ptr, dp->tc_part_idx, dp->status};
     for (void* p : ptrs) cudaFree(p);
@@ -359,7 +385,7 @@ void device_plan_destroy(DevicePlan* dp) {
 
 void device_set_profiling(DevicePlan* dp, int max_applies) {
     if (max_applies < 0 || max_applies > 100000) throw Error(-1, "max_applies out of range");
-    while ((int)dp->events.size() < 7 * max_applies) {
+    while ((int)dp->events.size() < kProfEvents * max_applies) {
         cudaEvent_t e;
         CUDA_CHECK(cudaEventCreate(&e));
         dp->events.push_back((void*)e);
@@ -367,6 +393,7 @@ void device_set_profiling(DevicePlan* dp, int max_applies) {
     dp->prof_cap = max_applies;
     dp->prof_count = 0;
     dp->prof_launches.assign(max_applies, 0);
+    dp->prof_main_launches.assign(max_applies, 0);
 }
 
 int device_status(DevicePlan* dp) {
@@ -377,19 +404,26 @@ int device_status(DevicePlan* dp) {
     return v;
 }
 
-void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_applies) {
+void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_applies, double* ms_main,
+                         int* main_launches) {
     if (dp->prof_cap == 0) throw Error(-6, "profiling is not enabled");
     for (int i = 0; i < 6; ++i) ms6[i] = 0;
     *launches = 0;
+    *ms_main = 0;
+    *main_launches = 0;
     for (int a = 0; a < dp->prof_count; ++a) {
-        CUDA_CHECK(cudaEventSynchronize((cudaEvent_t)dp->events[a * 7 + 6]));
+        cudaEvent_t* ev = (cudaEvent_t*)&dp->events[a * kProfEvents];
+        CUDA_CHECK(cudaEventSynchronize(ev[6]));
         for (int i = 0; i < 6; ++i) {
             float ms = 0;
-            CUDA_CHECK(cudaEventElapsedTime(&ms, (cudaEvent_t)dp->events[a * 7 + i],
-                                            (cudaEvent_t)dp->events[a * 7 + i + 1]));
+            CUDA_CHECK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
             ms6[i] += ms;
         }
+        float ms = 0;
+        CUDA_CHECK(cudaEventElapsedTime(&ms, ev[kMainEvent], ev[3]));
+        *ms_main += ms;
         *launches += dp->prof_launches[a];
+        *main_launches += dp->prof_main_launches[a];
     }
     *n_applies = dp->prof_count;
 }

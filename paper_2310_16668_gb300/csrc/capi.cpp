@@ -26,7 +26,7 @@ struct skel_plan {
     bool host_only = false;
     double t_upload = 0;
     int64_t n_items = 0, pairs_direct = 0, pairs_far = 0;
-    int64_t n_tc_items = 0, n_tc_tiles = 0, n_mix_items = 0;
+    int64_t n_tc_items = 0, n_tc_tiles = 0, n_mix_items = 0, pairs_tc = 0;
 };
 
 namespace {
@@ -89,6 +89,7 @@ void finalize(skel_plan* h, const skel_options* opts) {
     h->n_tc_items = (int64_t)lay.tc_items.size();
     h->n_tc_tiles = (int64_t)lay.tc_list.size();
     h->n_mix_items = (int64_t)lay.mix_items.size();
+    h->pairs_tc = lay.pairs_tc;
     if (!h->host_only) h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max);
     h->t_upload = now() - t0;
 }
@@ -239,6 +240,7 @@ int skel_info(skel_handle h, skel_stats* s) {
         s->n_tc_items = h->n_tc_items;
         s->n_tc_tiles = h->n_tc_tiles;
         s->n_mix_items = h->n_mix_items;
+        s->pairs_tc = h->pairs_tc;
     });
 }
 
@@ -460,7 +462,7 @@ int skel_last_timings(skel_handle h, skel_timings* t) {
     return guarded([&] {
         if (!h || !t) throw Error(SKEL_ERR_ARG, "NULL argument");
         if (!h->dev) throw Error(SKEL_ERR_STATE, "plan was built host-only");
-        skel::device_last_timings(h->dev, t->ms, &t->launches, &t->n_applies);
+        skel::device_last_timings(h->dev, t->ms, &t->launches, &t->n_applies, &t->ms_main, &t->main_launches);
     });
 }
 

@@ -25,10 +25,10 @@ struct DevicePlan {
     int32_t* box_nslot = nullptr;
     int32_t* slot_start = nullptr;
     int32_t* pos = nullptr;
-    int64_t* perm_entry = nullptr;
-    int64_t* perm_point = nullptr;
+    int64_t* eop = nullptr;                // user point -> its leaf entry
     UpBox* up = nullptr;
     std::vector<int64_t> up_level_ptr;     // host copy
+    std::vector<int32_t> up_level_maxk, up_level_maxr;   // per level: largest k, |I| - k
     int64_t* task_src = nullptr;
     uint64_t* task_mask = nullptr;
     int32_t* task_flags = nullptr;
@@ -50,10 +50,11 @@ struct DevicePlan {
     DeviceBuffers* p64 = nullptr;
     DeviceBuffers* p32 = nullptr;
     // optional per-phase CUDA events (permute_in, up, near, reduce, down,
-    // permute_out): 7 events for each of up to prof_cap applies
+    // permute_out, end; then the start of the main translation kernel):
+    // kProfEvents events for each of up to prof_cap applies
     std::vector<void*> events;
     int prof_cap = 0, prof_count = 0;
-    std::vector<int> prof_launches;
+    std::vector<int> prof_launches, prof_main_launches;
     // host-pointer staging (allocated on first host-pointer call)
     void* stage_in = nullptr;
     void* stage_out = nullptr;
@@ -69,7 +70,8 @@ void device_set_profiling(DevicePlan* dp, int max_applies);
 // read and clear the device status word (synchronizes the device)
 int device_status(DevicePlan* dp);
 // summed milliseconds of the 6 phases over the captured applies (waits for them)
-void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_applies);
+void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_applies, double* ms_main,
+                         int* main_launches);
 
 // Algorithm 2 on `stream`. q, u: device pointers in user order (n x nrhs,
 // each right-hand side contiguous). transpose: run with conj(T).

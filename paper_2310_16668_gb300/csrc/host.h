@@ -159,6 +159,7 @@ struct Layout {
     std::vector<int64_t> tc_part_ptr, tc_part_idx;
     int64_t tc_n_slots = 0;
     int64_t pairs_direct = 0, pairs_far = 0;
+    int64_t pairs_tc = 0;   // kept evaluations inside tensor-core items
 };
 
 void build_layout(const Plan& p, Layout& lay);

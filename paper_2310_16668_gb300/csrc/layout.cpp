@@ -243,6 +243,7 @@ void build_layout(const Plan& p, Layout& lay) {
     lay.tc_tiles.clear();
     lay.tc_list.clear();
     lay.tc_items.clear();
+    lay.pairs_tc = 0;
     // one item: rows [row_off, row_off + nrows) whose slot j covers rows
     // [sst[j], sst[j+1]); targets = (box, first slot of that box in the item,
     // row of the box's first entry)
@@ -292,7 +293,11 @@ void build_layout(const Plan& p, Layout& lay) {
                         if ((keepslot[k][is] >> j) & 1) st.keep[is] |= bits;
                 }
                 bool any = false;
-                for (int is = 0; is < nslot; ++is) any |= st.keep[is] != 0;
+                for (int is = 0; is < nslot; ++is) {
+                    any |= st.keep[is] != 0;
+                    const int32_t rows_is = std::min(sst[is + 1], nrows) - std::max(sst[is], 0);
+                    if (rows_is > 0) lay.pairs_tc += (int64_t)rows_is * __builtin_popcount(st.keep[is]);
+                }
                 if (!any) continue;
                 if (lay.tc_list.size() - it.list_lo == (size_t)kTcMaxTiles) {   // split long lists
                     it.list_hi = (int32_t)lay.tc_list.size();

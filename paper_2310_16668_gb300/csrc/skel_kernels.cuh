@@ -48,156 +48,210 @@ template <class S> __device__ __forceinline__ S warp_sum(S v) {
 }
 
 // ---- permutation ------------------------------------------------------------------
-template <class S>
-__global__ void permute_in(const int64_t* __restrict__ pe, const int64_t* __restrict__ pp,
-                           const S* __restrict__ q, S* __restrict__ Q, int64_t N, int nrhs) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= N * nrhs) return;
-    const int64_t i = g % N, r = g / N;
-    Q[pe[i] * nrhs + r] = q[r * N + pp[i]];
-}
+// q (user point order; each right-hand side a column of N) -> Q (entry space,
+// one row of nrhs per entry). eop[p] = the leaf entry of user point p. A tile
+// of 32 points x 32 right-hand sides goes through shared memory, so the
+// column reads and the row writes are both contiguous.
+constexpr int kPermTile = 32;
+constexpr int kPermThreads = 256;
 
 template <class S>
-__global__ void permute_out(const int64_t* __restrict__ pe, const int64_t* __restrict__ pp,
-                            const S* __restrict__ U, S* __restrict__ u, int64_t N, int nrhs) {
+__global__ void __launch_bounds__(kPermThreads) permute_in(const int64_t* __restrict__ eop, const S* __restrict__ q,
+                                                           S* __restrict__ Q, int64_t N, int nrhs) {
+    __shared__ S t[kPermTile][kPermTile + 1];
+    const int64_t p0 = (int64_t)blockIdx.x * kPermTile;
+    const int r0 = blockIdx.y * kPermTile;
+    const int tx = threadIdx.x % kPermTile, ty = threadIdx.x / kPermTile;
+    for (int k = ty; k < kPermTile; k += kPermThreads / kPermTile)
+        if (r0 + k < nrhs && p0 + tx < N) t[k][tx] = q[(int64_t)(r0 + k) * N + p0 + tx];
+    __syncthreads();
+    for (int k = ty; k < kPermTile; k += kPermThreads / kPermTile)
+        if (p0 + k < N && r0 + tx < nrhs) Q[eop[p0 + k] * nrhs + r0 + tx] = t[tx][k];
+}
+
+template <class S>
+__global__ void __launch_bounds__(kPermThreads) permute_out(const int64_t* __restrict__ eop, const S* __restrict__ U,
+                                                            S* __restrict__ u, int64_t N, int nrhs) {
+    __shared__ S t[kPermTile][kPermTile + 1];
+    const int64_t p0 = (int64_t)blockIdx.x * kPermTile;
+    const int r0 = blockIdx.y * kPermTile;
+    const int tx = threadIdx.x % kPermTile, ty = threadIdx.x / kPermTile;
+    for (int k = ty; k < kPermTile; k += kPermThreads / kPermTile)
+        if (p0 + k < N && r0 + tx < nrhs) t[k][tx] = U[eop[p0 + k] * nrhs + r0 + tx];
+    __syncthreads();
+    for (int k = ty; k < kPermTile; k += kPermThreads / kPermTile)
+        if (r0 + k < nrhs && p0 + tx < N) u[(int64_t)(r0 + k) * N + p0 + tx] = t[tx][k];
+}
+
+// few right-hand sides: one element per thread, points fastest (contiguous
+// column reads / writes on the user side)
+template <class S>
+__global__ void permute_in_narrow(const int64_t* __restrict__ eop, const S* __restrict__ q, S* __restrict__ Q,
+                                  int64_t N, int nrhs) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N * nrhs) return;
-    const int64_t i = g % N, r = g / N;
-    u[r * N + pp[i]] = U[pe[i] * nrhs + r];
+    const int64_t p = g % N, r = g / N;
+    Q[eop[p] * nrhs + r] = q[g];
 }
 
-// ---- upward: qhat_S = q_S + T q_R into the parent's slot ---------------------------
-// One CTA per box, a small GEMM (k x r) x (r x nrhs): rows of q_R are gathered
-// into shared memory 32 at a time; each thread owns up to kOwn (row, group of
-// RG right-hand sides) outputs; T (column-major, k contiguous) is read
-// coalesced across rows.
-constexpr int kUpThreads = 256;
-constexpr int kOwn = 4;
-constexpr int kJT = 32;
-
-template <class S, int RG>
-__global__ void __launch_bounds__(kUpThreads) up_kernel(const UpBox* __restrict__ up, const int32_t* __restrict__ pos,
-                                                        const S* __restrict__ T, S* Q, int nrhs, bool conjT) {
-    extern __shared__ unsigned char smem_raw[];
-    S* qs = reinterpret_cast<S*>(smem_raw);              // kJT x nrhs
-    const UpBox u = up[blockIdx.x];
-    const int k = u.k, r = u.n - u.k;
-    const int ng = (nrhs + RG - 1) / RG;
-    const int total = k * ng;
-    for (int base = 0; base < total; base += kUpThreads * kOwn) {
-        S acc[kOwn][RG];
-#pragma unroll
-        for (int o = 0; o < kOwn; ++o)
-#pragma unroll
-            for (int c = 0; c < RG; ++c) acc[o][c] = zero<S>();
-        for (int j0 = 0; j0 < r; j0 += kJT) {
-            const int jn = min(kJT, r - j0);
-            __syncthreads();
-            for (int e = threadIdx.x; e < jn * nrhs; e += kUpThreads) {
-                const int jj = e / nrhs, c = e % nrhs;
-                qs[e] = Q[(u.off + pos[u.off + k + j0 + jj]) * nrhs + c];
-            }
-            __syncthreads();
-#pragma unroll
-            for (int o = 0; o < kOwn; ++o) {
-                const int task = base + o * kUpThreads + threadIdx.x;
-                if (task >= total) break;
-                const int i = task % k, g = task / k;
-                const S* Ti = T + u.T_off + i + (int64_t)j0 * k;
-                for (int jj = 0; jj < jn; ++jj) {
-                    S tv = Ti[(int64_t)jj * k];
-                    if (conjT) tv = conj(tv);
-#pragma unroll
-                    for (int c = 0; c < RG; ++c)
-                        if (g * RG + c < nrhs) acc[o][c] += tv * qs[jj * nrhs + g * RG + c];
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 0; o < kOwn; ++o) {
-            const int task = base + o * kUpThreads + threadIdx.x;
-            if (task >= total) break;
-            const int i = task % k, g = task / k;
-            const int64_t src = (u.off + pos[u.off + i]) * nrhs, dst = (u.dst + i) * nrhs;
-#pragma unroll
-            for (int c = 0; c < RG; ++c) {
-                const int cc = g * RG + c;
-                if (cc < nrhs) Q[dst + cc] = Q[src + cc] + acc[o][c];
-            }
-        }
-    }
+template <class S>
+__global__ void permute_out_narrow(const int64_t* __restrict__ eop, const S* __restrict__ U, S* __restrict__ u,
+                                   int64_t N, int nrhs) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N * nrhs) return;
+    const int64_t p = g % N, r = g / N;
+    u[g] = U[eop[p] * nrhs + r];
 }
 
-// ---- downward: uhat = U[parent slot]; u_S += uhat; u_R += T^* uhat -------------------
-// One CTA per box; uhat rows are staged in shared memory 32 at a time and the
-// transposed copy Tt (r x k, column-major: r contiguous) is read coalesced
-// across the output rows j of R.
-template <class S, int RG>
-__global__ void __launch_bounds__(kUpThreads) down_kernel(const UpBox* __restrict__ up, const int32_t* __restrict__ pos,
-                                                          const S* __restrict__ Tt, S* U, int nrhs, bool transpose) {
-    extern __shared__ unsigned char smem_raw[];
-    S* us = reinterpret_cast<S*>(smem_raw);              // kJT x nrhs
+// ---- upward / downward passes: tiled small GEMMs ---------------------------------------
+// Upward (qhat_S = q_S + T q_R into the parent's slot): output rows i < k,
+// inner index j < r, A(i, j) = T[i + j k] (T column-major k x r), B row j =
+// the q row of R entry j. Downward (u_S += uhat, then u_R += T^* uhat): output
+// rows j < r, inner index i < k, A(j, i) = Tt[j + i r] (the transposed copy,
+// column-major r x k), B row i = uhat_i (the parent's slot). A CTA owns 32
+// output rows x 32 right-hand sides of one box (grid y, z) and stages the A
+// block (inner index major) and the gathered B rows through shared memory 32
+// inner indices at a time; a thread accumulates 4 rows x 4 right-hand sides
+// from one 4-row and one 4-column shared-memory vector per inner index.
+// conj_op applies the complex conjugate to A (T^* downward, conj(T) for the
+// transposed apply).
+constexpr int kGT = 32;
+constexpr int kGThreads = 64;
+
+template <class S> __device__ __forceinline__ void lds4(const S* p, S* v) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = p[q];
+}
+template <> __device__ __forceinline__ void lds4<float>(const float* p, float* v) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+}
+
+template <class S, bool DOWN>
+__global__ void __launch_bounds__(kGThreads, sizeof(S) <= 4 ? 12 : 4) updown_kernel(const UpBox* __restrict__ up,
+                                                           const int32_t* __restrict__ pos,
+                                                           const S* __restrict__ T, S* X, int nrhs, bool conj_op) {
+    constexpr int kPer = kGT * kGT / kGThreads;           // A and B elements per thread per chunk
+    constexpr int kRowStep = kGThreads / kGT;             // rows covered by one pass of the CTA
+    // register prefetch of the next chunk for element types up to 8 bytes
+    constexpr bool kPrefetch = sizeof(S) <= 8;
+    __shared__ __align__(16) S As[kGT][kGT];              // As[inner][row]
+    __shared__ __align__(16) S Bs[kGT][kGT];              // Bs[inner][column]; the output tile at the end
     const UpBox u = up[blockIdx.x];
     const int k = u.k, r = u.n - u.k;
-    for (int e = threadIdx.x; e < k * nrhs; e += kUpThreads) {
-        const int i = e / nrhs, c = e % nrhs;
-        U[(u.off + pos[u.off + i]) * nrhs + c] += U[(u.dst + i) * nrhs + c];
+    const int nout = DOWN ? r : k, ninner = DOWN ? k : r;
+    const int row0 = blockIdx.y * kGT, c0 = blockIdx.z * kGT;
+    const int tid = threadIdx.x;
+    // every global access below: lane = a contiguous index (a row of T or a
+    // column of X), warp / pass = the other index
+    const int lx = tid % kGT, ly = tid / kGT;
+    if (DOWN && blockIdx.y == 0) {                        // u_S += uhat, this CTA's columns
+        if (c0 + lx < nrhs)
+            for (int i = ly; i < k; i += kRowStep)
+                X[(u.off + pos[u.off + i]) * nrhs + c0 + lx] += X[(u.dst + i) * nrhs + c0 + lx];
     }
-    const int ng = (nrhs + RG - 1) / RG;
-    const int total = r * ng;
-    for (int base = 0; base < total; base += kUpThreads * kOwn) {
-        S acc[kOwn][RG];
+    if (row0 >= nout) return;
+    S ra[kPer], rb[kPer];
+    auto load = [&](int j0) {
+        const int jn = min(kGT, ninner - j0);
 #pragma unroll
-        for (int o = 0; o < kOwn; ++o)
-#pragma unroll
-            for (int c = 0; c < RG; ++c) acc[o][c] = zero<S>();
-        for (int i0 = 0; i0 < k; i0 += kJT) {
-            const int in = min(kJT, k - i0);
-            __syncthreads();
-            for (int e = threadIdx.x; e < in * nrhs; e += kUpThreads) us[e] = U[(u.dst + i0) * nrhs + e];
-            __syncthreads();
-#pragma unroll
-            for (int o = 0; o < kOwn; ++o) {
-                const int task = base + o * kUpThreads + threadIdx.x;
-                if (task >= total) break;
-                const int j = task % r, g = task / r;
-                const S* Tj = Tt + u.T_off + j + (int64_t)i0 * r;
-                for (int ii = 0; ii < in; ++ii) {
-                    S tv = Tj[(int64_t)ii * r];
-                    if (!transpose) tv = conj(tv);
-#pragma unroll
-                    for (int c = 0; c < RG; ++c)
-                        if (g * RG + c < nrhs) acc[o][c] += tv * us[ii * nrhs + g * RG + c];
-                }
+        for (int t = 0; t < kPer; ++t) {
+            const int b = ly + t * kRowStep;
+            S v = zero<S>();
+            if (row0 + lx < nout && b < jn) {
+                v = T[u.T_off + row0 + lx + (int64_t)(j0 + b) * nout];
+                if (conj_op) v = conj(v);
             }
+            ra[t] = v;
         }
 #pragma unroll
-        for (int o = 0; o < kOwn; ++o) {
-            const int task = base + o * kUpThreads + threadIdx.x;
-            if (task >= total) break;
-            const int j = task % r, g = task / r;
-            const int64_t e = (u.off + pos[u.off + k + j]) * nrhs;
-#pragma unroll
-            for (int c = 0; c < RG; ++c) {
-                const int cc = g * RG + c;
-                if (cc < nrhs) U[e + cc] += acc[o][c];
+        for (int t = 0; t < kPer; ++t) {
+            const int b = ly + t * kRowStep;
+            S v = zero<S>();
+            if (b < jn && c0 + lx < nrhs) {
+                const int64_t row = DOWN ? (u.dst + j0 + b) : (u.off + pos[u.off + k + j0 + b]);
+                v = X[row * nrhs + c0 + lx];
             }
+            rb[t] = v;
+        }
+    };
+    const int ti = tid >> 3, tc = tid & 7;                // rows 4ti .. 4ti+3; columns 4tc .. 4tc+3
+    S acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = zero<S>();
+    if (kPrefetch) load(0);
+    for (int j0 = 0; j0 < ninner; j0 += kGT) {
+        if (!kPrefetch) load(j0);
+        __syncthreads();                                  // the previous chunk's reads are done
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            As[ly + t * kRowStep][lx] = ra[t];
+            Bs[ly + t * kRowStep][lx] = rb[t];
+        }
+        __syncthreads();
+        if (kPrefetch && j0 + kGT < ninner) load(j0 + kGT);   // next chunk in flight during the products
+#pragma unroll 4
+        for (int jj = 0; jj < kGT; ++jj) {
+            S av[4], bv[4];
+            lds4(&As[jj][4 * ti], av);
+            lds4(&Bs[jj][4 * tc], bv);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] += av[a] * bv[c];
+        }
+    }
+    // the output tile goes through shared memory so that each row is written
+    // by consecutive lanes
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Bs[4 * ti + a][4 * tc + c] = acc[a][c];
+    __syncthreads();
+    if (c0 + lx < nrhs) {
+        for (int i = ly; i < kGT && row0 + i < nout; i += kRowStep) {
+            const int orow = row0 + i;
+            const S v = Bs[i][lx];
+            if (DOWN) X[(u.off + pos[u.off + k + orow]) * nrhs + c0 + lx] += v;
+            else X[(u.dst + orow) * nrhs + c0 + lx] = X[(u.off + pos[u.off + orow]) * nrhs + c0 + lx] + v;
         }
     }
 }
 
 // ---- reduction of near-field partial sums ------------------------------------------
-// U[e] = sum of the entry's partial sums (slot * 32 + row), in a fixed order
-template <class S>
+// U[e] = sum of the entry's partial sums (slot * 32 + row), in a fixed order.
+// A thread owns W consecutive right-hand sides of one entry (one 16-byte
+// load per partial sum when W * sizeof(S) = 16) and issues the loads of up
+// to four partial sums before adding them in order.
+template <class S, int W>
 __global__ void reduce_kernel(const int64_t* __restrict__ ptr, const int64_t* __restrict__ idx,
                               const S* __restrict__ part, S* __restrict__ U, int nrhs, int64_t n_tot) {
+    struct alignas(W * sizeof(S)) Vec { S v[W]; };
+    const int nq = nrhs / W;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_tot * nrhs) return;
-    const int64_t e = g / nrhs;
-    const int r = (int)(g % nrhs);
-    S s = zero<S>();
-    for (int64_t p = ptr[e]; p < ptr[e + 1]; ++p) s += part[idx[p] * nrhs + r];
-    U[e * nrhs + r] = s;
+    if (g >= n_tot * nq) return;
+    const int64_t e = g / nq;
+    const int c = (int)(g % nq) * W;
+    Vec s;
+#pragma unroll
+    for (int w = 0; w < W; ++w) s.v[w] = zero<S>();
+    const int64_t p1 = ptr[e + 1];
+    for (int64_t p = ptr[e]; p < p1; p += 4) {
+        Vec v[4];
+        const int m = (int)min((int64_t)4, p1 - p);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (t < m) v[t] = *reinterpret_cast<const Vec*>(part + idx[p + t] * nrhs + c);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (t < m)
+#pragma unroll
+                for (int w = 0; w < W; ++w) s.v[w] += v[t].v[w];
+    }
+    *reinterpret_cast<Vec*>(U + e * nrhs + c) = s;
 }
 
 // ---- near field ------------------------------------------------------------------------

@@ -15,7 +15,8 @@
 //     hi*lo + lo*hi for each of 4 K-steps) and commits them to the stage's
 //     "empty" mbarrier;
 //   * warps 0-7 (compute, two threads per target row, 16 sources each): wait
-//     "full", lay the source coordinates out per axis, evaluate the kernel
+//     "full", copy the source coordinates once per target slot, one array
+//     per axis, evaluate the kernel
 //     block two sources per paired FP32 instruction (fadd2 / fmul2 / ffma2),
 //     split each value into TF32 hi + lo,
 //     convert the charge block into the B operand (K-major, no swizzle,
@@ -32,7 +33,10 @@
 // of each product.
 //
 // Masks: a source that a target row's slot must skip (the regrouped
-// subtractions of Algorithm 2) gets G = 0 in that row. Waiting threads sleep
+// subtractions of Algorithm 2) gets G = 0 in that row: in that slot's copy of
+// the coordinates it sits at 1e30, where r^2 overflows to +inf and the kernel
+// value is exactly 0, so the evaluation itself has no per-source test.
+// Each half of the compute warps drains 16 of the 32 accumulator columns. Waiting threads sleep
 // in the mbarrier (suspend-time hint) rather than spin, and every wait is
 // bounded by wall time (globaltimer, 2 s); on timeout the kernel raises the status word, keeps the protocol
 // going without hanging, waits (bounded) for its copies and MMAs and always
@@ -64,19 +68,24 @@ struct alignas(128) TcStage {
     SrcTile tile;                              // 64 B
     float4 xh[32];                             // source coordinates (hi)
     float4 xl[32];                             // lo parts (touching-leaf tiles)
-    float sx[32], sy[32], sz[32];              // the same coordinates, one array per axis (hi)
-    float lx[32], ly[32], lz[32];              // lo parts per axis
     float qraw[32 * kTcMaxRhs];                // raw charge rows
     float bhi[32 * 32];                        // B operand, TF32 hi
     float blo[32 * 32];                        // B operand, TF32 lo
 };
+// per target slot, the tile's source coordinates one array per axis (x at
+// 0, y at 32, z at 64), a source the slot skips moved to kFar; the slot
+// stride of 104 floats puts two slots' copies 8 banks apart
+constexpr int kSlotStride = 104;
+constexpr float kFar = 1e30f;                  // r^2 from here overflows to +inf: 1/r = 0
 struct TcShared {
     TcStage st[kNS];
+    float cx[2][kMaxSlots * kSlotStride];      // double-buffered per-slot coordinates (hi)
+    float cl[2][3 * 32];                       // lo parts per axis (touching-leaf tiles)
     uint64_t full[kNS], afull[kNS], empty[kNS];  // per data stage
     uint32_t tmem;
     uint32_t slots;
 };
-constexpr int kTcSmemRequest = 108 * 1024;    // at most two CTAs (2 x 256 TMEM columns) per SM
+constexpr int kTcSmemRequest = 112 * 1024;    // at most two CTAs (2 x 256 TMEM columns) per SM
 static_assert(sizeof(TcShared) <= kTcSmemRequest, "shared memory plan");
 
 struct TcArgs {
@@ -184,9 +193,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// kernel value without its constant factor (see Green<>)
-template <int KIND> __device__ __forceinline__ float tc_green(float r2) {
-    return KIND == 0 ? logf(r2) : rsqrtf(r2);
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15])
+                 : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// kernel value without its constant factor (see Green<>). 3D: the PTX
+// approximate reciprocal square root with subnormals flushed (rsqrt(+inf) = 0
+// gives the masked sources their zero); touching-leaf tiles also zero r^2 <=
+// FLT_MIN (pairs closer than 1.1e-19, coincident points included). 2D: log r^2,
+// zero for r^2 = +inf (masked) and, on touching-leaf tiles, for r^2 = 0.
+template <int KIND, bool ADJ> __device__ __forceinline__ float tc_green(float r2) {
+    if (KIND == 0) {
+        const bool on = r2 < 3.0e38f && (!ADJ || r2 > 0.f);
+        return on ? logf(r2) : 0.f;
+    }
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+    return (!ADJ || r2 > 1.17549435e-38f) ? y : 0.f;
 }
 
 // TF32 hi part of a finite float, rounded to nearest (ties away from zero):
@@ -194,9 +222,10 @@ template <int KIND> __device__ __forceinline__ float tc_green(float r2) {
 __device__ __forceinline__ uint32_t tf32_hi(float g) { return (__float_as_uint(g) + 0x1000u) & 0xFFFFE000u; }
 
 // 16 sources (j0 .. j0+15) against this thread's target, two sources per
-// paired FP32 instruction. nt / nl hold the negated target coordinates.
-template <int KIND, bool ADJ, bool MASKED>
-__device__ __forceinline__ void tc_eval16(const TcStage& st, int j0, float4 nt, float4 nl, uint32_t keep,
+// paired FP32 instruction. c: this row's slot copy of the coordinates; cl: lo
+// parts; nt / nl: the negated target coordinates.
+template <int KIND, bool ADJ>
+__device__ __forceinline__ void tc_eval16(const float* c, const float* cl, int j0, float4 nt, float4 nl,
                                           uint32_t* ghi, uint32_t* glo) {
     const float2 ntx = make_float2(nt.x, nt.x), nty = make_float2(nt.y, nt.y), ntz = make_float2(nt.z, nt.z);
     float2 nlx, nly, nlz;
@@ -204,24 +233,18 @@ __device__ __forceinline__ void tc_eval16(const TcStage& st, int j0, float4 nt, 
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
         const int j = j0 + 2 * p;
-        float2 dx = __fadd2_rn(*reinterpret_cast<const float2*>(&st.sx[j]), ntx);
-        float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(&st.sy[j]), nty);
-        float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(&st.sz[j]), ntz);
+        float2 dx = __fadd2_rn(*reinterpret_cast<const float2*>(&c[j]), ntx);
+        float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(&c[32 + j]), nty);
+        float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(&c[64 + j]), ntz);
         if (ADJ) {
-            dx = __fadd2_rn(dx, __fadd2_rn(*reinterpret_cast<const float2*>(&st.lx[j]), nlx));
-            dy = __fadd2_rn(dy, __fadd2_rn(*reinterpret_cast<const float2*>(&st.ly[j]), nly));
-            dz = __fadd2_rn(dz, __fadd2_rn(*reinterpret_cast<const float2*>(&st.lz[j]), nlz));
+            dx = __fadd2_rn(dx, __fadd2_rn(*reinterpret_cast<const float2*>(&cl[j]), nlx));
+            dy = __fadd2_rn(dy, __fadd2_rn(*reinterpret_cast<const float2*>(&cl[32 + j]), nly));
+            dz = __fadd2_rn(dz, __fadd2_rn(*reinterpret_cast<const float2*>(&cl[64 + j]), nlz));
         }
         float2 r2 = __fmul2_rn(dx, dx);
         r2 = __ffma2_rn(dy, dy, r2);
         r2 = __ffma2_rn(dz, dz, r2);
-        float g0 = tc_green<KIND>(r2.x), g1 = tc_green<KIND>(r2.y);
-        if (MASKED || ADJ) {
-            const bool on0 = ((keep >> (2 * p)) & 1u) && (!ADJ || r2.x > 0.f);
-            const bool on1 = ((keep >> (2 * p + 1)) & 1u) && (!ADJ || r2.y > 0.f);
-            g0 = on0 ? g0 : 0.f;
-            g1 = on1 ? g1 : 0.f;
-        }
+        const float g0 = tc_green<KIND, ADJ>(r2.x), g1 = tc_green<KIND, ADJ>(r2.y);
         const uint32_t h0 = tf32_hi(g0), h1 = tf32_hi(g1);
         // lo = g - hi (exact); the tensor core truncates it to TF32
         const float2 lo = __ffma2_rn(make_float2(__uint_as_float(h0), __uint_as_float(h1)), make_float2(-1.f, -1.f),
@@ -337,19 +360,21 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         const int qoff = bj * a.nrhs + a.r0 + bn;
         const int boffw = (warp * kBLbo + bn * 16) >> 2;         // slab bj/4 = warp, row bn
         static_assert(7 * kBLbo + 31 * 16 + 16 <= 32 * 32 * 4, "B operand stays inside bhi/blo");
-        float acc[kTcN];
+        // each half of the compute warps owns 16 of the 32 accumulator columns
+        float acc[kTcN / 2];
 #pragma unroll
-        for (int c = 0; c < kTcN; ++c) acc[c] = 0.f;
+        for (int c = 0; c < kTcN / 2; ++c) acc[c] = 0.f;
         auto drain = [&](int m) {                              // add tile m's accumulator
             if (!mbar_wait(sm_addr(&S.empty[m % kNS]), (uint32_t)((m / kNS) & 1))) err = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (half == 0) {
-                uint32_t v[kTcN];
-                tmem_ld32(tbase + lane_off + kColD + 32u * (m & 1), v);
+            uint32_t v[kTcN / 2];
+            tmem_ld16(tbase + lane_off + kColD + 32u * (m & 1) + 16u * half, v);
 #pragma unroll
-                for (int c = 0; c < kTcN; ++c) acc[c] += __uint_as_float(v[c]);
-            }
+            for (int c = 0; c < kTcN / 2; ++c) acc[c] += __uint_as_float(v[c]);
         };
+        // per-slot coordinate copies: thread (slot is, source j)
+        const int cj = tid & 31, cis = tid >> 5;
+        static_assert(kTcCompute == 32 * kMaxSlots, "one compute thread per (slot, source)");
         for (int u = 0; u < ntile; ++u) {
             const int s = u % kNS;
             if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNS) & 1))) err = true;
@@ -357,15 +382,24 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             const int cnt = st.tile.cnt;
             const bool adj = (st.tile.flags & TASK_ADJ) != 0;
             const uint32_t keep = valid ? (st.tile.keep[myslot] >> (16 * half)) & 0xFFFFu : 0u;
-            // coordinates per axis (sources past cnt are never kept)
-            if (tid < 96) {
-                const float4 v = st.xh[tid & 31];
-                const int c = tid >> 5;
-                (c == 0 ? st.sx : c == 1 ? st.sy : st.sz)[tid & 31] = c == 0 ? v.x : c == 1 ? v.y : v.z;
-            } else if (adj && tid < 192) {
-                const float4 v = st.xl[tid & 31];
-                const int c = (tid >> 5) - 3;
-                (c == 0 ? st.lx : c == 1 ? st.ly : st.lz)[tid & 31] = c == 0 ? v.x : c == 1 ? v.y : v.z;
+            // this tile's coordinates per slot and axis; a skipped source (and
+            // any j >= cnt, never kept) sits at kFar. Buffer u & 1 was last read
+            // in tile u - 2, before every compute warp passed tile u - 1's barrier.
+            float* cx = S.cx[u & 1];
+            float* cl = S.cl[u & 1];
+            if (cis < nslot) {
+                const float4 v = st.xh[cj];
+                const bool kept = (st.tile.keep[cis] >> cj) & 1u;
+                float* d = cx + cis * kSlotStride + cj;
+                d[0] = kept ? v.x : kFar;
+                d[32] = kept ? v.y : kFar;
+                d[64] = kept ? v.z : kFar;
+            }
+            if (adj && cis == kMaxSlots - 1) {
+                const float4 v = cj < cnt ? st.xl[cj] : make_float4(0.f, 0.f, 0.f, 0.f);
+                cl[cj] = v.x;
+                cl[32 + cj] = v.y;
+                cl[64 + cj] = v.z;
             }
             asm volatile("bar.sync 1, %0;" :: "r"(kTcCompute) : "memory");   // compute warps only
             // B operand of this stage (sources beyond cnt are zero)
@@ -385,15 +419,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             if (u >= 2) drain(u - 2);                          // frees accumulator (u & 1)
             uint32_t ghi[16], glo[16];
             const int j0 = 16 * half;
+            const float* c = cx + myslot * kSlotStride;
             if (__all_sync(0xffffffffu, keep == 0)) {
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) ghi[jj] = glo[jj] = 0u;
             } else if (adj) {
-                tc_eval16<KIND, true, true>(st, j0, nt, nl, keep, ghi, glo);
-            } else if (__all_sync(0xffffffffu, keep == 0xFFFFu)) {
-                tc_eval16<KIND, false, false>(st, j0, nt, nl, keep, ghi, glo);
+                tc_eval16<KIND, true>(c, cl, j0, nt, nl, ghi, glo);
             } else {
-                tc_eval16<KIND, false, true>(st, j0, nt, nl, keep, ghi, glo);
+                tc_eval16<KIND, false>(c, cl, j0, nt, nl, ghi, glo);
             }
             // A buffer u % kNA was last read by MMA(u - kNA), complete since drain(u - 2)
             const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + 16u * half;
@@ -405,12 +438,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             mbar_arrive(sm_addr(&S.afull[s]));
         }
         for (int m = (ntile >= 2 ? ntile - 2 : 0); m < ntile; ++m) drain(m);
-        if (half == 0 && valid) {
+        if (valid) {
             const float scale = (float)green_scale<KIND>();
             const int64_t base = ((int64_t)(out_slot + (row >> 5)) * kChunk + (row & 31)) * a.nrhs;
+            const int c0 = a.r0 + 16 * half;
 #pragma unroll
-            for (int c = 0; c < kTcN; ++c)
-                if (a.r0 + c < a.nrhs) a.partial[base + a.r0 + c] = scale * acc[c];
+            for (int c = 0; c < kTcN / 2; ++c)
+                if (c0 + c < a.nrhs) a.partial[base + c0 + c] = scale * acc[c];
         }
     }
     if (err) atomicExch(a.status, 1);
