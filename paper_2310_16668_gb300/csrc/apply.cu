@@ -194,14 +194,13 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
         launches += launch_near<Real, CPLX>(dp->kind, a, nrhs, ceil_div(dp->n_mix, kNearWarps), st);
         CUDA_CHECK(cudaGetLastError());
     }
-    mark(dp, kMainEvent, st);
     TcArgs t;
     t.items = dp->tc_items;
     t.tiles = dp->tc_tiles;
     t.list = dp->tc_list;
     t.X = (const float4*)b->X;
     t.Xlo = (const float4*)b->Xlo;
-    t.Q = (const float*)b->Q;
+    t.B = dp->tc_b;
     t.partial = (float*)b->partial;
     t.nrhs = nrhs;
     t.status = dp->status;
@@ -217,6 +216,12 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     tc_launches = 0;
     for (int r0 = 0; r0 < nrhs; r0 += kTcN, ++launches, ++tc_launches) {
         t.r0 = r0;
+        // the pass's B operand blocks, then the translations
+        tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q,
+                                                               nrhs, r0, dp->tc_b);
+        CUDA_CHECK(cudaGetLastError());
+        ++launches;
+        if (r0 == 0) mark(dp, kMainEvent, st);
         if (kidx == 0) tc_near_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
         else tc_near_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
         CUDA_CHECK(cudaGetLastError());
@@ -349,6 +354,12 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
         dp->tc_items = upload(lay.tc_items, dp->bytes);
         dp->tc_list = upload(lay.tc_list, dp->bytes);
         dp->n_tc = (int64_t)lay.tc_items.size();
+        if (dp->n_tc > 0 && !dp->cplx) {
+            dp->chunk_start = upload(lay.chunk_start, dp->bytes);
+            dp->chunk_cnt = upload(lay.chunk_cnt, dp->bytes);
+            dp->n_chunks = (int64_t)lay.chunk_start.size();
+            dp->tc_b = dalloc<float>((size_t)dp->n_chunks * 2048, dp->bytes);
+        }
         dp->tc_n_slots = lay.tc_n_slots;
         dp->tc_part_ptr = upload(lay.tc_part_ptr, dp->bytes);
         dp->tc_part_idx = upload(lay.tc_part_idx, dp->bytes);
@@ -373,7 +384,8 @@ void device_plan_destroy(DevicePlan* dp) {
     cudaSetDevice(dp->device);
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
-                    dp->tc_items, dp->tc_list, dp->tc_part_ptr, dp->tc_part_idx, dp->status};
+                    dp->tc_items, dp->tc_list, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
+                    dp->chunk_start, dp->chunk_cnt, dp->tc_b};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);

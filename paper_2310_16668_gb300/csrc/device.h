@@ -46,6 +46,10 @@ struct DevicePlan {
     int64_t tc_n_slots = 0;
     int64_t* tc_part_ptr = nullptr;        // per entry: its partial sums (tensor-core mode)
     int64_t* tc_part_idx = nullptr;
+    int64_t* chunk_start = nullptr;        // source chunks (32 entries of one box)
+    int32_t* chunk_cnt = nullptr;
+    int64_t n_chunks = 0;
+    float* tc_b = nullptr;                 // B operand per chunk for one 32-column pass (hi, lo)
     int* status = nullptr;                 // device word raised by a bounded wait that gave up
     DeviceBuffers* p64 = nullptr;
     DeviceBuffers* p32 = nullptr;

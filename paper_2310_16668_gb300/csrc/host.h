@@ -111,7 +111,8 @@ struct SrcTile {                        // 64 bytes; copied into shared memory b
     int32_t cnt;                        // sources (1..32)
     int32_t flags;                      // TASK_ADJ
     uint32_t keep[kMaxSlots];           // per target slot: bit j = the slot keeps source j
-    int32_t pad[4];
+    int32_t chunk;                      // its source chunk (the B operand block of these 32 sources)
+    int32_t pad[3];
 };
 static_assert(sizeof(SrcTile) == 64, "SrcTile is one 64-byte bulk copy");
 
@@ -158,6 +159,11 @@ struct Layout {
     std::vector<TcItem> tc_items;
     std::vector<int64_t> tc_part_ptr, tc_part_idx;
     int64_t tc_n_slots = 0;
+    // source chunks: 32 consecutive entries of one box (the last one ragged);
+    // box b's chunk c is box_chunk0[b] + c
+    std::vector<int64_t> box_chunk0;    // nb
+    std::vector<int64_t> chunk_start;   // first entry of each chunk
+    std::vector<int32_t> chunk_cnt;     // entries in it (1..32)
     int64_t pairs_direct = 0, pairs_far = 0;
     int64_t pairs_tc = 0;   // kept evaluations inside tensor-core items
 };

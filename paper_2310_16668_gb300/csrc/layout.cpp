@@ -244,6 +244,17 @@ void build_layout(const Plan& p, Layout& lay) {
     lay.tc_list.clear();
     lay.tc_items.clear();
     lay.pairs_tc = 0;
+    lay.box_chunk0.assign(nb, -1);
+    lay.chunk_start.clear();
+    lay.chunk_cnt.clear();
+    for (int64_t b = 0; b < nb; ++b) {
+        if (lay.box_off[b] < 0) continue;
+        lay.box_chunk0[b] = (int64_t)lay.chunk_start.size();
+        for (int32_t p0 = 0; p0 < lay.box_n[b]; p0 += kTcK) {
+            lay.chunk_start.push_back(lay.box_off[b] + p0);
+            lay.chunk_cnt.push_back(std::min(kTcK, lay.box_n[b] - p0));
+        }
+    }
     // one item: rows [row_off, row_off + nrows) whose slot j covers rows
     // [sst[j], sst[j+1]); targets = (box, first slot of that box in the item,
     // row of the box's first entry)
@@ -283,6 +294,7 @@ void build_layout(const Plan& p, Layout& lay) {
             for (int32_t p0 = 0; p0 < n; p0 += kTcK) {
                 SrcTile st{};
                 st.start = lay.box_off[src] + p0;
+                st.chunk = (int32_t)(lay.box_chunk0[src] + p0 / kTcK);
                 st.cnt = std::min(kTcK, n - p0);
                 st.flags = srcs[k].second;
                 for (int j = 0; j < lay.box_nslot[src]; ++j) {

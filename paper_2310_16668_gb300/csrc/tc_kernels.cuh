@@ -4,43 +4,44 @@
 // leaves packed together) the translations are
 // U[128 x 32] += G[128 x K] Q[K x 32] over the K source entries of the box's
 // tasks, G_ij = G(x_i, y_j) evaluated on the fly, 32 sources per pipeline
-// tile. The CTA is warp-specialised:
+// tile. Before the translations of a 32-column pass, tc_bprep_kernel writes
+// the B operand of every source chunk (32 consecutive entries of one box) in
+// the MMA's shared-memory layout (K-major, no swizzle, 8 x 16-byte core
+// matrices: 512 bytes between core matrices along K, 128 bytes between groups
+// of 8 right-hand sides), split into TF32 hi and lo. The CTA is
+// warp-specialised:
 //   * warp 8, one thread (producer): for tile t it waits until data stage
 //     t % 6 is free, arms that stage's "full" mbarrier with the byte count and
-//     issues bulk copies (cp.async.bulk) of the tile descriptor, the 32 source
-//     coordinates and the 32 raw charge rows into shared memory, running up
-//     to six tiles ahead of the compute warps;
+//     issues bulk copies (cp.async.bulk) of the chunk's B hi and lo blocks,
+//     the tile descriptor and the source coordinates into shared memory,
+//     running up to six tiles ahead of the compute warps;
 //   * warp 9, one thread (MMA issuer): for tile m it waits for "A full" and
 //     issues 12 tcgen05.mma (kind::tf32, M = 128, N = 32, K = 8: hi*hi +
 //     hi*lo + lo*hi for each of 4 K-steps) and commits them to the stage's
 //     "empty" mbarrier;
 //   * warps 0-7 (compute, two threads per target row, 16 sources each): wait
-//     "full", copy the source coordinates once per target slot, one array
-//     per axis, evaluate the kernel
-//     block two sources per paired FP32 instruction (fadd2 / fmul2 / ffma2),
-//     split each value into TF32 hi + lo,
-//     convert the charge block into the B operand (K-major, no swizzle,
-//     8 x 16-byte core matrices: 512 bytes between core matrices along K,
-//     128 bytes between groups of 8 right-hand sides), add the finished
-//     accumulator of tile u - 2 into FP32 registers, write A with tcgen05.st
-//     (TMEM lane = row, column = source) and arrive on "A full".
+//     "full", copy their 16 source coordinates once per target slot their
+//     rows fall in (one array per axis, warp-private, so only __syncwarp),
+//     evaluate the kernel block two sources per paired FP32 instruction
+//     (fadd2 / fmul2 / ffma2), split each value into TF32 hi + lo, add the
+//     finished accumulator of tile u - 2 into FP32 registers, write A with
+//     tcgen05.st (TMEM lane = row, column = source) and arrive on "A full".
 // Six data stages and three A buffers keep the bulk copies (issued up to six
 // tiles ahead), the kernel evaluation and the tensor core busy at the same
-// time; the two accumulator
-// tiles alternate, so each tensor-memory accumulation covers one tile only
-// (32 sources) and every longer sum is an FP32 round-to-nearest register sum.
-// The dropped lo*lo term and the truncation of the lo parts are below 2^-21
-// of each product.
+// time; the two accumulator tiles alternate, so each tensor-memory
+// accumulation covers one tile only (32 sources) and every longer sum is an
+// FP32 round-to-nearest register sum. The dropped lo*lo term and the
+// truncation of the lo parts are below 2^-21 of each product.
 //
 // Masks: a source that a target row's slot must skip (the regrouped
 // subtractions of Algorithm 2) gets G = 0 in that row: in that slot's copy of
 // the coordinates it sits at 1e30, where r^2 overflows to +inf and the kernel
 // value is exactly 0, so the evaluation itself has no per-source test.
-// Each half of the compute warps drains 16 of the 32 accumulator columns. Waiting threads sleep
-// in the mbarrier (suspend-time hint) rather than spin, and every wait is
-// bounded by wall time (globaltimer, 2 s); on timeout the kernel raises the status word, keeps the protocol
-// going without hanging, waits (bounded) for its copies and MMAs and always
-// frees its tensor memory.
+// Each half of the compute warps drains 16 of the 32 accumulator columns.
+// Waiting threads sleep in the mbarrier (suspend-time hint) rather than spin,
+// and every wait is bounded by wall time (globaltimer, 2 s); on timeout the
+// kernel raises the status word, keeps the protocol going without hanging,
+// waits (bounded) for its copies and MMAs and always frees its tensor memory.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -65,22 +66,20 @@ constexpr uint32_t kSleepNs = 20000;           // suspend hint of one wait attem
 constexpr uint64_t kWaitLimitNs = 2000000000ull; // a wait gives up after 2 s
 
 struct alignas(128) TcStage {
+    float bhi[32 * 32];                        // B operand, TF32 hi (bulk-copied, already converted)
+    float blo[32 * 32];                        // B operand, TF32 lo
     SrcTile tile;                              // 64 B
     float4 xh[32];                             // source coordinates (hi)
     float4 xl[32];                             // lo parts (touching-leaf tiles)
-    float qraw[32 * kTcMaxRhs];                // raw charge rows
-    float bhi[32 * 32];                        // B operand, TF32 hi
-    float blo[32 * 32];                        // B operand, TF32 lo
 };
-// per target slot, the tile's source coordinates one array per axis (x at
-// 0, y at 32, z at 64), a source the slot skips moved to kFar; the slot
-// stride of 104 floats puts two slots' copies 8 banks apart
-constexpr int kSlotStride = 104;
+// per compute warp: for each target slot its 32 rows touch, the coordinates
+// of its 16 sources, one array per axis (x at 0, y at 16, z at 32); a source
+// the slot skips sits at kFar
+constexpr int kWarpSlotFloats = 48;
 constexpr float kFar = 1e30f;                  // r^2 from here overflows to +inf: 1/r = 0
 struct TcShared {
     TcStage st[kNS];
-    float cx[2][kMaxSlots * kSlotStride];      // double-buffered per-slot coordinates (hi)
-    float cl[2][3 * 32];                       // lo parts per axis (touching-leaf tiles)
+    float wc[kTcCompute / 32][kMaxSlots * kWarpSlotFloats];
     uint64_t full[kNS], afull[kNS], empty[kNS];  // per data stage
     uint32_t tmem;
     uint32_t slots;
@@ -94,9 +93,9 @@ struct TcArgs {
     const int32_t* list;
     const float4* X;
     const float4* Xlo;
-    const float* Q;
+    const float* B;                            // per source chunk: B hi (1024 floats), then B lo
     float* partial;
-    int nrhs;                                  // row length of Q (multiple of 4, <= kTcMaxRhs)
+    int nrhs;                                  // right-hand sides (row length of the partial sums)
     int r0;                                    // first right-hand side of this pass
     int* status;
 };
@@ -222,24 +221,26 @@ template <int KIND, bool ADJ> __device__ __forceinline__ float tc_green(float r2
 __device__ __forceinline__ uint32_t tf32_hi(float g) { return (__float_as_uint(g) + 0x1000u) & 0xFFFFE000u; }
 
 // 16 sources (j0 .. j0+15) against this thread's target, two sources per
-// paired FP32 instruction. c: this row's slot copy of the coordinates; cl: lo
-// parts; nt / nl: the negated target coordinates.
+// paired FP32 instruction. c: this row's slot copy of the 16 coordinates (per
+// axis); xl: the stage's lo parts (touching-leaf tiles); nt / nl: the negated
+// target coordinates.
 template <int KIND, bool ADJ>
-__device__ __forceinline__ void tc_eval16(const float* c, const float* cl, int j0, float4 nt, float4 nl,
+__device__ __forceinline__ void tc_eval16(const float* c, const float4* xl, int j0, float4 nt, float4 nl,
                                           uint32_t* ghi, uint32_t* glo) {
     const float2 ntx = make_float2(nt.x, nt.x), nty = make_float2(nt.y, nt.y), ntz = make_float2(nt.z, nt.z);
     float2 nlx, nly, nlz;
     if (ADJ) nlx = make_float2(nl.x, nl.x), nly = make_float2(nl.y, nl.y), nlz = make_float2(nl.z, nl.z);
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
-        const int j = j0 + 2 * p;
-        float2 dx = __fadd2_rn(*reinterpret_cast<const float2*>(&c[j]), ntx);
-        float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(&c[32 + j]), nty);
-        float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(&c[64 + j]), ntz);
+        const int jj = 2 * p;
+        float2 dx = __fadd2_rn(*reinterpret_cast<const float2*>(&c[jj]), ntx);
+        float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(&c[16 + jj]), nty);
+        float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(&c[32 + jj]), ntz);
         if (ADJ) {
-            dx = __fadd2_rn(dx, __fadd2_rn(*reinterpret_cast<const float2*>(&cl[j]), nlx));
-            dy = __fadd2_rn(dy, __fadd2_rn(*reinterpret_cast<const float2*>(&cl[32 + j]), nly));
-            dz = __fadd2_rn(dz, __fadd2_rn(*reinterpret_cast<const float2*>(&cl[64 + j]), nlz));
+            const float4 l0 = xl[j0 + jj], l1 = xl[j0 + jj + 1];
+            dx = __fadd2_rn(dx, __fadd2_rn(make_float2(l0.x, l1.x), nlx));
+            dy = __fadd2_rn(dy, __fadd2_rn(make_float2(l0.y, l1.y), nly));
+            dz = __fadd2_rn(dz, __fadd2_rn(make_float2(l0.z, l1.z), nlz));
         }
         float2 r2 = __fmul2_rn(dx, dx);
         r2 = __ffma2_rn(dy, dy, r2);
@@ -249,11 +250,41 @@ __device__ __forceinline__ void tc_eval16(const float* c, const float* cl, int j
         // lo = g - hi (exact); the tensor core truncates it to TF32
         const float2 lo = __ffma2_rn(make_float2(__uint_as_float(h0), __uint_as_float(h1)), make_float2(-1.f, -1.f),
                                      make_float2(g0, g1));
-        ghi[2 * p] = h0;
-        ghi[2 * p + 1] = h1;
-        glo[2 * p] = __float_as_uint(lo.x);
-        glo[2 * p + 1] = __float_as_uint(lo.y);
+        ghi[jj] = h0;
+        ghi[jj + 1] = h1;
+        glo[jj] = __float_as_uint(lo.x);
+        glo[jj + 1] = __float_as_uint(lo.y);
     }
+}
+
+// B operand of one source chunk for right-hand sides r0 .. r0+31, in the
+// shared-memory layout of the MMA (element (n, j) at float (j/4)*128 + n*4 +
+// j%4), split into TF32 hi (rounded to nearest) and lo = q - hi; entries past
+// the chunk and columns past nrhs are zero. Thread: n = tid % 32, sources
+// 4 (tid / 32) .. +3.
+__global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict__ chunk_start,
+                                                       const int32_t* __restrict__ chunk_cnt,
+                                                       const float* __restrict__ Q, int nrhs, int r0,
+                                                       float* __restrict__ B) {
+    const int64_t ch = blockIdx.x;
+    const int n = threadIdx.x & 31, jq = threadIdx.x >> 5;
+    const int64_t start = chunk_start[ch];
+    const int cnt = chunk_cnt[ch];
+    float v[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int j = 4 * jq + c;
+        v[c] = (j < cnt && r0 + n < nrhs) ? Q[(start + j) * nrhs + r0 + n] : 0.f;
+    }
+    float4 h, l;
+    h.x = __uint_as_float(to_tf32(v[0]));
+    h.y = __uint_as_float(to_tf32(v[1]));
+    h.z = __uint_as_float(to_tf32(v[2]));
+    h.w = __uint_as_float(to_tf32(v[3]));
+    l = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
+    float* dst = B + ch * 2048 + jq * 128 + n * 4;
+    *reinterpret_cast<float4*>(dst) = h;
+    *reinterpret_cast<float4*>(dst + 1024) = l;
 }
 
 template <int KIND>
@@ -292,26 +323,30 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             const SrcTile* gnext = ntile > 0 ? a.tiles + a.list[list_lo] : nullptr;
             int64_t n_start = gnext ? gnext->start : 0;
             int n_cnt = gnext ? gnext->cnt : 0, n_flags = gnext ? gnext->flags : 0;
+            int n_chunk = gnext ? gnext->chunk : 0;
             for (int t = 0; t < ntile; ++t) {
                 const int s = t % kNS;
                 const SrcTile* g = gnext;
                 const int64_t start = n_start;
                 const int cnt = n_cnt;
                 const bool adj = (n_flags & TASK_ADJ) != 0;
+                const float* bsrc = a.B + (int64_t)n_chunk * 2048;
                 if (t + 1 < ntile) {                         // prefetch the next descriptor
                     gnext = a.tiles + a.list[list_lo + t + 1];
                     n_start = gnext->start;
                     n_cnt = gnext->cnt;
                     n_flags = gnext->flags;
+                    n_chunk = gnext->chunk;
                 }
                 if (t >= kNS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNS) / kNS) & 1))) err = true;
-                const uint32_t bytes = 64u + 16u * cnt * (adj ? 2u : 1u) + 4u * cnt * a.nrhs;
+                const uint32_t bytes = 64u + 16u * cnt * (adj ? 2u : 1u) + 2u * 4096u;
                 const uint32_t bar = sm_addr(&S.full[s]);
                 mbar_arrive_tx(bar, bytes);
+                bulk_g2s(sm_addr(S.st[s].bhi), bsrc, 4096u, bar);
+                bulk_g2s(sm_addr(S.st[s].blo), bsrc + 1024, 4096u, bar);
                 bulk_g2s(sm_addr(&S.st[s].tile), g, 64u, bar);
                 bulk_g2s(sm_addr(S.st[s].xh), a.X + start, 16u * cnt, bar);
                 if (adj) bulk_g2s(sm_addr(S.st[s].xl), a.Xlo + start, 16u * cnt, bar);
-                bulk_g2s(sm_addr(S.st[s].qraw), a.Q + start * a.nrhs, 4u * cnt * a.nrhs, bar);
             }
             // all bulk copies have landed before the CTA may exit
             for (int t = (ntile > kNS ? ntile - kNS : 0); t < ntile; ++t)
@@ -353,13 +388,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         }
         const float4 nt = make_float4(-tx.x, -tx.y, -tx.z, 0.f), nl = make_float4(-tl.x, -tl.y, -tl.z, 0.f);
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-        // this thread's part of each charge block: right-hand side n = lane,
-        // sources j = 4*warp .. 4*warp+3 (one 16-byte core-matrix row)
-        const int bn = lane, bj = 4 * warp;
-        const bool bcol = a.r0 + bn < a.nrhs;                  // columns past nrhs stay zero
-        const int qoff = bj * a.nrhs + a.r0 + bn;
-        const int boffw = (warp * kBLbo + bn * 16) >> 2;         // slab bj/4 = warp, row bn
-        static_assert(7 * kBLbo + 31 * 16 + 16 <= 32 * 32 * 4, "B operand stays inside bhi/blo");
+        // the slots this warp's 32 rows fall in: s_lo .. s_lo + nsw - 1
+        const int r_first = 32 * (warp & 3), r_last = min(r_first + 31, nrows - 1);
+        int s_lo = 0, s_hi = 0;
+        for (int c = 1; c < nslot; ++c) {
+            if (r_first >= itp->slot_start[c]) s_lo = c;
+            if (r_last >= itp->slot_start[c]) s_hi = c;
+        }
+        const int nsw = max(1, s_hi - s_lo + 1);
+        const int myloc = min(max(myslot - s_lo, 0), kMaxSlots - 1);
+        float* wc = S.wc[warp];
         // each half of the compute warps owns 16 of the 32 accumulator columns
         float acc[kTcN / 2];
 #pragma unroll
@@ -372,68 +410,43 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
 #pragma unroll
             for (int c = 0; c < kTcN / 2; ++c) acc[c] += __uint_as_float(v[c]);
         };
-        // per-slot coordinate copies: thread (slot is, source j)
-        const int cj = tid & 31, cis = tid >> 5;
-        static_assert(kTcCompute == 32 * kMaxSlots, "one compute thread per (slot, source)");
         for (int u = 0; u < ntile; ++u) {
             const int s = u % kNS;
             if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNS) & 1))) err = true;
             TcStage& st = S.st[s];
-            const int cnt = st.tile.cnt;
             const bool adj = (st.tile.flags & TASK_ADJ) != 0;
             const uint32_t keep = valid ? (st.tile.keep[myslot] >> (16 * half)) & 0xFFFFu : 0u;
-            // this tile's coordinates per slot and axis; a skipped source (and
-            // any j >= cnt, never kept) sits at kFar. Buffer u & 1 was last read
-            // in tile u - 2, before every compute warp passed tile u - 1's barrier.
-            float* cx = S.cx[u & 1];
-            float* cl = S.cl[u & 1];
-            if (cis < nslot) {
-                const float4 v = st.xh[cj];
-                const bool kept = (st.tile.keep[cis] >> cj) & 1u;
-                float* d = cx + cis * kSlotStride + cj;
+            const int j0 = 16 * half;
+            // this warp's copy of its 16 sources per slot and axis; a skipped
+            // source (and any j >= cnt, never kept) sits at kFar. Every lane
+            // has finished reading the previous tile's copy.
+            __syncwarp();
+            for (int p = lane; p < nsw * 16; p += 32) {
+                const int ls = p >> 4, jj = p & 15;
+                const float4 v = st.xh[j0 + jj];
+                const bool kept = (st.tile.keep[s_lo + ls] >> (j0 + jj)) & 1u;
+                float* d = wc + ls * kWarpSlotFloats + jj;
                 d[0] = kept ? v.x : kFar;
-                d[32] = kept ? v.y : kFar;
-                d[64] = kept ? v.z : kFar;
+                d[16] = kept ? v.y : kFar;
+                d[32] = kept ? v.z : kFar;
             }
-            if (adj && cis == kMaxSlots - 1) {
-                const float4 v = cj < cnt ? st.xl[cj] : make_float4(0.f, 0.f, 0.f, 0.f);
-                cl[cj] = v.x;
-                cl[32 + cj] = v.y;
-                cl[64 + cj] = v.z;
-            }
-            asm volatile("bar.sync 1, %0;" :: "r"(kTcCompute) : "memory");   // compute warps only
-            // B operand of this stage (sources beyond cnt are zero)
-            {
-                float v[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) v[c] = (bcol && bj + c < cnt) ? st.qraw[qoff + c * a.nrhs] : 0.f;
-                float4 h, l;
-                h.x = __uint_as_float(to_tf32(v[0]));
-                h.y = __uint_as_float(to_tf32(v[1]));
-                h.z = __uint_as_float(to_tf32(v[2]));
-                h.w = __uint_as_float(to_tf32(v[3]));
-                l = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
-                *reinterpret_cast<float4*>(&st.bhi[boffw]) = h;
-                *reinterpret_cast<float4*>(&st.blo[boffw]) = l;
-            }
+            __syncwarp();
             if (u >= 2) drain(u - 2);                          // frees accumulator (u & 1)
             uint32_t ghi[16], glo[16];
-            const int j0 = 16 * half;
-            const float* c = cx + myslot * kSlotStride;
+            const float* c = wc + myloc * kWarpSlotFloats;
             if (__all_sync(0xffffffffu, keep == 0)) {
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) ghi[jj] = glo[jj] = 0u;
             } else if (adj) {
-                tc_eval16<KIND, true>(c, cl, j0, nt, nl, ghi, glo);
+                tc_eval16<KIND, true>(c, st.xl, j0, nt, nl, ghi, glo);
             } else {
-                tc_eval16<KIND, false>(c, cl, j0, nt, nl, ghi, glo);
+                tc_eval16<KIND, false>(c, st.xl, j0, nt, nl, ghi, glo);
             }
             // A buffer u % kNA was last read by MMA(u - kNA), complete since drain(u - 2)
             const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + 16u * half;
             tmem_st16(acol, ghi);
             tmem_st16(acol + 32u, glo);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(sm_addr(&S.afull[s]));
         }
