@@ -197,7 +197,6 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     TcArgs t;
     t.items = dp->tc_items;
     t.tiles = dp->tc_tiles;
-    t.list = dp->tc_list;
     t.X = (const float4*)b->X;
     t.Xlo = (const float4*)b->Xlo;
     t.B = dp->tc_b;
@@ -352,7 +351,6 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
         dp->n_mix = (int64_t)lay.mix_items.size();
         dp->tc_tiles = upload(lay.tc_tiles, dp->bytes);
         dp->tc_items = upload(lay.tc_items, dp->bytes);
-        dp->tc_list = upload(lay.tc_list, dp->bytes);
         dp->n_tc = (int64_t)lay.tc_items.size();
         if (dp->n_tc > 0 && !dp->cplx) {
             dp->chunk_start = upload(lay.chunk_start, dp->bytes);
@@ -384,7 +382,7 @@ void device_plan_destroy(DevicePlan* dp) {
     cudaSetDevice(dp->device);
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
-                    dp->tc_items, dp->tc_list, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
+                    dp->tc_items, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
                     dp->chunk_start, dp->chunk_cnt, dp->tc_b};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)

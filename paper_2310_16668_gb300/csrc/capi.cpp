@@ -87,7 +87,7 @@ void finalize(skel_plan* h, const skel_options* opts) {
     h->pairs_direct = lay.pairs_direct;
     h->pairs_far = lay.pairs_far;
     h->n_tc_items = (int64_t)lay.tc_items.size();
-    h->n_tc_tiles = (int64_t)lay.tc_list.size();
+    h->n_tc_tiles = (int64_t)lay.tc_tiles.size();
     h->n_mix_items = (int64_t)lay.mix_items.size();
     h->pairs_tc = lay.pairs_tc;
     if (!h->host_only) h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max);

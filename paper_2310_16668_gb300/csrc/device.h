@@ -41,7 +41,6 @@ struct DevicePlan {
     int64_t n_mix = 0;
     SrcTile* tc_tiles = nullptr;
     TcItem* tc_items = nullptr;
-    int32_t* tc_list = nullptr;
     int64_t n_tc = 0;
     int64_t tc_n_slots = 0;
     int64_t* tc_part_ptr = nullptr;        // per entry: its partial sums (tensor-core mode)

@@ -124,7 +124,7 @@ struct TcItem {                         // 64 bytes
     int32_t nrows;                      // valid rows (<= 128)
     int32_t nslot;
     int32_t slot_start[kMaxSlots + 1];  // first row of each slot (may be < 0 for a box's later rows)
-    int32_t list_lo, list_hi;           // range in tc_list (indices of the tiles it needs)
+    int32_t list_lo, list_hi;           // its tiles: [list_lo, list_hi) of tc_tiles
     int32_t slot;                       // first of its 4 partial-sum slots (32 rows each)
 };
 static_assert(sizeof(TcItem) == 64, "TcItem layout");
@@ -155,7 +155,6 @@ struct Layout {
     // leaves, CUDA-core items for the remaining small boxes
     std::vector<WorkItem> mix_items;
     std::vector<SrcTile> tc_tiles;
-    std::vector<int32_t> tc_list;
     std::vector<TcItem> tc_items;
     std::vector<int64_t> tc_part_ptr, tc_part_idx;
     int64_t tc_n_slots = 0;

@@ -241,7 +241,6 @@ void build_layout(const Plan& p, Layout& lay) {
     simt_items([&](int64_t b) { return !is_tc(b) && !packable(b); }, lay.mix_items, 0);
     int64_t slot = (int64_t)lay.mix_items.size();
     lay.tc_tiles.clear();
-    lay.tc_list.clear();
     lay.tc_items.clear();
     lay.pairs_tc = 0;
     lay.box_chunk0.assign(nb, -1);
@@ -286,7 +285,7 @@ void build_layout(const Plan& p, Layout& lay) {
         it.nrows = nrows;
         it.nslot = nslot;
         for (int j = 0; j <= nslot; ++j) it.slot_start[j] = sst[j];
-        it.list_lo = (int32_t)lay.tc_list.size();
+        it.list_lo = (int32_t)lay.tc_tiles.size();
         for (size_t k = 0; k < srcs.size(); ++k) {
             const int64_t src = srcs[k].first;
             const int32_t* ssS = &lay.slot_start[src * (kMaxSlots + 1)];
@@ -311,19 +310,18 @@ void build_layout(const Plan& p, Layout& lay) {
                     if (rows_is > 0) lay.pairs_tc += (int64_t)rows_is * __builtin_popcount(st.keep[is]);
                 }
                 if (!any) continue;
-                if (lay.tc_list.size() - it.list_lo == (size_t)kTcMaxTiles) {   // split long lists
-                    it.list_hi = (int32_t)lay.tc_list.size();
+                if (lay.tc_tiles.size() - it.list_lo == (size_t)kTcMaxTiles) {   // split long lists
+                    it.list_hi = (int32_t)lay.tc_tiles.size();
                     it.slot = (int32_t)slot;
                     lay.tc_items.push_back(it);
                     for (int32_t r = 0; r < nrows; ++r) parts.push_back({row_off + r, slot * kChunk + r});
                     slot += kTcRows / kChunk;
                     it.list_lo = it.list_hi;
                 }
-                lay.tc_list.push_back((int32_t)lay.tc_tiles.size());
                 lay.tc_tiles.push_back(st);
             }
         }
-        it.list_hi = (int32_t)lay.tc_list.size();
+        it.list_hi = (int32_t)lay.tc_tiles.size();
         it.slot = (int32_t)slot;
         lay.tc_items.push_back(it);
         for (int32_t r = 0; r < nrows; ++r) parts.push_back({row_off + r, slot * kChunk + r});

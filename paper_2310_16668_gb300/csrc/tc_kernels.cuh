@@ -53,7 +53,9 @@
 
 namespace skel {
 
-constexpr int kTcCompute = 256;                // compute threads (8 warps)
+constexpr int kTpr = 2;                        // compute threads per target row
+constexpr int kTcCompute = 128 * kTpr;         // compute threads
+constexpr int kSrcPerThread = 32 / kTpr;       // sources of a tile each compute thread evaluates
 constexpr int kTcThreads = kTcCompute + 64;    // + the producer warp and the MMA warp
 constexpr int kTcN = 32;                       // right-hand sides per pass (MMA N)
 constexpr int kTcMaxRhs = 64;                  // charge row length the stages hold
@@ -73,9 +75,9 @@ struct alignas(128) TcStage {
     float4 xl[32];                             // lo parts (touching-leaf tiles)
 };
 // per compute warp: for each target slot its 32 rows touch, the coordinates
-// of its 16 sources, one array per axis (x at 0, y at 16, z at 32); a source
-// the slot skips sits at kFar
-constexpr int kWarpSlotFloats = 48;
+// of its kSrcPerThread sources, one array per axis (x, y, z); a source the
+// slot skips sits at kFar
+constexpr int kWarpSlotFloats = 3 * kSrcPerThread;
 constexpr float kFar = 1e30f;                  // r^2 from here overflows to +inf: 1/r = 0
 struct TcShared {
     TcStage st[kNS];
@@ -89,8 +91,7 @@ static_assert(sizeof(TcShared) <= kTcSmemRequest, "shared memory plan");
 
 struct TcArgs {
     const TcItem* items;
-    const SrcTile* tiles;
-    const int32_t* list;
+    const SrcTile* tiles;                      // item i's tiles: [list_lo, list_hi) of this array
     const float4* X;
     const float4* Xlo;
     const float* B;                            // per source chunk: B hi (1024 floats), then B lo
@@ -180,6 +181,18 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
                     "r"(v[15]) : "memory");
 }
 
+// issue only; the values are valid after tcgen05.wait::ld
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr) : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                  "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -221,10 +234,10 @@ template <int KIND, bool ADJ> __device__ __forceinline__ float tc_green(float r2
 __device__ __forceinline__ uint32_t tf32_hi(float g) { return (__float_as_uint(g) + 0x1000u) & 0xFFFFE000u; }
 
 // 16 sources (j0 .. j0+15) against this thread's target, two sources per
-// paired FP32 instruction. c: this row's slot copy of the 16 coordinates (per
-// axis); xl: the stage's lo parts (touching-leaf tiles); nt / nl: the negated
-// target coordinates.
-template <int KIND, bool ADJ>
+// paired FP32 instruction. c: this row's slot copy of these 16 coordinates
+// (axes AX floats apart); xl: the stage's lo parts (touching-leaf tiles);
+// nt / nl: the negated target coordinates.
+template <int KIND, bool ADJ, int AX>
 __device__ __forceinline__ void tc_eval16(const float* c, const float4* xl, int j0, float4 nt, float4 nl,
                                           uint32_t* ghi, uint32_t* glo) {
     const float2 ntx = make_float2(nt.x, nt.x), nty = make_float2(nt.y, nt.y), ntz = make_float2(nt.z, nt.z);
@@ -234,8 +247,8 @@ __device__ __forceinline__ void tc_eval16(const float* c, const float4* xl, int 
     for (int p = 0; p < 8; ++p) {
         const int jj = 2 * p;
         float2 dx = __fadd2_rn(*reinterpret_cast<const float2*>(&c[jj]), ntx);
-        float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(&c[16 + jj]), nty);
-        float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(&c[32 + jj]), ntz);
+        float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(&c[AX + jj]), nty);
+        float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(&c[2 * AX + jj]), ntz);
         if (ADJ) {
             const float4 l0 = xl[j0 + jj], l1 = xl[j0 + jj + 1];
             dx = __fadd2_rn(dx, __fadd2_rn(make_float2(l0.x, l1.x), nlx));
@@ -318,36 +331,43 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
     bool err = false;
 
     if (warp == kTcCompute / 32) {
-        // ---------------- producer (one thread): bulk copies up to kNS tiles ahead ----------------
-        if (lane == 0) {
-            const SrcTile* gnext = ntile > 0 ? a.tiles + a.list[list_lo] : nullptr;
-            int64_t n_start = gnext ? gnext->start : 0;
-            int n_cnt = gnext ? gnext->cnt : 0, n_flags = gnext ? gnext->flags : 0;
-            int n_chunk = gnext ? gnext->chunk : 0;
-            for (int t = 0; t < ntile; ++t) {
-                const int s = t % kNS;
-                const SrcTile* g = gnext;
-                const int64_t start = n_start;
-                const int cnt = n_cnt;
-                const bool adj = (n_flags & TASK_ADJ) != 0;
-                const float* bsrc = a.B + (int64_t)n_chunk * 2048;
-                if (t + 1 < ntile) {                         // prefetch the next descriptor
-                    gnext = a.tiles + a.list[list_lo + t + 1];
-                    n_start = gnext->start;
-                    n_cnt = gnext->cnt;
-                    n_flags = gnext->flags;
-                    n_chunk = gnext->chunk;
-                }
-                if (t >= kNS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNS) / kNS) & 1))) err = true;
-                const uint32_t bytes = 64u + 16u * cnt * (adj ? 2u : 1u) + 2u * 4096u;
-                const uint32_t bar = sm_addr(&S.full[s]);
-                mbar_arrive_tx(bar, bytes);
-                bulk_g2s(sm_addr(S.st[s].bhi), bsrc, 4096u, bar);
-                bulk_g2s(sm_addr(S.st[s].blo), bsrc + 1024, 4096u, bar);
-                bulk_g2s(sm_addr(&S.st[s].tile), g, 64u, bar);
-                bulk_g2s(sm_addr(S.st[s].xh), a.X + start, 16u * cnt, bar);
-                if (adj) bulk_g2s(sm_addr(S.st[s].xl), a.Xlo + start, 16u * cnt, bar);
+        // ---------------- producer warp: bulk copies up to kNS tiles ahead ----------------
+        // the lanes fetch the descriptors of 32 tiles at a time; lane 0
+        // issues each tile's copies
+        for (int t0 = 0; t0 < ntile; t0 += 32) {
+            int64_t d_start = 0;
+            int d_cnt = 0, d_flags = 0, d_chunk = 0;
+            if (t0 + lane < ntile) {
+                const SrcTile* g = a.tiles + list_lo + t0 + lane;
+                d_start = g->start;
+                d_cnt = g->cnt;
+                d_flags = g->flags;
+                d_chunk = g->chunk;
             }
+            const int nb = min(32, ntile - t0);
+            for (int i = 0; i < nb; ++i) {
+                const int t = t0 + i;
+                const int s = t % kNS;
+                const int64_t start = __shfl_sync(0xffffffffu, d_start, i);
+                const int cnt = __shfl_sync(0xffffffffu, d_cnt, i);
+                const bool adj = (__shfl_sync(0xffffffffu, d_flags, i) & TASK_ADJ) != 0;
+                const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
+                if (t >= kNS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNS) / kNS) & 1))) err = true;
+                if (lane == 0) {
+                    const float* bsrc = a.B + (int64_t)chunk * 2048;
+                    const uint32_t bytes = 64u + 16u * cnt * (adj ? 2u : 1u) + 2u * 4096u;
+                    const uint32_t bar = sm_addr(&S.full[s]);
+                    mbar_arrive_tx(bar, bytes);
+                    bulk_g2s(sm_addr(S.st[s].bhi), bsrc, 4096u, bar);
+                    bulk_g2s(sm_addr(S.st[s].blo), bsrc + 1024, 4096u, bar);
+                    bulk_g2s(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar);
+                    bulk_g2s(sm_addr(S.st[s].xh), a.X + start, 16u * cnt, bar);
+                    if (adj) bulk_g2s(sm_addr(S.st[s].xl), a.Xlo + start, 16u * cnt, bar);
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0) {
             // all bulk copies have landed before the CTA may exit
             for (int t = (ntile > kNS ? ntile - kNS : 0); t < ntile; ++t)
                 if (!mbar_wait(sm_addr(&S.full[t % kNS]), (uint32_t)((t / kNS) & 1))) err = true;
@@ -398,54 +418,76 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         const int nsw = max(1, s_hi - s_lo + 1);
         const int myloc = min(max(myslot - s_lo, 0), kMaxSlots - 1);
         float* wc = S.wc[warp];
-        // each half of the compute warps owns 16 of the 32 accumulator columns
-        float acc[kTcN / 2];
+        constexpr int kCols = kTcN / kTpr;                     // accumulator columns this thread owns
+        constexpr uint32_t kKeepMask = kSrcPerThread == 32 ? 0xFFFFFFFFu : (1u << kSrcPerThread) - 1u;
+        const int j0 = kSrcPerThread * half;
+        float acc[kCols];
 #pragma unroll
-        for (int c = 0; c < kTcN / 2; ++c) acc[c] = 0.f;
+        for (int c = 0; c < kCols; ++c) acc[c] = 0.f;
         auto drain = [&](int m) {                              // add tile m's accumulator
             if (!mbar_wait(sm_addr(&S.empty[m % kNS]), (uint32_t)((m / kNS) & 1))) err = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint32_t v[kTcN / 2];
-            tmem_ld16(tbase + lane_off + kColD + 32u * (m & 1) + 16u * half, v);
+            uint32_t v[kCols];
+            const uint32_t col = tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kCols * half);
+            if constexpr (kCols == 32) tmem_ld32(col, v);
+            else tmem_ld16(col, v);
 #pragma unroll
-            for (int c = 0; c < kTcN / 2; ++c) acc[c] += __uint_as_float(v[c]);
+            for (int c = 0; c < kCols; ++c) acc[c] += __uint_as_float(v[c]);
         };
         for (int u = 0; u < ntile; ++u) {
             const int s = u % kNS;
+            // tile u - 2's accumulator (frees accumulator u & 1): its load is
+            // issued now and added after the coordinate copy
+            uint32_t dv[kCols];
+            if (kCols == 32 && u >= 2) {
+                const int m = u - 2;
+                if (!mbar_wait(sm_addr(&S.empty[m % kNS]), (uint32_t)((m / kNS) & 1))) err = true;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                tmem_ld32_issue(tbase + lane_off + kColD + 32u * (m & 1), dv);
+            }
             if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNS) & 1))) err = true;
             TcStage& st = S.st[s];
             const bool adj = (st.tile.flags & TASK_ADJ) != 0;
-            const uint32_t keep = valid ? (st.tile.keep[myslot] >> (16 * half)) & 0xFFFFu : 0u;
-            const int j0 = 16 * half;
-            // this warp's copy of its 16 sources per slot and axis; a skipped
+            const uint32_t keep = valid ? (st.tile.keep[myslot] >> j0) & kKeepMask : 0u;
+            // this warp's copy of its sources per slot and axis; a skipped
             // source (and any j >= cnt, never kept) sits at kFar. Every lane
             // has finished reading the previous tile's copy.
             __syncwarp();
-            for (int p = lane; p < nsw * 16; p += 32) {
-                const int ls = p >> 4, jj = p & 15;
+            for (int p = lane; p < nsw * kSrcPerThread; p += 32) {
+                const int ls = p / kSrcPerThread, jj = p % kSrcPerThread;
                 const float4 v = st.xh[j0 + jj];
                 const bool kept = (st.tile.keep[s_lo + ls] >> (j0 + jj)) & 1u;
                 float* d = wc + ls * kWarpSlotFloats + jj;
                 d[0] = kept ? v.x : kFar;
-                d[16] = kept ? v.y : kFar;
-                d[32] = kept ? v.z : kFar;
+                d[kSrcPerThread] = kept ? v.y : kFar;
+                d[2 * kSrcPerThread] = kept ? v.z : kFar;
             }
             __syncwarp();
-            if (u >= 2) drain(u - 2);                          // frees accumulator (u & 1)
-            uint32_t ghi[16], glo[16];
-            const float* c = wc + myloc * kWarpSlotFloats;
-            if (__all_sync(0xffffffffu, keep == 0)) {
+            if (kCols == 32 && u >= 2) {
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) ghi[jj] = glo[jj] = 0u;
-            } else if (adj) {
-                tc_eval16<KIND, true>(c, st.xl, j0, nt, nl, ghi, glo);
-            } else {
-                tc_eval16<KIND, false>(c, st.xl, j0, nt, nl, ghi, glo);
+                for (int c = 0; c < kCols; ++c) acc[c] += __uint_as_float(dv[c]);
+            } else if (u >= 2) {
+                drain(u - 2);
             }
             // A buffer u % kNA was last read by MMA(u - kNA), complete since drain(u - 2)
-            const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + 16u * half;
-            tmem_st16(acol, ghi);
-            tmem_st16(acol + 32u, glo);
+            const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + (uint32_t)j0;
+            const float* c = wc + myloc * kWarpSlotFloats;
+            const bool none = __all_sync(0xffffffffu, keep == 0);
+#pragma unroll
+            for (int g = 0; g < kSrcPerThread / 16; ++g) {
+                uint32_t ghi[16], glo[16];
+                if (none) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) ghi[jj] = glo[jj] = 0u;
+                } else if (adj) {
+                    tc_eval16<KIND, true, kSrcPerThread>(c + 16 * g, st.xl, j0 + 16 * g, nt, nl, ghi, glo);
+                } else {
+                    tc_eval16<KIND, false, kSrcPerThread>(c + 16 * g, st.xl, j0 + 16 * g, nt, nl, ghi, glo);
+                }
+                tmem_st16(acol + 16u * g, ghi);
+                tmem_st16(acol + 32u + 16u * g, glo);
+            }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(sm_addr(&S.afull[s]));
@@ -454,9 +496,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         if (valid) {
             const float scale = (float)green_scale<KIND>();
             const int64_t base = ((int64_t)(out_slot + (row >> 5)) * kChunk + (row & 31)) * a.nrhs;
-            const int c0 = a.r0 + 16 * half;
+            const int c0 = a.r0 + kCols * half;
 #pragma unroll
-            for (int c = 0; c < kTcN / 2; ++c)
+            for (int c = 0; c < kCols; ++c)
                 if (c0 + c < a.nrhs) a.partial[base + c0 + c] = scale * acc[c];
         }
     }
