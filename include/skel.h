@@ -51,9 +51,9 @@ extern "C" {
 #define SKEL_FP64     0   /* FP64 arithmetic, double charges/potentials            */
 #define SKEL_FP32     1   /* FP32 arithmetic on the CUDA cores, float in/out       */
 #define SKEL_FP32_TC  2   /* FP32 kernel evaluation, tensor-core contractions over
-                             right-hand sides (3-pass TF32 split, FP32 accumulate);
-                             real kernels with nrhs a multiple of 4 — otherwise the
-                             FP32 CUDA-core path runs */
+                             right-hand sides (3-pass TF32 split, FP32 accumulate)
+                             in passes of 32 columns; real kernels with nrhs >= 4 —
+                             otherwise the FP32 CUDA-core path runs */
 
 typedef struct skel_plan* skel_handle;
 
@@ -229,8 +229,7 @@ int skel_neighbors_export(skel_handle h, int which, int64_t* ptr, int64_t* list)
  * are created here, not in the apply). m = 0 turns it off. skel_last_timings
  * waits for the captured applies and returns each phase's duration summed
  * over them, in milliseconds, with the number of kernels they launched and
- * the number of applies captured. An FP32_TC apply of more than 64
- * right-hand sides runs in chunks of 64, each captured as one apply.
+ * the number of applies captured.
  */
 typedef struct {
     double ms[6];          /* permute_in, upward, translations, reduce, downward, permute_out */

@@ -446,15 +446,9 @@ void device_apply(DevicePlan* dp, const void* q, void* u, int nrhs, int precisio
         else run_apply<double, false>(dp, dp->p64, q, u, nrhs, transpose, false, st);
     } else if (dp->cplx) {
         run_apply<float, true>(dp, dp->p32, q, u, nrhs, transpose, false, st);
-    } else if (precision == 2 && nrhs % 4 == 0) {
-        // tensor-core path: at most kTcMaxRhs right-hand sides per apply
-        const float* qf = (const float*)q;
-        float* uf = (float*)u;
-        for (int c0 = 0; c0 < nrhs; c0 += kTcMaxRhs) {
-            const int nc = std::min(kTcMaxRhs, nrhs - c0);
-            run_apply<float, false>(dp, dp->p32, qf + (int64_t)c0 * dp->N, uf + (int64_t)c0 * dp->N, nc, transpose,
-                                    true, st);
-        }
+    } else if (precision == 2 && nrhs >= 4) {
+        // tensor-core translations, one pass per 32 right-hand sides
+        run_apply<float, false>(dp, dp->p32, q, u, nrhs, transpose, true, st);
     } else {
         run_apply<float, false>(dp, dp->p32, q, u, nrhs, transpose, false, st);
     }

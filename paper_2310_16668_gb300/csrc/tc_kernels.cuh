@@ -58,7 +58,6 @@ constexpr int kTcCompute = 128 * kTpr;         // compute threads
 constexpr int kSrcPerThread = 32 / kTpr;       // sources of a tile each compute thread evaluates
 constexpr int kTcThreads = kTcCompute + 64;    // + the producer warp and the MMA warp
 constexpr int kTcN = 32;                       // right-hand sides per pass (MMA N)
-constexpr int kTcMaxRhs = 64;                  // charge row length the stages hold
 constexpr int kNS = 6;                         // data stages (bulk-copy destinations)
 constexpr int kNA = 3;                         // A-operand buffers in tensor memory
 constexpr uint32_t kTmemCols = 256;
