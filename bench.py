@@ -41,14 +41,25 @@ SM_COUNT = 152
 MUFU_PER_SM_CLK = 16      # MUFU (rsqrt) results per SM per clock
 
 
+# --workload name -> workload in paper_2310_16668_gb300.workloads
+WORKLOAD_KEYS = {"laplace3d": "LAPLACE3D_1M", "sphere_cluster": "LAPLACE3D_ADAPTIVE_4M",
+                 "helmholtz3d": "HELMHOLTZ3D_1M", "laplace2d": "LAPLACE2D_16K", "curves2d": "CURVES2D_256"}
+
+
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp32_tc", choices=["fp32_tc", "fp32", "fp64"])
-    p.add_argument("--nrhs", type=int, default=32)
+    p.add_argument("--workload", default="laplace3d", choices=list(WORKLOAD_KEYS),
+                   help="laplace3d: the headline (3D Laplace, N = 2^20 uniform); sphere_cluster: 3D Laplace, "
+                        "N = 2^22 on a sphere plus a Gaussian cluster; helmholtz3d: kappa = 25, N = 2^20; "
+                        "laplace2d: N = 16384; curves2d: 256 independent 2D point sets on closed curves, "
+                        "applied as one CUDA graph")
+    p.add_argument("--precision", default=None, choices=["fp32_tc", "fp32", "fp64"],
+                   help="default: fp32_tc for the Laplace kernels, fp32 (complex64) for Helmholtz")
+    p.add_argument("--nrhs", type=int, default=None, help="default 32 (curves2d: 4)")
     p.add_argument("--tol", type=float, default=None)
     p.add_argument("--n", type=int, default=None, help="override N (testing only)")
     p.add_argument("--no-e2e", action="store_true")
@@ -172,11 +183,11 @@ def whole_job_value(n: int, nrhs: int, world: int, ms_step: float) -> float:
     return n * nrhs * world / (ms_step * 1e-3) / 1e6
 
 
-def oracle_direct_sample(x, q0, targets):
-    """The oracle's FP64 direct sum at `targets` (cpu_baseline leg)."""
+def oracle_direct_sample(kind, x, q0, targets, kappa=0.0):
+    """The oracle's FP64 (complex128) direct sum at `targets` (cpu_baseline leg)."""
     from oracle import direct
     t0 = time.perf_counter()
-    u = direct.direct_sum("laplace3d", x, q0, targets=targets)
+    u = direct.direct_sum(kind, x, q0, targets=targets, kappa=kappa)
     return u, time.perf_counter() - t0, direct.num_threads()
 
 
@@ -184,37 +195,128 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    import dataclasses
     from oracle import direct
     from paper_2310_16668_gb300 import workloads as W
-    wl = W.LAPLACE3D_1M
-    n = args.n or wl.n
-    x = W.points_uniform(n, 3, wl.seed)
-    q0 = W.charges_normal(n, 1, wl.seed + 1000)[:, 0]
+    if args.workload == "curves2d":
+        # the oracle on the largest of the curve sets
+        cs = W.CURVES2D_256
+        i = int(np.argmax(cs.sizes()))
+        wl0 = W.Workload(cs.name, "laplace2d", 2, int(cs.sizes()[i]), cs.leaf, cs.tol, 1, charges="uniform")
+        x = W.points_curve(wl0.n, cs.seed * 100003 + i)
+        q0 = np.ascontiguousarray(cs.make_charges(i, wl0.n, 1)[:, 0])
+        wl, n = wl0, wl0.n
+    else:
+        wl0 = getattr(W, WORKLOAD_KEYS[args.workload])
+        n = args.n or wl0.n
+        wl = dataclasses.replace(wl0, n=n)
+        x = wl.make_points()
+        q0 = np.ascontiguousarray(wl.make_charges(1)[:, 0])
     per_step = max(16, min(1024, int(1e9 // n)))       # ~1e9 pair evaluations per step
     rng = np.random.default_rng(7)
     for _ in range(args.warmup):
-        direct.direct_sum("laplace3d", x, q0, targets=rng.choice(n, per_step, replace=False))
+        direct.direct_sum(wl.kernel, x, q0, targets=rng.choice(n, per_step, replace=False), kappa=wl.kappa)
     times = []
     for _ in range(args.steps):
         tg = rng.choice(n, per_step, replace=False)
         t0 = time.perf_counter()
-        direct.direct_sum("laplace3d", x, q0, targets=tg)
+        direct.direct_sum(wl.kernel, x, q0, targets=tg, kappa=wl.kappa)
         times.append(time.perf_counter() - t0)
     T = sum(times)
     value = per_step * args.steps / T / 1e6
     cores = direct.num_threads()
+    metric = METRIC if args.workload == "laplace3d" else f"Mpts·RHS/s, {wl0.name} apply"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": metric, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl.name, "N": n, "nrhs": 1, "sample_targets_per_step": per_step,
+        "config": {"workload": wl0.name, "N": n, "nrhs": 1, "sample_targets_per_step": per_step,
                    "method": "oracle FP64 direct sum (plain C, OpenMP), throughput extrapolated per target"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} random targets x {n} sources x 1 RHS per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_curves(args):
+    """Batched 2D Laplace: every set's apply (and the batched adjoint) captured
+    into one CUDA graph; value = total points x right-hand sides / replay time."""
+    import torch
+    from paper_2310_16668_gb300 import SkelBatch
+    from paper_2310_16668_gb300 import workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cs = W.CURVES2D_256
+    nrhs = args.nrhs or cs.nrhs
+    prec = args.precision or "fp32_tc"
+    sets = cs.make_point_sets()
+    t0 = time.perf_counter()
+    batch = SkelBatch(sets, "laplace2d", args.tol or cs.tol, cs.leaf, nrhs_max=nrhs)
+    t_build = time.perf_counter() - t0
+    ntot = int(sum(batch.sizes))
+    rdt = torch.float64 if prec == "fp64" else torch.float32
+    qs = [torch.from_numpy(np.ascontiguousarray(cs.make_charges(i, len(x), nrhs).T)).to(dev, rdt)
+          for i, x in enumerate(sets)]
+    us = [torch.empty_like(q) for q in qs]
+    gs = [torch.empty_like(q).normal_() for q in qs]
+    vs = [torch.empty_like(q) for q in qs]
+    g_fwd = batch.capture(qs, us, nrhs, prec)
+    g_both = batch.capture(qs, us, nrhs, prec, adjoint_qs=gs, adjoint_us=vs)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(g, steps):
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_fwd = timed(g_fwd, args.steps)
+    clk = clocks.stop()
+    ms_both = timed(g_both, args.steps)
+    value = ntot * nrhs / (ms_fwd * 1e-3) / 1e6
+    g_fwd.replay()
+    torch.cuda.synchronize()
+    # errors: the largest sets' RHS 0 at 1024 sampled targets against the oracle
+    from oracle import direct
+    errs, t_cpu, n_eval = [], 0.0, 0
+    for i in np.argsort(batch.sizes)[-4:]:
+        x = sets[i]
+        tg = np.sort(np.random.default_rng(int(i)).choice(len(x), min(1024, len(x)), replace=False))
+        q0 = qs[i][0].double().cpu().numpy()
+        t1 = time.perf_counter()
+        ref = direct.direct_sum("laplace2d", x, q0, targets=tg)
+        t_cpu += time.perf_counter() - t1
+        n_eval += len(tg)
+        errs.append(float(np.abs(us[i][0].double().cpu().numpy()[tg] - ref).max() / np.abs(ref).max()))
+    line = {
+        "metric": f"Mpts·RHS/s, {cs.name} batched apply (CUDA graph of all sets)", "value": value,
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fwd,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": cs.name, "n_sets": len(sets), "N_total": ntot, "N_min": int(min(batch.sizes)),
+                   "N_max": int(max(batch.sizes)), "nrhs": nrhs, "leaf": cs.leaf, "tol": args.tol or cs.tol,
+                   "precision": prec, "t_build_s": t_build},
+        "forward_and_adjoint_ms": ms_both,
+        "relerr_largest_sets": errs,
+        "cpu_baseline": {"value": n_eval / t_cpu / 1e6, "unit": UNIT, "cores": direct.num_threads(),
+                         "kind": "oracle", "sample": f"FP64 direct sum at {n_eval} targets of the 4 largest sets"},
+        "gpu_launches": None,
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons")},
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
     return 0
 
 
@@ -232,22 +334,28 @@ def run_ours(args):
     from paper_2310_16668_gb300 import SkelFMM
     from paper_2310_16668_gb300 import workloads as W
 
-    wl = W.LAPLACE3D_1M
-    n = args.n or wl.n
-    tol = args.tol or wl.tol
-    nrhs = args.nrhs
-    seed = replica_seed(wl.seed, rank)  # independent replica per rank
-    x = W.points_uniform(n, 3, seed)
-    q = W.charges_normal(n, nrhs, seed + 1000)
+    import dataclasses
+    wl0 = getattr(W, WORKLOAD_KEYS[args.workload])
+    n = args.n or wl0.n
+    tol = args.tol or wl0.tol
+    nrhs = args.nrhs or 32
+    # independent replica per rank: the workload's recipe with its own seed
+    wl = dataclasses.replace(wl0, n=n, seed=replica_seed(wl0.seed, rank))
+    x = wl.make_points()
+    q = wl.make_charges(nrhs)
+    cplx = wl.kernel == "helmholtz3d"
     threads = max(1, (os.cpu_count() or 1) // max(1, int(os.environ.get("LOCAL_WORLD_SIZE", world))))
     t0 = time.perf_counter()
-    fmm = SkelFMM(x, wl.kernel, tol, wl.leaf, nrhs_max=nrhs, num_threads=threads)
+    fmm = SkelFMM(x, wl.kernel, tol, wl.leaf, kappa=wl.kappa, nrhs_max=nrhs, num_threads=threads)
     t_build = time.perf_counter() - t0
     info = fmm.info()
     pairs = info["pairs_direct"] + info["pairs_far"]
 
-    prec = args.precision
-    rdt = torch.float64 if prec == "fp64" else torch.float32
+    prec = args.precision or ("fp32" if cplx else "fp32_tc")
+    if cplx:
+        rdt = torch.complex128 if prec == "fp64" else torch.complex64
+    else:
+        rdt = torch.float64 if prec == "fp64" else torch.float32
     # column-major n x nrhs device buffers (each right-hand side contiguous)
     qc = torch.from_numpy(np.ascontiguousarray(q.T)).to(dev, rdt)
     uc = torch.empty_like(qc)
@@ -282,15 +390,15 @@ def run_ours(args):
     value = whole_job_value(n, nrhs, world, ms_step)
 
     # errors against the oracle's direct sum on sampled targets (RHS 0)
-    u_main = uc[0].double().cpu().numpy()
-    sample = wl.make_sample() if n == wl.n else np.sort(np.random.default_rng(5).choice(n, min(4096, n), replace=False))
+    u_main = uc[0].cpu().numpy().astype(np.complex128 if cplx else np.float64)
+    sample = wl.make_sample() if n == wl0.n else np.sort(np.random.default_rng(5).choice(n, min(4096, n), replace=False))
     out = {}
     if rank == 0 and not args.no_cpu_baseline:
-        # the oracle on 65,536 targets (about 10 s on 16 cores) that include the
-        # 4096 error-check targets
-        extra = np.random.default_rng(11).choice(n, min(n, 65536), replace=False)
+        # the oracle on about 2^36 / N targets (65,536 at N = 2^20: about 10 s
+        # on 16 cores) that include the 4096 error-check targets
+        extra = np.random.default_rng(11).choice(n, min(n, max(4096, (1 << 36) // n)), replace=False)
         big = np.union1d(sample, extra)
-        ref_big, t_cpu, cores = oracle_direct_sample(x, q[:, 0], big)
+        ref_big, t_cpu, cores = oracle_direct_sample(wl.kernel, x, np.ascontiguousarray(q[:, 0]), big, wl.kappa)
         ref = ref_big[np.searchsorted(big, sample)]
         scale = np.abs(ref).max()
         out["relerr"] = float(np.abs(u_main[sample] - ref).max() / scale)
@@ -303,7 +411,7 @@ def run_ours(args):
     # plain FP64 single-RHS apply on the same plan (the comparator)
     fp64 = None
     if not args.no_fp64 and prec != "fp64":
-        q64 = torch.from_numpy(np.ascontiguousarray(q[:, :1].T)).to(dev, torch.float64)
+        q64 = torch.from_numpy(np.ascontiguousarray(q[:, :1].T)).to(dev, torch.complex128 if cplx else torch.float64)
         u64 = torch.empty_like(q64)
         k64 = max(1, min(args.steps, 5))
         for _ in range(2):
@@ -357,12 +465,14 @@ def run_ours(args):
     near_ms_per_launch = phases["main_near"] / phases["main_launches"]
     achieved = units / (near_ms_per_launch * 1e-3) / 1e9
     sm_mhz = clk.get("sm_mhz") or 2070.0
+    # one MUFU operation per evaluation (reciprocal square root in 3D, the
+    # logarithm in 2D); for Helmholtz the same figure is an upper bound
     peak = SM_COUNT * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e9
     peaks, peaks_kind = measured_peaks()
     roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
             "frac": achieved / peak, "traffic": ncu_traffic(kname, prec),
-            "peak_basis": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU rsqrt/clk x median SM clock under load "
-                          f"({sm_mhz:.0f} MHz)",
+            "peak_basis": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU ops/clk x median SM clock under load "
+                          f"({sm_mhz:.0f} MHz), one MUFU op per kernel evaluation",
             "per_launch_ms": near_ms_per_launch, "launches_per_step": n_near,
             "algorithmic_units": f"{units} kernel evaluations per launch ({unit_note})"}
     if prec == "fp32_tc":
@@ -375,10 +485,12 @@ def run_ours(args):
         roof["tensor"] = {"achieved": tc_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc_tflops / tf32_peak,
                           "issued_tflops": issued,
                           "peak_basis": f"TF32 = 0.5 x {peaks_kind} bf16 burst ({peaks['bf16_tflops']} TFLOP/s)"}
+    metric = METRIC if args.workload == "laplace3d" else f"Mpts·RHS/s, {wl0.name} apply: {prec} vs plain FP64"
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": ("c128" if cplx else "f64") if prec == "fp64" else ("c64" if cplx else "f32"),
+        "data": "synthetic",
         "config": {"workload": wl.name, "N": n, "nrhs": nrhs, "leaf": wl.leaf, "tol": tol, "precision": prec,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2: operators + entry arrays "
@@ -407,6 +519,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "curves2d":
+        return run_curves(args)
     return run_ours(args)
 
 

@@ -137,6 +137,23 @@ int skel_apply(skel_handle h, const void* q, void* u, int nrhs, int precision,
 int skel_apply_transpose(skel_handle h, const void* ubar, void* qbar, int nrhs,
                          int precision, void* stream);
 
+/*
+ * skel_apply_batch — skel_apply (transpose = 0) or skel_apply_transpose
+ * (transpose = 1) on nsets independent plans, queued back to back on one
+ * stream with no host synchronisation, so that a whole batch of point sets
+ * (and its adjoint) can be captured into one CUDA graph.
+ *   hs         nsets handles, all with device plans on the current device
+ *   q, u       nsets device pointers each (plan i: n_i x nrhs column-major);
+ *              host pointers are rejected (no staging inside a batch)
+ *   nrhs       1 <= nrhs <= every plan's nrhs_max
+ * Every argument is checked before anything is queued (SKEL_ERR_ARG,
+ * SKEL_ERR_STATE); each plan works in its own buffers, so the sets share no
+ * memory. The paper applies one point set at a time; batching independent
+ * sets is this library's addition.
+ */
+int skel_apply_batch(const skel_handle* hs, int nsets, const void* const* q, void* const* u, int nrhs,
+                     int precision, int transpose, void* stream);
+
 /* skel_free — release the handle and all its memory; NULL is a no-op. */
 void skel_free(skel_handle h);
 

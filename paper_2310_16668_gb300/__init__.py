@@ -5,4 +5,4 @@ The compute lives in ``libskel.so`` (C-ABI in ``include/skel.h``): host FP64
 tree + interpolative decompositions, sm_103a CUDA kernels for the apply.
 This package is the thin Python binding.
 """
-from .api import SkelApply, SkelFMM, skel_apply  # noqa: F401
+from .api import SkelApply, SkelBatch, SkelFMM, skel_apply  # noqa: F401

@@ -209,6 +209,55 @@ class SkelApply(torch.autograd.Function):
         return fmm.apply_transpose(g, ctx.precision), None, None
 
 
+class SkelBatch:
+    """Many independent point sets: one plan each, applied together.
+
+    ``apply_into`` queues every set's apply (or transpose apply) on one stream
+    through ``skel_apply_batch``, without host synchronisation, so that a
+    whole batch and its adjoint can be captured into one CUDA graph
+    (``capture``).
+    """
+
+    def __init__(self, point_sets, kernel: str = "laplace2d", tol: float = 1e-7, leaf_size: int = 64,
+                 kappa: float = 0.0, nrhs_max: int = 4, num_threads: int = 0):
+        self._lib = _lib.load()
+        self.plans = [SkelFMM(p, kernel, tol, leaf_size, kappa=kappa, nrhs_max=nrhs_max, num_threads=num_threads)
+                      for p in point_sets]
+        self.sizes = [f.n for f in self.plans]
+        self._hs = (ctypes.c_void_p * len(self.plans))(*[f._h.value for f in self.plans])
+
+    def apply_into(self, qs, us, nrhs: int, precision: str = "fp32_tc", transpose: bool = False, stream=None):
+        """qs[i], us[i]: device tensors holding set i's n_i x nrhs column-major buffers."""
+        if len(qs) != len(self.plans) or len(us) != len(self.plans):
+            raise ValueError("one q and one u per set")
+        if stream is None:
+            stream = torch.cuda.current_stream(qs[0].device).cuda_stream if qs else 0
+        qp = (ctypes.c_void_p * len(qs))(*[t.data_ptr() for t in qs])
+        up = (ctypes.c_void_p * len(us))(*[t.data_ptr() for t in us])
+        check(self._lib.skel_apply_batch(self._hs, len(self.plans), qp, up, int(nrhs), _lib.PRECISIONS[precision],
+                                         int(bool(transpose)), ctypes.c_void_p(stream)))
+
+    def capture(self, qs, us, nrhs: int, precision: str = "fp32_tc", adjoint_qs=None, adjoint_us=None):
+        """A CUDA graph of the batched apply (and, if given, the batched
+        transpose apply on adjoint_qs -> adjoint_us). Replay with .replay()."""
+        self.apply_into(qs, us, nrhs, precision)              # warm-up outside the capture
+        if adjoint_qs is not None:
+            self.apply_into(adjoint_qs, adjoint_us, nrhs, precision, transpose=True)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                self.apply_into(qs, us, nrhs, precision)
+                if adjoint_qs is not None:
+                    self.apply_into(adjoint_qs, adjoint_us, nrhs, precision, transpose=True)
+        return g
+
+    def close(self):
+        for f in self.plans:
+            f.close()
+
+
 def skel_apply(q, fmm: SkelFMM, precision: str = "fp64"):
     """Differentiable apply (backward = transpose apply)."""
     return SkelApply.apply(q, fmm, precision)

@@ -125,8 +125,14 @@ void up_down(bool down, const DevicePlan* dp, int l, const S* T, S* X, int nrhs,
     const int64_t b0 = dp->up_level_ptr[l], b1 = dp->up_level_ptr[l + 1];
     const int nout = down ? dp->up_level_maxr[l] : dp->up_level_maxk[l];
     const dim3 grid((unsigned)(b1 - b0), std::max(1u, ceil_div(nout, kGT)), ceil_div(nrhs, kGT));
-    if (down) updown_kernel<S, true><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
-    else updown_kernel<S, false><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
+    const int ninner = down ? dp->up_level_maxk[l] : dp->up_level_maxr[l];
+    if (ninner > kGT) {
+        if (down) updown_kernel<S, true, true><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
+        else updown_kernel<S, false, true><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
+    } else {
+        if (down) updown_kernel<S, true, false><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
+        else updown_kernel<S, false, false><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
+    }
 }
 
 template <class S>

@@ -205,6 +205,31 @@ int skel_apply_transpose(skel_handle h, const void* ubar, void* qbar, int nrhs, 
     return do_apply(h, ubar, qbar, nrhs, precision, stream, true);
 }
 
+int skel_apply_batch(const skel_handle* hs, int nsets, const void* const* q, void* const* u, int nrhs,
+                     int precision, int transpose, void* stream) {
+    return guarded([&] {
+        if (!hs || !q || !u) throw Error(SKEL_ERR_ARG, "NULL argument");
+        if (nsets < 0) throw Error(SKEL_ERR_ARG, "nsets must be >= 0");
+        if (precision != SKEL_FP64 && precision != SKEL_FP32 && precision != SKEL_FP32_TC)
+            throw Error(SKEL_ERR_ARG, "unknown precision");
+        int cur = 0;
+        cudaGetDevice(&cur);
+        // validate everything before queueing anything
+        for (int i = 0; i < nsets; ++i) {
+            skel_handle h = hs[i];
+            if (!h) throw Error(SKEL_ERR_ARG, "handle " + std::to_string(i) + " is NULL");
+            if (h->host_only || !h->dev) throw Error(SKEL_ERR_STATE, "plan " + std::to_string(i) + " is host-only");
+            if (h->dev->device != cur) throw Error(SKEL_ERR_STATE, "plan " + std::to_string(i) + " is on another device");
+            if (nrhs < 1 || nrhs > h->nrhs_max) throw Error(SKEL_ERR_ARG, "nrhs out of range for plan " + std::to_string(i));
+            if (!q[i] || !u[i] || q[i] == u[i]) throw Error(SKEL_ERR_ARG, "bad q / u for plan " + std::to_string(i));
+            if (!is_device_ptr(q[i]) || !is_device_ptr(u[i]))
+                throw Error(SKEL_ERR_ARG, "skel_apply_batch takes device pointers only (plan " + std::to_string(i) + ")");
+        }
+        for (int i = 0; i < nsets; ++i)
+            skel::device_apply(hs[i]->dev, q[i], u[i], nrhs, precision, transpose != 0, stream);
+    });
+}
+
 void skel_free(skel_handle h) {
     if (!h) return;
     skel::device_plan_destroy(h->dev);

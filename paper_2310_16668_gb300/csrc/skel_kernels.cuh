@@ -127,14 +127,15 @@ template <> __device__ __forceinline__ void lds4<float>(const float* p, float* v
     v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
 }
 
-template <class S, bool DOWN>
-__global__ void __launch_bounds__(kGThreads, sizeof(S) <= 4 ? 12 : 4) updown_kernel(const UpBox* __restrict__ up,
+template <class S, bool DOWN, bool PREFETCH>
+__global__ void __launch_bounds__(kGThreads, sizeof(S) <= 4 ? (PREFETCH ? 12 : 16) : 4) updown_kernel(const UpBox* __restrict__ up,
                                                            const int32_t* __restrict__ pos,
                                                            const S* __restrict__ T, S* X, int nrhs, bool conj_op) {
     constexpr int kPer = kGT * kGT / kGThreads;           // A and B elements per thread per chunk
     constexpr int kRowStep = kGThreads / kGT;             // rows covered by one pass of the CTA
-    // register prefetch of the next chunk for element types up to 8 bytes
-    constexpr bool kPrefetch = sizeof(S) <= 8;
+    // register prefetch of the next chunk (levels with several chunks; element
+    // types up to 8 bytes); single-chunk levels save the registers instead
+    constexpr bool kPrefetch = PREFETCH && sizeof(S) <= 8;
     __shared__ __align__(16) S As[kGT][kGT];              // As[inner][row]
     __shared__ __align__(16) S Bs[kGT][kGT];              // Bs[inner][column]; the output tile at the end
     const UpBox u = up[blockIdx.x];

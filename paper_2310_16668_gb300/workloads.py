@@ -147,3 +147,27 @@ HELMHOLTZ3D_1M = Workload("helmholtz3d_k25_uniform_n1048576", "helmholtz3d", 3, 
                           kappa=25.0, charges="complex", seed=3)
 
 WORKLOADS = {w.name: w for w in (LAPLACE2D_16K, LAPLACE3D_1M, LAPLACE3D_ADAPTIVE_4M, HELMHOLTZ3D_1M)}
+
+
+@dataclass(frozen=True)
+class CurveSets:
+    """Many independent 2D point sets on random smooth closed curves
+    (the batched 2D Laplace workload)."""
+    name: str = "laplace2d_curves_256sets"
+    n_sets: int = 256
+    leaf: int = 64
+    tol: float = 1e-7
+    nrhs: int = 4
+    seed: int = 4
+
+    def sizes(self) -> np.ndarray:
+        return curve_set_sizes(self.n_sets, self.seed)
+
+    def make_point_sets(self) -> list:
+        return [points_curve(int(n), self.seed * 100003 + i) for i, n in enumerate(self.sizes())]
+
+    def make_charges(self, i: int, n: int, nrhs: int | None = None) -> np.ndarray:
+        return charges_uniform(n, self.nrhs if nrhs is None else nrhs, self.seed * 100003 + i + 7)
+
+
+CURVES2D_256 = CurveSets()

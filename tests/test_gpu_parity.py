@@ -196,3 +196,82 @@ def test_full_size_laplace3d_sampled():
     e64, e32, etc = relerr(u64, ref), relerr(u32, ref), relerr(utc[tg, 0], ref)
     print(f"full size: relerr fp64 {e64:.3e}  fp32 {e32:.3e}  fp32_tc {etc:.3e}  info {fmm.info()}")
     assert e64 < 10 * wl.tol and e32 < 10 * wl.tol and etc < 10 * wl.tol
+
+
+@pytest.mark.slow
+def test_full_size_sphere_cluster_sampled():
+    """Adaptive 3D Laplace, N = 2^22 on the unit sphere plus a Gaussian cluster
+    (a deep tree with coarse and fine neighbors), 32 right-hand sides on the
+    tensor-core path: sampled targets against the oracle's direct sum."""
+    wl = W.LAPLACE3D_ADAPTIVE_4M
+    x = wl.make_points()
+    qall = wl.make_charges(32)
+    fmm = SkelFMM(x, wl.kernel, wl.tol, wl.leaf, nrhs_max=32)
+    info = fmm.info()
+    assert info["n_coarse"] > 0 and info["n_fine"] > 0
+    tg = wl.make_sample()
+    utc = fmm.apply(torch.from_numpy(qall).cuda().float(), "fp32_tc").cpu().numpy()
+    fmm.device_status()
+    for r in (0, 31):
+        ref = direct.direct_sum(wl.kernel, x, np.ascontiguousarray(qall[:, r]), targets=tg)
+        e = relerr(utc[tg, r], ref)
+        print(f"sphere+cluster: RHS {r} relerr {e:.3e}  levels {info['n_levels']}")
+        assert e < 10 * wl.tol
+
+
+@pytest.mark.slow
+def test_full_size_helmholtz_sampled():
+    """3D Helmholtz (kappa = 25), N = 2^20: complex64 and complex128 applies
+    at sampled targets against the oracle's complex128 direct sum."""
+    wl = W.HELMHOLTZ3D_1M
+    x = wl.make_points()
+    q = wl.make_charges(4)
+    fmm = SkelFMM(x, wl.kernel, wl.tol, wl.leaf, kappa=wl.kappa, nrhs_max=4)
+    tg = wl.make_sample()[:1024]
+    ref = direct.direct_sum(wl.kernel, x, np.ascontiguousarray(q[:, 1]), targets=tg, kappa=wl.kappa)
+    qt = torch.from_numpy(q).cuda()
+    u64 = fmm.apply(qt, "fp64").cpu().numpy()[tg, 1]
+    u32 = fmm.apply(qt.to(torch.complex64), "fp32").cpu().numpy()[tg, 1]
+    fmm.device_status()
+    e64, e32 = relerr(u64, ref), relerr(u32, ref)
+    print(f"helmholtz: relerr complex128 {e64:.3e} complex64 {e32:.3e}")
+    assert e64 < 10 * wl.tol and e32 < 10 * wl.tol
+
+
+def test_batched_curve_sets_and_graph():
+    """Several independent 2D point sets on closed curves: the batched apply
+    equals each set's own apply, matches the oracle's direct sum within
+    10 tol, and a CUDA graph of the batch plus its adjoint replays to the
+    same result."""
+    from paper_2310_16668_gb300 import SkelBatch
+    cs = W.CurveSets(n_sets=6, seed=21)
+    sets = [W.points_curve(n, 900 + i) for i, n in enumerate((700, 1500, 2600, 1100, 3300, 900))]
+    nrhs = 4
+    b = SkelBatch(sets, "laplace2d", cs.tol, 16, nrhs_max=nrhs)
+    qs = [torch.from_numpy(np.ascontiguousarray(cs.make_charges(i, len(x), nrhs).T)).cuda().float()
+          for i, x in enumerate(sets)]
+    us = [torch.empty_like(q) for q in qs]
+    b.apply_into(qs, us, nrhs, "fp32_tc")
+    torch.cuda.synchronize()
+    for i, (f, x) in enumerate(zip(b.plans, sets)):
+        one = torch.empty_like(qs[i])
+        f.apply_into(qs[i], one, nrhs, "fp32_tc")
+        torch.cuda.synchronize()
+        assert torch.equal(one, us[i])                        # same kernels, same order
+        ref = direct.direct_sum("laplace2d", x, qs[i][2].double().cpu().numpy())
+        assert relerr(us[i][2].double().cpu().numpy(), ref) < 10 * cs.tol + 1e-5
+    # graph: forward batch + adjoint batch, replayed on fresh inputs
+    gs = [torch.randn_like(q) for q in qs]
+    vs = [torch.empty_like(q) for q in qs]
+    g = b.capture(qs, us, nrhs, "fp32_tc", adjoint_qs=gs, adjoint_us=vs)
+    for q in qs:
+        q.mul_(-2.0)
+    g.replay()
+    torch.cuda.synchronize()
+    for i, f in enumerate(b.plans):
+        e1, e2 = torch.empty_like(qs[i]), torch.empty_like(gs[i])
+        f.apply_into(qs[i], e1, nrhs, "fp32_tc")
+        f.apply_into(gs[i], e2, nrhs, "fp32_tc", transpose=True)
+        torch.cuda.synchronize()
+        assert torch.equal(e1, us[i]) and torch.equal(e2, vs[i])
+    b.close()
