@@ -223,7 +223,8 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
         t.r0 = r0;
         // the pass's B operand blocks, then the translations
         tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q,
-                                                               nrhs, r0, dp->tc_b);
+                                                               nrhs, r0, (const float4*)b->X,
+                                                               (const float4*)b->Xlo, dp->tc_b);
         CUDA_CHECK(cudaGetLastError());
         ++launches;
         if (r0 == 0) mark(dp, kMainEvent, st);
@@ -362,7 +363,7 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
             dp->chunk_start = upload(lay.chunk_start, dp->bytes);
             dp->chunk_cnt = upload(lay.chunk_cnt, dp->bytes);
             dp->n_chunks = (int64_t)lay.chunk_start.size();
-            dp->tc_b = dalloc<float>((size_t)dp->n_chunks * 2048, dp->bytes);
+            dp->tc_b = dalloc<float>((size_t)dp->n_chunks * kChunkFloats, dp->bytes);
         }
         dp->tc_n_slots = lay.tc_n_slots;
         dp->tc_part_ptr = upload(lay.tc_part_ptr, dp->bytes);

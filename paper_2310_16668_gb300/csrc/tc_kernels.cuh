@@ -5,16 +5,17 @@
 // U[128 x 32] += G[128 x K] Q[K x 32] over the K source entries of the box's
 // tasks, G_ij = G(x_i, y_j) evaluated on the fly, 32 sources per pipeline
 // tile. Before the translations of a 32-column pass, tc_bprep_kernel writes
-// the B operand of every source chunk (32 consecutive entries of one box) in
-// the MMA's shared-memory layout (K-major, no swizzle, 8 x 16-byte core
-// matrices: 512 bytes between core matrices along K, 128 bytes between groups
-// of 8 right-hand sides), split into TF32 hi and lo. The CTA is
-// warp-specialised:
-//   * warp 8, one thread (producer): for tile t it waits until data stage
-//     t % 6 is free, arms that stage's "full" mbarrier with the byte count and
-//     issues bulk copies (cp.async.bulk) of the chunk's B hi and lo blocks,
-//     the tile descriptor and the source coordinates into shared memory,
-//     running up to six tiles ahead of the compute warps;
+// every source chunk (32 consecutive entries of one box) as one contiguous
+// block: its B operand in the MMA's shared-memory layout (K-major, no
+// swizzle, 8 x 16-byte core matrices: 512 bytes between core matrices along
+// K, 128 bytes between groups of 8 right-hand sides), split into TF32 hi and
+// lo, followed by the chunk's coordinates. The CTA is warp-specialised:
+//   * warp 8 (producer; lanes fetch 32 tile descriptors at a time, lane 0
+//     issues): for tile t it waits until data stage t % 6 is free, arms that
+//     stage's "full" mbarrier with the byte count and issues two bulk copies
+//     (cp.async.bulk): the source chunk as the prep kernel laid it out (B hi,
+//     B lo, coordinates; 9 KB) and the tile descriptor, running up to six
+//     tiles ahead of the compute warps;
 //   * warp 9, one thread (MMA issuer): for tile m it waits for "A full" and
 //     issues 12 tcgen05.mma (kind::tf32, M = 128, N = 32, K = 8: hi*hi +
 //     hi*lo + lo*hi for each of 4 K-steps) and commits them to the stage's
@@ -46,6 +47,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 
 #include "host.h"
@@ -66,13 +68,17 @@ constexpr uint32_t kColA = 64;                 // A[b]: hi at 64+64b, lo at 96+6
 constexpr uint32_t kSleepNs = 20000;           // suspend hint of one wait attempt
 constexpr uint64_t kWaitLimitNs = 2000000000ull; // a wait gives up after 2 s
 
+// one source chunk as the prep kernel lays it out in global memory and one
+// bulk copy moves it: B hi, B lo, source coordinates (hi, lo)
+constexpr int kChunkFloats = 2 * 1024 + 2 * 128;
 struct alignas(128) TcStage {
     float bhi[32 * 32];                        // B operand, TF32 hi (bulk-copied, already converted)
     float blo[32 * 32];                        // B operand, TF32 lo
-    SrcTile tile;                              // 64 B
     float4 xh[32];                             // source coordinates (hi)
     float4 xl[32];                             // lo parts (touching-leaf tiles)
+    SrcTile tile;                              // 64 B: the tile's descriptor (its own copy)
 };
+static_assert(offsetof(TcStage, tile) == kChunkFloats * 4, "chunk blob is contiguous in the stage");
 // per compute warp: for each target slot its 32 rows touch, the coordinates
 // of its kSrcPerThread sources, one array per axis (x, y, z); a source the
 // slot skips sits at kFar
@@ -93,7 +99,7 @@ struct TcArgs {
     const SrcTile* tiles;                      // item i's tiles: [list_lo, list_hi) of this array
     const float4* X;
     const float4* Xlo;
-    const float* B;                            // per source chunk: B hi (1024 floats), then B lo
+    const float* B;                            // per source chunk (kChunkFloats): B hi, B lo, coordinates
     float* partial;
     int nrhs;                                  // right-hand sides (row length of the partial sums)
     int r0;                                    // first right-hand side of this pass
@@ -228,10 +234,6 @@ template <int KIND, bool ADJ> __device__ __forceinline__ float tc_green(float r2
     return (!ADJ || r2 > 1.17549435e-38f) ? y : 0.f;
 }
 
-// TF32 hi part of a finite float, rounded to nearest (ties away from zero):
-// the same value as cvt.rna.tf32.f32 for finite inputs, in two integer ops
-__device__ __forceinline__ uint32_t tf32_hi(float g) { return (__float_as_uint(g) + 0x1000u) & 0xFFFFE000u; }
-
 // 16 sources (j0 .. j0+15) against this thread's target, two sources per
 // paired FP32 instruction. c: this row's slot copy of these 16 coordinates
 // (axes AX floats apart); xl: the stage's lo parts (touching-leaf tiles);
@@ -242,41 +244,53 @@ __device__ __forceinline__ void tc_eval16(const float* c, const float4* xl, int 
     const float2 ntx = make_float2(nt.x, nt.x), nty = make_float2(nt.y, nt.y), ntz = make_float2(nt.z, nt.z);
     float2 nlx, nly, nlz;
     if (ADJ) nlx = make_float2(nl.x, nl.x), nly = make_float2(nl.y, nl.y), nlz = make_float2(nl.z, nl.z);
+    const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const int jj = 2 * p;
-        float2 dx = __fadd2_rn(*reinterpret_cast<const float2*>(&c[jj]), ntx);
-        float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(&c[AX + jj]), nty);
-        float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(&c[2 * AX + jj]), ntz);
-        if (ADJ) {
-            const float4 l0 = xl[j0 + jj], l1 = xl[j0 + jj + 1];
-            dx = __fadd2_rn(dx, __fadd2_rn(make_float2(l0.x, l1.x), nlx));
-            dy = __fadd2_rn(dy, __fadd2_rn(make_float2(l0.y, l1.y), nly));
-            dz = __fadd2_rn(dz, __fadd2_rn(make_float2(l0.z, l1.z), nlz));
+    for (int q = 0; q < 4; ++q) {
+        // four sources per axis in one 16-byte load
+        const float4 X = *reinterpret_cast<const float4*>(&c[4 * q]);
+        const float4 Y = *reinterpret_cast<const float4*>(&c[AX + 4 * q]);
+        const float4 Z = *reinterpret_cast<const float4*>(&c[2 * AX + 4 * q]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jj = 4 * q + 2 * h;
+            float2 dx = __fadd2_rn(h ? make_float2(X.z, X.w) : make_float2(X.x, X.y), ntx);
+            float2 dy = __fadd2_rn(h ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y), nty);
+            float2 dz = __fadd2_rn(h ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y), ntz);
+            if (ADJ) {
+                const float4 l0 = xl[j0 + jj], l1 = xl[j0 + jj + 1];
+                dx = __fadd2_rn(dx, __fadd2_rn(make_float2(l0.x, l1.x), nlx));
+                dy = __fadd2_rn(dy, __fadd2_rn(make_float2(l0.y, l1.y), nly));
+                dz = __fadd2_rn(dz, __fadd2_rn(make_float2(l0.z, l1.z), nlz));
+            }
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 g = make_float2(tc_green<KIND, ADJ>(r2.x), tc_green<KIND, ADJ>(r2.y));
+            // Veltkamp's split: hi = t - (t - g) with t = (2^13 + 1) g keeps 11
+            // significant bits of g (exactly a TF32 value, rounded to
+            // nearest); lo = g - hi is exact
+            const float2 t = __fmul2_rn(g, split);
+            const float2 hi = __ffma2_rn(__ffma2_rn(g, m1, t), m1, t);
+            const float2 lo = __ffma2_rn(hi, m1, g);
+            ghi[jj] = __float_as_uint(hi.x);
+            ghi[jj + 1] = __float_as_uint(hi.y);
+            glo[jj] = __float_as_uint(lo.x);
+            glo[jj + 1] = __float_as_uint(lo.y);
         }
-        float2 r2 = __fmul2_rn(dx, dx);
-        r2 = __ffma2_rn(dy, dy, r2);
-        r2 = __ffma2_rn(dz, dz, r2);
-        const float g0 = tc_green<KIND, ADJ>(r2.x), g1 = tc_green<KIND, ADJ>(r2.y);
-        const uint32_t h0 = tf32_hi(g0), h1 = tf32_hi(g1);
-        // lo = g - hi (exact); the tensor core truncates it to TF32
-        const float2 lo = __ffma2_rn(make_float2(__uint_as_float(h0), __uint_as_float(h1)), make_float2(-1.f, -1.f),
-                                     make_float2(g0, g1));
-        ghi[jj] = h0;
-        ghi[jj + 1] = h1;
-        glo[jj] = __float_as_uint(lo.x);
-        glo[jj + 1] = __float_as_uint(lo.y);
     }
 }
 
-// B operand of one source chunk for right-hand sides r0 .. r0+31, in the
-// shared-memory layout of the MMA (element (n, j) at float (j/4)*128 + n*4 +
-// j%4), split into TF32 hi (rounded to nearest) and lo = q - hi; entries past
-// the chunk and columns past nrhs are zero. Thread: n = tid % 32, sources
-// 4 (tid / 32) .. +3.
+// One source chunk for right-hand sides r0 .. r0+31, laid out as the stage
+// holds it: the B operand in the shared-memory layout of the MMA (element
+// (n, j) at float (j/4)*128 + n*4 + j%4), split into TF32 hi (rounded to
+// nearest) and lo = q - hi, then the chunk's 32 source coordinates (hi) and
+// their lo parts; entries past the chunk and columns past nrhs are zero.
+// Thread: n = tid % 32, sources 4 (tid / 32) .. +3.
 __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict__ chunk_start,
                                                        const int32_t* __restrict__ chunk_cnt,
                                                        const float* __restrict__ Q, int nrhs, int r0,
+                                                       const float4* __restrict__ X, const float4* __restrict__ Xlo,
                                                        float* __restrict__ B) {
     const int64_t ch = blockIdx.x;
     const int n = threadIdx.x & 31, jq = threadIdx.x >> 5;
@@ -294,9 +308,16 @@ __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict
     h.z = __uint_as_float(to_tf32(v[2]));
     h.w = __uint_as_float(to_tf32(v[3]));
     l = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
-    float* dst = B + ch * 2048 + jq * 128 + n * 4;
-    *reinterpret_cast<float4*>(dst) = h;
-    *reinterpret_cast<float4*>(dst + 1024) = l;
+    float* blob = B + ch * kChunkFloats;
+    *reinterpret_cast<float4*>(blob + jq * 128 + n * 4) = h;
+    *reinterpret_cast<float4*>(blob + 1024 + jq * 128 + n * 4) = l;
+    // the chunk's coordinates (hi then lo; zero past cnt)
+    if (threadIdx.x < 64) {
+        const int j = threadIdx.x & 31;
+        const float4* src = threadIdx.x < 32 ? X : Xlo;
+        const float4 c = j < cnt ? src[start + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4*>(blob + 2048)[threadIdx.x] = c;
+    }
 }
 
 template <int KIND>
@@ -334,34 +355,20 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         // the lanes fetch the descriptors of 32 tiles at a time; lane 0
         // issues each tile's copies
         for (int t0 = 0; t0 < ntile; t0 += 32) {
-            int64_t d_start = 0;
-            int d_cnt = 0, d_flags = 0, d_chunk = 0;
-            if (t0 + lane < ntile) {
-                const SrcTile* g = a.tiles + list_lo + t0 + lane;
-                d_start = g->start;
-                d_cnt = g->cnt;
-                d_flags = g->flags;
-                d_chunk = g->chunk;
-            }
+            const int d_chunk = t0 + lane < ntile ? a.tiles[list_lo + t0 + lane].chunk : 0;
             const int nb = min(32, ntile - t0);
             for (int i = 0; i < nb; ++i) {
                 const int t = t0 + i;
                 const int s = t % kNS;
-                const int64_t start = __shfl_sync(0xffffffffu, d_start, i);
-                const int cnt = __shfl_sync(0xffffffffu, d_cnt, i);
-                const bool adj = (__shfl_sync(0xffffffffu, d_flags, i) & TASK_ADJ) != 0;
                 const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
                 if (t >= kNS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNS) / kNS) & 1))) err = true;
                 if (lane == 0) {
-                    const float* bsrc = a.B + (int64_t)chunk * 2048;
-                    const uint32_t bytes = 64u + 16u * cnt * (adj ? 2u : 1u) + 2u * 4096u;
+                    // two bulk copies: the chunk (B hi, B lo, coordinates) and
+                    // the tile's descriptor
                     const uint32_t bar = sm_addr(&S.full[s]);
-                    mbar_arrive_tx(bar, bytes);
-                    bulk_g2s(sm_addr(S.st[s].bhi), bsrc, 4096u, bar);
-                    bulk_g2s(sm_addr(S.st[s].blo), bsrc + 1024, 4096u, bar);
+                    mbar_arrive_tx(bar, 4u * kChunkFloats + 64u);
+                    bulk_g2s(sm_addr(S.st[s].bhi), a.B + (int64_t)chunk * kChunkFloats, 4u * kChunkFloats, bar);
                     bulk_g2s(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar);
-                    bulk_g2s(sm_addr(S.st[s].xh), a.X + start, 16u * cnt, bar);
-                    if (adj) bulk_g2s(sm_addr(S.st[s].xl), a.Xlo + start, 16u * cnt, bar);
                 }
                 __syncwarp();
             }
