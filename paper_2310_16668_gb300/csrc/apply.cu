@@ -190,15 +190,22 @@ NearArgs<Real, CPLX> near_args(DevicePlan* dp, DeviceBuffers* b, const WorkItem*
     return a;
 }
 
-// tensor-core translations (real kernels, FP32): CUDA-core items for the
-// small boxes, then one tensor-core pass per 32 right-hand sides
+// tensor-core translations (real kernels, FP32): the CUDA-core items for
+// the small non-leaf boxes and the reduction of their partial sums (which
+// writes every row of U, zero where no CUDA-core item contributes), then one
+// tensor-core pass per 32 right-hand sides, whose items write their rows of U
+// directly (each row has exactly one item)
 template <class Real, bool CPLX>
 int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_launches) {
     int launches = 0;
     if (dp->n_mix > 0) {
+        using S = typename Scal<Real, CPLX>::T;
         auto a = near_args<Real, CPLX>(dp, b, dp->mix_items, dp->n_mix, nrhs);
         launches += launch_near<Real, CPLX>(dp->kind, a, nrhs, ceil_div(dp->n_mix, kNearWarps), st);
         CUDA_CHECK(cudaGetLastError());
+        reduce<S>(dp->tc_part_ptr, dp->tc_part_idx, (const S*)b->partial, (S*)b->U, nrhs, dp->n_tot, st);
+        CUDA_CHECK(cudaGetLastError());
+        ++launches;
     }
     TcArgs t;
     t.items = dp->tc_items;
@@ -206,7 +213,7 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     t.X = (const float4*)b->X;
     t.Xlo = (const float4*)b->Xlo;
     t.B = dp->tc_b;
-    t.partial = (float*)b->partial;
+    t.U = (float*)b->U;
     t.nrhs = nrhs;
     t.status = dp->status;
     static bool attr_set[2] = {false, false};
@@ -224,7 +231,8 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
         // the pass's B operand blocks, then the translations
         tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q,
                                                                nrhs, r0, (const float4*)b->X,
-                                                               (const float4*)b->Xlo, dp->tc_b);
+                                                               (const float4*)b->Xlo,
+                                                               (const float4*)dp->chunk_center, dp->tc_b);
         CUDA_CHECK(cudaGetLastError());
         ++launches;
         if (r0 == 0) mark(dp, kMainEvent, st);
@@ -268,9 +276,6 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
     if (tc) {
         launches += run_tc<Real, CPLX>(dp, b, nrhs, st, main_launches);
         mark(dp, 3, st);
-        ++launches;
-        reduce<S>(dp->tc_part_ptr, dp->tc_part_idx, part, U, nrhs, dp->n_tot, st);
-        CUDA_CHECK(cudaGetLastError());
     } else if (dp->n_items > 0) {
         auto a = near_args<Real, CPLX>(dp, b, dp->items, dp->n_items, nrhs);
         const unsigned grid = ceil_div(dp->n_items, kNearWarps);
@@ -362,6 +367,7 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
         if (dp->n_tc > 0 && !dp->cplx) {
             dp->chunk_start = upload(lay.chunk_start, dp->bytes);
             dp->chunk_cnt = upload(lay.chunk_cnt, dp->bytes);
+            dp->chunk_center = upload(lay.chunk_center, dp->bytes);
             dp->n_chunks = (int64_t)lay.chunk_start.size();
             dp->tc_b = dalloc<float>((size_t)dp->n_chunks * kChunkFloats, dp->bytes);
         }
@@ -390,7 +396,7 @@ void device_plan_destroy(DevicePlan* dp) {
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
                     dp->tc_items, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
-                    dp->chunk_start, dp->chunk_cnt, dp->tc_b};
+                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);

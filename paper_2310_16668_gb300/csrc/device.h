@@ -47,6 +47,7 @@ struct DevicePlan {
     int64_t* tc_part_idx = nullptr;
     int64_t* chunk_start = nullptr;        // source chunks (32 entries of one box)
     int32_t* chunk_cnt = nullptr;
+    float* chunk_center = nullptr;         // 4 per chunk: its box's centre
     int64_t n_chunks = 0;
     float* tc_b = nullptr;                 // B operand per chunk for one 32-column pass (hi, lo)
     int* status = nullptr;                 // device word raised by a bounded wait that gave up

@@ -104,7 +104,6 @@ struct WorkItem {                       // one warp: 32 targets x a task range
 constexpr int kTcRows = 128;
 constexpr int kTcK = 32;
 constexpr int kTcMinRows = 96;          // boxes with fewer entries use the CUDA-core kernel
-constexpr int kTcMaxTiles = 128;        // source tiles per tensor-core work item
 
 struct SrcTile {                        // 64 bytes; copied into shared memory by the bulk-copy engine
     int64_t start;                      // first source entry
@@ -112,7 +111,8 @@ struct SrcTile {                        // 64 bytes; copied into shared memory b
     int32_t flags;                      // TASK_ADJ
     uint32_t keep[kMaxSlots];           // per target slot: bit j = the slot keeps source j
     int32_t chunk;                      // its source chunk (the B operand block of these 32 sources)
-    int32_t pad[3];
+    float cen[3];                       // the source box's centre (FP32): the chunk's coordinates are
+                                        // stored relative to it
 };
 static_assert(sizeof(SrcTile) == 64, "SrcTile is one 64-byte bulk copy");
 
@@ -125,7 +125,7 @@ struct TcItem {                         // 64 bytes
     int32_t nslot;
     int32_t slot_start[kMaxSlots + 1];  // first row of each slot (may be < 0 for a box's later rows)
     int32_t list_lo, list_hi;           // its tiles: [list_lo, list_hi) of tc_tiles
-    int32_t slot;                       // first of its 4 partial-sum slots (32 rows each)
+    int32_t slot;                       // unused (the item writes its rows of U directly)
 };
 static_assert(sizeof(TcItem) == 64, "TcItem layout");
 
@@ -163,6 +163,7 @@ struct Layout {
     std::vector<int64_t> box_chunk0;    // nb
     std::vector<int64_t> chunk_start;   // first entry of each chunk
     std::vector<int32_t> chunk_cnt;     // entries in it (1..32)
+    std::vector<float> chunk_center;    // 4 per chunk: its box's centre (FP32), 0
     int64_t pairs_direct = 0, pairs_far = 0;
     int64_t pairs_tc = 0;   // kept evaluations inside tensor-core items
 };

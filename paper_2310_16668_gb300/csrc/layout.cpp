@@ -246,12 +246,20 @@ void build_layout(const Plan& p, Layout& lay) {
     lay.box_chunk0.assign(nb, -1);
     lay.chunk_start.clear();
     lay.chunk_cnt.clear();
+    lay.chunk_center.clear();
+    // box centres in FP32: the tensor-core path measures coordinates from the
+    // source box's centre, so FP32 keeps their resolution relative to the box
+    auto box_center = [&](int64_t b, int d) {
+        const double h = t.side / (double)(1ll << t.level[b]);
+        return (float)(t.corner[d] + ((double)t.coord[b * dim + d] + 0.5) * h);
+    };
     for (int64_t b = 0; b < nb; ++b) {
         if (lay.box_off[b] < 0) continue;
         lay.box_chunk0[b] = (int64_t)lay.chunk_start.size();
         for (int32_t p0 = 0; p0 < lay.box_n[b]; p0 += kTcK) {
             lay.chunk_start.push_back(lay.box_off[b] + p0);
             lay.chunk_cnt.push_back(std::min(kTcK, lay.box_n[b] - p0));
+            for (int d = 0; d < 4; ++d) lay.chunk_center.push_back(d < dim ? box_center(b, d) : 0.f);
         }
     }
     // one item: rows [row_off, row_off + nrows) whose slot j covers rows
@@ -294,6 +302,7 @@ void build_layout(const Plan& p, Layout& lay) {
                 SrcTile st{};
                 st.start = lay.box_off[src] + p0;
                 st.chunk = (int32_t)(lay.box_chunk0[src] + p0 / kTcK);
+                for (int d = 0; d < 3; ++d) st.cen[d] = d < dim ? box_center(src, d) : 0.f;
                 st.cnt = std::min(kTcK, n - p0);
                 st.flags = srcs[k].second;
                 for (int j = 0; j < lay.box_nslot[src]; ++j) {
@@ -310,22 +319,13 @@ void build_layout(const Plan& p, Layout& lay) {
                     if (rows_is > 0) lay.pairs_tc += (int64_t)rows_is * __builtin_popcount(st.keep[is]);
                 }
                 if (!any) continue;
-                if (lay.tc_tiles.size() - it.list_lo == (size_t)kTcMaxTiles) {   // split long lists
-                    it.list_hi = (int32_t)lay.tc_tiles.size();
-                    it.slot = (int32_t)slot;
-                    lay.tc_items.push_back(it);
-                    for (int32_t r = 0; r < nrows; ++r) parts.push_back({row_off + r, slot * kChunk + r});
-                    slot += kTcRows / kChunk;
-                    it.list_lo = it.list_hi;
-                }
                 lay.tc_tiles.push_back(st);
             }
         }
+        // the whole list stays one item: its rows get exactly one writer
         it.list_hi = (int32_t)lay.tc_tiles.size();
-        it.slot = (int32_t)slot;
+        it.slot = 0;
         lay.tc_items.push_back(it);
-        for (int32_t r = 0; r < nrows; ++r) parts.push_back({row_off + r, slot * kChunk + r});
-        slot += kTcRows / kChunk;
     };
     for (int64_t b = 0; b < nb; ++b) {
         if (lay.box_off[b] < 0 || !is_tc(b)) continue;
@@ -354,6 +354,12 @@ void build_layout(const Plan& p, Layout& lay) {
         sst[tg.size()] = rows;
         emit(row_off, rows, (int)tg.size(), sst, tg);
     }
+    // longest lists first, so that the long items start early
+    std::stable_sort(lay.tc_items.begin(), lay.tc_items.end(), [](const TcItem& a, const TcItem& c) {
+        return a.list_hi - a.list_lo > c.list_hi - c.list_lo;
+    });
+    // the partial sums of the CUDA-core items (small non-leaf boxes) only;
+    // tensor-core items write their rows of U directly
     lay.tc_n_slots = slot;
     to_csr(parts, lay.tc_part_ptr, lay.tc_part_idx);
 }

@@ -60,6 +60,7 @@ constexpr int kTcCompute = 128 * kTpr;         // compute threads
 constexpr int kSrcPerThread = 32 / kTpr;       // sources of a tile each compute thread evaluates
 constexpr int kTcThreads = kTcCompute + 64;    // + the producer warp and the MMA warp
 constexpr int kTcN = 32;                       // right-hand sides per pass (MMA N)
+constexpr int kTcGroup = 128;                  // tiles summed in registers before the outer sum
 constexpr int kNS = 6;                         // data stages (bulk-copy destinations)
 constexpr int kNA = 3;                         // A-operand buffers in tensor memory
 constexpr uint32_t kTmemCols = 256;
@@ -87,6 +88,7 @@ constexpr float kFar = 1e30f;                  // r^2 from here overflows to +in
 struct TcShared {
     TcStage st[kNS];
     float wc[kTcCompute / 32][kMaxSlots * kWarpSlotFloats];
+    float outer[kTcN / kTpr][kTcCompute];      // per compute thread: the sum of its flushed tile groups
     uint64_t full[kNS], afull[kNS], empty[kNS];  // per data stage
     uint32_t tmem;
     uint32_t slots;
@@ -100,8 +102,8 @@ struct TcArgs {
     const float4* X;
     const float4* Xlo;
     const float* B;                            // per source chunk (kChunkFloats): B hi, B lo, coordinates
-    float* partial;
-    int nrhs;                                  // right-hand sides (row length of the partial sums)
+    float* U;                                  // entry rows of nrhs (this item's rows are written here)
+    int nrhs;                                  // right-hand sides (row length of U)
     int r0;                                    // first right-hand side of this pass
     int* status;
 };
@@ -184,18 +186,6 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
                  :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
                     "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
                     "r"(v[15]) : "memory");
-}
-
-// issue only; the values are valid after tcgen05.wait::ld
-__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t* v) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                 : "r"(taddr) : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
@@ -284,14 +274,16 @@ __device__ __forceinline__ void tc_eval16(const float* c, const float4* xl, int 
 // One source chunk for right-hand sides r0 .. r0+31, laid out as the stage
 // holds it: the B operand in the shared-memory layout of the MMA (element
 // (n, j) at float (j/4)*128 + n*4 + j%4), split into TF32 hi (rounded to
-// nearest) and lo = q - hi, then the chunk's 32 source coordinates (hi) and
-// their lo parts; entries past the chunk and columns past nrhs are zero.
+// nearest) and lo = q - hi, then the chunk's 32 source coordinates (hi part
+// minus the box centre: FP32 then resolves them to the box size, not to the
+// domain size) and their lo parts; entries past the chunk and columns past
+// nrhs are zero.
 // Thread: n = tid % 32, sources 4 (tid / 32) .. +3.
 __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict__ chunk_start,
                                                        const int32_t* __restrict__ chunk_cnt,
                                                        const float* __restrict__ Q, int nrhs, int r0,
                                                        const float4* __restrict__ X, const float4* __restrict__ Xlo,
-                                                       float* __restrict__ B) {
+                                                       const float4* __restrict__ center, float* __restrict__ B) {
     const int64_t ch = blockIdx.x;
     const int n = threadIdx.x & 31, jq = threadIdx.x >> 5;
     const int64_t start = chunk_start[ch];
@@ -311,11 +303,19 @@ __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict
     float* blob = B + ch * kChunkFloats;
     *reinterpret_cast<float4*>(blob + jq * 128 + n * 4) = h;
     *reinterpret_cast<float4*>(blob + 1024 + jq * 128 + n * 4) = l;
-    // the chunk's coordinates (hi then lo; zero past cnt)
+    // the chunk's coordinates: hi parts measured from the box centre, then
+    // the lo parts (zero past cnt)
     if (threadIdx.x < 64) {
         const int j = threadIdx.x & 31;
-        const float4* src = threadIdx.x < 32 ? X : Xlo;
-        const float4 c = j < cnt ? src[start + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < cnt) {
+            if (threadIdx.x < 32) {
+                const float4 x = X[start + j], o = center[ch];
+                c = make_float4(x.x - o.x, x.y - o.y, x.z - o.z, 0.f);
+            } else {
+                c = Xlo[start + j];
+            }
+        }
         reinterpret_cast<float4*>(blob + 2048)[threadIdx.x] = c;
     }
 }
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const TcItem* itp = a.items + blockIdx.x;
     const int64_t row_off = itp->row_off;
-    const int nrows = itp->nrows, nslot = itp->nslot, list_lo = itp->list_lo, out_slot = itp->slot;
+    const int nrows = itp->nrows, nslot = itp->nslot, list_lo = itp->list_lo;
     const int ntile = itp->list_hi - list_lo;
 
     if (tid == 0) {
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             tx = a.X[row_off + row];
             tl = a.Xlo[row_off + row];
         }
-        const float4 nt = make_float4(-tx.x, -tx.y, -tx.z, 0.f), nl = make_float4(-tl.x, -tl.y, -tl.z, 0.f);
+        const float4 nl = make_float4(-tl.x, -tl.y, -tl.z, 0.f);
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         // the slots this warp's 32 rows fall in: s_lo .. s_lo + nsw - 1
         const int r_first = 32 * (warp & 3), r_last = min(r_first + 31, nrows - 1);
@@ -427,9 +427,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         constexpr int kCols = kTcN / kTpr;                     // accumulator columns this thread owns
         constexpr uint32_t kKeepMask = kSrcPerThread == 32 ? 0xFFFFFFFFu : (1u << kSrcPerThread) - 1u;
         const int j0 = kSrcPerThread * half;
+        // two-level FP32 sum: acc adds the tiles of a group of kTcGroup, the
+        // shared-memory `outer` adds the groups (keeps long lists accurate)
         float acc[kCols];
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) acc[c] = 0.f;
+        for (int c = 0; c < kCols; ++c) {
+            acc[c] = 0.f;
+            S.outer[c][tid] = 0.f;
+        }
         auto drain = [&](int m) {                              // add tile m's accumulator
             if (!mbar_wait(sm_addr(&S.empty[m % kNS]), (uint32_t)((m / kNS) & 1))) err = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -439,21 +444,24 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             else tmem_ld16(col, v);
 #pragma unroll
             for (int c = 0; c < kCols; ++c) acc[c] += __uint_as_float(v[c]);
+            if (m % kTcGroup == kTcGroup - 1) {
+#pragma unroll
+                for (int c = 0; c < kCols; ++c) {
+                    S.outer[c][tid] += acc[c];
+                    acc[c] = 0.f;
+                }
+            }
         };
         for (int u = 0; u < ntile; ++u) {
             const int s = u % kNS;
-            // tile u - 2's accumulator (frees accumulator u & 1): its load is
-            // issued now and added after the coordinate copy
-            uint32_t dv[kCols];
-            if (kCols == 32 && u >= 2) {
-                const int m = u - 2;
-                if (!mbar_wait(sm_addr(&S.empty[m % kNS]), (uint32_t)((m / kNS) & 1))) err = true;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                tmem_ld32_issue(tbase + lane_off + kColD + 32u * (m & 1), dv);
-            }
             if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNS) & 1))) err = true;
             TcStage& st = S.st[s];
             const bool adj = (st.tile.flags & TASK_ADJ) != 0;
+            // the target measured from the source box's centre (the frame of
+            // the chunk's coordinates); touching leaves keep hi and lo apart
+            const float cx = st.tile.cen[0], cy = st.tile.cen[1], cz = st.tile.cen[2];
+            const float4 nt = adj ? make_float4(cx - tx.x, cy - tx.y, cz - tx.z, 0.f)
+                                  : make_float4((cx - tx.x) - tl.x, (cy - tx.y) - tl.y, (cz - tx.z) - tl.z, 0.f);
             const uint32_t keep = valid ? (st.tile.keep[myslot] >> j0) & kKeepMask : 0u;
             // this warp's copy of its sources per slot and axis; a skipped
             // source (and any j >= cnt, never kept) sits at kFar. Every lane
@@ -469,13 +477,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                 d[2 * kSrcPerThread] = kept ? v.z : kFar;
             }
             __syncwarp();
-            if (kCols == 32 && u >= 2) {
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int c = 0; c < kCols; ++c) acc[c] += __uint_as_float(dv[c]);
-            } else if (u >= 2) {
-                drain(u - 2);
-            }
+            if (u >= 2) drain(u - 2);                          // frees accumulator (u & 1)
             // A buffer u % kNA was last read by MMA(u - kNA), complete since drain(u - 2)
             const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + (uint32_t)j0;
             const float* c = wc + myloc * kWarpSlotFloats;
@@ -499,13 +501,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             mbar_arrive(sm_addr(&S.afull[s]));
         }
         for (int m = (ntile >= 2 ? ntile - 2 : 0); m < ntile; ++m) drain(m);
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) acc[c] += S.outer[c][tid];
         if (valid) {
             const float scale = (float)green_scale<KIND>();
-            const int64_t base = ((int64_t)(out_slot + (row >> 5)) * kChunk + (row & 31)) * a.nrhs;
+            const int64_t base = (row_off + row) * a.nrhs;
             const int c0 = a.r0 + kCols * half;
 #pragma unroll
             for (int c = 0; c < kCols; ++c)
-                if (c0 + c < a.nrhs) a.partial[base + c0 + c] = scale * acc[c];
+                if (c0 + c < a.nrhs) a.U[base + c0 + c] = scale * acc[c];
         }
     }
     if (err) atomicExch(a.status, 1);
