@@ -233,10 +233,12 @@ void build_layout(const Plan& p, Layout& lay) {
     to_csr(parts, lay.part_ptr, lay.part_idx);
 
     // ---- tensor-core mode --------------------------------------------------------
-    // large boxes: their own 128-row items; small leaves: packed, consecutive
-    // in box order (so neighbouring in space), up to 128 rows and 8 leaves per
-    // item, one keep-mask slot per leaf; any other small box: CUDA-core items
-    auto is_tc = [&](int64_t b) { return lay.box_n[b] >= kTcMinRows; };
+    // tree boxes and large leaves: their own 128-row items (a small tree box
+    // fills part of one: at many right-hand sides that still beats the CUDA
+    // cores); small leaves: packed, consecutive in box order (so neighbouring
+    // in space), up to 128 rows and 8 leaves per item, one keep-mask slot per
+    // leaf. The CUDA-core list for the remaining boxes is then empty.
+    auto is_tc = [&](int64_t b) { return !t.is_leaf[b] || lay.box_n[b] >= kTcMinRows; };
     auto packable = [&](int64_t b) { return !is_tc(b) && t.is_leaf[b]; };
     simt_items([&](int64_t b) { return !is_tc(b) && !packable(b); }, lay.mix_items, 0);
     int64_t slot = (int64_t)lay.mix_items.size();
