@@ -59,8 +59,9 @@ def oracle_case(request):
     return kind, x, sk, fmm
 
 
-@pytest.mark.parametrize("nrhs", [1, 3])
+@pytest.mark.parametrize("nrhs", [1, 3, 4])
 def test_apply_matches_oracle(oracle_case, nrhs):
+    """nrhs = 4 puts the real kernels' FP32_TC apply on the tensor cores."""
     kind, x, sk, fmm = oracle_case
     q = _charges(kind, x.shape[0], nrhs, 11)
     ref = oap.skeleton_apply(sk, q)
@@ -95,11 +96,12 @@ def test_tensor_core_many_rhs(nrhs, b):
 
 def test_transpose_matches_oracle(oracle_case):
     kind, x, sk, fmm = oracle_case
-    q = _charges(kind, x.shape[0], 2, 12)
+    q = _charges(kind, x.shape[0], 4, 12)
     ref = oap.skeleton_apply(sk, q, transpose=True)
     qt = torch.from_numpy(q).cuda()
     assert relerr(fmm.apply_transpose(qt, "fp64").cpu().numpy(), ref) < 1e-12
     assert relerr(fmm.apply_transpose(qt, "fp32").cpu().numpy(), ref) < 1e-5
+    assert relerr(fmm.apply_transpose(qt, "fp32_tc").cpu().numpy(), ref) < 1e-5
 
 
 def test_host_pointers_match_device(oracle_case):
