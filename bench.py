@@ -43,7 +43,8 @@ MUFU_PER_SM_CLK = 16      # MUFU (rsqrt) results per SM per clock
 
 # --workload name -> workload in paper_2310_16668_gb300.workloads
 WORKLOAD_KEYS = {"laplace3d": "LAPLACE3D_1M", "sphere_cluster": "LAPLACE3D_ADAPTIVE_4M",
-                 "helmholtz3d": "HELMHOLTZ3D_1M", "laplace2d": "LAPLACE2D_16K", "curves2d": "CURVES2D_256"}
+                 "helmholtz3d": "HELMHOLTZ3D_1M", "laplace2d": "LAPLACE2D_16K", "curves2d": "CURVES2D_256",
+                 "helmholtz2d": "HELMHOLTZ2D_1M"}
 
 
 def parse_args():
@@ -56,7 +57,7 @@ def parse_args():
                    help="laplace3d: the headline (3D Laplace, N = 2^20 uniform); sphere_cluster: 3D Laplace, "
                         "N = 2^22 on a sphere plus a Gaussian cluster; helmholtz3d: kappa = 25, N = 2^20; "
                         "laplace2d: N = 16384; curves2d: 256 independent 2D point sets on closed curves, "
-                        "applied as one CUDA graph")
+                        "applied as one CUDA graph; helmholtz2d: kappa = 100, N = 2^20 uniform in 2D")
     p.add_argument("--precision", default=None, choices=["fp32_tc", "fp32", "fp64"],
                    help="default: fp32_tc for the Laplace kernels, fp32 (complex64) for Helmholtz")
     p.add_argument("--nrhs", type=int, default=None, help="default 32 (curves2d: 4)")
@@ -343,7 +344,7 @@ def run_ours(args):
     wl = dataclasses.replace(wl0, n=n, seed=replica_seed(wl0.seed, rank))
     x = wl.make_points()
     q = wl.make_charges(nrhs)
-    cplx = wl.kernel == "helmholtz3d"
+    cplx = wl.kernel in ("helmholtz3d", "helmholtz2d")
     threads = max(1, (os.cpu_count() or 1) // max(1, int(os.environ.get("LOCAL_WORLD_SIZE", world))))
     t0 = time.perf_counter()
     fmm = SkelFMM(x, wl.kernel, tol, wl.leaf, kappa=wl.kappa, nrhs_max=nrhs, num_threads=threads)

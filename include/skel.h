@@ -46,6 +46,8 @@ extern "C" {
 #define SKEL_LAPLACE_2D    0    /* G = -log|x-y| / (2 pi)          */
 #define SKEL_LAPLACE_3D    1    /* G = 1 / (4 pi |x-y|)            */
 #define SKEL_HELMHOLTZ_3D  2    /* G = e^{i kappa r} / (4 pi r)    */
+#define SKEL_HELMHOLTZ_2D  3    /* G = (i/4) H_0^(1)(kappa r), kappa > 0 (the 2D Helmholtz
+                                   experiments of Section 5); complex like HELMHOLTZ_3D */
 
 /* ---- apply precisions ------------------------------------------------- */
 #define SKEL_FP64     0   /* FP64 arithmetic, double charges/potentials            */
@@ -58,7 +60,7 @@ extern "C" {
 typedef struct skel_plan* skel_handle;
 
 typedef struct {
-    int    kind;    /* SKEL_LAPLACE_2D | SKEL_LAPLACE_3D | SKEL_HELMHOLTZ_3D */
+    int    kind;    /* SKEL_LAPLACE_2D | SKEL_LAPLACE_3D | SKEL_HELMHOLTZ_3D | SKEL_HELMHOLTZ_2D */
     double kappa;   /* wavenumber, Helmholtz only                             */
 } skel_kernel;
 
@@ -292,7 +294,7 @@ int skel_device_status(skel_handle h);
  * call before any stream capture.
  * Errors: SKEL_ERR_ARG for NULL or host pointers, bad sizes, or a problem
  * whose partial sums exceed the array (n up to 131,072 for real kernels,
- * 91,168 for Helmholtz); SKEL_ERR_CUDA.
+ * 91,168 for the Helmholtz kernels); SKEL_ERR_CUDA.
  */
 int skel_direct_noalloc(const double* points, int64_t n, int dim, skel_kernel k,
                         const double* q, double* u, int nrhs, void* stream);

@@ -18,7 +18,7 @@ import numpy as np
 from . import kernels
 from .build import LIB_PATH, build
 
-_KIND_CODE = {"laplace2d": 0, "laplace3d": 1, "helmholtz3d": 2}
+_KIND_CODE = {"laplace2d": 0, "laplace3d": 1, "helmholtz3d": 2, "helmholtz2d": 3}
 _lib = None
 
 

@@ -4,6 +4,9 @@ Laplace (Eq. (2)):   2D  G = -log|x-y| / (2 pi),   3D  G = 1 / (4 pi |x-y|).
 Helmholtz 3D (Eq. (5)): the paper prints (1/4) e^{i kappa r} / r; this
 library uses the free-space normalisation e^{i kappa r} / (4 pi r) (a global
 scale; the method is unchanged).
+Helmholtz 2D (Section 5, the 2D Helmholtz experiments): the free-space
+fundamental solution G = (i/4) H_0^(1)(kappa r), with the Hankel function
+taken from scipy.special (a library routine).
 
 The matrix A has zero diagonal (Section 1, below Eq. (3)); coincident points
 (r == 0) are given G = 0 as well, the same rule as the diagonal.
@@ -17,15 +20,20 @@ from __future__ import annotations
 
 import numpy as np
 
-KINDS = ("laplace2d", "laplace3d", "helmholtz3d", "poly2")
+KINDS = ("laplace2d", "laplace3d", "helmholtz3d", "helmholtz2d", "poly2")
 
 
 def is_complex(kind: str) -> bool:
-    return kind == "helmholtz3d"
+    return kind in ("helmholtz3d", "helmholtz2d")
 
 
 def kernel_dim(kind: str) -> int | None:
-    return {"laplace2d": 2, "laplace3d": 3, "helmholtz3d": 3}.get(kind)
+    return {"laplace2d": 2, "laplace3d": 3, "helmholtz3d": 3, "helmholtz2d": 2}.get(kind)
+
+
+def _hankel_2d(kr: np.ndarray) -> np.ndarray:
+    from scipy.special import hankel1
+    return 0.25j * hankel1(0, kr)
 
 
 def kernel_matrix(kind: str, xt: np.ndarray, xs: np.ndarray, kappa: float = 0.0) -> np.ndarray:
@@ -48,6 +56,8 @@ def kernel_matrix(kind: str, xt: np.ndarray, xs: np.ndarray, kappa: float = 0.0)
         g = 1.0 / (4.0 * np.pi * rs)
     elif kind == "helmholtz3d":
         g = np.exp(1j * kappa * rs) / (4.0 * np.pi * rs)
+    elif kind == "helmholtz2d":
+        g = _hankel_2d(kappa * rs)
     else:
         raise ValueError(kind)
     g[zero] = 0.0
@@ -62,4 +72,6 @@ def kernel_scalar(kind: str, r: float, kappa: float = 0.0):
         return 1.0 / (4.0 * np.pi * r)
     if kind == "helmholtz3d":
         return np.exp(1j * kappa * r) / (4.0 * np.pi * r)
+    if kind == "helmholtz2d":
+        return complex(_hankel_2d(np.array(kappa * r)))
     raise ValueError(kind)

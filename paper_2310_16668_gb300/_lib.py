@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libskel.so")
 SKEL_OK = 0
 ERRORS = {-1: "SKEL_ERR_ARG", -2: "SKEL_ERR_OOM", -3: "SKEL_ERR_CUDA", -4: "SKEL_ERR_TIMEOUT",
           -5: "SKEL_ERR_NUMERIC", -6: "SKEL_ERR_STATE"}
-KERNELS = {"laplace2d": 0, "laplace3d": 1, "helmholtz3d": 2}
+KERNELS = {"laplace2d": 0, "laplace3d": 1, "helmholtz3d": 2, "helmholtz2d": 3}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_tc": 2}
 
 # every symbol include/skel.h declares

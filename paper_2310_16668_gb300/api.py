@@ -37,7 +37,7 @@ class SkelFMM:
         self._lib = _lib.load()
         self.kernel = kernel
         self.kappa = float(kappa)
-        self.is_complex = kernel == "helmholtz3d"
+        self.is_complex = kernel in ("helmholtz3d", "helmholtz2d")
         self.nrhs_max = int(nrhs_max)
         if _handle is not None:
             self._h = _handle

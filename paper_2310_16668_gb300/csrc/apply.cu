@@ -324,7 +324,7 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
         dp->dim = p.tree.dim;
         dp->kind = p.kind;
         dp->kappa = p.kappa;
-        dp->cplx = p.kind == 2;
+        dp->cplx = p.kind == 2 || p.kind == 3;
         dp->N = p.tree.n;
         dp->n_tot = lay.n_tot;
         dp->nrhs_max = nrhs_max;

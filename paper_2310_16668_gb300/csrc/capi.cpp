@@ -60,12 +60,16 @@ int guarded(F&& f) {
 }
 
 void check_kernel(skel_kernel k, int dim) {
-    if (k.kind != SKEL_LAPLACE_2D && k.kind != SKEL_LAPLACE_3D && k.kind != SKEL_HELMHOLTZ_3D)
+    if (k.kind != SKEL_LAPLACE_2D && k.kind != SKEL_LAPLACE_3D && k.kind != SKEL_HELMHOLTZ_3D &&
+        k.kind != SKEL_HELMHOLTZ_2D)
         throw Error(SKEL_ERR_ARG, "unknown kernel kind");
-    if ((k.kind == SKEL_LAPLACE_2D) != (dim == 2) || (dim != 2 && dim != 3))
-        throw Error(SKEL_ERR_ARG, "dim does not match the kernel (2D Laplace: dim 2, others: dim 3)");
+    const bool two_d = k.kind == SKEL_LAPLACE_2D || k.kind == SKEL_HELMHOLTZ_2D;
+    if (two_d != (dim == 2) || (dim != 2 && dim != 3))
+        throw Error(SKEL_ERR_ARG, "dim does not match the kernel (2D kernels: dim 2, others: dim 3)");
     if (k.kind == SKEL_HELMHOLTZ_3D && !(std::isfinite(k.kappa) && k.kappa >= 0))
         throw Error(SKEL_ERR_ARG, "kappa must be finite and >= 0");
+    if (k.kind == SKEL_HELMHOLTZ_2D && !(std::isfinite(k.kappa) && k.kappa > 0))
+        throw Error(SKEL_ERR_ARG, "kappa must be finite and > 0 for the 2D Helmholtz kernel");
 }
 
 void check_points(const double* pts, int64_t n, int dim) {
@@ -390,7 +394,7 @@ int skel_plan_import(const double* points, int64_t n, int dim, skel_kernel kern,
             }
             // index sets and IDs
             skel::Skel& sk = P.sk;
-            sk.cplx = kern.kind == SKEL_HELMHOLTZ_3D;
+            sk.cplx = kern.kind == SKEL_HELMHOLTZ_3D || kern.kind == SKEL_HELMHOLTZ_2D;
             sk.idx_ptr.assign(idx_ptr, idx_ptr + nb + 1);
             if (sk.idx_ptr[0] != 0) throw Error(SKEL_ERR_ARG, "idx_ptr[0] != 0");
             for (int64_t b = 0; b < nb; ++b)

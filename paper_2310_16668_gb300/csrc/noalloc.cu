@@ -52,6 +52,10 @@ __device__ __forceinline__ void na_green(double r2, double kappa, double& gr, do
         gr = log(r2);
     } else if (KIND == 1) {
         gr = rsqrt(r2);
+    } else if (KIND == 3) {
+        const double kr = kappa * sqrt(r2);
+        gr = -y0(kr);
+        gi = j0(kr);
     } else {
         const double ri = rsqrt(r2);
         double s, c;
@@ -66,7 +70,7 @@ template <int KIND>
 __global__ void __launch_bounds__(kNaWarps * 32)
 na_partial_kernel(const double* __restrict__ x, int64_t n, int dim, const double* __restrict__ q, int r,
                   double kappa, double* __restrict__ part, int64_t nblk, int64_t nitems) {
-    constexpr int W = KIND == 2 ? 2 : 1;                    // doubles per charge
+    constexpr int W = (KIND == 2 || KIND == 3) ? 2 : 1;    // doubles per charge
     __shared__ double sx[kNaWarps][32][4 + W];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kNaWarps + warp;
@@ -90,7 +94,7 @@ na_partial_kernel(const double* __restrict__ x, int64_t n, int dim, const double
             const double dx = tx[0] - sx[warp][jj][0], dy = tx[1] - sx[warp][jj][1], dz = tx[2] - sx[warp][jj][2];
             double gr, gi;
             na_green<KIND>(dx * dx + dy * dy + dz * dz, kappa, gr, gi);
-            if (KIND == 2) {
+            if (W == 2) {
                 const double qr = sx[warp][jj][4], qi = sx[warp][jj][5];
                 ar += gr * qr - gi * qi;
                 ai += gr * qi + gi * qr;
@@ -101,7 +105,7 @@ na_partial_kernel(const double* __restrict__ x, int64_t n, int dim, const double
         __syncwarp();
     }
     part[(item * 32 + lane) * W] = ar;
-    if (KIND == 2) part[(item * 32 + lane) * W + 1] = ai;
+    if (W == 2) part[(item * 32 + lane) * W + 1] = ai;
 }
 
 // u_i (right-hand side r) = scale * sum over source blocks, in block order
@@ -136,11 +140,13 @@ extern "C" int skel_direct_noalloc(const double* points, int64_t n, int dim, ske
     using namespace skel;
     if (!points || !q || !u) return set_error(SKEL_ERR_ARG, "NULL argument");
     if (n < 1 || nrhs < 1) return set_error(SKEL_ERR_ARG, "n and nrhs must be >= 1");
-    if (k.kind != SKEL_LAPLACE_2D && k.kind != SKEL_LAPLACE_3D && k.kind != SKEL_HELMHOLTZ_3D)
+    if (k.kind != SKEL_LAPLACE_2D && k.kind != SKEL_LAPLACE_3D && k.kind != SKEL_HELMHOLTZ_3D &&
+        k.kind != SKEL_HELMHOLTZ_2D)
         return set_error(SKEL_ERR_ARG, "unknown kernel kind");
-    if ((k.kind == SKEL_LAPLACE_2D) != (dim == 2) || (dim != 2 && dim != 3))
+    const bool two_d = k.kind == SKEL_LAPLACE_2D || k.kind == SKEL_HELMHOLTZ_2D;
+    if (two_d != (dim == 2) || (dim != 2 && dim != 3))
         return set_error(SKEL_ERR_ARG, "dim does not match the kernel");
-    const int W = k.kind == SKEL_HELMHOLTZ_3D ? 2 : 1;
+    const int W = (k.kind == SKEL_HELMHOLTZ_3D || k.kind == SKEL_HELMHOLTZ_2D) ? 2 : 1;
     const int64_t nchunk = (n + 31) / 32, nblk = (n + kNaSrcBlock - 1) / kNaSrcBlock;
     const int64_t nitems = nchunk * nblk;
     if ((double)nitems * 32.0 * W * sizeof(double) > (double)kStaticScratchBytes)
@@ -167,15 +173,17 @@ extern "C" int skel_direct_noalloc(const double* points, int64_t n, int dim, ske
     double* part = static_cast<double*>(scratch);
     cudaStream_t st = (cudaStream_t)stream;
     const double pi = 3.14159265358979323846;
-    const double scale = k.kind == SKEL_LAPLACE_2D ? -1.0 / (4.0 * pi) : 1.0 / (4.0 * pi);
+    const double scale = k.kind == SKEL_LAPLACE_2D ? -1.0 / (4.0 * pi) : k.kind == SKEL_HELMHOLTZ_2D ? 0.25 : 1.0 / (4.0 * pi);
     const unsigned grid = (unsigned)((nitems + kNaWarps - 1) / kNaWarps);
     for (int r = 0; r < nrhs; ++r) {
         if (k.kind == SKEL_LAPLACE_2D)
             na_partial_kernel<0><<<grid, kNaWarps * 32, 0, st>>>(points, n, dim, q, r, k.kappa, part, nblk, nitems);
         else if (k.kind == SKEL_LAPLACE_3D)
             na_partial_kernel<1><<<grid, kNaWarps * 32, 0, st>>>(points, n, dim, q, r, k.kappa, part, nblk, nitems);
-        else
+        else if (k.kind == SKEL_HELMHOLTZ_3D)
             na_partial_kernel<2><<<grid, kNaWarps * 32, 0, st>>>(points, n, dim, q, r, k.kappa, part, nblk, nitems);
+        else
+            na_partial_kernel<3><<<grid, kNaWarps * 32, 0, st>>>(points, n, dim, q, r, k.kappa, part, nblk, nitems);
         if (W == 2) na_reduce_kernel<2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, n, nblk, r, scale, u);
         else na_reduce_kernel<1><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, n, nblk, r, scale, u);
     }

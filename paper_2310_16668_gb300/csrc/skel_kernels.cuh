@@ -285,6 +285,13 @@ __device__ __forceinline__ float log_(float x) { return logf(x); }
 __device__ __forceinline__ double log_(double x) { return log(x); }
 __device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float j0_(float x) { return j0f(x); }
+__device__ __forceinline__ double j0_(double x) { return j0(x); }
+__device__ __forceinline__ float y0_(float x) { return y0f(x); }
+__device__ __forceinline__ double y0_(double x) { return y0(x); }
+
+// kernels with complex values: 3D and 2D Helmholtz
+__host__ __device__ constexpr bool cplx_kind(int kind) { return kind == 2 || kind == 3; }
 
 // kernel value without its constant factor (applied once per target):
 // Laplace 2D: log r^2 (factor -1/(4 pi)); Laplace 3D: 1/r (factor 1/(4 pi));
@@ -306,6 +313,16 @@ template <class Real> struct Green<Real, 2> {
     }
     static __device__ __forceinline__ Cx<Real> zero_() { return {Real(0), Real(0)}; }
 };
+// 2D Helmholtz: (i/4) H_0^(1)(kappa r) = (i/4) (J_0 + i Y_0); the 1/4 is in
+// green_scale, the CUDA math library's Bessel functions give J_0 and Y_0
+template <class Real> struct Green<Real, 3> {
+    using G = Cx<Real>;
+    static __device__ __forceinline__ Cx<Real> eval(Real r2, Real kappa) {
+        const Real kr = kappa * sqrt(r2);
+        return {-y0_(kr), j0_(kr)};
+    }
+    static __device__ __forceinline__ Cx<Real> zero_() { return {Real(0), Real(0)}; }
+};
 template <class G, class S> __device__ __forceinline__ void madd(S& acc, G g, S q);
 template <> __device__ __forceinline__ void madd<float, float>(float& a, float g, float q) { a = fmaf(g, q, a); }
 template <> __device__ __forceinline__ void madd<double, double>(double& a, double g, double q) { a = fma(g, q, a); }
@@ -319,17 +336,19 @@ template <> __device__ __forceinline__ void madd<Cx<double>, Cx<double>>(Cx<doub
 }
 
 template <int KIND> __host__ __device__ constexpr double green_scale() {
-    return KIND == 0 ? -1.0 / (4.0 * 3.14159265358979323846) : 1.0 / (4.0 * 3.14159265358979323846);
+    return KIND == 0   ? -1.0 / (4.0 * 3.14159265358979323846)
+           : KIND == 3 ? 0.25
+                       : 1.0 / (4.0 * 3.14159265358979323846);
 }
 
 // One source slot [s0, s1) against the warp's 32 targets.
 template <class Real, int KIND, int RT, bool ADJ>
-__device__ __forceinline__ void near_slot(const NearArgs<Real, KIND == 2>& a, int64_t s0, int64_t s1, int r0,
+__device__ __forceinline__ void near_slot(const NearArgs<Real, cplx_kind(KIND)>& a, int64_t s0, int64_t s1, int r0,
                                           typename RealT<Real>::V4 tx, typename RealT<Real>::V4 tl,
                                           typename RealT<Real>::V4* sx, typename RealT<Real>::V4* sl,
-                                          typename Scal<Real, KIND == 2>::T* sq, int lane,
-                                          typename Scal<Real, KIND == 2>::T* part) {
-    using S = typename Scal<Real, KIND == 2>::T;
+                                          typename Scal<Real, cplx_kind(KIND)>::T* sq, int lane,
+                                          typename Scal<Real, cplx_kind(KIND)>::T* part) {
+    using S = typename Scal<Real, cplx_kind(KIND)>::T;
     using Gr = Green<Real, KIND>;
     constexpr bool LO = ADJ && sizeof(Real) == 4;
     for (int64_t b = s0; b < s1; b += 32) {
@@ -362,9 +381,9 @@ __device__ __forceinline__ void near_slot(const NearArgs<Real, KIND == 2>& a, in
 }
 
 template <class Real, int KIND, int RT>
-__global__ void __launch_bounds__(kNearWarps * 32) near_kernel(const NearArgs<Real, KIND == 2> a, int r0) {
+__global__ void __launch_bounds__(kNearWarps * 32) near_kernel(const NearArgs<Real, cplx_kind(KIND)> a, int r0) {
     using V4 = typename RealT<Real>::V4;
-    using S = typename Scal<Real, KIND == 2>::T;
+    using S = typename Scal<Real, cplx_kind(KIND)>::T;
     __shared__ V4 s_x[kNearWarps][32];
     __shared__ V4 s_l[kNearWarps][sizeof(Real) == 4 ? 32 : 1];
     __shared__ S s_q[kNearWarps][32 * RT];
@@ -423,7 +442,7 @@ __global__ void __launch_bounds__(kNearWarps * 32) near_kernel(const NearArgs<Re
 // single 32-wide pass measured slower: its registers and shared memory halve
 // the resident warps)
 template <class Real, int KIND>
-int launch_near_kind(const NearArgs<Real, KIND == 2>& a, int nrhs, unsigned grid, cudaStream_t st) {
+int launch_near_kind(const NearArgs<Real, cplx_kind(KIND)>& a, int nrhs, unsigned grid, cudaStream_t st) {
     if (nrhs == 1) {
         near_kernel<Real, KIND, 1><<<grid, kNearWarps * 32, 0, st>>>(a, 0);
         return 1;
@@ -448,14 +467,15 @@ inline int launch_near<double, false>(int kind, const NearArgs<double, false>& a
                      : launch_near_kind<double, 1>(a, nrhs, grid, st);
 }
 template <>
-inline int launch_near<float, true>(int, const NearArgs<float, true>& a, int nrhs, unsigned grid,
+inline int launch_near<float, true>(int kind, const NearArgs<float, true>& a, int nrhs, unsigned grid,
                                      cudaStream_t st) {
-    return launch_near_kind<float, 2>(a, nrhs, grid, st);
+    return kind == 3 ? launch_near_kind<float, 3>(a, nrhs, grid, st) : launch_near_kind<float, 2>(a, nrhs, grid, st);
 }
 template <>
-inline int launch_near<double, true>(int, const NearArgs<double, true>& a, int nrhs, unsigned grid,
+inline int launch_near<double, true>(int kind, const NearArgs<double, true>& a, int nrhs, unsigned grid,
                                       cudaStream_t st) {
-    return launch_near_kind<double, 2>(a, nrhs, grid, st);
+    return kind == 3 ? launch_near_kind<double, 3>(a, nrhs, grid, st)
+                     : launch_near_kind<double, 2>(a, nrhs, grid, st);
 }
 
 }  // namespace skel

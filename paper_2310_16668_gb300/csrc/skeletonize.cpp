@@ -76,12 +76,17 @@ template <> double kval<double>(int kind, double, const double* x, const double*
     if (kind == 0) return -std::log(std::sqrt(r2)) / (2.0 * kPi);
     return 1.0 / (4.0 * kPi * std::sqrt(r2));
 }
-template <> std::complex<double> kval<std::complex<double>>(int, double kappa, const double* x,
+template <> std::complex<double> kval<std::complex<double>>(int kind, double kappa, const double* x,
                                                             const double* y, int dim) {
     double r2 = 0;
     for (int d = 0; d < dim; ++d) r2 += (x[d] - y[d]) * (x[d] - y[d]);
     if (r2 == 0.0) return 0.0;
     double r = std::sqrt(r2);
+    if (kind == 3) {
+        // (i/4) H_0^(1)(kappa r) = (i/4) (J_0 + i Y_0), from the C++17 special functions
+        const double kr = kappa * r;
+        return std::complex<double>(-0.25 * std::cyl_neumann(0.0, kr), 0.25 * std::cyl_bessel_j(0.0, kr));
+    }
     return std::complex<double>(std::cos(kappa * r), std::sin(kappa * r)) / (4.0 * kPi * r);
 }
 
@@ -239,7 +244,7 @@ void skeletonize_all(Plan& P, const std::vector<std::vector<int64_t>>& leaf_poin
 }  // namespace
 
 std::complex<double> kernel_value(int kind, double kappa, const double* x, const double* y, int dim) {
-    if (kind == 2) return kval<std::complex<double>>(kind, kappa, x, y, dim);
+    if (kind == 2 || kind == 3) return kval<std::complex<double>>(kind, kappa, x, y, dim);
     return kval<double>(kind, kappa, x, y, dim);
 }
 
@@ -249,7 +254,7 @@ void build_skeletons(Plan& P, const std::vector<std::vector<int64_t>>& leaf_poin
 #else
     nthreads = 1;
 #endif
-    P.sk.cplx = (P.kind == 2);
+    P.sk.cplx = (P.kind == 2 || P.kind == 3);
     if (P.sk.cplx)
         skeletonize_all<std::complex<double>>(P, leaf_points, nthreads);
     else

@@ -99,7 +99,7 @@ def sample_targets(n: int, m: int, seed: int) -> np.ndarray:
 class Workload:
     """One benchmark/parity configuration (kernel, sizes, tolerance)."""
     name: str
-    kernel: str          # "laplace2d" | "laplace3d" | "helmholtz3d"
+    kernel: str          # "laplace2d" | "laplace3d" | "helmholtz3d" | "helmholtz2d"
     dim: int
     n: int
     leaf: int
@@ -146,7 +146,10 @@ LAPLACE3D_ADAPTIVE_4M = Workload("laplace3d_sphere_cluster_n4194304", "laplace3d
 HELMHOLTZ3D_1M = Workload("helmholtz3d_k25_uniform_n1048576", "helmholtz3d", 3, 1 << 20, 128, 1e-6, 1,
                           kappa=25.0, charges="complex", seed=3)
 
-WORKLOADS = {w.name: w for w in (LAPLACE2D_16K, LAPLACE3D_1M, LAPLACE3D_ADAPTIVE_4M, HELMHOLTZ3D_1M)}
+HELMHOLTZ2D_1M = Workload("helmholtz2d_k100_uniform_n1048576", "helmholtz2d", 2, 1 << 20, 64, 1e-6, 1,
+                          kappa=100.0, charges="complex", seed=5)
+
+WORKLOADS = {w.name: w for w in (LAPLACE2D_16K, LAPLACE3D_1M, LAPLACE3D_ADAPTIVE_4M, HELMHOLTZ3D_1M, HELMHOLTZ2D_1M)}
 
 
 @dataclass(frozen=True)

@@ -34,7 +34,8 @@ def test_library_exports_every_header_symbol():
         assert hasattr(lib, name), name
 
 
-CASES = [("laplace2d", 2, 3000, 12, 1e-8), ("laplace3d", 3, 3000, 16, 1e-6), ("helmholtz3d", 3, 2500, 16, 1e-6)]
+CASES = [("laplace2d", 2, 3000, 12, 1e-8), ("laplace3d", 3, 3000, 16, 1e-6), ("helmholtz3d", 3, 2500, 16, 1e-6),
+         ("helmholtz2d", 2, 2500, 16, 1e-8)]
 
 
 @pytest.mark.parametrize("kind,dim,n,b,tol", CASES)
@@ -74,7 +75,7 @@ def test_host_build_matches_oracle(kind, dim, n, b, tol):
         assert res <= 30 * tol * np.linalg.norm(m, 2)
         assert abs(k - int(sk.k[bx])) <= 1
     # the library's operators drive the oracle's Algorithm 2 to the direct sum
-    q = (W.charges_complex if kind == "helmholtz3d" else W.charges_normal)(x.shape[0], 1, 2)[:, 0]
+    q = (W.charges_complex if kind in ("helmholtz3d", "helmholtz2d") else W.charges_normal)(x.shape[0], 1, 2)[:, 0]
     u = oap.skeleton_apply(skeletons_from_plan(t, kind, pl, kappa=25.0), q)
     assert relerr(u, direct.direct_sum(kind, x, q, kappa=25.0)) < 10 * tol
 

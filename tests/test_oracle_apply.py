@@ -146,13 +146,29 @@ def test_single_leaf_root_is_direct():
     assert _relerr(oap.skeleton_apply(sk, q), direct.direct_sum("laplace3d", x, q)) < 1e-14
 
 
-@pytest.mark.parametrize("kind,dim", [("laplace3d", 3), ("laplace2d", 2)])
+@pytest.mark.parametrize("kind,dim", [("laplace3d", 3), ("laplace2d", 2), ("helmholtz2d", 2)])
 def test_keep_all_is_direct(kind, dim):
     x = _clustered(900, dim, 21)
     q = W.charges_normal(x.shape[0], 1, 22)[:, 0]
-    sk = osk.Skeletons(otree.Tree(x, 6), kind, 1e-6, keep_all=True)
-    ref = direct.direct_sum(kind, x, q)
+    if kind == "helmholtz2d":
+        q = q + 0.5j * W.charges_normal(x.shape[0], 1, 23)[:, 0]
+    sk = osk.Skeletons(otree.Tree(x, 6), kind, 1e-6, keep_all=True, kappa=25.0)
+    ref = direct.direct_sum(kind, x, q, kappa=25.0)
     assert _relerr(oap.skeleton_apply(sk, q), ref) < 1e-13
+
+
+def test_helmholtz2d_accuracy_and_transpose():
+    """2D Helmholtz (kappa = 25): the skeleton apply reaches the direct sum
+    within 10 tol, and <A~ q, p> = <q, A~^T p> under the bilinear form."""
+    x = _clustered(1500, 2, 24)
+    n = x.shape[0]
+    q = W.charges_complex(n, 1, 25)[:, 0]
+    p = W.charges_complex(n, 1, 26)[:, 0]
+    sk = osk.Skeletons(otree.Tree(x, 16), "helmholtz2d", 1e-8, kappa=25.0)
+    assert _relerr(oap.skeleton_apply(sk, q), direct.direct_sum("helmholtz2d", x, q, kappa=25.0)) < 1e-7
+    lhs = np.sum(oap.skeleton_apply(sk, q) * p)
+    rhs = np.sum(q * oap.skeleton_apply(sk, p, transpose=True))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
 
 
 def test_proxy_convergence():

@@ -26,9 +26,28 @@ def test_kernel_closed_forms():
     assert abs(g.real) < 1e-16 and g.imag == pytest.approx(1.0 / (2 * math.pi), rel=1e-14)
 
 
-@pytest.mark.parametrize("kind", ["laplace2d", "laplace3d", "helmholtz3d", "poly2"])
+def test_helmholtz2d_published_values_and_laplace_limit():
+    """2D Helmholtz G = (i/4) H_0^(1)(kappa r) = (-Y_0 + i J_0) / 4 at
+    kappa r = 1, with J_0(1) and Y_0(1) from Abramowitz and Stegun, Table 9.1;
+    and for kappa -> 0, G minus the 2D Laplace kernel -log(r)/(2 pi) tends to
+    the r-independent constant -(log(kappa / 2) + Euler's gamma)/(2 pi) + i/4
+    (the small-argument form of Y_0, A&S 9.1.13)."""
+    j0_1, y0_1 = 0.765197686557966551, 0.088256964215676958
+    g = kernels.kernel_scalar("helmholtz2d", 1.0, kappa=1.0)
+    assert g.real == pytest.approx(-y0_1 / 4, rel=1e-13)
+    assert g.imag == pytest.approx(j0_1 / 4, rel=1e-13)
+    g2 = kernels.kernel_scalar("helmholtz2d", 0.5, kappa=2.0)        # same kappa r
+    assert abs(g2 - g) < 1e-15
+    kappa, gamma = 1e-7, 0.5772156649015329
+    limit = complex(-(math.log(kappa / 2) + gamma) / (2 * math.pi), 0.25)
+    for r in (0.01, 0.3, 2.0):
+        d = kernels.kernel_scalar("helmholtz2d", r, kappa=kappa) - kernels.kernel_scalar("laplace2d", r)
+        assert abs(d - limit) < 1e-9
+
+
+@pytest.mark.parametrize("kind", ["laplace2d", "laplace3d", "helmholtz3d", "helmholtz2d", "poly2"])
 def test_zero_diagonal_and_coincident(kind):
-    dim = 2 if kind == "laplace2d" else 3
+    dim = 2 if kind in ("laplace2d", "helmholtz2d") else 3
     x = W.points_uniform(5, dim, 0)
     x = np.vstack([x, x[2:3]])       # a duplicated point
     g = kernels.kernel_matrix(kind, x, x, kappa=3.0)
@@ -95,7 +114,7 @@ def test_direct_vs_python_pairs(kind, dim):
         assert np.allclose(u, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("kind,dim", [("laplace2d", 2), ("laplace3d", 3), ("helmholtz3d", 3)])
+@pytest.mark.parametrize("kind,dim", [("laplace2d", 2), ("laplace3d", 3), ("helmholtz3d", 3), ("helmholtz2d", 2)])
 def test_c_vs_numpy_multi_rhs_and_targets(kind, dim):
     n = 700
     x = W.points_uniform(n, dim, 11)
