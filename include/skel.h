@@ -69,6 +69,10 @@ typedef struct {
     int nrhs_max;     /* largest nrhs any later apply will use, <= 256; 0 = 32           */
     int host_only;    /* 1 = build the plan on the host only; apply returns SKEL_ERR_STATE */
     int num_threads;  /* host threads used by the build; 0 = all                          */
+    int device_build; /* 1 = Algorithm 1 (proxy matrices, pivoted QR, T) on the current
+                         CUDA device in FP64, one CTA per box; 0 = on the host. Same
+                         ranks and operators up to rounding (ties in the pivot order
+                         may resolve differently). Needs host_only = 0.               */
 } skel_options;
 
 typedef struct {
@@ -93,6 +97,9 @@ typedef struct {
     int64_t n_mix_items;     /* FP32_TC: CUDA-core items for the remaining small boxes */
     int64_t pairs_tc;        /* FP32_TC: kernel evaluations (of pairs_direct + pairs_far)
                                 done by the tensor-core items, per 32 right-hand sides */
+    int     skel_on_device;  /* 1 if Algorithm 1 ran on the GPU (device_build)          */
+    double  t_id_kernels;    /* device build: seconds inside the ID kernels (CUDA events) */
+    double  id_gflop;        /* device build: GFLOP of the QR reflector updates (FP64)   */
 } skel_stats;
 
 /*

@@ -24,16 +24,20 @@ _DTYPES = {("fp64", False): torch.float64, ("fp64", True): torch.complex128,
            ("fp32_tc", False): torch.float32, ("fp32_tc", True): torch.complex64}
 
 
-def _options(proxy_p, nrhs_max, host_only, num_threads):
-    return SkelOptions(int(proxy_p), int(nrhs_max), int(bool(host_only)), int(num_threads))
+def _options(proxy_p, nrhs_max, host_only, num_threads, device_build=False):
+    return SkelOptions(int(proxy_p), int(nrhs_max), int(bool(host_only)), int(num_threads), int(bool(device_build)))
 
 
 class SkelFMM:
-    """One skeletonized-FMM plan (Algorithm 1 done, ready for Algorithm 2)."""
+    """One skeletonized-FMM plan (Algorithm 1 done, ready for Algorithm 2).
+
+    ``device_build=True`` runs Algorithm 1 (proxy matrices, pivoted QR, T) on
+    the current CUDA device instead of the host cores.
+    """
 
     def __init__(self, points, kernel: str = "laplace3d", tol: float = 1e-6, leaf_size: int = 128,
                  kappa: float = 0.0, proxy_p: int = 0, nrhs_max: int = 32, host_only: bool = False,
-                 num_threads: int = 0, _handle=None):
+                 num_threads: int = 0, device_build: bool = False, _handle=None):
         self._lib = _lib.load()
         self.kernel = kernel
         self.kappa = float(kappa)
@@ -45,7 +49,7 @@ class SkelFMM:
             pts = np.ascontiguousarray(points, dtype=np.float64)
             n, dim = pts.shape
             h = ctypes.c_void_p()
-            opts = _options(proxy_p, nrhs_max, host_only, num_threads)
+            opts = _options(proxy_p, nrhs_max, host_only, num_threads, device_build)
             check(self._lib.skel_build(pts.ctypes.data, n, dim, SkelKernel(_lib.KERNELS[kernel], self.kappa),
                                        float(tol), int(leaf_size), ctypes.byref(opts), ctypes.byref(h)))
             self._h = h
@@ -219,9 +223,10 @@ class SkelBatch:
     """
 
     def __init__(self, point_sets, kernel: str = "laplace2d", tol: float = 1e-7, leaf_size: int = 64,
-                 kappa: float = 0.0, nrhs_max: int = 4, num_threads: int = 0):
+                 kappa: float = 0.0, nrhs_max: int = 4, num_threads: int = 0, device_build: bool = False):
         self._lib = _lib.load()
-        self.plans = [SkelFMM(p, kernel, tol, leaf_size, kappa=kappa, nrhs_max=nrhs_max, num_threads=num_threads)
+        self.plans = [SkelFMM(p, kernel, tol, leaf_size, kappa=kappa, nrhs_max=nrhs_max, num_threads=num_threads,
+                              device_build=device_build)
                       for p in point_sets]
         self.sizes = [f.n for f in self.plans]
         self._hs = (ctypes.c_void_p * len(self.plans))(*[f._h.value for f in self.plans])

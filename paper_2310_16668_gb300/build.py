@@ -21,7 +21,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CXX_SOURCES = ["tree.cpp", "skeletonize.cpp", "layout.cpp", "capi.cpp"]
-CU_SOURCES = ["apply.cu", "noalloc.cu"]
+CU_SOURCES = ["apply.cu", "noalloc.cu", "build_gpu.cu"]
 # integer cell coordinates must be computed with plain IEEE operations
 NO_CONTRACT = {"tree.cpp", "capi.cpp"}
 

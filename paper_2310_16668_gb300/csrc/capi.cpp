@@ -175,6 +175,8 @@ int skel_build(const double* points, int64_t n, int dim, skel_kernel k, double t
         check_points(points, n, dim);
         if (!(tol > 0 && tol < 1)) throw Error(SKEL_ERR_ARG, "tol must be in (0, 1)");
         if (leaf_size < 1) throw Error(SKEL_ERR_ARG, "leaf_size must be >= 1");
+        if (opts && opts->device_build && opts->host_only)
+            throw Error(SKEL_ERR_ARG, "device_build needs a device plan (host_only = 0)");
         skel_plan* h = new skel_plan();
         try {
             skel::Plan& P = h->plan;
@@ -188,7 +190,12 @@ int skel_build(const double* points, int64_t n, int dim, skel_kernel k, double t
             std::vector<std::vector<int64_t>> leaf_points;
             skel::build_tree(points, n, dim, leaf_size, P.tree, leaf_points);
             double t1 = now();
-            skel::build_skeletons(P, leaf_points, opts ? opts->num_threads : 0);
+            if (opts && opts->device_build) {
+                skel::build_skeletons_device(P, leaf_points);
+                P.skel_on_device = true;
+            } else {
+                skel::build_skeletons(P, leaf_points, opts ? opts->num_threads : 0);
+            }
             P.t_tree = t1 - t0;
             P.t_skel = now() - t1;
             finalize(h, opts);
@@ -270,6 +277,9 @@ int skel_info(skel_handle h, skel_stats* s) {
         s->n_tc_tiles = h->n_tc_tiles;
         s->n_mix_items = h->n_mix_items;
         s->pairs_tc = h->pairs_tc;
+        s->skel_on_device = P.skel_on_device ? 1 : 0;
+        s->t_id_kernels = P.t_id_kernels;
+        s->id_gflop = P.id_flops * 1e-9;
     });
 }
 

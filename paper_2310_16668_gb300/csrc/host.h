@@ -58,6 +58,9 @@ struct Plan {
     Tree tree;
     Skel sk;
     double t_tree = 0, t_skel = 0;
+    bool skel_on_device = false;     // Algorithm 1 ran on the GPU
+    double t_id_kernels = 0;         // seconds in the device ID kernels (device build)
+    double id_flops = 0;             // FP64 flops of their reflector updates
 };
 
 bool touches(int la, const int64_t* ca, int lb, const int64_t* cb, int dim);
@@ -75,6 +78,21 @@ void finish_tree(Tree& t);
 // Algorithm 1: IDs of all boxes on levels L..2 (level-1 boxes keep S = I_B).
 void build_skeletons(Plan& p, const std::vector<std::vector<int64_t>>& leaf_points,
                      int nthreads);
+
+// The same on the GPU (FP64 / complex128 pivoted QR per box, one CTA each);
+// the host keeps only the integer bookkeeping between levels.
+void build_skeletons_device(Plan& p, const std::vector<std::vector<int64_t>>& leaf_points);
+
+// Proxy points of a box with centre c and side a (Section 2.1): p first-kind
+// Chebyshev nodes per edge (2D) or p x p per face (3D) of the concentric
+// box of side 2.95 a.
+void proxy_points(const double* c, double a, int dim, int p, std::vector<double>& out);
+
+// Flatten per-box index sets, pivots, ranks and T blocks (raw doubles,
+// complex entries as two) into p.sk.
+void store_skeletons(Plan& p, const std::vector<std::vector<int64_t>>& idx,
+                     const std::vector<std::vector<int64_t>>& piv, const std::vector<std::vector<double>>& Tw,
+                     const std::vector<int32_t>& kk);
 
 // Host kernel values for the proxy matrices.
 std::complex<double> kernel_value(int kind, double kappa, const double* x,

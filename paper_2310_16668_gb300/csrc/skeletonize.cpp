@@ -37,37 +37,6 @@ inline double abs2(const std::complex<double>& v) { return std::norm(v); }
 inline double conj_(double v) { return v; }
 inline std::complex<double> conj_(const std::complex<double>& v) { return std::conj(v); }
 
-void proxy_points(const double* c, double a, int dim, int p, std::vector<double>& out) {
-    const double h = 0.5 * kProxyScale * a;
-    std::vector<double> t(p);
-    for (int k = 1; k <= p; ++k) t[k - 1] = h * std::cos((2.0 * k - 1.0) * kPi / (2.0 * p));
-    out.clear();
-    if (dim == 2) {
-        for (int axis = 0; axis < 2; ++axis)
-            for (double sgn : {-1.0, 1.0})
-                for (int i = 0; i < p; ++i) {
-                    double v[2];
-                    v[axis] = sgn * h;
-                    v[1 - axis] = t[i];
-                    out.push_back(c[0] + v[0]);
-                    out.push_back(c[1] + v[1]);
-                }
-    } else {
-        for (int axis = 0; axis < 3; ++axis) {
-            int o0 = axis == 0 ? 1 : 0, o1 = axis == 2 ? 1 : 2;
-            for (double sgn : {-1.0, 1.0})
-                for (int i = 0; i < p; ++i)
-                    for (int j = 0; j < p; ++j) {
-                        double v[3];
-                        v[axis] = sgn * h;
-                        v[o0] = t[i];
-                        v[o1] = t[j];
-                        for (int d = 0; d < 3; ++d) out.push_back(c[d] + v[d]);
-                    }
-        }
-    }
-}
-
 template <class S> S kval(int kind, double kappa, const double* x, const double* y, int dim);
 template <> double kval<double>(int kind, double, const double* x, const double* y, int dim) {
     double r2 = 0;
@@ -221,27 +190,72 @@ void skeletonize_all(Plan& P, const std::vector<std::vector<int64_t>>& leaf_poin
         std::iota(piv[0].begin(), piv[0].end(), 0);
         kk[0] = (int32_t)idx[0].size();
     }
-    // flatten
+    std::vector<std::vector<double>> Tw(nb);
+    const int w = sk.cplx ? 2 : 1;
+    for (int64_t b = 0; b < nb; ++b) {
+        const double* src = reinterpret_cast<const double*>(Tb[b].data());
+        Tw[b].assign(src, src + Tb[b].size() * w);
+    }
+    store_skeletons(P, idx, piv, Tw, kk);
+}
+
+}  // namespace
+
+void proxy_points(const double* c, double a, int dim, int p, std::vector<double>& out) {
+    const double h = 0.5 * kProxyScale * a;
+    std::vector<double> t(p);
+    for (int k = 1; k <= p; ++k) t[k - 1] = h * std::cos((2.0 * k - 1.0) * kPi / (2.0 * p));
+    out.clear();
+    if (dim == 2) {
+        for (int axis = 0; axis < 2; ++axis)
+            for (double sgn : {-1.0, 1.0})
+                for (int i = 0; i < p; ++i) {
+                    double v[2];
+                    v[axis] = sgn * h;
+                    v[1 - axis] = t[i];
+                    out.push_back(c[0] + v[0]);
+                    out.push_back(c[1] + v[1]);
+                }
+    } else {
+        for (int axis = 0; axis < 3; ++axis) {
+            int o0 = axis == 0 ? 1 : 0, o1 = axis == 2 ? 1 : 2;
+            for (double sgn : {-1.0, 1.0})
+                for (int i = 0; i < p; ++i)
+                    for (int j = 0; j < p; ++j) {
+                        double v[3];
+                        v[axis] = sgn * h;
+                        v[o0] = t[i];
+                        v[o1] = t[j];
+                        for (int d = 0; d < 3; ++d) out.push_back(c[d] + v[d]);
+                    }
+        }
+    }
+}
+
+// Flatten per-box index sets, pivots, ranks and T blocks (raw doubles:
+// complex entries as two) into the plan.
+void store_skeletons(Plan& P, const std::vector<std::vector<int64_t>>& idx,
+                     const std::vector<std::vector<int64_t>>& piv, const std::vector<std::vector<double>>& Tw,
+                     const std::vector<int32_t>& kk) {
+    Skel& sk = P.sk;
+    const int64_t nb = P.tree.nb;
+    const int w = sk.cplx ? 2 : 1;
     sk.idx_ptr.assign(nb + 1, 0);
     sk.T_ptr.assign(nb + 1, 0);
     sk.k = kk;
     for (int64_t b = 0; b < nb; ++b) {
         sk.idx_ptr[b + 1] = sk.idx_ptr[b] + (int64_t)idx[b].size();
-        sk.T_ptr[b + 1] = sk.T_ptr[b] + (int64_t)Tb[b].size();
+        sk.T_ptr[b + 1] = sk.T_ptr[b] + (int64_t)(Tw[b].size() / w);
     }
     sk.idx.resize(sk.idx_ptr[nb]);
     sk.piv.resize(sk.idx_ptr[nb]);
-    const int w = sk.cplx ? 2 : 1;
     sk.T.resize((size_t)sk.T_ptr[nb] * w);
     for (int64_t b = 0; b < nb; ++b) {
         std::copy(idx[b].begin(), idx[b].end(), sk.idx.begin() + sk.idx_ptr[b]);
         std::copy(piv[b].begin(), piv[b].end(), sk.piv.begin() + sk.idx_ptr[b]);
-        const double* src = reinterpret_cast<const double*>(Tb[b].data());
-        std::copy(src, src + Tb[b].size() * w, sk.T.begin() + sk.T_ptr[b] * w);
+        std::copy(Tw[b].begin(), Tw[b].end(), sk.T.begin() + sk.T_ptr[b] * w);
     }
 }
-
-}  // namespace
 
 std::complex<double> kernel_value(int kind, double kappa, const double* x, const double* y, int dim) {
     if (kind == 2 || kind == 3) return kval<std::complex<double>>(kind, kappa, x, y, dim);

@@ -132,6 +132,7 @@ def test_argument_errors():
     bad = x.copy()
     bad[5, 1] = np.nan
     _expect(-5, SkelFMM, bad, "laplace3d", 1e-6, 16, host_only=True)     # non-finite
+    _expect(-1, SkelFMM, x, "laplace3d", 1e-6, 16, host_only=True, device_build=True)  # needs a device
     f = SkelFMM(x, "laplace3d", 1e-6, 16, host_only=True)
     _expect(-6, f.apply, np.zeros(300))                                   # host-only plan
     lib = _lib.load()
