@@ -65,6 +65,8 @@ def parse_args():
     p.add_argument("--n", type=int, default=None, help="override N (testing only)")
     p.add_argument("--build", default="host", choices=["host", "device"],
                    help="where Algorithm 1 runs (outside the timed region either way)")
+    p.add_argument("--store-tiles", action="store_true",
+                   help="stored-operator mode: kernel tiles evaluated once at build, read by every apply")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -350,7 +352,7 @@ def run_ours(args):
     threads = max(1, (os.cpu_count() or 1) // max(1, int(os.environ.get("LOCAL_WORLD_SIZE", world))))
     t0 = time.perf_counter()
     fmm = SkelFMM(x, wl.kernel, tol, wl.leaf, kappa=wl.kappa, nrhs_max=nrhs, num_threads=threads,
-                  device_build=args.build == "device")
+                  device_build=args.build == "device", store_tiles=args.store_tiles)
     t_build = time.perf_counter() - t0
     info = fmm.info()
     pairs = info["pairs_direct"] + info["pairs_far"]
@@ -486,6 +488,21 @@ def run_ours(args):
                           f"({sm_mhz:.0f} MHz), one MUFU op per kernel evaluation",
             "per_launch_ms": near_ms_per_launch, "launches_per_step": n_near,
             "algorithmic_units": f"{units} kernel evaluations per launch ({unit_note})"}
+    stored = prec == "fp32_tc" and info["stored_tile_bytes"] > 0
+    if stored:
+        # stored-operator mode: the kernel reads every tile's 16 KB of kernel
+        # values once per 32-column pass and writes its rows of U; the
+        # chunks' B blocks (8 KB per chunk, mostly L2 hits) are left out
+        kname = "tc_stored_kernel"
+        alg_bytes = info["stored_tile_bytes"] + info["n_index"] * 32 * 4
+        roof.update({"kernel": kname, "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                     "achieved": alg_bytes / (near_ms_per_launch * 1e-3) / 1e9,
+                     "traffic": ncu_traffic(kname, prec),
+                     "peak_basis": f"{peaks_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_units": f"{alg_bytes} bytes per launch (stored tiles {info['stored_tile_bytes']} "
+                                          f"+ U rows {info['n_index']} x 32 x 4)",
+                     "evaluation_rate_gpair_s": achieved})
+        roof["frac"] = roof["achieved"] / roof["peak"]
     if prec == "fp32_tc":
         # the same launch against the tensor pipe: algorithmic 2 flops per
         # evaluation and right-hand side (32 per launch); the pipe issues 3
@@ -512,7 +529,8 @@ def run_ours(args):
         "build": {"where": args.build, "t_build_s": t_build, "t_tree_s": info["t_tree"], "t_skel_s": info["t_skel"],
                   "t_upload_s": info["t_upload"], "host_threads": threads,
                   "t_id_kernels_s": info["t_id_kernels"] if args.build == "device" else None,
-                  "id_gflop": info["id_gflop"] if args.build == "device" else None},
+                  "id_gflop": info["id_gflop"] if args.build == "device" else None,
+                  "stored_tile_bytes": info["stored_tile_bytes"]},
         "comparator_fp64": fp64,
         "phases_ms_per_step": {k: v / phases["n_applies"] for k, v in phases.items()
                                if k not in ("launches", "n_applies", "main_launches")},

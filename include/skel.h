@@ -73,6 +73,12 @@ typedef struct {
                          CUDA device in FP64, one CTA per box; 0 = on the host. Same
                          ranks and operators up to rounding (ties in the pivot order
                          may resolve differently). Needs host_only = 0.               */
+    int store_tiles;  /* 1 = stored-operator mode: evaluate every tensor-core tile's
+                         128 x 32 kernel values once at build and keep them on the
+                         device (n_tc_tiles x 16 KB); FP32_TC applies then read them
+                         instead of evaluating the kernel. Same results bit for bit.
+                         Real kernels only (ignored otherwise). SKEL_ERR_OOM if the
+                         tiles do not fit.                                            */
 } skel_options;
 
 typedef struct {
@@ -100,6 +106,7 @@ typedef struct {
     int     skel_on_device;  /* 1 if Algorithm 1 ran on the GPU (device_build)          */
     double  t_id_kernels;    /* device build: seconds inside the ID kernels (CUDA events) */
     double  id_gflop;        /* device build: GFLOP of the QR reflector updates (FP64)   */
+    int64_t stored_tile_bytes; /* store_tiles: device bytes of the stored kernel tiles   */
 } skel_stats;
 
 /*

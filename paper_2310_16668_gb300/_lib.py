@@ -30,7 +30,8 @@ class SkelKernel(ctypes.Structure):
 
 class SkelOptions(ctypes.Structure):
     _fields_ = [("proxy_p", ctypes.c_int), ("nrhs_max", ctypes.c_int),
-                ("host_only", ctypes.c_int), ("num_threads", ctypes.c_int), ("device_build", ctypes.c_int)]
+                ("host_only", ctypes.c_int), ("num_threads", ctypes.c_int), ("device_build", ctypes.c_int),
+                ("store_tiles", ctypes.c_int)]
 
 
 class SkelStats(ctypes.Structure):
@@ -44,7 +45,8 @@ class SkelStats(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("n_tc_items", ctypes.c_int64),
                 ("n_tc_tiles", ctypes.c_int64), ("n_mix_items", ctypes.c_int64),
                 ("pairs_tc", ctypes.c_int64), ("skel_on_device", ctypes.c_int),
-                ("t_id_kernels", ctypes.c_double), ("id_gflop", ctypes.c_double)]
+                ("t_id_kernels", ctypes.c_double), ("id_gflop", ctypes.c_double),
+                ("stored_tile_bytes", ctypes.c_int64)]
 
 
 class SkelPlanDims(ctypes.Structure):

@@ -24,20 +24,23 @@ _DTYPES = {("fp64", False): torch.float64, ("fp64", True): torch.complex128,
            ("fp32_tc", False): torch.float32, ("fp32_tc", True): torch.complex64}
 
 
-def _options(proxy_p, nrhs_max, host_only, num_threads, device_build=False):
-    return SkelOptions(int(proxy_p), int(nrhs_max), int(bool(host_only)), int(num_threads), int(bool(device_build)))
+def _options(proxy_p, nrhs_max, host_only, num_threads, device_build=False, store_tiles=False):
+    return SkelOptions(int(proxy_p), int(nrhs_max), int(bool(host_only)), int(num_threads), int(bool(device_build)),
+                       int(bool(store_tiles)))
 
 
 class SkelFMM:
     """One skeletonized-FMM plan (Algorithm 1 done, ready for Algorithm 2).
 
     ``device_build=True`` runs Algorithm 1 (proxy matrices, pivoted QR, T) on
-    the current CUDA device instead of the host cores.
+    the current CUDA device instead of the host cores. ``store_tiles=True``
+    keeps every tensor-core tile's kernel values on the device (16 KB per
+    tile) so that FP32_TC applies read them instead of evaluating the kernel.
     """
 
     def __init__(self, points, kernel: str = "laplace3d", tol: float = 1e-6, leaf_size: int = 128,
                  kappa: float = 0.0, proxy_p: int = 0, nrhs_max: int = 32, host_only: bool = False,
-                 num_threads: int = 0, device_build: bool = False, _handle=None):
+                 num_threads: int = 0, device_build: bool = False, store_tiles: bool = False, _handle=None):
         self._lib = _lib.load()
         self.kernel = kernel
         self.kappa = float(kappa)
@@ -49,7 +52,7 @@ class SkelFMM:
             pts = np.ascontiguousarray(points, dtype=np.float64)
             n, dim = pts.shape
             h = ctypes.c_void_p()
-            opts = _options(proxy_p, nrhs_max, host_only, num_threads, device_build)
+            opts = _options(proxy_p, nrhs_max, host_only, num_threads, device_build, store_tiles)
             check(self._lib.skel_build(pts.ctypes.data, n, dim, SkelKernel(_lib.KERNELS[kernel], self.kappa),
                                        float(tol), int(leaf_size), ctypes.byref(opts), ctypes.byref(h)))
             self._h = h

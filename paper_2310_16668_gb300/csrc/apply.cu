@@ -195,6 +195,19 @@ NearArgs<Real, CPLX> near_args(DevicePlan* dp, DeviceBuffers* b, const WorkItem*
 // writes every row of U, zero where no CUDA-core item contributes), then one
 // tensor-core pass per 32 right-hand sides, whose items write their rows of U
 // directly (each row has exactly one item)
+// dynamic shared memory above 48 KB for every tensor-core kernel (once per process)
+void set_tc_attributes() {
+    static bool done = false;
+    if (done) return;
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcsSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcsSmemRequest));
+    done = true;
+}
+
 template <class Real, bool CPLX>
 int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_launches) {
     int launches = 0;
@@ -214,17 +227,12 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     t.Xlo = (const float4*)b->Xlo;
     t.B = dp->tc_b;
     t.U = (float*)b->U;
+    t.A = dp->tc_a;
     t.nrhs = nrhs;
     t.status = dp->status;
-    static bool attr_set[2] = {false, false};
     const int kidx = dp->kind == 0 ? 0 : 1;
-    if (!attr_set[kidx]) {
-        if (kidx == 0)
-            CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-        else
-            CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-        attr_set[kidx] = true;
-    }
+    const bool stored = dp->tc_a != nullptr;
+    set_tc_attributes();
     tc_launches = 0;
     for (int r0 = 0; r0 < nrhs; r0 += kTcN, ++launches, ++tc_launches) {
         t.r0 = r0;
@@ -236,8 +244,13 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
         CUDA_CHECK(cudaGetLastError());
         ++launches;
         if (r0 == 0) mark(dp, kMainEvent, st);
-        if (kidx == 0) tc_near_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
-        else tc_near_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+        if (stored) {
+            if (kidx == 0) tc_stored_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTcsSmemRequest, st>>>(t);
+            else tc_stored_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTcsSmemRequest, st>>>(t);
+        } else {
+            if (kidx == 0) tc_near_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+            else tc_near_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+        }
         CUDA_CHECK(cudaGetLastError());
     }
     return launches;
@@ -317,7 +330,7 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
 
 }  // namespace
 
-DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
+DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, bool store_tiles) {
     DevicePlan* dp = new DevicePlan();
     try {
         CUDA_CHECK(cudaGetDevice(&dp->device));
@@ -380,7 +393,40 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max) {
         make_buffers<double>(dp, lay, dp->p64);
         dp->p32 = new DeviceBuffers();
         make_buffers<float>(dp, lay, dp->p32);
+        if (store_tiles && dp->n_tc > 0 && !dp->cplx) {
+            // evaluate every tile once (the on-the-fly kernel with zero
+            // charges, recording the values it hands to the tensor core)
+            dp->n_tc_tiles = (int64_t)lay.tc_tiles.size();
+            float* A = dalloc<float>((size_t)dp->n_tc_tiles * kTileFloats, dp->bytes);
+            dp->tc_a = A;
+            DeviceBuffers* b = dp->p32;
+            CUDA_CHECK(cudaMemset(b->Q, 0, (size_t)dp->n_tot * sizeof(float)));
+            set_tc_attributes();
+            tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q, 1,
+                                                             0, (const float4*)b->X, (const float4*)b->Xlo,
+                                                             (const float4*)dp->chunk_center, dp->tc_b);
+            CUDA_CHECK(cudaGetLastError());
+            TcArgs t;
+            t.items = dp->tc_items;
+            t.tiles = dp->tc_tiles;
+            t.X = (const float4*)b->X;
+            t.Xlo = (const float4*)b->Xlo;
+            t.B = dp->tc_b;
+            t.U = (float*)b->U;
+            t.A = A;
+            t.nrhs = 1;
+            t.r0 = 0;
+            t.status = dp->status;
+            if (dp->kind == 0) tc_near_kernel<0, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest>>>(t);
+            else tc_near_kernel<1, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest>>>(t);
+            CUDA_CHECK(cudaGetLastError());
+        }
         CUDA_CHECK(cudaDeviceSynchronize());
+        if (store_tiles) {
+            int stv = 0;
+            CUDA_CHECK(cudaMemcpy(&stv, dp->status, sizeof(int), cudaMemcpyDeviceToHost));
+            if (stv != 0) throw Error(-4, "the fill pass of the stored tiles timed out");
+        }
     } catch (...) {
         device_plan_destroy(dp);
         throw;
@@ -396,7 +442,7 @@ void device_plan_destroy(DevicePlan* dp) {
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
                     dp->tc_items, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
-                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b};
+                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);

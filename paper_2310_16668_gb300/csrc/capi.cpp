@@ -94,7 +94,7 @@ void finalize(skel_plan* h, const skel_options* opts) {
     h->n_tc_tiles = (int64_t)lay.tc_tiles.size();
     h->n_mix_items = (int64_t)lay.mix_items.size();
     h->pairs_tc = lay.pairs_tc;
-    if (!h->host_only) h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max);
+    if (!h->host_only) h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max, opts && opts->store_tiles);
     h->t_upload = now() - t0;
 }
 
@@ -280,6 +280,8 @@ int skel_info(skel_handle h, skel_stats* s) {
         s->skel_on_device = P.skel_on_device ? 1 : 0;
         s->t_id_kernels = P.t_id_kernels;
         s->id_gflop = P.id_flops * 1e-9;
+        s->stored_tile_bytes = h->dev ? h->dev->n_tc_tiles * (int64_t)(128 * 32 * sizeof(float)) *
+                                            (h->dev->tc_a != nullptr) : 0;
     });
 }
 

@@ -50,6 +50,8 @@ struct DevicePlan {
     float* chunk_center = nullptr;         // 4 per chunk: its box's centre
     int64_t n_chunks = 0;
     float* tc_b = nullptr;                 // B operand per chunk for one 32-column pass (hi, lo)
+    float* tc_a = nullptr;                 // stored-operator mode: every tile's kernel values
+    int64_t n_tc_tiles = 0;
     int* status = nullptr;                 // device word raised by a bounded wait that gave up
     DeviceBuffers* p64 = nullptr;
     DeviceBuffers* p32 = nullptr;
@@ -66,8 +68,10 @@ struct DevicePlan {
     int64_t bytes = 0;
 };
 
-// Upload a layout; throws Error on failure.
-DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max);
+// Upload a layout; throws Error on failure. store_tiles: also evaluate every
+// tensor-core tile's kernel values once and keep them (n_tiles x 16 KB), so
+// that FP32_TC applies read them instead of evaluating (real kernels).
+DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, bool store_tiles = false);
 void device_plan_destroy(DevicePlan* dp);
 // capture the phases of the next max_applies applies (0 = off)
 void device_set_profiling(DevicePlan* dp, int max_applies);

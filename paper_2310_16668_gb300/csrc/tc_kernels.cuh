@@ -103,6 +103,7 @@ struct TcArgs {
     const float4* Xlo;
     const float* B;                            // per source chunk (kChunkFloats): B hi, B lo, coordinates
     float* U;                                  // entry rows of nrhs (this item's rows are written here)
+    float* A;                                  // stored kernel tiles (kTileFloats per tile), or null
     int nrhs;                                  // right-hand sides (row length of U)
     int r0;                                    // first right-hand side of this pass
     int* status;
@@ -320,7 +321,17 @@ __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict
     }
 }
 
-template <int KIND>
+// Stored kernel tiles (the stored-operator mode): tile t of the tile list
+// keeps its 128 x 32 kernel values (unscaled FP32, zero where a row's slot
+// skips the source) at A + t * kTileFloats, ordered so that compute thread
+// (row, half) reads its 16 values as four 16-byte words with consecutive rows
+// adjacent: value (row, j = 16 half + 4 q + e) at ((half * 4 + q) * 128 + row) * 4 + e.
+constexpr int kTileFloats = 128 * 32;
+__device__ __forceinline__ int64_t tile_word(int half, int q, int row) { return ((half * 4 + q) * 128 + row); }
+
+// RECORD: also write every tile's kernel values to a.A (the fill pass of the
+// stored-operator mode; the values are the ones the MMA consumes, hi + lo).
+template <int KIND, bool RECORD = false>
 __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcShared& S = *reinterpret_cast<TcShared*>(smem_raw);
@@ -495,7 +506,194 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                 }
                 tmem_st16(acol + 16u * g, ghi);
                 tmem_st16(acol + 32u + 16u * g, glo);
+                if constexpr (RECORD) {
+                    float4* dst = reinterpret_cast<float4*>(a.A + (int64_t)(list_lo + u) * kTileFloats);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int jj = 4 * q;
+                        dst[tile_word(half, q, row)] =
+                            make_float4(__uint_as_float(ghi[jj]) + __uint_as_float(glo[jj]),
+                                        __uint_as_float(ghi[jj + 1]) + __uint_as_float(glo[jj + 1]),
+                                        __uint_as_float(ghi[jj + 2]) + __uint_as_float(glo[jj + 2]),
+                                        __uint_as_float(ghi[jj + 3]) + __uint_as_float(glo[jj + 3]));
+                    }
+                }
             }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(sm_addr(&S.afull[s]));
+        }
+        for (int m = (ntile >= 2 ? ntile - 2 : 0); m < ntile; ++m) drain(m);
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) acc[c] += S.outer[c][tid];
+        if (valid) {
+            const float scale = (float)green_scale<KIND>();
+            const int64_t base = (row_off + row) * a.nrhs;
+            const int c0 = a.r0 + kCols * half;
+#pragma unroll
+            for (int c = 0; c < kCols; ++c)
+                if (c0 + c < a.nrhs) a.U[base + c0 + c] = scale * acc[c];
+        }
+    }
+    if (err) atomicExch(a.status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(kTmemCols));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stored-operator mode: the same translations with the kernel values read
+// from the tiles a RECORD pass wrote, instead of evaluated. Per tile the
+// producer copies 24 KB (the chunk's B hi + lo and the 16 KB kernel tile);
+// the compute warps only split the values into TF32 hi + lo and write A to
+// tensor memory. The MMA issue, the accumulator drain and the two-level sum
+// are those of tc_near_kernel, so both modes give the same result bit for
+// bit. Bound: HBM, n_tiles x 16 KB of kernel values per pass.
+static_assert(kSrcPerThread == 16, "stored tiles assume two compute threads per row");
+constexpr int kNSS = 3;                        // data stages (24 KB each)
+struct alignas(128) TcSStage {
+    float b[2 * 1024];                         // B hi, B lo (the first 8 KB of the chunk block)
+    float4 ga[kTileFloats / 4];                // the tile's kernel values
+};
+struct TcSShared {
+    TcSStage st[kNSS];
+    float outer[kTcN / kTpr][kTcCompute];
+    uint64_t full[kNSS], afull[kNSS], empty[kNSS];
+    uint32_t tmem;
+};
+constexpr int kTcsSmemRequest = 100 * 1024;   // two CTAs per SM
+static_assert(sizeof(TcSShared) <= kTcsSmemRequest, "shared memory plan (stored mode)");
+
+template <int KIND>
+__global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSShared& S = *reinterpret_cast<TcSShared*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const TcItem* itp = a.items + blockIdx.x;
+    const int64_t row_off = itp->row_off;
+    const int nrows = itp->nrows, list_lo = itp->list_lo;
+    const int ntile = itp->list_hi - list_lo;
+
+    if (tid == 0) {
+        for (int s = 0; s < kNSS; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sm_addr(&S.afull[s])), "r"(kTcCompute));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.empty[s])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(sm_addr(&S.tmem)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = S.tmem;
+    bool err = false;
+
+    if (warp == kTcCompute / 32) {
+        // ---------------- producer warp ----------------
+        for (int t0 = 0; t0 < ntile; t0 += 32) {
+            const int d_chunk = t0 + lane < ntile ? a.tiles[list_lo + t0 + lane].chunk : 0;
+            const int nb = min(32, ntile - t0);
+            for (int i = 0; i < nb; ++i) {
+                const int t = t0 + i;
+                const int s = t % kNSS;
+                const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
+                if (t >= kNSS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1))) err = true;
+                if (lane == 0) {
+                    const uint32_t bar = sm_addr(&S.full[s]);
+                    mbar_arrive_tx(bar, 4u * 2048u + 4u * kTileFloats);
+                    bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
+                    bulk_g2s(sm_addr(S.st[s].ga), a.A + (int64_t)(list_lo + t) * kTileFloats, 4u * kTileFloats, bar);
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0) {
+            for (int t = (ntile > kNSS ? ntile - kNSS : 0); t < ntile; ++t)
+                if (!mbar_wait(sm_addr(&S.full[t % kNSS]), (uint32_t)((t / kNSS) & 1))) err = true;
+        }
+    } else if (warp == kTcCompute / 32 + 1) {
+        // ---------------- MMA issuer (one thread) ----------------
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                                   ((128u >> 4) << 24);
+            for (int m = 0; m < ntile; ++m) {
+                const int s = m % kNSS, ab = m % kNA;
+                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kNSS) & 1))) err = true;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t bh = sm_addr(S.st[s].b), bl = bh + 4u * 1024u;
+                const uint32_t d = tbase + kColD + 32u * (m & 1);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t ahi = tbase + kColA + 64u * ab + 8u * k, alo = ahi + 32u;
+                    mma_tf32(d, ahi, smem_desc(bh + 2u * kBLbo * k), idesc, k > 0 ? 1u : 0u);
+                    mma_tf32(d, ahi, smem_desc(bl + 2u * kBLbo * k), idesc, 1u);
+                    mma_tf32(d, alo, smem_desc(bh + 2u * kBLbo * k), idesc, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(sm_addr(&S.empty[s])) : "memory");
+            }
+        }
+    } else {
+        // ---------------- compute warps ----------------
+        const int row = tid & 127, half = tid >> 7;
+        const bool valid = row < nrows;
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        constexpr int kCols = kTcN / kTpr;
+        const int j0 = kSrcPerThread * half;
+        float acc[kCols];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+            acc[c] = 0.f;
+            S.outer[c][tid] = 0.f;
+        }
+        auto drain = [&](int m) {
+            if (!mbar_wait(sm_addr(&S.empty[m % kNSS]), (uint32_t)((m / kNSS) & 1))) err = true;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t v[kCols];
+            tmem_ld16(tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kCols * half), v);
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) acc[c] += __uint_as_float(v[c]);
+            if (m % kTcGroup == kTcGroup - 1) {
+#pragma unroll
+                for (int c = 0; c < kCols; ++c) {
+                    S.outer[c][tid] += acc[c];
+                    acc[c] = 0.f;
+                }
+            }
+        };
+        const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
+        for (int u = 0; u < ntile; ++u) {
+            const int s = u % kNSS;
+            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNSS) & 1))) err = true;
+            uint32_t ghi[16], glo[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 g4 = S.st[s].ga[tile_word(half, q, row)];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 g = h ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
+                    const float2 t = __fmul2_rn(g, split);
+                    const float2 hi = __ffma2_rn(__ffma2_rn(g, m1, t), m1, t);
+                    const float2 lo = __ffma2_rn(hi, m1, g);
+                    const int jj = 4 * q + 2 * h;
+                    ghi[jj] = __float_as_uint(hi.x);
+                    ghi[jj + 1] = __float_as_uint(hi.y);
+                    glo[jj] = __float_as_uint(lo.x);
+                    glo[jj + 1] = __float_as_uint(lo.y);
+                }
+            }
+            if (u >= 2) drain(u - 2);
+            const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + (uint32_t)j0;
+            tmem_st16(acol, ghi);
+            tmem_st16(acol + 32u, glo);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(sm_addr(&S.afull[s]));

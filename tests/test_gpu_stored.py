@@ -1,0 +1,72 @@
+"""Stored-operator mode (``store_tiles``): the tensor-core apply reading kernel
+tiles evaluated once at build must equal the on-the-fly apply bit for bit
+(the stored values are exactly the ones the tensor core consumed), and so
+inherits its parity with the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import direct
+from paper_2310_16668_gb300 import SkelFMM
+from paper_2310_16668_gb300 import workloads as W
+from tests._util import clustered, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_16668_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("kind,dim,dist,b,tol", [("laplace3d", 3, "uniform", 64, 1e-6),
+                                                 ("laplace3d", 3, "clustered", 32, 1e-6),
+                                                 ("laplace2d", 2, "clustered", 32, 1e-8)])
+@pytest.mark.parametrize("nrhs", [32, 64])
+def test_stored_tiles_equal_on_the_fly(kind, dim, dist, b, tol, nrhs):
+    x = W.points_uniform(20000, dim, 31) if dist == "uniform" else clustered(12000, dim, 31)
+    fs = SkelFMM(x, kind, tol, b, nrhs_max=nrhs, store_tiles=True)
+    fo = SkelFMM(x, kind, tol, b, nrhs_max=nrhs)
+    info = fs.info()
+    assert info["stored_tile_bytes"] == info["n_tc_tiles"] * 128 * 32 * 4 > 0
+    assert fo.info()["stored_tile_bytes"] == 0
+    q = torch.from_numpy(W.charges_normal(x.shape[0], nrhs, 32)).cuda().float()
+    us = fs.apply(q, "fp32_tc")
+    uo = fo.apply(q, "fp32_tc")
+    fs.device_status()
+    assert torch.equal(us, uo)
+    ut = fs.apply_transpose(q, "fp32_tc")
+    assert torch.equal(ut, us)                         # real kernels: A~^T = A~
+    # and against the direct sum (RHS 0)
+    ref = direct.direct_sum(kind, x, q[:, 0].double().cpu().numpy())
+    assert relerr(us[:, 0].double().cpu().numpy(), ref) < 10 * tol + 1e-5
+
+
+def test_stored_tiles_ignored_for_complex_kernels():
+    x = clustered(3000, 3, 33)
+    f = SkelFMM(x, "helmholtz3d", 1e-6, 24, kappa=25.0, store_tiles=True)
+    assert f.info()["stored_tile_bytes"] == 0
+    q = torch.from_numpy(W.charges_complex(x.shape[0], 1, 34)[:, 0]).cuda()
+    u = f.apply(q, "fp64").cpu().numpy()
+    assert relerr(u, direct.direct_sum("helmholtz3d", x, q.cpu().numpy(), kappa=25.0)) < 1e-5
+
+
+@pytest.mark.slow
+def test_full_size_stored_tiles():
+    wl = W.LAPLACE3D_1M
+    x = wl.make_points()
+    qall = torch.from_numpy(wl.make_charges(32)).cuda().float()
+    fs = SkelFMM(x, wl.kernel, wl.tol, wl.leaf, nrhs_max=32, store_tiles=True, device_build=True)
+    us = fs.apply(qall, "fp32_tc")
+    fs.device_status()
+    tg = wl.make_sample()
+    ref = direct.direct_sum(wl.kernel, x, qall[:, 0].double().cpu().numpy(), targets=tg)
+    e = relerr(us[:, 0].double().cpu().numpy()[tg], ref)
+    info = fs.info()
+    print(f"stored tiles: {info['stored_tile_bytes'] / 1e9:.1f} GB, device bytes {info['device_bytes'] / 1e9:.1f} GB, "
+          f"relerr fp32_tc {e:.3e}")
+    assert e < 10 * wl.tol
