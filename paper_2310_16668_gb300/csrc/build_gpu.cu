@@ -117,15 +117,18 @@ struct IdArgs {
     double kappa, tol;
 };
 
-template <int KIND>
-__global__ void __launch_bounds__(kIdThreads) id_kernel(IdArgs A) {
+// NT threads per CTA: 256 on levels with many boxes, 1024 where few boxes
+// (the top levels) would leave most SMs idle
+template <int KIND, int NT>
+__global__ void __launch_bounds__(NT) id_kernel(IdArgs A) {
+    constexpr int kW = NT / 32;
     using S = typename Gd<KIND>::S;
     extern __shared__ __align__(16) unsigned char id_smem[];
     S* v = reinterpret_cast<S*>(id_smem);                  // m
     S* rdiag = v + A.m;                                     // m
     double* nrm = reinterpret_cast<double*>(rdiag + A.m);   // n_max
-    __shared__ double red_v[kIdWarps];
-    __shared__ int red_i[kIdWarps];
+    __shared__ double red_v[kW];
+    __shared__ int red_i[kW];
     __shared__ int sh_p;
     __shared__ double sh_sum;
 
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(kIdThreads) id_kernel(IdArgs A) {
     int32_t* piv = A.piv_out + e0;
 
     // proxy matrix: rows = proxy points (then their conjugates), columns = I_B
-    for (int64_t e = tid; e < (int64_t)m * n; e += kIdThreads) {
+    for (int64_t e = tid; e < (int64_t)m * n; e += NT) {
         const int j = (int)(e / m), i = (int)(e - (int64_t)j * m);
         const int ip = i < np ? i : i - np;
         const double* x = A.pts + I[j] * dim;
@@ -153,9 +156,9 @@ __global__ void __launch_bounds__(kIdThreads) id_kernel(IdArgs A) {
         if (i >= np) g = cj(g);
         M[e] = g;
     }
-    for (int c = tid; c < n; c += kIdThreads) piv[c] = c;
+    for (int c = tid; c < n; c += NT) piv[c] = c;
     __syncthreads();
-    for (int c = warp; c < n; c += kIdWarps) {
+    for (int c = warp; c < n; c += kW) {
         const S* col = M + (size_t)c * m;
         double s = 0.0;
         for (int i = lane; i < m; i += 32) s += sq(col[i]);
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(kIdThreads) id_kernel(IdArgs A) {
         // pivot: the largest remaining norm, ties to the lowest index
         double bv = -1.0;
         int bi = n;
-        for (int c = j + tid; c < n; c += kIdThreads)
+        for (int c = j + tid; c < n; c += NT)
             if (nrm[c] > bv) { bv = nrm[c]; bi = c; }
         for (int o = 16; o > 0; o >>= 1) {
             const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(kIdThreads) id_kernel(IdArgs A) {
         if (tid == 0) {
             double wv = red_v[0];
             int wi = red_i[0];
-            for (int w = 1; w < kIdWarps; ++w)
+            for (int w = 1; w < kW; ++w)
                 if (red_v[w] > wv || (red_v[w] == wv && red_i[w] < wi)) { wv = red_v[w]; wi = red_i[w]; }
             sh_p = wi;
         }
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(kIdThreads) id_kernel(IdArgs A) {
         if (cn == 0.0 || !(cn > A.tol * r00)) { k = j; break; }
         // swap columns j and p (every row: rows above j hold R), keeping the
         // pivot column's trailing part as the reflector's vector
-        for (int i = tid; i < m; i += kIdThreads) {
+        for (int i = tid; i < m; i += NT) {
             const S pv = M[(size_t)p * m + i];
             if (p != j) {
                 M[(size_t)p * m + i] = M[(size_t)j * m + i];
@@ -227,20 +230,20 @@ __global__ void __launch_bounds__(kIdThreads) id_kernel(IdArgs A) {
         }
         __syncthreads();
         double part = 0.0;
-        for (int i = j + tid; i < m; i += kIdThreads) part += sq(v[i]);
+        for (int i = j + tid; i < m; i += NT) part += sq(v[i]);
         part = wsum(part);
         if (lane == 0) red_v[warp] = part;
         __syncthreads();
         if (tid == 0) {
             double s = 0.0;
-            for (int w = 0; w < kIdWarps; ++w) s += red_v[w];
+            for (int w = 0; w < kW; ++w) s += red_v[w];
             sh_sum = s;
         }
         __syncthreads();
         const double vn2 = sh_sum;
         if (vn2 > 0.0) {
             const double two = 2.0 / vn2;
-            for (int c = j + 1 + warp; c < n; c += kIdWarps) {
+            for (int c = j + 1 + warp; c < n; c += kW) {
                 S* col = M + (size_t)c * m;
                 S dot = zero_of<S>();
                 for (int i = j + lane; i < m; i += 32) dot = dot + cj(v[i]) * col[i];
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(kIdThreads) id_kernel(IdArgs A) {
     }
     if (k < 1) k = 1;
     // T = R_11^{-1} R_12, in place over rows 0..k-1 of columns k..n-1
-    for (int c = k + tid; c < n; c += kIdThreads) {
+    for (int c = k + tid; c < n; c += NT) {
         S* col = M + (size_t)c * m;
         for (int i = k - 1; i >= 0; --i) {
             S acc = col[i];
@@ -423,11 +426,16 @@ void build_skeletons_device(Plan& P, const std::vector<std::vector<int64_t>>& le
                 A.tol = P.tol;
                 const size_t smem = 2 * (size_t)m * sz + (size_t)n_max * sizeof(double);
                 if (smem > 200 * 1024) throw Error(-1, "device build: a box is too large for shared memory");
-                void (*kern)(IdArgs) = P.kind == 0 ? id_kernel<0> : P.kind == 1 ? id_kernel<1>
-                                     : P.kind == 2 ? id_kernel<2> : id_kernel<3>;
+                const bool wide = nbox < 2 * 152;           // fewer boxes than two per SM
+                const int nt = wide ? 1024 : kIdThreads;
+                void (*kern)(IdArgs) =
+                    wide ? (P.kind == 0 ? id_kernel<0, 1024> : P.kind == 1 ? id_kernel<1, 1024>
+                            : P.kind == 2 ? id_kernel<2, 1024> : id_kernel<3, 1024>)
+                         : (P.kind == 0 ? id_kernel<0, kIdThreads> : P.kind == 1 ? id_kernel<1, kIdThreads>
+                            : P.kind == 2 ? id_kernel<2, kIdThreads> : id_kernel<3, kIdThreads>);
                 BCHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 BCHECK(cudaEventRecord(ev0));
-                kern<<<(unsigned)nbox, kIdThreads, smem>>>(A);
+                kern<<<(unsigned)nbox, nt, smem>>>(A);
                 BCHECK(cudaGetLastError());
                 BCHECK(cudaEventRecord(ev1));
                 std::vector<int32_t> hk(nbox);
