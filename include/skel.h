@@ -74,8 +74,9 @@ typedef struct {
                          ranks and operators up to rounding (ties in the pivot order
                          may resolve differently). Needs host_only = 0.               */
     int store_tiles;  /* 1 = stored-operator mode: evaluate every tensor-core tile's
-                         128 x 32 kernel values once at build and keep them on the
-                         device (n_tc_tiles x 16 KB); FP32_TC applies then read them
+                         kernel values (its item's rows x 32 sources) once at build
+                         and keep them on the device (at most n_tc_tiles x 16 KB;
+                         skel_stats.stored_tile_bytes); FP32_TC applies then read them
                          instead of evaluating the kernel. Same results bit for bit.
                          Real kernels only (ignored otherwise). SKEL_ERR_OOM if the
                          tiles do not fit.                                            */

@@ -228,6 +228,7 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     t.B = dp->tc_b;
     t.U = (float*)b->U;
     t.A = dp->tc_a;
+    t.abase = dp->tc_abase;
     t.nrhs = nrhs;
     t.status = dp->status;
     const int kidx = dp->kind == 0 ? 0 : 1;
@@ -396,9 +397,20 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, b
         if (store_tiles && dp->n_tc > 0 && !dp->cplx) {
             // evaluate every tile once (the on-the-fly kernel with zero
             // charges, recording the values it hands to the tensor core)
+            // each item's tiles keep its nrows rows only
             dp->n_tc_tiles = (int64_t)lay.tc_tiles.size();
-            float* A = dalloc<float>((size_t)dp->n_tc_tiles * kTileFloats, dp->bytes);
+            std::vector<int64_t> abase(lay.tc_items.size());
+            int64_t nf = 0;
+            for (size_t i = 0; i < lay.tc_items.size(); ++i) {
+                const TcItem& it = lay.tc_items[i];
+                if (it.nrows < 1 || it.nrows > kTcRows) throw Error(-5, "tensor-core item with no rows");
+                abase[i] = nf;
+                nf += (int64_t)(it.list_hi - it.list_lo) * it.nrows * 32;
+            }
+            dp->tc_abase = upload(abase, dp->bytes);
+            float* A = dalloc<float>((size_t)nf, dp->bytes);
             dp->tc_a = A;
+            dp->stored_bytes = nf * (int64_t)sizeof(float);
             DeviceBuffers* b = dp->p32;
             CUDA_CHECK(cudaMemset(b->Q, 0, (size_t)dp->n_tot * sizeof(float)));
             set_tc_attributes();
@@ -414,6 +426,7 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, b
             t.B = dp->tc_b;
             t.U = (float*)b->U;
             t.A = A;
+            t.abase = dp->tc_abase;
             t.nrhs = 1;
             t.r0 = 0;
             t.status = dp->status;
@@ -442,7 +455,7 @@ void device_plan_destroy(DevicePlan* dp) {
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
                     dp->tc_items, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
-                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a};
+                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a, dp->tc_abase};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);

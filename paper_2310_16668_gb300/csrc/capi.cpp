@@ -280,8 +280,7 @@ int skel_info(skel_handle h, skel_stats* s) {
         s->skel_on_device = P.skel_on_device ? 1 : 0;
         s->t_id_kernels = P.t_id_kernels;
         s->id_gflop = P.id_flops * 1e-9;
-        s->stored_tile_bytes = h->dev ? h->dev->n_tc_tiles * (int64_t)(128 * 32 * sizeof(float)) *
-                                            (h->dev->tc_a != nullptr) : 0;
+        s->stored_tile_bytes = h->dev ? h->dev->stored_bytes : 0;
     });
 }
 

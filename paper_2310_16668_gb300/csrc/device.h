@@ -51,7 +51,9 @@ struct DevicePlan {
     int64_t n_chunks = 0;
     float* tc_b = nullptr;                 // B operand per chunk for one 32-column pass (hi, lo)
     float* tc_a = nullptr;                 // stored-operator mode: every tile's kernel values
+    int64_t* tc_abase = nullptr;           // per tensor-core item: first float of its tiles in tc_a
     int64_t n_tc_tiles = 0;
+    int64_t stored_bytes = 0;
     int* status = nullptr;                 // device word raised by a bounded wait that gave up
     DeviceBuffers* p64 = nullptr;
     DeviceBuffers* p32 = nullptr;
@@ -69,7 +71,7 @@ struct DevicePlan {
 };
 
 // Upload a layout; throws Error on failure. store_tiles: also evaluate every
-// tensor-core tile's kernel values once and keep them (n_tiles x 16 KB), so
+// tensor-core tile's kernel values once and keep them (nrows x 128 B per tile), so
 // that FP32_TC applies read them instead of evaluating (real kernels).
 DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, bool store_tiles = false);
 void device_plan_destroy(DevicePlan* dp);

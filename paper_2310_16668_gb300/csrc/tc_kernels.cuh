@@ -103,7 +103,8 @@ struct TcArgs {
     const float4* Xlo;
     const float* B;                            // per source chunk (kChunkFloats): B hi, B lo, coordinates
     float* U;                                  // entry rows of nrhs (this item's rows are written here)
-    float* A;                                  // stored kernel tiles (kTileFloats per tile), or null
+    float* A;                                  // stored kernel tiles, or null
+    const int64_t* abase;                      // per item: first float of its stored tiles
     int nrhs;                                  // right-hand sides (row length of U)
     int r0;                                    // first right-hand side of this pass
     int* status;
@@ -321,13 +322,14 @@ __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict
     }
 }
 
-// Stored kernel tiles (the stored-operator mode): tile t of the tile list
-// keeps its 128 x 32 kernel values (unscaled FP32, zero where a row's slot
-// skips the source) at A + t * kTileFloats, ordered so that compute thread
-// (row, half) reads its 16 values as four 16-byte words with consecutive rows
-// adjacent: value (row, j = 16 half + 4 q + e) at ((half * 4 + q) * 128 + row) * 4 + e.
-constexpr int kTileFloats = 128 * 32;
-__device__ __forceinline__ int64_t tile_word(int half, int q, int row) { return ((half * 4 + q) * 128 + row); }
+// Stored kernel tiles (the stored-operator mode): the u-th tile of an item
+// with nrows rows keeps its nrows x 32 kernel values (unscaled FP32, zero
+// where a row's slot skips the source; rows past nrows are not stored) at
+// A + abase[item] + u * nrows * 32, ordered so that compute thread (row,
+// half) reads its 16 values as four 16-byte words with consecutive rows
+// adjacent: value (row, j = 16 half + 4 q + e) at ((half * 4 + q) * nrows + row) * 4 + e.
+constexpr int kTileFloats = 128 * 32;          // the largest tile
+__device__ __forceinline__ int tile_word(int half, int q, int row, int nrows) { return (half * 4 + q) * nrows + row; }
 
 // RECORD: also write every tile's kernel values to a.A (the fill pass of the
 // stored-operator mode; the values are the ones the MMA consumes, hi + lo).
@@ -507,11 +509,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                 tmem_st16(acol + 16u * g, ghi);
                 tmem_st16(acol + 32u + 16u * g, glo);
                 if constexpr (RECORD) {
-                    float4* dst = reinterpret_cast<float4*>(a.A + (int64_t)(list_lo + u) * kTileFloats);
+                    float4* dst = reinterpret_cast<float4*>(a.A + a.abase[blockIdx.x] + (int64_t)u * nrows * 32);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int jj = 4 * q;
-                        dst[tile_word(half, q, row)] =
+                        if (valid) dst[tile_word(half, q, row, nrows)] =
                             make_float4(__uint_as_float(ghi[jj]) + __uint_as_float(glo[jj]),
                                         __uint_as_float(ghi[jj + 1]) + __uint_as_float(glo[jj + 1]),
                                         __uint_as_float(ghi[jj + 2]) + __uint_as_float(glo[jj + 2]),
@@ -551,7 +553,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
 // the compute warps only split the values into TF32 hi + lo and write A to
 // tensor memory. The MMA issue, the accumulator drain and the two-level sum
 // are those of tc_near_kernel, so both modes give the same result bit for
-// bit. Bound: HBM, n_tiles x 16 KB of kernel values per pass.
+// bit. Bound: HBM, nrows x 128 bytes of kernel values per tile and pass.
 static_assert(kSrcPerThread == 16, "stored tiles assume two compute threads per row");
 constexpr int kNSS = 3;                        // data stages (24 KB each)
 struct alignas(128) TcSStage {
@@ -598,6 +600,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
 
     if (warp == kTcCompute / 32) {
         // ---------------- producer warp ----------------
+        const float* tiles_src = a.A + a.abase[blockIdx.x];
+        const uint32_t tile_bytes = 128u * (uint32_t)nrows;    // nrows x 32 floats (1 <= nrows <= 128)
         for (int t0 = 0; t0 < ntile; t0 += 32) {
             const int d_chunk = t0 + lane < ntile ? a.tiles[list_lo + t0 + lane].chunk : 0;
             const int nb = min(32, ntile - t0);
@@ -608,9 +612,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
                 if (t >= kNSS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1))) err = true;
                 if (lane == 0) {
                     const uint32_t bar = sm_addr(&S.full[s]);
-                    mbar_arrive_tx(bar, 4u * 2048u + 4u * kTileFloats);
+                    mbar_arrive_tx(bar, 4u * 2048u + tile_bytes);
                     bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
-                    bulk_g2s(sm_addr(S.st[s].ga), a.A + (int64_t)(list_lo + t) * kTileFloats, 4u * kTileFloats, bar);
+                    bulk_g2s(sm_addr(S.st[s].ga), tiles_src + (int64_t)t * nrows * 32, tile_bytes, bar);
                 }
                 __syncwarp();
             }
@@ -676,7 +680,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             uint32_t ghi[16], glo[16];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 g4 = S.st[s].ga[tile_word(half, q, row)];
+                const float4 g4 = valid ? S.st[s].ga[tile_word(half, q, row, nrows)] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const float2 g = h ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
