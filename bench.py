@@ -67,6 +67,9 @@ def parse_args():
                    help="where Algorithm 1 runs (outside the timed region either way)")
     p.add_argument("--store-tiles", action="store_true",
                    help="stored-operator mode: kernel tiles evaluated once at build, read by every apply")
+    p.add_argument("--tune", default="auto", choices=["auto", "none"],
+                   help="auto: skel_autotune after the build (per-level up/down variants; stored or on-the-fly "
+                        "kernel tiles, chosen by measurement); none: the default rules, tiles on the fly")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -354,10 +357,20 @@ def run_ours(args):
     fmm = SkelFMM(x, wl.kernel, tol, wl.leaf, kappa=wl.kappa, nrhs_max=nrhs, num_threads=threads,
                   device_build=args.build == "device", store_tiles=args.store_tiles)
     t_build = time.perf_counter() - t0
+    prec = args.precision or ("fp32" if cplx else "fp32_tc")
+    tuning = None
+    if args.tune == "auto" and not cplx and prec != "fp64":
+        # outside the timed region, like the build: measure the variants on
+        # this plan and keep the faster ones (results are unchanged)
+        t0 = time.perf_counter()
+        try:
+            tuning = fmm.autotune(nrhs, allow_store=True)
+            tuning["t_tune_s"] = time.perf_counter() - t0
+        except Exception as e:                          # keep the untuned plan
+            tuning = {"error": str(e)}
     info = fmm.info()
     pairs = info["pairs_direct"] + info["pairs_far"]
 
-    prec = args.precision or ("fp32" if cplx else "fp32_tc")
     if cplx:
         rdt = torch.complex128 if prec == "fp64" else torch.complex64
     else:
@@ -524,8 +537,11 @@ def run_ours(args):
                    "l2": "inputs larger than L2: operators + entry arrays "
                          f"{info['device_bytes'] / 1e9:.2f} GB resident",
                    "k_max": info["k_max"], "levels": info["n_levels"], "t_build_s": t_build,
-                   "pairs_per_apply": pairs},
+                   "pairs_per_apply": pairs,
+                   "translations": ("stored kernel tiles" if info["stored_tile_bytes"] > 0 else "kernel on the fly")
+                                   + (", chosen by skel_autotune" if tuning and "error" not in tuning else "")},
         "relerr": out.get("relerr"),
+        "tuning": tuning,
         "build": {"where": args.build, "t_build_s": t_build, "t_tree_s": info["t_tree"], "t_skel_s": info["t_skel"],
                   "t_upload_s": info["t_upload"], "host_threads": threads,
                   "t_id_kernels_s": info["t_id_kernels"] if args.build == "device" else None,

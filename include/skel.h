@@ -291,6 +291,34 @@ int skel_last_timings(skel_handle h, skel_timings* t);
 int skel_device_status(skel_handle h);
 
 /*
+ * skel_autotune — pick, by measurement on this plan and device, the variants
+ * the FP32 applies of nrhs right-hand sides will use: per tree level the
+ * up/down kernel (plain or with register prefetch of the next inner chunk),
+ * and for the tensor-core translations (real kernels, nrhs >= 4) whether the
+ * kernel values are evaluated on the fly or read from stored tiles (the
+ * choice between operators stored and evaluated on the fly; stored only if
+ * allow_store and the tiles fit the free device memory with 2 GB to spare;
+ * tiles that lose are freed). Every variant computes the same result, so
+ * tuning changes speed and memory only. Synchronous on `stream`, uses the
+ * plan's own buffers (no concurrent apply on the handle; not capturable).
+ *   h            plan with a device part; real kernels only
+ *   nrhs         1 .. nrhs_max
+ *   out          may be NULL; receives the measurements
+ * Errors: SKEL_ERR_ARG, SKEL_ERR_STATE (host-only plan), SKEL_ERR_OOM,
+ * SKEL_ERR_CUDA, SKEL_ERR_TIMEOUT (a bounded wait of the fill pass gave up).
+ */
+typedef struct {
+    double ms_onfly;          /* one tensor-core pass, kernel evaluated on the fly (-1: not timed) */
+    double ms_stored;         /* the same reading stored tiles (-1: not timed)                   */
+    int    stored;            /* 1 if the plan keeps stored tiles after tuning                  */
+    int    n_updown;          /* up/down level launches measured                                */
+    int    n_changed;         /* of those, choices unlike the default rule                      */
+    double ms_updown_default; /* their summed time with the default rule                        */
+    double ms_updown_tuned;   /* and with the chosen variants                                   */
+} skel_tuning;
+int skel_autotune(skel_handle h, int nrhs, int allow_store, void* stream, skel_tuning* out);
+
+/*
  * skel_direct_noalloc — u = A q by direct summation (FP64; complex128 for
  * Helmholtz), for callers that cannot allocate device memory: code running
  * inside a framework that owns (and has reserved) the device memory pool, or

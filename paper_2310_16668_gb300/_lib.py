@@ -21,7 +21,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_tc": 2}
 SYMBOLS = ("skel_build", "skel_apply", "skel_apply_transpose", "skel_free", "skel_info",
            "skel_last_error", "skel_plan_get_dims", "skel_plan_export", "skel_plan_import",
            "skel_neighbors_export", "skel_set_profiling", "skel_last_timings",
-           "skel_device_status", "skel_direct_noalloc", "skel_apply_batch")
+           "skel_device_status", "skel_direct_noalloc", "skel_apply_batch", "skel_autotune")
 
 
 class SkelKernel(ctypes.Structure):
@@ -60,6 +60,12 @@ class SkelTimings(ctypes.Structure):
                 ("ms_main", ctypes.c_double), ("main_launches", ctypes.c_int)]
 
 
+class SkelTuning(ctypes.Structure):
+    _fields_ = [("ms_onfly", ctypes.c_double), ("ms_stored", ctypes.c_double), ("stored", ctypes.c_int),
+                ("n_updown", ctypes.c_int), ("n_changed", ctypes.c_int),
+                ("ms_updown_default", ctypes.c_double), ("ms_updown_tuned", ctypes.c_double)]
+
+
 class SkelError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -95,6 +101,7 @@ def load() -> ctypes.CDLL:
     lib.skel_device_status.argtypes = [P]
     lib.skel_direct_noalloc.argtypes = [P, I64, I, SkelKernel, P, P, I, P]
     lib.skel_apply_batch.argtypes = [P, I, P, P, I, I, I, P]
+    lib.skel_autotune.argtypes = [P, I, I, P, ctypes.POINTER(SkelTuning)]
     for name in SYMBOLS:
         if name not in ("skel_free", "skel_last_error"):
             getattr(lib, name).restype = ctypes.c_int

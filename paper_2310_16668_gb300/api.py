@@ -15,7 +15,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import SkelKernel, SkelOptions, SkelPlanDims, SkelStats, SkelTimings, check
+from ._lib import SkelKernel, SkelOptions, SkelPlanDims, SkelStats, SkelTimings, SkelTuning, check
 
 PHASES = ("permute_in", "upward", "translations", "reduce", "downward", "permute_out")
 
@@ -143,6 +143,17 @@ class SkelFMM:
     def device_status(self) -> None:
         """Raise SkelError(SKEL_ERR_TIMEOUT) if a bounded device wait gave up."""
         check(self._lib.skel_device_status(self._h))
+
+    def autotune(self, nrhs: int | None = None, allow_store: bool = True, stream=None) -> dict:
+        """Measure and keep the fastest kernel variants for FP32 applies of nrhs
+        right-hand sides (skel_autotune): per-level up/down variants and, for
+        the tensor-core path, stored or on-the-fly kernel tiles."""
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        t = SkelTuning()
+        check(self._lib.skel_autotune(self._h, int(nrhs or self.nrhs_max), int(bool(allow_store)),
+                                      ctypes.c_void_p(stream or 0), ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in SkelTuning._fields_}
 
     def apply_into(self, q_cm, u_cm, nrhs: int, precision: str = "fp32_tc", transpose: bool = False,
                    stream=None) -> None:

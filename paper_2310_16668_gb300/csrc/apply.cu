@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 #include "device.h"
 #include "skel_kernels.cuh"
@@ -126,7 +127,12 @@ void up_down(bool down, const DevicePlan* dp, int l, const S* T, S* X, int nrhs,
     const int nout = down ? dp->up_level_maxr[l] : dp->up_level_maxk[l];
     const dim3 grid((unsigned)(b1 - b0), std::max(1u, ceil_div(nout, kGT)), ceil_div(nrhs, kGT));
     const int ninner = down ? dp->up_level_maxk[l] : dp->up_level_maxr[l];
-    if (ninner > kGT) {
+    bool pref = ninner > kGT;                              // the default rule
+    if (std::is_same<S, float>::value) {                   // FP32 levels the autotuner measured
+        const std::vector<int8_t>& t = down ? dp->pref_down : dp->pref_up;
+        if (l < (int)t.size() && t[l] >= 0) pref = t[l] != 0;
+    }
+    if (pref) {
         if (down) updown_kernel<S, true, true><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
         else updown_kernel<S, false, true><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
     } else {
@@ -329,6 +335,60 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
     }
 }
 
+// Stored-operator mode: evaluate every tile once (the on-the-fly kernel with
+// zero charges, recording the values it hands to the tensor core) into a
+// new allocation; synchronous.
+void fill_tiles(DevicePlan* dp, cudaStream_t st) {
+    if (dp->tc_a) return;
+    int64_t bytes = 0;
+    dp->tc_abase = upload(dp->tc_abase_host, bytes);
+    try {
+        dp->tc_a = dalloc<float>((size_t)dp->store_floats, bytes);
+    } catch (...) {
+        cudaFree(dp->tc_abase);
+        dp->tc_abase = nullptr;
+        throw;
+    }
+    dp->bytes += bytes;
+    dp->stored_bytes = dp->store_floats * (int64_t)sizeof(float);
+    DeviceBuffers* b = dp->p32;
+    CUDA_CHECK(cudaMemsetAsync(b->Q, 0, (size_t)dp->n_tot * sizeof(float), st));
+    set_tc_attributes();
+    tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q, 1, 0,
+                                                           (const float4*)b->X, (const float4*)b->Xlo,
+                                                           (const float4*)dp->chunk_center, dp->tc_b);
+    CUDA_CHECK(cudaGetLastError());
+    TcArgs t;
+    t.items = dp->tc_items;
+    t.tiles = dp->tc_tiles;
+    t.X = (const float4*)b->X;
+    t.Xlo = (const float4*)b->Xlo;
+    t.B = dp->tc_b;
+    t.U = (float*)b->U;
+    t.A = dp->tc_a;
+    t.abase = dp->tc_abase;
+    t.nrhs = 1;
+    t.r0 = 0;
+    t.status = dp->status;
+    if (dp->kind == 0) tc_near_kernel<0, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+    else tc_near_kernel<1, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+    CUDA_CHECK(cudaGetLastError());
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    int stv = 0;
+    CUDA_CHECK(cudaMemcpy(&stv, dp->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (stv != 0) throw Error(-4, "the fill pass of the stored tiles timed out");
+}
+
+void drop_tiles(DevicePlan* dp) {
+    if (!dp->tc_a) return;
+    cudaFree(dp->tc_a);
+    cudaFree(dp->tc_abase);
+    dp->tc_a = nullptr;
+    dp->tc_abase = nullptr;
+    dp->bytes -= dp->stored_bytes + (int64_t)(dp->tc_abase_host.size() * sizeof(int64_t));
+    dp->stored_bytes = 0;
+}
+
 }  // namespace
 
 DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, bool store_tiles) {
@@ -394,52 +454,21 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, b
         make_buffers<double>(dp, lay, dp->p64);
         dp->p32 = new DeviceBuffers();
         make_buffers<float>(dp, lay, dp->p32);
-        if (store_tiles && dp->n_tc > 0 && !dp->cplx) {
-            // evaluate every tile once (the on-the-fly kernel with zero
-            // charges, recording the values it hands to the tensor core)
-            // each item's tiles keep its nrows rows only
+        if (dp->n_tc > 0 && !dp->cplx) {
+            // where each item's stored tiles would go (its nrows rows only)
             dp->n_tc_tiles = (int64_t)lay.tc_tiles.size();
-            std::vector<int64_t> abase(lay.tc_items.size());
+            dp->tc_abase_host.resize(lay.tc_items.size());
             int64_t nf = 0;
             for (size_t i = 0; i < lay.tc_items.size(); ++i) {
                 const TcItem& it = lay.tc_items[i];
                 if (it.nrows < 1 || it.nrows > kTcRows) throw Error(-5, "tensor-core item with no rows");
-                abase[i] = nf;
+                dp->tc_abase_host[i] = nf;
                 nf += (int64_t)(it.list_hi - it.list_lo) * it.nrows * 32;
             }
-            dp->tc_abase = upload(abase, dp->bytes);
-            float* A = dalloc<float>((size_t)nf, dp->bytes);
-            dp->tc_a = A;
-            dp->stored_bytes = nf * (int64_t)sizeof(float);
-            DeviceBuffers* b = dp->p32;
-            CUDA_CHECK(cudaMemset(b->Q, 0, (size_t)dp->n_tot * sizeof(float)));
-            set_tc_attributes();
-            tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q, 1,
-                                                             0, (const float4*)b->X, (const float4*)b->Xlo,
-                                                             (const float4*)dp->chunk_center, dp->tc_b);
-            CUDA_CHECK(cudaGetLastError());
-            TcArgs t;
-            t.items = dp->tc_items;
-            t.tiles = dp->tc_tiles;
-            t.X = (const float4*)b->X;
-            t.Xlo = (const float4*)b->Xlo;
-            t.B = dp->tc_b;
-            t.U = (float*)b->U;
-            t.A = A;
-            t.abase = dp->tc_abase;
-            t.nrhs = 1;
-            t.r0 = 0;
-            t.status = dp->status;
-            if (dp->kind == 0) tc_near_kernel<0, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest>>>(t);
-            else tc_near_kernel<1, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest>>>(t);
-            CUDA_CHECK(cudaGetLastError());
+            dp->store_floats = nf;
+            if (store_tiles) fill_tiles(dp, 0);
         }
         CUDA_CHECK(cudaDeviceSynchronize());
-        if (store_tiles) {
-            int stv = 0;
-            CUDA_CHECK(cudaMemcpy(&stv, dp->status, sizeof(int), cudaMemcpyDeviceToHost));
-            if (stv != 0) throw Error(-4, "the fill pass of the stored tiles timed out");
-        }
     } catch (...) {
         device_plan_destroy(dp);
         throw;
@@ -524,6 +553,92 @@ void device_apply(DevicePlan* dp, const void* q, void* u, int nrhs, int precisio
     } else {
         run_apply<float, false>(dp, dp->p32, q, u, nrhs, transpose, false, st);
     }
+}
+
+TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* stream) {
+    if (dp->cplx) throw Error(-1, "autotune: real kernels only");
+    if (nrhs < 1 || nrhs > dp->nrhs_max) throw Error(-1, "autotune: nrhs must be in [1, nrhs_max]");
+    cudaStream_t st = (cudaStream_t)stream;
+    TuneReport rep;
+    const int saved_cap = dp->prof_cap;
+    dp->prof_cap = 0;                                      // no profiling events while measuring
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    try {
+        CUDA_CHECK(cudaEventCreate(&e0));
+        CUDA_CHECK(cudaEventCreate(&e1));
+        DeviceBuffers* b = dp->p32;
+        const size_t qbytes = (size_t)dp->n_tot * dp->nrhs_max * sizeof(float);
+        CUDA_CHECK(cudaMemsetAsync(b->Q, 0, qbytes, st));  // zero data: timing only, nothing grows
+        CUDA_CHECK(cudaMemsetAsync(b->U, 0, qbytes, st));
+        auto time_ms = [&](auto&& launch, int reps) {
+            launch();                                      // warm-up
+            CUDA_CHECK(cudaEventRecord(e0, st));
+            for (int i = 0; i < reps; ++i) launch();
+            CUDA_CHECK(cudaEventRecord(e1, st));
+            CUDA_CHECK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+            CUDA_CHECK(cudaGetLastError());
+            return (double)ms / reps;
+        };
+        // 1. up/down variant per level
+        const int nl = (int)dp->up_level_ptr.size() - 1;
+        dp->pref_up.assign(std::max(nl, 0), -1);
+        dp->pref_down.assign(std::max(nl, 0), -1);
+        for (int l = 2; l <= dp->L && l < nl; ++l) {
+            if (dp->up_level_ptr[l + 1] == dp->up_level_ptr[l]) continue;
+            for (int down = 0; down < 2; ++down) {
+                std::vector<int8_t>& t = down ? dp->pref_down : dp->pref_up;
+                const float* T = (const float*)(down ? b->Tt : b->T);
+                double ms[2];
+                for (int v = 0; v < 2; ++v) {
+                    t[l] = (int8_t)v;
+                    ms[v] = time_ms([&] { up_down<float>(down != 0, dp, l, T, (float*)(down ? b->U : b->Q), nrhs,
+                                                         down != 0, st); }, 5);
+                }
+                const int ninner = down ? dp->up_level_maxk[l] : dp->up_level_maxr[l];
+                const int def = ninner > kGT ? 1 : 0;
+                const int best = ms[1] < ms[0] ? 1 : 0;
+                t[l] = (int8_t)best;
+                rep.ms_updown_default += ms[def];
+                rep.ms_updown_tuned += ms[best];
+                rep.n_changed += best != def;
+                ++rep.n_levels;
+            }
+        }
+        // 2. tensor-core translations: on the fly or stored tiles
+        if (dp->n_tc > 0 && nrhs >= 4) {
+            int passes = 0;
+            auto tc = [&] { run_tc<float, false>(dp, b, nrhs, st, passes); };
+            float* keep_a = dp->tc_a;
+            int64_t* keep_base = dp->tc_abase;
+            dp->tc_a = nullptr;                            // time the on-the-fly kernel
+            dp->tc_abase = nullptr;
+            rep.ms_onfly = time_ms(tc, 3);
+            dp->tc_a = keep_a;
+            dp->tc_abase = keep_base;
+            if (!dp->tc_a && allow_store) {
+                size_t free_b = 0, total_b = 0;
+                CUDA_CHECK(cudaMemGetInfo(&free_b, &total_b));
+                const size_t need = (size_t)dp->store_floats * sizeof(float) + ((size_t)2 << 30);
+                if (free_b > need) fill_tiles(dp, st);
+            }
+            if (dp->tc_a) {
+                rep.ms_stored = time_ms(tc, 3);
+                if (rep.ms_stored >= rep.ms_onfly) drop_tiles(dp);
+            }
+            rep.stored = dp->tc_a != nullptr;
+        }
+    } catch (...) {
+        dp->prof_cap = saved_cap;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        throw;
+    }
+    dp->prof_cap = saved_cap;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rep;
 }
 
 }  // namespace skel

@@ -518,4 +518,23 @@ int skel_device_status(skel_handle h) {
     return SKEL_OK;
 }
 
+int skel_autotune(skel_handle h, int nrhs, int allow_store, void* stream, skel_tuning* out) {
+    return guarded([&] {
+        if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");
+        if (!h->dev) throw Error(SKEL_ERR_STATE, "plan was built host-only");
+        if (h->dev->cplx) throw Error(SKEL_ERR_ARG, "autotune covers the real kernels");
+        if (nrhs < 1 || nrhs > h->nrhs_max) throw Error(SKEL_ERR_ARG, "nrhs must be in [1, nrhs_max]");
+        const skel::TuneReport r = skel::device_autotune(h->dev, nrhs, allow_store != 0, stream);
+        if (out) {
+            out->ms_onfly = r.ms_onfly;
+            out->ms_stored = r.ms_stored;
+            out->stored = r.stored;
+            out->n_updown = r.n_levels;
+            out->n_changed = r.n_changed;
+            out->ms_updown_default = r.ms_updown_default;
+            out->ms_updown_tuned = r.ms_updown_tuned;
+        }
+    });
+}
+
 }  // extern "C"

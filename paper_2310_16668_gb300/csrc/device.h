@@ -52,8 +52,13 @@ struct DevicePlan {
     float* tc_b = nullptr;                 // B operand per chunk for one 32-column pass (hi, lo)
     float* tc_a = nullptr;                 // stored-operator mode: every tile's kernel values
     int64_t* tc_abase = nullptr;           // per tensor-core item: first float of its tiles in tc_a
+    std::vector<int64_t> tc_abase_host;    // the same offsets on the host (kept to fill later)
+    int64_t store_floats = 0;              // floats the stored tiles take
     int64_t n_tc_tiles = 0;
-    int64_t stored_bytes = 0;
+    int64_t stored_bytes = 0;              // 0 unless the tiles are stored
+    // FP32 up/down variant per level (-1: the default rule, 0: plain, 1:
+    // register prefetch), set by the autotuner
+    std::vector<int8_t> pref_up, pref_down;
     int* status = nullptr;                 // device word raised by a bounded wait that gave up
     DeviceBuffers* p64 = nullptr;
     DeviceBuffers* p32 = nullptr;
@@ -82,6 +87,19 @@ int device_status(DevicePlan* dp);
 // summed milliseconds of the 6 phases over the captured applies (waits for them)
 void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_applies, double* ms_main,
                          int* main_launches);
+
+// Measure and keep the faster variants for FP32 applies of nrhs right-hand
+// sides: per level the up/down kernel (plain or register prefetch), and,
+// for the tensor-core path, on-the-fly or stored kernel tiles (stored only
+// if allow_store and the tiles fit the free device memory). Synchronous;
+// uses the plan's own buffers.
+struct TuneReport {
+    double ms_onfly = -1, ms_stored = -1;  // one tensor-core pass (bprep + translations)
+    int stored = 0;                         // the plan keeps stored tiles after tuning
+    int n_levels = 0, n_changed = 0;        // up/down launches timed, choices unlike the default rule
+    double ms_updown_default = 0, ms_updown_tuned = 0;  // summed over the levels, one launch each
+};
+TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* stream);
 
 // Algorithm 2 on `stream`. q, u: device pointers in user order (n x nrhs,
 // each right-hand side contiguous). transpose: run with conj(T).

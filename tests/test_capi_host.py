@@ -124,6 +124,10 @@ def test_import_rejects_inconsistent_plans():
     bad(coord=lambda a: a.__setitem__((leaf, 0), a[leaf, 0] ^ 1))   # box moved away from its points
 
 
+def lib_autotune_null():
+    return _lib.load().skel_autotune(None, 4, 1, None, None)
+
+
 def test_argument_errors():
     x = W.points_uniform(300, 3, 0)
     _expect(-1, SkelFMM, x, "laplace3d", 0.0, 16, host_only=True)        # tol
@@ -135,6 +139,8 @@ def test_argument_errors():
     _expect(-1, SkelFMM, x, "laplace3d", 1e-6, 16, host_only=True, device_build=True)  # needs a device
     f = SkelFMM(x, "laplace3d", 1e-6, 16, host_only=True)
     _expect(-6, f.apply, np.zeros(300))                                   # host-only plan
+    _expect(-6, f.autotune, 4)                                            # nothing to tune on the host
+    assert lib_autotune_null() == -1
     lib = _lib.load()
     assert lib.skel_apply(None, None, None, 1, 0, None) == -1
     lib.skel_free(None)                                                   # NULL is a no-op

@@ -70,3 +70,25 @@ def test_full_size_stored_tiles():
     print(f"stored tiles: {info['stored_tile_bytes'] / 1e9:.1f} GB, device bytes {info['device_bytes'] / 1e9:.1f} GB, "
           f"relerr fp32_tc {e:.3e}")
     assert e < 10 * wl.tol
+
+
+@pytest.mark.parametrize("kind,dim", [("laplace3d", 3), ("laplace2d", 2)])
+def test_autotune_keeps_results(kind, dim):
+    """The autotuner only picks among variants that compute the same thing:
+    the FP32 and FP32_TC applies are bit for bit what they were before."""
+    x = clustered(12000, dim, 35)
+    f = SkelFMM(x, kind, 1e-6, 32, nrhs_max=32)
+    q = torch.from_numpy(W.charges_normal(x.shape[0], 32, 36)).cuda().float()
+    tc0, s0 = f.apply(q, "fp32_tc"), f.apply(q[:, :3].contiguous(), "fp32")
+    rep = f.autotune(32, allow_store=True)
+    assert rep["ms_onfly"] > 0 and rep["n_updown"] > 0
+    assert rep["ms_updown_tuned"] <= rep["ms_updown_default"] + 1e-9
+    assert (rep["stored"] == 1) == (f.info()["stored_tile_bytes"] > 0)
+    if rep["stored"]:
+        assert 0 < rep["ms_stored"] < rep["ms_onfly"]
+    tc1, s1 = f.apply(q, "fp32_tc"), f.apply(q[:, :3].contiguous(), "fp32")
+    f.device_status()
+    assert torch.equal(tc0, tc1) and torch.equal(s0, s1)
+    rep2 = f.autotune(32, allow_store=False)          # tuning again is allowed
+    assert torch.equal(f.apply(q, "fp32_tc"), tc0)
+    assert rep2["n_updown"] == rep["n_updown"]
