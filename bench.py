@@ -137,8 +137,11 @@ class ClockSampler:
 
 
 def kernel_source_sha() -> str:
+    """Hash of the files that define the device kernels' code (the kernels and
+    the structures they read); a committed traffic figure counts only while
+    it matches."""
     h = hashlib.sha256()
-    for f in ("skel_kernels.cuh", "apply.cu", "tc_kernels.cuh"):
+    for f in ("skel_kernels.cuh", "tc_kernels.cuh", "host.h"):
         p = os.path.join(ROOT, "paper_2310_16668_gb300", "csrc", f)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
