@@ -1,16 +1,24 @@
-// Algorithm 2 (FMM apply) on the GPU: CUDA-core kernels in FP64 and FP32.
+// Algorithm 2 (FMM apply) on the GPU, and the device plan around it.
 //
 // One apply, all on one stream:
 //   permute_in            q (user order)  -> leaf entries of Q
-//   up_kernel, l = L..2   qhat_S = q_S + T q_R, written into the parent's slot
-//   near_kernel           every translation (ifo / ifs / tfo / level-1 sum,
-//                         subtractions folded in as slot masks, see layout.cpp)
-//                         into per-work-item partial sums
-//   reduce_kernel         partial sums -> U (deterministic order)
-//   down_kernel, l = 2..L uhat_S = U[parent slot]; u_S += uhat; u_R += T^* uhat
+//   updown_kernel (up),   qhat_S = q_S + T q_R, written into the parent's slot
+//     l = L..2
+//   translations          every translation (ifo / ifs / tfo / level-1 sum,
+//                         subtractions folded in as slot masks, see layout.cpp):
+//                         FP64 / FP32 / complex: near_kernel into per-work-item
+//                         partial sums, then reduce_kernel -> U (fixed order);
+//                         FP32_TC: tc_bprep_kernel + tc_near_kernel (kernel
+//                         evaluated on the fly) or tc_stored_kernel (stored
+//                         tiles) per 32 right-hand sides, writing U directly
+//   updown_kernel (down), uhat_S = U[parent slot]; u_S += uhat; u_R += T^* uhat
+//     l = 2..L
 //   permute_out           leaf entries of U -> u (user order)
 //
-// The near field is the hot loop: a warp owns 32 targets (one per lane, in
+// device_autotune measures the variants (up/down kernel per level; stored or
+// on-the-fly tiles) on a plan and keeps the faster ones.
+//
+// The CUDA-core near field: a warp owns 32 targets (one per lane, in
 // registers) and streams the sources of its task range through a per-warp
 // shared-memory tile, every lane reading the same source (a broadcast).
 // Tasks between touching leaves (TASK_ADJ) hold the only close pairs: in FP32
