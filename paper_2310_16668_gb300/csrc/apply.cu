@@ -343,9 +343,20 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
     }
 }
 
+// Free the stored tiles (the plan falls back to the on-the-fly kernel).
+void drop_tiles(DevicePlan* dp) {
+    if (!dp->tc_a) return;
+    cudaFree(dp->tc_a);
+    cudaFree(dp->tc_abase);
+    dp->tc_a = nullptr;
+    dp->tc_abase = nullptr;
+    dp->bytes -= dp->stored_bytes + (int64_t)(dp->tc_abase_host.size() * sizeof(int64_t));
+    dp->stored_bytes = 0;
+}
+
 // Stored-operator mode: evaluate every tile once (the on-the-fly kernel with
 // zero charges, recording the values it hands to the tensor core) into a
-// new allocation; synchronous.
+// new allocation; synchronous. On any failure the tiles are freed again.
 void fill_tiles(DevicePlan* dp, cudaStream_t st) {
     if (dp->tc_a) return;
     int64_t bytes = 0;
@@ -359,43 +370,39 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st) {
     }
     dp->bytes += bytes;
     dp->stored_bytes = dp->store_floats * (int64_t)sizeof(float);
-    DeviceBuffers* b = dp->p32;
-    CUDA_CHECK(cudaMemsetAsync(b->Q, 0, (size_t)dp->n_tot * sizeof(float), st));
-    set_tc_attributes();
-    tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q, 1, 0,
-                                                           (const float4*)b->X, (const float4*)b->Xlo,
-                                                           (const float4*)dp->chunk_center, dp->tc_b);
-    CUDA_CHECK(cudaGetLastError());
-    TcArgs t;
-    t.items = dp->tc_items;
-    t.tiles = dp->tc_tiles;
-    t.X = (const float4*)b->X;
-    t.Xlo = (const float4*)b->Xlo;
-    t.B = dp->tc_b;
-    t.U = (float*)b->U;
-    t.A = dp->tc_a;
-    t.abase = dp->tc_abase;
-    t.nrhs = 1;
-    t.r0 = 0;
-    t.status = dp->status;
-    if (dp->kind == 0) tc_near_kernel<0, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
-    else tc_near_kernel<1, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
-    CUDA_CHECK(cudaGetLastError());
-    CUDA_CHECK(cudaStreamSynchronize(st));
-    int stv = 0;
-    CUDA_CHECK(cudaMemcpy(&stv, dp->status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (stv != 0) throw Error(-4, "the fill pass of the stored tiles timed out");
+    try {
+        DeviceBuffers* b = dp->p32;
+        CUDA_CHECK(cudaMemsetAsync(b->Q, 0, (size_t)dp->n_tot * sizeof(float), st));
+        set_tc_attributes();
+        tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q, 1, 0,
+                                                               (const float4*)b->X, (const float4*)b->Xlo,
+                                                               (const float4*)dp->chunk_center, dp->tc_b);
+        CUDA_CHECK(cudaGetLastError());
+        TcArgs t;
+        t.items = dp->tc_items;
+        t.tiles = dp->tc_tiles;
+        t.X = (const float4*)b->X;
+        t.Xlo = (const float4*)b->Xlo;
+        t.B = dp->tc_b;
+        t.U = (float*)b->U;
+        t.A = dp->tc_a;
+        t.abase = dp->tc_abase;
+        t.nrhs = 1;
+        t.r0 = 0;
+        t.status = dp->status;
+        if (dp->kind == 0) tc_near_kernel<0, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+        else tc_near_kernel<1, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+        CUDA_CHECK(cudaGetLastError());
+        CUDA_CHECK(cudaStreamSynchronize(st));
+        int stv = 0;
+        CUDA_CHECK(cudaMemcpy(&stv, dp->status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (stv != 0) throw Error(-4, "the fill pass of the stored tiles timed out");
+    } catch (...) {
+        drop_tiles(dp);
+        throw;
+    }
 }
 
-void drop_tiles(DevicePlan* dp) {
-    if (!dp->tc_a) return;
-    cudaFree(dp->tc_a);
-    cudaFree(dp->tc_abase);
-    dp->tc_a = nullptr;
-    dp->tc_abase = nullptr;
-    dp->bytes -= dp->stored_bytes + (int64_t)(dp->tc_abase_host.size() * sizeof(int64_t));
-    dp->stored_bytes = 0;
-}
 
 }  // namespace
 
@@ -571,6 +578,8 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
     const int saved_cap = dp->prof_cap;
     dp->prof_cap = 0;                                      // no profiling events while measuring
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float* keep_a = nullptr;                               // stored tiles hidden while timing
+    int64_t* keep_base = nullptr;
     try {
         CUDA_CHECK(cudaEventCreate(&e0));
         CUDA_CHECK(cudaEventCreate(&e1));
@@ -618,13 +627,15 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
         if (dp->n_tc > 0 && nrhs >= 4) {
             int passes = 0;
             auto tc = [&] { run_tc<float, false>(dp, b, nrhs, st, passes); };
-            float* keep_a = dp->tc_a;
-            int64_t* keep_base = dp->tc_abase;
+            keep_a = dp->tc_a;
+            keep_base = dp->tc_abase;
             dp->tc_a = nullptr;                            // time the on-the-fly kernel
             dp->tc_abase = nullptr;
             rep.ms_onfly = time_ms(tc, 3);
             dp->tc_a = keep_a;
             dp->tc_abase = keep_base;
+            keep_a = nullptr;
+            keep_base = nullptr;
             if (!dp->tc_a && allow_store) {
                 size_t free_b = 0, total_b = 0;
                 CUDA_CHECK(cudaMemGetInfo(&free_b, &total_b));
@@ -639,6 +650,10 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
         }
     } catch (...) {
         dp->prof_cap = saved_cap;
+        if (keep_a) {
+            dp->tc_a = keep_a;
+            dp->tc_abase = keep_base;
+        }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         throw;
