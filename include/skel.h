@@ -111,7 +111,8 @@ typedef struct {
 } skel_stats;
 
 /*
- * skel_build — tree, neighbor lists and Algorithm 1 on the host, then upload.
+ * skel_build — tree, neighbor lists (Section 3.1) and Algorithm 1 (on the
+ * host, or on the GPU with opts.device_build), then the device plan.
  *   points     host, n x dim row-major FP64, copied; must be finite
  *   n, dim     n >= 1; dim = 2 for SKEL_LAPLACE_2D, 3 otherwise
  *   k          kernel (kappa >= 0 for Helmholtz)
@@ -126,6 +127,23 @@ typedef struct {
 int skel_build(const double* points, int64_t n, int dim, skel_kernel k,
                double tol, int leaf_size, const skel_options* opts,
                skel_handle* out);
+
+/*
+ * skel_build_batch — skel_build for nsets independent point sets with the
+ * same kernel, tolerance, leaf size and options (the batched workload of many
+ * small sets; pair it with skel_apply_batch).
+ *   points     nsets host pointers, set i: n[i] x dim row-major FP64, copied
+ *   n          nsets sizes, each >= 1
+ *   out        nsets handles; all written on success, none on error
+ * Every argument of every set is checked before any work. The host phases of
+ * many sets run in parallel, one set per host thread (when nsets is at least
+ * the thread count and Algorithm 1 runs on the host); the device plans are
+ * created one after the other. On any error every plan built so far is
+ * freed; the message names the failing set. Errors as skel_build.
+ */
+int skel_build_batch(int nsets, const double* const* points, const int64_t* n, int dim,
+                     skel_kernel k, double tol, int leaf_size,
+                     const skel_options* opts, skel_handle* out);
 
 /*
  * skel_apply — u = A~ q by Algorithm 2 on the GPU.

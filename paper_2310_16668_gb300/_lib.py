@@ -21,7 +21,8 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_tc": 2}
 SYMBOLS = ("skel_build", "skel_apply", "skel_apply_transpose", "skel_free", "skel_info",
            "skel_last_error", "skel_plan_get_dims", "skel_plan_export", "skel_plan_import",
            "skel_neighbors_export", "skel_set_profiling", "skel_last_timings",
-           "skel_device_status", "skel_direct_noalloc", "skel_apply_batch", "skel_autotune")
+           "skel_device_status", "skel_direct_noalloc", "skel_apply_batch", "skel_autotune",
+           "skel_build_batch")
 
 
 class SkelKernel(ctypes.Structure):
@@ -102,6 +103,7 @@ def load() -> ctypes.CDLL:
     lib.skel_direct_noalloc.argtypes = [P, I64, I, SkelKernel, P, P, I, P]
     lib.skel_apply_batch.argtypes = [P, I, P, P, I, I, I, P]
     lib.skel_autotune.argtypes = [P, I, I, P, ctypes.POINTER(SkelTuning)]
+    lib.skel_build_batch.argtypes = [I, P, P, I, SkelKernel, D, I, ctypes.POINTER(SkelOptions), P]
     for name in SYMBOLS:
         if name not in ("skel_free", "skel_last_error"):
             getattr(lib, name).restype = ctypes.c_int

@@ -237,11 +237,26 @@ class SkelBatch:
     """
 
     def __init__(self, point_sets, kernel: str = "laplace2d", tol: float = 1e-7, leaf_size: int = 64,
-                 kappa: float = 0.0, nrhs_max: int = 4, num_threads: int = 0, device_build: bool = False):
+                 kappa: float = 0.0, nrhs_max: int = 4, num_threads: int = 0, device_build: bool = False,
+                 host_only: bool = False):
         self._lib = _lib.load()
-        self.plans = [SkelFMM(p, kernel, tol, leaf_size, kappa=kappa, nrhs_max=nrhs_max, num_threads=num_threads,
-                              device_build=device_build)
-                      for p in point_sets]
+        # every set's plan in one skel_build_batch call (the host phases of
+        # the sets run in parallel)
+        pts = [np.ascontiguousarray(p, dtype=np.float64) for p in point_sets]
+        if not pts:
+            raise ValueError("no point sets")
+        dim = pts[0].shape[1]
+        if any(p.ndim != 2 or p.shape[1] != dim for p in pts):
+            raise ValueError("every set must be an (n_i, dim) array of one dim")
+        ns = len(pts)
+        pp = (ctypes.c_void_p * ns)(*[p.ctypes.data for p in pts])
+        nn = (ctypes.c_int64 * ns)(*[p.shape[0] for p in pts])
+        out = (ctypes.c_void_p * ns)()
+        opts = _options(0, nrhs_max, host_only, num_threads, device_build)
+        check(self._lib.skel_build_batch(ns, pp, nn, dim, SkelKernel(_lib.KERNELS[kernel], float(kappa)), float(tol),
+                                         int(leaf_size), ctypes.byref(opts), out))
+        self.plans = [SkelFMM(None, kernel, tol, leaf_size, kappa=kappa, nrhs_max=nrhs_max,
+                              _handle=ctypes.c_void_p(out[i])) for i in range(ns)]
         self.sizes = [f.n for f in self.plans]
         self._hs = (ctypes.c_void_p * len(self.plans))(*[f._h.value for f in self.plans])
 

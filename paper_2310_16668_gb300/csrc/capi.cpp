@@ -158,6 +158,53 @@ int do_apply(skel_handle h, const void* q, void* u, int nrhs, int precision, voi
     });
 }
 
+void check_build_args(skel_kernel k, double tol, int leaf_size, const skel_options* opts) {
+    if (!(tol > 0 && tol < 1)) throw Error(SKEL_ERR_ARG, "tol must be in (0, 1)");
+    if (leaf_size < 1) throw Error(SKEL_ERR_ARG, "leaf_size must be >= 1");
+    if (opts && opts->device_build && opts->host_only)
+        throw Error(SKEL_ERR_ARG, "device_build needs a device plan (host_only = 0)");
+    (void)k;
+}
+
+// Tree, neighbor lists and Algorithm 1 of one point set (arguments already
+// checked); the device part comes in finalize(). threads: host threads of
+// the host ID build (0 = all).
+skel_plan* build_host(const double* points, int64_t n, int dim, skel_kernel k, double tol, int leaf_size,
+                      const skel_options* opts, int threads) {
+    skel_plan* h = new skel_plan();
+    try {
+        skel::Plan& P = h->plan;
+        P.kind = k.kind;
+        P.kappa = k.kappa;
+        P.tol = tol;
+        P.leaf_size = leaf_size;
+        P.proxy_p = (opts && opts->proxy_p > 0) ? opts->proxy_p : (dim == 2 ? 32 : 12);
+        P.pts.assign(points, points + n * dim);
+        double t0 = now();
+        std::vector<std::vector<int64_t>> leaf_points;
+        skel::build_tree(points, n, dim, leaf_size, P.tree, leaf_points);
+        double t1 = now();
+        if (opts && opts->device_build) {
+            skel::build_skeletons_device(P, leaf_points);
+            P.skel_on_device = true;
+        } else {
+            skel::build_skeletons(P, leaf_points, threads);
+        }
+        P.t_tree = t1 - t0;
+        P.t_skel = now() - t1;
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    return h;
+}
+
+void destroy(skel_plan* h) {
+    if (!h) return;
+    if (h->dev) skel::device_plan_destroy(h->dev);
+    delete h;
+}
+
 }  // namespace
 
 namespace skel {
@@ -173,38 +220,63 @@ int skel_build(const double* points, int64_t n, int dim, skel_kernel k, double t
         if (!out) throw Error(SKEL_ERR_ARG, "out is NULL");
         check_kernel(k, dim);
         check_points(points, n, dim);
-        if (!(tol > 0 && tol < 1)) throw Error(SKEL_ERR_ARG, "tol must be in (0, 1)");
-        if (leaf_size < 1) throw Error(SKEL_ERR_ARG, "leaf_size must be >= 1");
-        if (opts && opts->device_build && opts->host_only)
-            throw Error(SKEL_ERR_ARG, "device_build needs a device plan (host_only = 0)");
-        skel_plan* h = new skel_plan();
+        check_build_args(k, tol, leaf_size, opts);
+        skel_plan* h = build_host(points, n, dim, k, tol, leaf_size, opts, opts ? opts->num_threads : 0);
         try {
-            skel::Plan& P = h->plan;
-            P.kind = k.kind;
-            P.kappa = k.kappa;
-            P.tol = tol;
-            P.leaf_size = leaf_size;
-            P.proxy_p = (opts && opts->proxy_p > 0) ? opts->proxy_p : (dim == 2 ? 32 : 12);
-            P.pts.assign(points, points + n * dim);
-            double t0 = now();
-            std::vector<std::vector<int64_t>> leaf_points;
-            skel::build_tree(points, n, dim, leaf_size, P.tree, leaf_points);
-            double t1 = now();
-            if (opts && opts->device_build) {
-                skel::build_skeletons_device(P, leaf_points);
-                P.skel_on_device = true;
-            } else {
-                skel::build_skeletons(P, leaf_points, opts ? opts->num_threads : 0);
-            }
-            P.t_tree = t1 - t0;
-            P.t_skel = now() - t1;
             finalize(h, opts);
         } catch (...) {
-            if (h->dev) skel::device_plan_destroy(h->dev);
-            delete h;
+            destroy(h);
             throw;
         }
         *out = h;
+    });
+}
+
+int skel_build_batch(int nsets, const double* const* points, const int64_t* n, int dim, skel_kernel k, double tol,
+                     int leaf_size, const skel_options* opts, skel_handle* out) {
+    return guarded([&] {
+        if (nsets < 1 || !points || !n || !out) throw Error(SKEL_ERR_ARG, "nsets < 1 or a NULL array");
+        check_kernel(k, dim);
+        for (int i = 0; i < nsets; ++i) check_points(points[i], n[i], dim);
+        check_build_args(k, tol, leaf_size, opts);
+        std::vector<skel_plan*> hs(nsets, nullptr);
+        // host phases: many small sets in parallel (one thread each), few
+        // large ones one after the other with every thread; Algorithm 1 on
+        // the GPU always one after the other
+        int nthr = 1;
+#ifdef _OPENMP
+        nthr = (opts && opts->num_threads > 0) ? opts->num_threads : omp_get_max_threads();
+#endif
+        const bool across = !(opts && opts->device_build) && nsets >= nthr;
+        std::vector<int> codes(nsets, SKEL_OK);
+        std::vector<std::string> msgs(nsets);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthr) if (across)
+        for (int i = 0; i < nsets; ++i) {
+            try {
+                hs[i] = build_host(points[i], n[i], dim, k, tol, leaf_size, opts, across ? 1 : nthr);
+            } catch (const Error& e) {
+                codes[i] = e.code;
+                msgs[i] = e.what();
+            } catch (const std::bad_alloc&) {
+                codes[i] = SKEL_ERR_OOM;
+                msgs[i] = "host allocation failed";
+            } catch (const std::exception& e) {
+                codes[i] = SKEL_ERR_ARG;
+                msgs[i] = e.what();
+            } catch (...) {
+                codes[i] = SKEL_ERR_ARG;
+                msgs[i] = "unknown error";
+            }
+        }
+        try {
+            for (int i = 0; i < nsets; ++i)
+                if (codes[i] != SKEL_OK) throw Error(codes[i], "set " + std::to_string(i) + ": " + msgs[i]);
+            for (int i = 0; i < nsets; ++i) finalize(hs[i], opts);
+        } catch (...) {
+            for (skel_plan* h : hs) destroy(h);
+            throw;
+        }
+        for (int i = 0; i < nsets; ++i) out[i] = hs[i];
     });
 }
 

@@ -153,3 +153,38 @@ def test_single_leaf_root_plan():
     info = f.info()
     assert info["n_levels"] == 0 and info["n_boxes"] == 1
     assert info["pairs_direct"] == 40 * 40 and info["pairs_far"] == 0
+
+
+@pytest.mark.parametrize("threads", [2, 64])
+def test_build_batch_equals_single_builds(threads):
+    # threads = 2: sets built in parallel, one thread each; 64: one after
+    # the other with all threads. Either way each plan is the single build's.
+    from paper_2310_16668_gb300 import SkelBatch
+    sets = [W.points_curve(n, 100 + i) for i, n in enumerate((300, 1200, 50, 2000, 1))]
+    b = SkelBatch(sets, "laplace2d", 1e-7, 16, num_threads=threads, host_only=True)
+    assert b.sizes == [len(x) for x in sets]
+    for x, f in zip(sets, b.plans):
+        g = SkelFMM(x, "laplace2d", 1e-7, 16, host_only=True)
+        pa, pb = f.export_plan(), g.export_plan()
+        assert pa.keys() == pb.keys()
+        for key in pa:
+            assert np.array_equal(np.asarray(pa[key]), np.asarray(pb[key])), key
+
+
+def test_build_batch_errors_name_the_set():
+    from paper_2310_16668_gb300 import SkelBatch
+    from paper_2310_16668_gb300._lib import SkelError
+    sets = [W.points_uniform(100, 2, i) for i in range(4)]
+    sets[2] = sets[2].copy()
+    sets[2][7, 0] = np.inf
+    with pytest.raises(SkelError) as e:
+        SkelBatch(sets, "laplace2d", 1e-7, 16, host_only=True)
+    assert e.value.code == -5
+    with pytest.raises(SkelError) as e:
+        SkelBatch([W.points_uniform(100, 2, 0)] * 2, "laplace2d", 2.0, 16, host_only=True)   # tol
+    assert e.value.code == -1
+    with pytest.raises(SkelError) as e:                                                       # device build, no device
+        SkelBatch([W.points_uniform(100, 2, 0)], "laplace2d", 1e-7, 16, host_only=True, device_build=True)
+    assert e.value.code == -1
+    lib = _lib.load()
+    assert lib.skel_build_batch(0, None, None, 2, _lib.SkelKernel(0, 0.0), 1e-7, 16, None, None) == -1
