@@ -431,6 +431,7 @@ def run_ours(args):
             n_cpu += n_more
         scale = np.abs(ref).max()
         out["relerr"] = float(np.abs(u_main[sample] - ref).max() / scale)
+        out["relerr_l2"] = float(np.linalg.norm(u_main[sample] - ref) / np.linalg.norm(ref))
         out["cpu_baseline"] = {"value": n_cpu / t_cpu / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"FP64 direct sum at {n_cpu} random targets x {n} sources, "
                                          f"RHS 0 ({t_cpu:.1f} s); value = targets / s"}
@@ -456,7 +457,9 @@ def run_ours(args):
         fp64 = {"precision": "fp64", "nrhs": 1, "ms_per_step": ms64, "value": n / (ms64 * 1e-3) / 1e6,
                 "unit": UNIT}
         if ref is not None:
-            fp64["relerr"] = float(np.abs(u64[0].cpu().numpy()[sample] - ref).max() / np.abs(ref).max())
+            e64 = u64[0].cpu().numpy()[sample] - ref
+            fp64["relerr"] = float(np.abs(e64).max() / np.abs(ref).max())
+            fp64["relerr_l2"] = float(np.linalg.norm(e64) / np.linalg.norm(ref))
 
     # end to end through the C-ABI with pinned host buffers (H2D + apply + D2H per step)
     e2e = None
@@ -544,6 +547,7 @@ def run_ours(args):
                    "translations": ("stored kernel tiles" if info["stored_tile_bytes"] > 0 else "kernel on the fly")
                                    + (", chosen by skel_autotune" if tuning and "error" not in tuning else "")},
         "relerr": out.get("relerr"),
+        "relerr_l2": out.get("relerr_l2"),
         "tuning": tuning,
         "build": {"where": args.build, "t_build_s": t_build, "t_tree_s": info["t_tree"], "t_skel_s": info["t_skel"],
                   "t_upload_s": info["t_upload"], "host_threads": threads,

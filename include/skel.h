@@ -108,6 +108,7 @@ typedef struct {
     double  t_id_kernels;    /* device build: seconds inside the ID kernels (CUDA events) */
     double  id_gflop;        /* device build: GFLOP of the QR reflector updates (FP64)   */
     int64_t stored_tile_bytes; /* store_tiles: device bytes of the stored kernel tiles   */
+    int     n_proxy;         /* proxy points per box (2D: 4p, 3D: 6p^2; Section 2.1)     */
 } skel_stats;
 
 /*

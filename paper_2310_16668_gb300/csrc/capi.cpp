@@ -353,6 +353,7 @@ int skel_info(skel_handle h, skel_stats* s) {
         s->t_id_kernels = P.t_id_kernels;
         s->id_gflop = P.id_flops * 1e-9;
         s->stored_tile_bytes = h->dev ? h->dev->stored_bytes : 0;
+        s->n_proxy = t.dim == 2 ? 4 * P.proxy_p : 6 * P.proxy_p * P.proxy_p;
     });
 }
 

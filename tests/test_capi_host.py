@@ -60,6 +60,7 @@ def test_host_build_matches_oracle(kind, dim, n, b, tol):
         for bx in range(t.n_boxes):
             assert list(lst[ptr[bx]:ptr[bx + 1]]) == lists[bx]
     # IDs: library T on the oracle's own proxy matrix, and ranks vs the oracle
+    assert f.info()["n_proxy"] == len(osk.proxy_points(t.box_center(0), t.box_side(0), dim, osk.DEFAULT_P[dim]))
     sk = osk.Skeletons(t, kind, tol, kappa=25.0)
     ip, tp = pl["idx_ptr"], pl["T_ptr"]
     for bx in range(t.n_boxes):
