@@ -57,3 +57,18 @@ def test_input_generators_hold_no_method_arithmetic():
     for word in ("import torch", "_lib", "skel_", "def kernel", "hankel", "exp(1j", "4 * np.pi", "4.0 * np.pi",
                  "4 * math.pi", "np.log(np.sqrt", "1.0 / (4"):
         assert word not in text, word
+
+
+def test_product_fails_loudly_without_the_library():
+    # no CPU fallback: with the shared library missing, loading raises
+    import subprocess
+    import sys
+    code = ("import paper_2310_16668_gb300._lib as L\n"
+            "L.LIB_PATH = '/nonexistent/libskel.so'\n"
+            "L._lib = None\n"
+            "try:\n"
+            "    L.load()\n"
+            "except ImportError as e:\n"
+            "    print('raised', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.startswith("raised"), r.stdout + r.stderr
