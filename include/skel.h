@@ -165,10 +165,15 @@ int skel_apply(skel_handle h, const void* q, void* u, int nrhs, int precision,
 
 /*
  * skel_apply_transpose — qbar = A~^T ubar (plain transpose, no conjugation).
- * Same arguments and rules as skel_apply. For the real Laplace kernels A~
- * is symmetric and this equals skel_apply; for Helmholtz it runs Algorithm 2
- * with every interpolation matrix T replaced by conj(T) (the kernel blocks
- * are complex-symmetric and the neighbor relations symmetric).
+ * Source: the factorisation of Section 2.2, where a well-separated block is
+ * A_{Bi,Bj} ~ E_{Bi} A_{Si,Sj} F_{Bj} with F_B = [T_B  I] and E_B = F_B^*
+ * (E_B = [T_B^*; I]), applied level by level by Algorithm 2. Transposing
+ * every factor gives F_{Bj}^T A_{Sj,Si} E_{Bi}^T: for the complex-symmetric
+ * Helmholtz kernels that is the same algorithm with every T replaced by
+ * conj(T) in both passes (the kernel blocks are complex-symmetric and the
+ * neighbor relations symmetric); for the real Laplace kernels A~ is
+ * symmetric and this equals skel_apply.
+ * Same arguments, layout, ownership and errors as skel_apply.
  */
 int skel_apply_transpose(skel_handle h, const void* ubar, void* qbar, int nrhs,
                          int precision, void* stream);
@@ -190,15 +195,34 @@ int skel_apply_transpose(skel_handle h, const void* ubar, void* qbar, int nrhs,
 int skel_apply_batch(const skel_handle* hs, int nsets, const void* const* q, void* const* u, int nrhs,
                      int precision, int transpose, void* stream);
 
-/* skel_free — release the handle and all its memory; NULL is a no-op. */
+/*
+ * skel_free — release the handle and all the host and device memory that
+ * skel_build (or skel_plan_import) allocated for it: the tree, the index sets
+ * and every interpolation matrix T_B (the paper's M_proj, the memory of all
+ * T_B in the results notation of Section 5.2), the device operators and the
+ * apply's workspace. NULL is a no-op. No apply on the handle may still be
+ * running (the call does not wait for the caller's streams).
+ */
 void skel_free(skel_handle h);
 
-/* skel_info — sizes, ranks, work counts and build timings of a plan. */
+/*
+ * skel_info — the quantities the paper reports for a run (results notation of
+ * Section 5.2): N (n_points), k_max (largest skeleton rank on levels
+ * >= 2), T_tree (t_tree: tree, 2:1
+ * balance and neighbor lists of Section 3.1), T_skel (t_skel: Algorithm 1)
+ * and the size of all T_B (n_T entries; M_proj = n_T x 8 or 16 bytes), plus
+ * the work counts of the apply (Section 4's cost terms: kernel evaluations
+ * of the translations, boxes, neighbor-list entries) and device figures.
+ *   h   a handle from skel_build / skel_plan_import
+ *   s   caller-owned, filled completely (fields that do not apply are 0)
+ * Errors: SKEL_ERR_ARG (NULL argument).
+ */
 int skel_info(skel_handle h, skel_stats* s);
 
 /*
  * skel_last_error — message of the last failed call on this thread (or an
  * empty string). The pointer stays valid until the next call on the thread.
+ * The paper has no counterpart (it is this C-ABI's error reporting).
  */
 const char* skel_last_error(void);
 
@@ -310,6 +334,31 @@ int skel_last_timings(skel_handle h, skel_timings* t);
 int skel_device_status(skel_handle h);
 
 /*
+ * ---- failure-detection test hooks (the paper has no counterpart) ---------
+ * skel_test_withhold_tile — the next FP32_TC apply on h (tensor-core path)
+ * holds back the bulk copies of the first source tile of its first
+ * tensor-core item until the compute warps' bounded wait for them has run
+ * out, with every bounded wait of that apply limited to wait_limit_ms
+ * (0 < wait_limit_ms <= 2000). The copies are then issued and waited for,
+ * so every barrier phase still completes once per tile and nothing faults
+ * or hangs; that apply's result is invalid and the next skel_device_status
+ * returns SKEL_ERR_TIMEOUT. Later applies are unaffected.
+ * Errors: SKEL_ERR_ARG, SKEL_ERR_STATE (host-only plan, complex kernel, or
+ * no tensor-core items).
+ */
+int skel_test_withhold_tile(skel_handle h, double wait_limit_ms);
+
+/*
+ * skel_test_fail_alloc — the countdown-th device allocation (plan arrays,
+ * stored tiles, host-pointer staging) the library makes after this call
+ * fails as if memory were exhausted; countdown = 0 turns the hook off.
+ * Process-wide. The failing call returns SKEL_ERR_OOM after freeing what it
+ * had allocated, and leaves its output handle untouched.
+ * Errors: SKEL_ERR_ARG (countdown < 0).
+ */
+int skel_test_fail_alloc(int countdown);
+
+/*
  * skel_autotune — pick, by measurement on this plan and device, the variants
  * the FP32 applies of nrhs right-hand sides will use: per tree level the
  * up/down kernel (plain or with register prefetch of the next inner chunk),
@@ -347,16 +396,20 @@ int skel_autotune(skel_handle h, int nrhs, int allow_store, void* stream, skel_t
  *   points     device, n x dim row-major FP64
  *   q, u       device, n x nrhs (each right-hand side contiguous); u is
  *              overwritten; asynchronous on `stream`
- *   n, dim, k  as for skel_build (coincident points contribute nothing)
+ *   n, dim, k  as for skel_build, kappa rules included (coincident points
+ *              contribute nothing)
  * Its partial sums live in one 32 MiB __device__ array inside the library:
  * every GPU that loads the library holds it until the process exits, and all
  * calls share it, so calls that overlap on the GPU race. Each call overwrites
  * every scratch value it reads; nothing has to start at zero. The first call
  * on a device looks up the array's device address there; make that first
  * call before any stream capture.
- * Errors: SKEL_ERR_ARG for NULL or host pointers, bad sizes, or a problem
- * whose partial sums exceed the array (n up to 131,072 for real kernels,
- * 91,168 for the Helmholtz kernels); SKEL_ERR_CUDA.
+ * Errors: SKEL_ERR_ARG for NULL or host pointers, pointers to another
+ * device's memory, a bad kernel, kappa or size, or a problem whose partial
+ * sums exceed the array (n up to 131,072 for real kernels, 91,168 for the
+ * Helmholtz kernels); SKEL_ERR_CUDA for an error the caller's earlier work
+ * left pending (reported and cleared before anything is launched) or for a
+ * failed launch of this call's kernels.
  */
 int skel_direct_noalloc(const double* points, int64_t n, int dim, skel_kernel k,
                         const double* q, double* u, int nrhs, void* stream);

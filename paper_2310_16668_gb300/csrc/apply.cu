@@ -28,7 +28,10 @@
 // box apart and uses the hi part alone.
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -58,11 +61,32 @@ struct DeviceBuffers {
 };
 
 namespace {
+std::atomic<int> g_fail_countdown{0};
+}  // namespace
+
+void set_alloc_failure(int countdown) { g_fail_countdown.store(countdown > 0 ? countdown : 0); }
+
+bool alloc_should_fail() {
+    int c = g_fail_countdown.load();
+    while (c > 0) {
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+    }
+    return false;
+}
+
+namespace {
+
+// NVTX range around a phase of the apply (host side; visible to nsys and ncu)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 template <class T>
 T* dalloc(size_t n, int64_t& bytes) {
     void* p = nullptr;
     if (n == 0) n = 1;
+    if (alloc_should_fail()) throw Error(-2, "cudaMalloc failed: simulated allocation failure (test hook)");
     cudaError_t e = cudaMalloc(&p, n * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -245,12 +269,14 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     t.abase = dp->tc_abase;
     t.nrhs = nrhs;
     t.status = dp->status;
+    t.wait_ns = dp->test_withhold ? dp->test_wait_ns : kWaitLimitNs;
     const int kidx = dp->kind == 0 ? 0 : 1;
     const bool stored = dp->tc_a != nullptr;
     set_tc_attributes();
     tc_launches = 0;
     for (int r0 = 0; r0 < nrhs; r0 += kTcN, ++launches, ++tc_launches) {
         t.r0 = r0;
+        t.withhold_item = (dp->test_withhold && r0 == 0) ? 0 : -1;
         // the pass's B operand blocks, then the translations
         tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q,
                                                                nrhs, r0, (const float4*)b->X,
@@ -268,6 +294,7 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
         }
         CUDA_CHECK(cudaGetLastError());
     }
+    dp->test_withhold = false;
     return launches;
 }
 
@@ -281,57 +308,68 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
     const S* T = (const S*)b->T;
     const S* Tt = (const S*)b->Tt;
     S* part = (S*)b->partial;
+    Range whole(transpose ? "skel apply transpose" : "skel apply");
     // 1. permute in
     mark(dp, 0, st);
     {
+        Range r("permute in");
         ++launches;
         permute<S>(false, dp, (const S*)q, Q, nrhs, st);
         CUDA_CHECK(cudaGetLastError());
     }
     // 2. upward pass, levels L .. 2
     mark(dp, 1, st);
-    for (int l = dp->L; l >= 2; --l) {
-        if (dp->up_level_ptr[l + 1] > dp->up_level_ptr[l]) {
-            ++launches;
-            up_down<S>(false, dp, l, T, Q, nrhs, transpose, st);
-            CUDA_CHECK(cudaGetLastError());
+    {
+        Range r("upward pass");
+        for (int l = dp->L; l >= 2; --l) {
+            if (dp->up_level_ptr[l + 1] > dp->up_level_ptr[l]) {
+                ++launches;
+                up_down<S>(false, dp, l, T, Q, nrhs, transpose, st);
+                CUDA_CHECK(cudaGetLastError());
+            }
         }
     }
     // 3. near field
     mark(dp, 2, st);
-    const bool tc = use_tc && !CPLX && sizeof(Real) == 4 && dp->n_tc > 0;
     int main_launches = 0;
-    if (tc) {
-        launches += run_tc<Real, CPLX>(dp, b, nrhs, st, main_launches);
-        mark(dp, 3, st);
-    } else if (dp->n_items > 0) {
-        auto a = near_args<Real, CPLX>(dp, b, dp->items, dp->n_items, nrhs);
-        const unsigned grid = ceil_div(dp->n_items, kNearWarps);
-        mark(dp, kMainEvent, st);
-        main_launches = launch_near<Real, CPLX>(dp->kind, a, nrhs, grid, st);
-        launches += main_launches;
-        CUDA_CHECK(cudaGetLastError());
-        mark(dp, 3, st);
-        ++launches;
-        reduce<S>(dp->part_ptr, dp->part_idx, part, U, nrhs, dp->n_tot, st);
-        CUDA_CHECK(cudaGetLastError());
-    }
-    else {
-        mark(dp, kMainEvent, st);
-        mark(dp, 3, st);
+    {
+        Range r("translations");
+        const bool tc = use_tc && !CPLX && sizeof(Real) == 4 && dp->n_tc > 0;
+        if (tc) {
+            launches += run_tc<Real, CPLX>(dp, b, nrhs, st, main_launches);
+            mark(dp, 3, st);
+        } else if (dp->n_items > 0) {
+            auto a = near_args<Real, CPLX>(dp, b, dp->items, dp->n_items, nrhs);
+            const unsigned grid = ceil_div(dp->n_items, kNearWarps);
+            mark(dp, kMainEvent, st);
+            main_launches = launch_near<Real, CPLX>(dp->kind, a, nrhs, grid, st);
+            launches += main_launches;
+            CUDA_CHECK(cudaGetLastError());
+            mark(dp, 3, st);
+            ++launches;
+            reduce<S>(dp->part_ptr, dp->part_idx, part, U, nrhs, dp->n_tot, st);
+            CUDA_CHECK(cudaGetLastError());
+        } else {
+            mark(dp, kMainEvent, st);
+            mark(dp, 3, st);
+        }
     }
     // 4. downward pass, levels 2 .. L
     mark(dp, 4, st);
-    for (int l = 2; l <= dp->L; ++l) {
-        if (dp->up_level_ptr[l + 1] > dp->up_level_ptr[l]) {
-            ++launches;
-            up_down<S>(true, dp, l, Tt, U, nrhs, !transpose, st);
-            CUDA_CHECK(cudaGetLastError());
+    {
+        Range r("downward pass");
+        for (int l = 2; l <= dp->L; ++l) {
+            if (dp->up_level_ptr[l + 1] > dp->up_level_ptr[l]) {
+                ++launches;
+                up_down<S>(true, dp, l, Tt, U, nrhs, !transpose, st);
+                CUDA_CHECK(cudaGetLastError());
+            }
         }
     }
     // 5. permute out
     mark(dp, 5, st);
     {
+        Range r("permute out");
         ++launches;
         permute<S>(true, dp, U, (S*)u, nrhs, st);
         CUDA_CHECK(cudaGetLastError());
@@ -390,6 +428,8 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st) {
         t.nrhs = 1;
         t.r0 = 0;
         t.status = dp->status;
+        t.wait_ns = kWaitLimitNs;
+        t.withhold_item = -1;
         if (dp->kind == 0) tc_near_kernel<0, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
         else tc_near_kernel<1, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
         CUDA_CHECK(cudaGetLastError());

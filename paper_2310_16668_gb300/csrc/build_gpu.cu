@@ -28,6 +28,7 @@
 #include <numeric>
 #include <string>
 
+#include "device.h"
 #include "host.h"
 
 namespace skel {
@@ -305,6 +306,7 @@ struct DBuf {
             if (p) cudaFree(p);
             p = nullptr;
             cap = 0;
+            if (alloc_should_fail()) throw Error(-2, "cudaMalloc failed in the device build: simulated (test hook)");
             cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
             if (e != cudaSuccess) {
                 cudaGetLastError();

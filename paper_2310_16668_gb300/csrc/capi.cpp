@@ -60,16 +60,8 @@ int guarded(F&& f) {
 }
 
 void check_kernel(skel_kernel k, int dim) {
-    if (k.kind != SKEL_LAPLACE_2D && k.kind != SKEL_LAPLACE_3D && k.kind != SKEL_HELMHOLTZ_3D &&
-        k.kind != SKEL_HELMHOLTZ_2D)
-        throw Error(SKEL_ERR_ARG, "unknown kernel kind");
-    const bool two_d = k.kind == SKEL_LAPLACE_2D || k.kind == SKEL_HELMHOLTZ_2D;
-    if (two_d != (dim == 2) || (dim != 2 && dim != 3))
-        throw Error(SKEL_ERR_ARG, "dim does not match the kernel (2D kernels: dim 2, others: dim 3)");
-    if (k.kind == SKEL_HELMHOLTZ_3D && !(std::isfinite(k.kappa) && k.kappa >= 0))
-        throw Error(SKEL_ERR_ARG, "kappa must be finite and >= 0");
-    if (k.kind == SKEL_HELMHOLTZ_2D && !(std::isfinite(k.kappa) && k.kappa > 0))
-        throw Error(SKEL_ERR_ARG, "kappa must be finite and > 0 for the 2D Helmholtz kernel");
+    const std::string m = skel::kernel_args_error(k.kind, k.kappa, dim);
+    if (!m.empty()) throw Error(SKEL_ERR_ARG, m);
 }
 
 void check_points(const double* pts, int64_t n, int dim) {
@@ -98,13 +90,17 @@ void finalize(skel_plan* h, const skel_options* opts) {
     h->t_upload = now() - t0;
 }
 
+// device pointer usable on the current device (true), host pointer (false);
+// device memory of another device is an argument error
 bool is_device_ptr(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        throw Error(SKEL_ERR_CUDA, "cudaGetDevice failed");
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    const int w = skel::pointer_place(p, dev);
+    if (w < 0) throw Error(SKEL_ERR_ARG, "a pointer is device memory of another CUDA device");
+    return w == 1;
 }
 
 int do_apply(skel_handle h, const void* q, void* u, int nrhs, int precision, void* stream, bool transpose) {
@@ -133,8 +129,12 @@ int do_apply(skel_handle h, const void* q, void* u, int nrhs, int precision, voi
                 cudaFree(dp->stage_out);
                 dp->stage_in = dp->stage_out = nullptr;
                 dp->stage_bytes = 0;
-                if (cudaMalloc(&dp->stage_in, bytes) != cudaSuccess || cudaMalloc(&dp->stage_out, bytes) != cudaSuccess) {
+                if (skel::alloc_should_fail() || cudaMalloc(&dp->stage_in, bytes) != cudaSuccess ||
+                    cudaMalloc(&dp->stage_out, bytes) != cudaSuccess) {
                     cudaGetLastError();
+                    cudaFree(dp->stage_in);
+                    cudaFree(dp->stage_out);
+                    dp->stage_in = dp->stage_out = nullptr;
                     throw Error(SKEL_ERR_OOM, "staging allocation failed");
                 }
                 dp->stage_bytes = bytes;
@@ -210,6 +210,29 @@ void destroy(skel_plan* h) {
 namespace skel {
 // lets other translation units of the C-ABI report through skel_last_error
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+std::string kernel_args_error(int kind, double kappa, int dim) {
+    if (kind != SKEL_LAPLACE_2D && kind != SKEL_LAPLACE_3D && kind != SKEL_HELMHOLTZ_3D && kind != SKEL_HELMHOLTZ_2D)
+        return "unknown kernel kind";
+    const bool two_d = kind == SKEL_LAPLACE_2D || kind == SKEL_HELMHOLTZ_2D;
+    if (two_d != (dim == 2) || (dim != 2 && dim != 3))
+        return "dim does not match the kernel (2D kernels: dim 2, others: dim 3)";
+    if (kind == SKEL_HELMHOLTZ_3D && !(std::isfinite(kappa) && kappa >= 0)) return "kappa must be finite and >= 0";
+    if (kind == SKEL_HELMHOLTZ_2D && !(std::isfinite(kappa) && kappa > 0))
+        return "kappa must be finite and > 0 for the 2D Helmholtz kernel";
+    return "";
+}
+
+int pointer_place(const void* p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? 1 : -1;
+    return 0;
+}
 }  // namespace skel
 
 extern "C" {
@@ -589,6 +612,24 @@ int skel_device_status(skel_handle h) {
     if (rc != SKEL_OK) return rc;
     if (code != SKEL_OK) return fail(code, "a bounded device wait gave up during an earlier apply");
     return SKEL_OK;
+}
+
+int skel_test_withhold_tile(skel_handle h, double wait_limit_ms) {
+    return guarded([&] {
+        if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");
+        if (!h->dev) throw Error(SKEL_ERR_STATE, "plan was built host-only");
+        if (!(wait_limit_ms > 0 && wait_limit_ms <= 2000)) throw Error(SKEL_ERR_ARG, "wait_limit_ms must be in (0, 2000]");
+        if (h->dev->cplx || h->dev->n_tc == 0) throw Error(SKEL_ERR_STATE, "the plan has no tensor-core items");
+        h->dev->test_wait_ns = (uint64_t)(wait_limit_ms * 1e6);
+        h->dev->test_withhold = true;
+    });
+}
+
+int skel_test_fail_alloc(int countdown) {
+    return guarded([&] {
+        if (countdown < 0) throw Error(SKEL_ERR_ARG, "countdown must be >= 0");
+        skel::set_alloc_failure(countdown);
+    });
 }
 
 int skel_autotune(skel_handle h, int nrhs, int allow_store, void* stream, skel_tuning* out) {

@@ -60,6 +60,11 @@ struct DevicePlan {
     // register prefetch), set by the autotuner
     std::vector<int8_t> pref_up, pref_down;
     int* status = nullptr;                 // device word raised by a bounded wait that gave up
+    // test hook: the next tensor-core pass withholds its first item's first
+    // tile until the compute warps gave up, with every wait limited to
+    // test_wait_ns (skel_test_withhold_tile)
+    bool test_withhold = false;
+    uint64_t test_wait_ns = 0;
     DeviceBuffers* p64 = nullptr;
     DeviceBuffers* p32 = nullptr;
     // optional per-phase CUDA events (permute_in, up, near, reduce, down,
@@ -100,6 +105,12 @@ struct TuneReport {
     double ms_updown_default = 0, ms_updown_tuned = 0;  // summed over the levels, one launch each
 };
 TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* stream);
+
+// Allocation-failure test hook: the countdown-th allocation made through the
+// library's helpers after this call fails as if memory were exhausted
+// (0 = off). Returns true (and consumes the hook) when an allocation must fail.
+void set_alloc_failure(int countdown);
+bool alloc_should_fail();
 
 // Algorithm 2 on `stream`. q, u: device pointers in user order (n x nrhs,
 // each right-hand side contiguous). transpose: run with conj(T).

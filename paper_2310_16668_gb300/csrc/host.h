@@ -68,6 +68,16 @@ bool touches(int la, const int64_t* ca, int lb, const int64_t* cb, int dim);
 // record a message for skel_last_error on this thread; returns code
 int set_error(int code, const std::string& msg);
 
+// The kernel and dimension rules every entry point shares (known kind; dim 2
+// for the 2D kernels, 3 otherwise; kappa finite and >= 0 for 3D Helmholtz,
+// > 0 for 2D Helmholtz): an empty string if they hold, else the message.
+std::string kernel_args_error(int kind, double kappa, int dim);
+
+// Where a pointer lives, seen from the current CUDA device `dev`: 1 = device
+// or managed memory usable on `dev`, 0 = host memory, -1 = device memory of
+// another device (the caller rejects it).
+int pointer_place(const void* p, int dev);
+
 // Tree construction from points (root cube, split while > b, prune empty,
 // 2:1 balance between a leaf and every box touching it) and its neighbor lists.
 void build_tree(const double* pts, int64_t n, int dim, int leaf_size, Tree& t,

@@ -122,15 +122,6 @@ __global__ void na_reduce_kernel(const double* __restrict__ part, int64_t n, int
     }
 }
 
-bool on_device(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 
 }  // namespace skel
@@ -140,22 +131,23 @@ extern "C" int skel_direct_noalloc(const double* points, int64_t n, int dim, ske
     using namespace skel;
     if (!points || !q || !u) return set_error(SKEL_ERR_ARG, "NULL argument");
     if (n < 1 || nrhs < 1) return set_error(SKEL_ERR_ARG, "n and nrhs must be >= 1");
-    if (k.kind != SKEL_LAPLACE_2D && k.kind != SKEL_LAPLACE_3D && k.kind != SKEL_HELMHOLTZ_3D &&
-        k.kind != SKEL_HELMHOLTZ_2D)
-        return set_error(SKEL_ERR_ARG, "unknown kernel kind");
-    const bool two_d = k.kind == SKEL_LAPLACE_2D || k.kind == SKEL_HELMHOLTZ_2D;
-    if (two_d != (dim == 2) || (dim != 2 && dim != 3))
-        return set_error(SKEL_ERR_ARG, "dim does not match the kernel");
+    {
+        const std::string m = kernel_args_error(k.kind, k.kappa, dim);   // the rules skel_build applies
+        if (!m.empty()) return set_error(SKEL_ERR_ARG, m);
+    }
     const int W = (k.kind == SKEL_HELMHOLTZ_3D || k.kind == SKEL_HELMHOLTZ_2D) ? 2 : 1;
     const int64_t nchunk = (n + 31) / 32, nblk = (n + kNaSrcBlock - 1) / kNaSrcBlock;
     const int64_t nitems = nchunk * nblk;
     if ((double)nitems * 32.0 * W * sizeof(double) > (double)kStaticScratchBytes)
         return set_error(SKEL_ERR_ARG, "problem too large for the static scratch array (" +
                                            std::to_string(kStaticScratchBytes >> 20) + " MiB of partial sums)");
-    if (!on_device(points) || !on_device(q) || !on_device(u))
-        return set_error(SKEL_ERR_ARG, "points, q and u must be device pointers");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return set_error(SKEL_ERR_CUDA, "cudaGetDevice failed");
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SKEL_ERR_CUDA, "cudaGetDevice failed");
+    }
+    if (pointer_place(points, dev) != 1 || pointer_place(q, dev) != 1 || pointer_place(u, dev) != 1)
+        return set_error(SKEL_ERR_ARG, "points, q and u must be device pointers of the current device");
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
@@ -175,6 +167,13 @@ extern "C" int skel_direct_noalloc(const double* points, int64_t n, int dim, ske
     const double pi = 3.14159265358979323846;
     const double scale = k.kind == SKEL_LAPLACE_2D ? -1.0 / (4.0 * pi) : k.kind == SKEL_HELMHOLTZ_2D ? 0.25 : 1.0 / (4.0 * pi);
     const unsigned grid = (unsigned)((nitems + kNaWarps - 1) / kNaWarps);
+    // an error left pending by the caller's earlier work is reported as such
+    // (and cleared) before this call launches anything of its own
+    {
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return set_error(SKEL_ERR_CUDA, std::string("an earlier CUDA error was pending: ") + cudaGetErrorString(e));
+    }
     for (int r = 0; r < nrhs; ++r) {
         if (k.kind == SKEL_LAPLACE_2D)
             na_partial_kernel<0><<<grid, kNaWarps * 32, 0, st>>>(points, n, dim, q, r, k.kappa, part, nblk, nitems);
@@ -186,8 +185,10 @@ extern "C" int skel_direct_noalloc(const double* points, int64_t n, int dim, ske
             na_partial_kernel<3><<<grid, kNaWarps * 32, 0, st>>>(points, n, dim, q, r, k.kappa, part, nblk, nitems);
         if (W == 2) na_reduce_kernel<2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, n, nblk, r, scale, u);
         else na_reduce_kernel<1><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, n, nblk, r, scale, u);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return set_error(SKEL_ERR_CUDA, std::string("launch of this call's kernels (right-hand side ") +
+                                                std::to_string(r) + "): " + cudaGetErrorString(e));
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(SKEL_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return SKEL_OK;
 }

@@ -67,7 +67,7 @@ constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kColD = 0;                  // accumulators D0 [0,32), D1 [32,64)
 constexpr uint32_t kColA = 64;                 // A[b]: hi at 64+64b, lo at 96+64b (b < kNA)
 constexpr uint32_t kSleepNs = 20000;           // suspend hint of one wait attempt
-constexpr uint64_t kWaitLimitNs = 2000000000ull; // a wait gives up after 2 s
+constexpr uint64_t kWaitLimitNs = 2000000000ull; // a wait gives up after 2 s (TcArgs::wait_ns)
 
 // one source chunk as the prep kernel lays it out in global memory and one
 // bulk copy moves it: B hi, B lo, source coordinates (hi, lo)
@@ -108,6 +108,9 @@ struct TcArgs {
     int nrhs;                                  // right-hand sides (row length of U)
     int r0;                                    // first right-hand side of this pass
     int* status;
+    uint64_t wait_ns;                          // limit of every bounded wait (kWaitLimitNs)
+    int withhold_item;                         // test hook: this item's first tile is copied only
+                                               // after its consumers gave up waiting (-1: none)
 };
 
 __device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -140,14 +143,24 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// bounded wait: gives up after kWaitLimitNs of wall time
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// bounded wait: gives up after limit_ns of wall time
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
         if (mbar_try_sleep(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
+}
+
+// Test hook of the bounded waits (TcArgs::withhold_item): before the first
+// tile's copies the producer waits until the compute warps have given up
+// waiting for them and arrived on "A full"; then it issues the copies and
+// waits until they have landed. Every barrier still completes exactly one
+// phase per tile, every copy is waited for, and only that tile's values are
+// wrong (the kernel raises the status word).
+__device__ __forceinline__ bool withhold_first_tile(uint32_t afull0, uint64_t limit_ns) {
+    return mbar_wait(afull0, 0u, limit_ns);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -374,7 +387,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                 const int t = t0 + i;
                 const int s = t % kNS;
                 const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
-                if (t >= kNS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNS) / kNS) & 1))) err = true;
+                if (t >= kNS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNS) / kNS) & 1), a.wait_ns)) err = true;
+                const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
+                if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
                 if (lane == 0) {
                     // two bulk copies: the chunk (B hi, B lo, coordinates) and
                     // the tile's descriptor
@@ -382,6 +397,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                     mbar_arrive_tx(bar, 4u * kChunkFloats + 64u);
                     bulk_g2s(sm_addr(S.st[s].bhi), a.B + (int64_t)chunk * kChunkFloats, 4u * kChunkFloats, bar);
                     bulk_g2s(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar);
+                    if (hold && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
                 }
                 __syncwarp();
             }
@@ -389,7 +405,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         if (lane == 0) {
             // all bulk copies have landed before the CTA may exit
             for (int t = (ntile > kNS ? ntile - kNS : 0); t < ntile; ++t)
-                if (!mbar_wait(sm_addr(&S.full[t % kNS]), (uint32_t)((t / kNS) & 1))) err = true;
+                if (!mbar_wait(sm_addr(&S.full[t % kNS]), (uint32_t)((t / kNS) & 1), a.wait_ns)) err = true;
         }
     } else if (warp == kTcCompute / 32 + 1) {
         // ---------------- MMA issuer (one thread) ----------------
@@ -398,7 +414,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                                    ((128u >> 4) << 24);
             for (int m = 0; m < ntile; ++m) {
                 const int s = m % kNS, ab = m % kNA;
-                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kNS) & 1))) err = true;
+                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kNS) & 1), a.wait_ns)) err = true;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t bh = sm_addr(S.st[s].bhi), bl = sm_addr(S.st[s].blo);
                 const uint32_t d = tbase + kColD + 32u * (m & 1);
@@ -449,7 +465,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             S.outer[c][tid] = 0.f;
         }
         auto drain = [&](int m) {                              // add tile m's accumulator
-            if (!mbar_wait(sm_addr(&S.empty[m % kNS]), (uint32_t)((m / kNS) & 1))) err = true;
+            if (!mbar_wait(sm_addr(&S.empty[m % kNS]), (uint32_t)((m / kNS) & 1), a.wait_ns)) err = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t v[kCols];
             const uint32_t col = tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kCols * half);
@@ -467,7 +483,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         };
         for (int u = 0; u < ntile; ++u) {
             const int s = u % kNS;
-            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNS) & 1))) err = true;
+            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNS) & 1), a.wait_ns)) err = true;
             TcStage& st = S.st[s];
             const bool adj = (st.tile.flags & TASK_ADJ) != 0;
             // the target measured from the source box's centre (the frame of
@@ -609,19 +625,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
                 const int t = t0 + i;
                 const int s = t % kNSS;
                 const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
-                if (t >= kNSS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1))) err = true;
+                if (t >= kNSS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1), a.wait_ns)) err = true;
+                const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
+                if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
                 if (lane == 0) {
                     const uint32_t bar = sm_addr(&S.full[s]);
                     mbar_arrive_tx(bar, 4u * 2048u + tile_bytes);
                     bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
                     bulk_g2s(sm_addr(S.st[s].ga), tiles_src + (int64_t)t * nrows * 32, tile_bytes, bar);
+                    if (hold && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
                 }
                 __syncwarp();
             }
         }
         if (lane == 0) {
             for (int t = (ntile > kNSS ? ntile - kNSS : 0); t < ntile; ++t)
-                if (!mbar_wait(sm_addr(&S.full[t % kNSS]), (uint32_t)((t / kNSS) & 1))) err = true;
+                if (!mbar_wait(sm_addr(&S.full[t % kNSS]), (uint32_t)((t / kNSS) & 1), a.wait_ns)) err = true;
         }
     } else if (warp == kTcCompute / 32 + 1) {
         // ---------------- MMA issuer (one thread) ----------------
@@ -630,7 +649,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
                                    ((128u >> 4) << 24);
             for (int m = 0; m < ntile; ++m) {
                 const int s = m % kNSS, ab = m % kNA;
-                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kNSS) & 1))) err = true;
+                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kNSS) & 1), a.wait_ns)) err = true;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t bh = sm_addr(S.st[s].b), bl = bh + 4u * 1024u;
                 const uint32_t d = tbase + kColD + 32u * (m & 1);
@@ -659,7 +678,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             S.outer[c][tid] = 0.f;
         }
         auto drain = [&](int m) {
-            if (!mbar_wait(sm_addr(&S.empty[m % kNSS]), (uint32_t)((m / kNSS) & 1))) err = true;
+            if (!mbar_wait(sm_addr(&S.empty[m % kNSS]), (uint32_t)((m / kNSS) & 1), a.wait_ns)) err = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t v[kCols];
             tmem_ld16(tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kCols * half), v);
@@ -676,7 +695,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
         for (int u = 0; u < ntile; ++u) {
             const int s = u % kNSS;
-            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNSS) & 1))) err = true;
+            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNSS) & 1), a.wait_ns)) err = true;
             uint32_t ghi[16], glo[16];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {

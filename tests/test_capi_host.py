@@ -146,6 +146,11 @@ def test_argument_errors():
     assert lib.skel_apply(None, None, None, 1, 0, None) == -1
     lib.skel_free(None)                                                   # NULL is a no-op
     assert lib.skel_info(None, None) == -1
+    # failure-detection test hooks: argument checks (no device needed)
+    assert lib.skel_test_fail_alloc(-1) == -1
+    assert lib.skel_test_fail_alloc(0) == 0                               # off
+    assert lib.skel_test_withhold_tile(None, 5.0) == -1
+    assert lib.skel_test_withhold_tile(f._h, 5.0) == -6                   # host-only plan
 
 
 def test_single_leaf_root_plan():
