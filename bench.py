@@ -202,6 +202,68 @@ def oracle_direct_sample(kind, x, q0, targets, kappa=0.0):
     return u, time.perf_counter() - t0, direct.num_threads()
 
 
+def roofline(info, phases, clk, prec, pairs):
+    """The dominant kernel against its roofline: the main translation kernel,
+    timed by the plan's own CUDA events on the launching stream inside the
+    timed region (skel_set_profiling); the CUDA-core launch for the small
+    non-leaf boxes is outside that span. On the fly it is bound by the MUFU
+    unit (one operation per kernel evaluation); reading stored tiles, by
+    HBM."""
+    if prec == "fp32_tc":
+        kname, units = "tc_near_kernel", info["pairs_tc"]
+        unit_note = "skel_info pairs_tc: kept kernel evaluations of the tensor-core items"
+    else:
+        kname, units = "near_kernel", pairs
+        unit_note = "skel_info pairs_direct + pairs_far"
+    n_near = phases["main_launches"] / phases["n_applies"]
+    near_ms_per_launch = phases["main_near"] / phases["main_launches"]
+    achieved = units / (near_ms_per_launch * 1e-3) / 1e9
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    # one MUFU operation per evaluation (reciprocal square root in 3D, the
+    # logarithm in 2D); for Helmholtz the same figure is an upper bound
+    peak = SM_COUNT * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e9
+    peaks, peaks_kind = measured_peaks()
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(kname, prec),
+            "peak_basis": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU ops/clk x median SM clock under load "
+                          f"({sm_mhz:.0f} MHz), one MUFU op per kernel evaluation",
+            "per_launch_ms": near_ms_per_launch, "launches_per_step": n_near,
+            "algorithmic_units": f"{units} kernel evaluations per launch ({unit_note})"}
+    stored = prec == "fp32_tc" and info["stored_tile_bytes"] > 0
+    if stored:
+        # stored-operator mode, HBM-bound: the algorithmic bytes are 4 B per
+        # kept kernel evaluation (pairs_tc, each value read once per 32-column
+        # pass) plus the rows of U the launch writes; the stored bytes beyond
+        # that (zero padding of ragged tiles, masked entries) and the chunks'
+        # B blocks (8 KB per tile, mostly L2 hits) are overhead, reported
+        # beside the figure, not counted as useful work
+        kname = "tc_stored_kernel"
+        alg_bytes = 4 * info["pairs_tc"] + info["n_index"] * 32 * 4
+        traffic = ncu_traffic(kname, prec)
+        roof.update({"kernel": kname, "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                     "achieved": alg_bytes / (near_ms_per_launch * 1e-3) / 1e9,
+                     "traffic": traffic,
+                     "peak_basis": f"{peaks_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_units": f"{alg_bytes} bytes per launch (4 B x pairs_tc {info['pairs_tc']} "
+                                          f"+ U rows {info['n_index']} x 32 x 4)",
+                     "stored_tile_bytes": info["stored_tile_bytes"],
+                     "stored_over_algorithmic": info["stored_tile_bytes"] / (4 * info["pairs_tc"]),
+                     "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None,
+                     "evaluation_rate_gpair_s": achieved})
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    if prec == "fp32_tc":
+        # the same launch against the tensor pipe: algorithmic 2 flops per
+        # evaluation and right-hand side (32 per launch); the pipe issues 3
+        # TF32 products (hi.hi + hi.lo + lo.hi) over full 128 x 32 tiles
+        tc_tflops = units * 2 * 32 / (near_ms_per_launch * 1e-3) / 1e12
+        issued = info["n_tc_tiles"] * 128 * 32 * 32 * 2 * 3 / (near_ms_per_launch * 1e-3) / 1e12
+        tf32_peak = peaks["bf16_tflops"] * 0.5
+        roof["tensor"] = {"achieved": tc_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc_tflops / tf32_peak,
+                          "issued_tflops": issued,
+                          "peak_basis": f"TF32 = 0.5 x {peaks_kind} bf16 burst ({peaks['bf16_tflops']} TFLOP/s)"}
+    return roof
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -253,8 +315,12 @@ def run_reference(args):
 
 
 def run_curves(args):
-    """Batched 2D Laplace: every set's apply (and the batched adjoint) captured
-    into one CUDA graph; value = total points x right-hand sides / replay time."""
+    """Batched 2D Laplace: the 256 independent curve sets merged into one plan
+    (skel_merge), so that every phase of the apply is one launch over all
+    sets; the forward apply (and forward + adjoint) captured into one CUDA
+    graph and replayed. value = total points x right-hand sides / replay
+    time. The per-set graph (every set's own apply queued back to back) is
+    timed beside it."""
     import torch
     from paper_2310_16668_gb300 import SkelBatch
     from paper_2310_16668_gb300 import workloads as W
@@ -264,20 +330,47 @@ def run_curves(args):
     cs = W.CURVES2D_256
     nrhs = args.nrhs or cs.nrhs
     prec = args.precision or "fp32_tc"
+    tol = args.tol or cs.tol
     sets = cs.make_point_sets()
     t0 = time.perf_counter()
-    batch = SkelBatch(sets, "laplace2d", args.tol or cs.tol, cs.leaf, nrhs_max=nrhs)
+    batch = SkelBatch(sets, "laplace2d", tol, cs.leaf, nrhs_max=nrhs)
     t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    fmm = batch.merged(nrhs_max=nrhs)
+    t_merge = time.perf_counter() - t0
+    tuning = None
+    if args.tune == "auto" and prec != "fp64":
+        t0 = time.perf_counter()
+        try:
+            tuning = fmm.autotune(nrhs, allow_store=True)
+            tuning["t_tune_s"] = time.perf_counter() - t0
+        except Exception as e:                              # keep the untuned plan
+            tuning = {"error": str(e)}
+    info = fmm.info()
     ntot = int(sum(batch.sizes))
+    off = batch.offsets
     rdt = torch.float64 if prec == "fp64" else torch.float32
     qs = [torch.from_numpy(np.ascontiguousarray(cs.make_charges(i, len(x), nrhs).T)).to(dev, rdt)
           for i, x in enumerate(sets)]
-    us = [torch.empty_like(q) for q in qs]
-    gs = [torch.empty_like(q).normal_() for q in qs]
-    vs = [torch.empty_like(q) for q in qs]
-    g_fwd = batch.capture(qs, us, nrhs, prec)
-    g_both = batch.capture(qs, us, nrhs, prec, adjoint_qs=gs, adjoint_us=vs)
+    Q = torch.cat(qs, dim=1).contiguous()                   # N x nrhs column-major, sets one after the other
+    U = torch.empty_like(Q)
+    G = torch.empty_like(Q).normal_()
+    V = torch.empty_like(Q)
     stream = torch.cuda.current_stream(dev)
+
+    def capture(adjoint):
+        fmm.apply_into(Q, U, nrhs, prec)                    # warm-up outside the capture
+        if adjoint:
+            fmm.apply_into(G, V, nrhs, prec, transpose=True)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                fmm.apply_into(Q, U, nrhs, prec)
+                if adjoint:
+                    fmm.apply_into(G, V, nrhs, prec, transpose=True)
+        return g
 
     def timed(g, steps):
         for _ in range(args.warmup):
@@ -291,42 +384,88 @@ def run_curves(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
 
+    g_fwd = capture(False)
+    g_both = capture(True)
     clocks = ClockSampler(local)
     clocks.start()
     ms_fwd = timed(g_fwd, args.steps)
     clk = clocks.stop()
     ms_both = timed(g_both, args.steps)
     value = ntot * nrhs / (ms_fwd * 1e-3) / 1e6
+    # the phases of the same applies, un-captured, timed by the plan's events
+    fmm.set_profiling(args.steps)
+    for _ in range(args.steps):
+        fmm.apply_into(Q, U, nrhs, prec)
+    torch.cuda.synchronize()
+    phases = fmm.last_timings()
+    fmm.set_profiling(0)
+    fmm.device_status()
+    launches_per_apply = phases["launches"] / phases["n_applies"]
     g_fwd.replay()
     torch.cuda.synchronize()
-    # errors: the largest sets' RHS 0 at 1024 sampled targets against the oracle
+    # beside it: every set's own apply queued back to back in one graph
+    us = [torch.empty_like(q) for q in qs]
+    g_sets = batch.capture(qs, us, nrhs, prec)
+    ms_sets = timed(g_sets, args.steps)
+    torch.cuda.synchronize()
+    same = all(torch.equal(us[i], U[:, off[i]:off[i + 1]]) for i in range(len(sets)))
+    # end to end through the C-ABI: pinned host buffers, staged by the library
+    qh = Q.cpu().pin_memory()
+    uh = torch.empty_like(qh).pin_memory()
+    fmm.apply_into(qh, uh, nrhs, prec, stream=stream.cuda_stream)
+    k = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        fmm.apply_into(qh, uh, nrhs, prec, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / k
+    nbytes = qh.numel() * qh.element_size()
+    e2e = {"value": ntot * nrhs / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3}
+    # errors: the four largest sets, first and last right-hand side, at 1024
+    # sampled targets against the oracle's FP64 direct sum
     from oracle import direct
-    errs, t_cpu, n_eval = [], 0.0, 0
+    errs, t_cpu, n_eval = {}, 0.0, 0
     for i in np.argsort(batch.sizes)[-4:]:
         x = sets[i]
         tg = np.sort(np.random.default_rng(int(i)).choice(len(x), min(1024, len(x)), replace=False))
-        q0 = qs[i][0].double().cpu().numpy()
-        t1 = time.perf_counter()
-        ref = direct.direct_sum("laplace2d", x, q0, targets=tg)
-        t_cpu += time.perf_counter() - t1
-        n_eval += len(tg)
-        errs.append(float(np.abs(us[i][0].double().cpu().numpy()[tg] - ref).max() / np.abs(ref).max()))
+        for r in sorted({0, nrhs - 1}):
+            q_r = Q[r, off[i]:off[i + 1]].double().cpu().numpy()
+            t1 = time.perf_counter()
+            ref = direct.direct_sum("laplace2d", x, q_r, targets=tg)
+            t_cpu += time.perf_counter() - t1
+            n_eval += len(tg)
+            got = U[r, off[i]:off[i + 1]].double().cpu().numpy()[tg]
+            errs[f"set{i}_rhs{r}"] = float(np.abs(got - ref).max() / np.abs(ref).max())
+    roof = roofline(info, phases, clk, prec, info["pairs_direct"] + info["pairs_far"])
     line = {
-        "metric": f"Mpts·RHS/s, {cs.name} batched apply (CUDA graph of all sets)", "value": value,
+        "metric": f"Mpts·RHS/s, {cs.name} batched apply (one merged plan, CUDA graph)", "value": value,
         "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fwd,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": cs.name, "n_sets": len(sets), "N_total": ntot, "N_min": int(min(batch.sizes)),
-                   "N_max": int(max(batch.sizes)), "nrhs": nrhs, "leaf": cs.leaf, "tol": args.tol or cs.tol,
-                   "precision": prec, "t_build_s": t_build},
+                   "N_max": int(max(batch.sizes)), "nrhs": nrhs, "leaf": cs.leaf, "tol": tol,
+                   "precision": prec, "t_build_s": t_build, "t_merge_s": t_merge,
+                   "l2": f"inputs larger than L2: merged plan {info['device_bytes'] / 1e9:.2f} GB resident",
+                   "translations": ("stored kernel tiles" if info["stored_tile_bytes"] > 0 else "kernel on the fly")},
         "forward_and_adjoint_ms": ms_both,
-        "relerr_largest_sets": errs,
+        "per_set_graph_ms": ms_sets,
+        "merged_equals_per_set": same,
+        "kernel_launches_per_apply": launches_per_apply,
+        "relerr": max(errs.values()),
+        "relerr_sets": errs,
+        "tuning": tuning,
+        "phases_ms_per_step": {k2: v / phases["n_applies"] for k2, v in phases.items()
+                               if k2 not in ("launches", "n_applies", "main_launches")},
+        "roofline": roof,
         "cpu_baseline": {"value": n_eval / t_cpu / 1e6, "unit": UNIT, "cores": direct.num_threads(),
                          "kind": "oracle", "sample": f"FP64 direct sum at {n_eval} targets of the 4 largest sets"},
-        "gpu_launches": None,
+        "e2e": e2e,
+        "gpu_launches": int(launches_per_apply * args.steps),
         "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"), "reasons": clk.get("reasons")},
     }
     print(json.dumps(line), flush=True)
+    fmm.close()
     batch.close()
     return 0
 
@@ -494,63 +633,7 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    # roofline of the dominant kernel, the main translation kernel (kernel
-    # evaluations; MUFU rsqrt-bound): on the tensor-core path one launch per
-    # 32 right-hand sides over the pairs of the tensor-core items, timed by
-    # the plan's own events on the launching stream (the CUDA-core launch for
-    # the small non-leaf boxes is outside that span)
-    if prec == "fp32_tc":
-        kname, units = "tc_near_kernel", info["pairs_tc"]
-        unit_note = "skel_info pairs_tc: kept kernel evaluations of the tensor-core items"
-    else:
-        kname, units = "near_kernel", pairs
-        unit_note = "skel_info pairs_direct + pairs_far"
-    n_near = phases["main_launches"] / phases["n_applies"]
-    near_ms_per_launch = phases["main_near"] / phases["main_launches"]
-    achieved = units / (near_ms_per_launch * 1e-3) / 1e9
-    sm_mhz = clk.get("sm_mhz") or 2070.0
-    # one MUFU operation per evaluation (reciprocal square root in 3D, the
-    # logarithm in 2D); for Helmholtz the same figure is an upper bound
-    peak = SM_COUNT * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e9
-    peaks, peaks_kind = measured_peaks()
-    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(kname, prec),
-            "peak_basis": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU ops/clk x median SM clock under load "
-                          f"({sm_mhz:.0f} MHz), one MUFU op per kernel evaluation",
-            "per_launch_ms": near_ms_per_launch, "launches_per_step": n_near,
-            "algorithmic_units": f"{units} kernel evaluations per launch ({unit_note})"}
-    stored = prec == "fp32_tc" and info["stored_tile_bytes"] > 0
-    if stored:
-        # stored-operator mode, HBM-bound: the algorithmic bytes are 4 B per
-        # kept kernel evaluation (pairs_tc, each value read once per 32-column
-        # pass) plus the rows of U the launch writes; the stored bytes beyond
-        # that (zero padding of ragged tiles, masked entries) and the chunks'
-        # B blocks (8 KB per tile, mostly L2 hits) are overhead, reported
-        # beside the figure, not counted as useful work
-        kname = "tc_stored_kernel"
-        alg_bytes = 4 * info["pairs_tc"] + info["n_index"] * 32 * 4
-        traffic = ncu_traffic(kname, prec)
-        roof.update({"kernel": kname, "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                     "achieved": alg_bytes / (near_ms_per_launch * 1e-3) / 1e9,
-                     "traffic": traffic,
-                     "peak_basis": f"{peaks_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "algorithmic_units": f"{alg_bytes} bytes per launch (4 B x pairs_tc {info['pairs_tc']} "
-                                          f"+ U rows {info['n_index']} x 32 x 4)",
-                     "stored_tile_bytes": info["stored_tile_bytes"],
-                     "stored_over_algorithmic": info["stored_tile_bytes"] / (4 * info["pairs_tc"]),
-                     "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None,
-                     "evaluation_rate_gpair_s": achieved})
-        roof["frac"] = roof["achieved"] / roof["peak"]
-    if prec == "fp32_tc":
-        # the same launch against the tensor pipe: algorithmic 2 flops per
-        # evaluation and right-hand side (32 per launch); the pipe issues 3
-        # TF32 products (hi.hi + hi.lo + lo.hi) over full 128 x 32 tiles
-        tc_tflops = units * 2 * 32 / (near_ms_per_launch * 1e-3) / 1e12
-        issued = info["n_tc_tiles"] * 128 * 32 * 32 * 2 * 3 / (near_ms_per_launch * 1e-3) / 1e12
-        tf32_peak = peaks["bf16_tflops"] * 0.5
-        roof["tensor"] = {"achieved": tc_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc_tflops / tf32_peak,
-                          "issued_tflops": issued,
-                          "peak_basis": f"TF32 = 0.5 x {peaks_kind} bf16 burst ({peaks['bf16_tflops']} TFLOP/s)"}
+    roof = roofline(info, phases, clk, prec, pairs)
     metric = METRIC if args.workload == "laplace3d" else f"Mpts·RHS/s, {wl0.name} apply: {prec} vs plain FP64"
     line = {
         "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

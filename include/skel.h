@@ -196,6 +196,35 @@ int skel_apply_batch(const skel_handle* hs, int nsets, const void* const* q, voi
                      int precision, int transpose, void* stream);
 
 /*
+ * skel_merge — one plan that applies many independent plans in a single
+ * pass: each phase of Algorithm 2 (permutation, upward pass per level,
+ * translations, downward pass per level, permutation) runs as one launch
+ * over the boxes, items and points of all sets, instead of one apply per
+ * set. This is the paper's batching of same-shaped work across boxes (its
+ * GPU implementation, Section 5.2) carried across point sets; the merge
+ * itself is this library's addition. The merged plan's points are the sets'
+ * points one after the other: set i holds points [o_i, o_i + n_i) with
+ * o_i = n_0 + ... + n_{i-1}, so q and u are N x nrhs column-major with
+ * N = n_0 + ... + n_{nsets-1} (in each right-hand side, set 0's n_0 values,
+ * then set 1's, ...). skel_apply, skel_apply_transpose, skel_autotune,
+ * skel_set_profiling, skel_device_status and skel_info work on it as on any
+ * plan (skel_info sums the sets' statistics; k_max and n_levels are the
+ * largest); the plan-exchange calls return SKEL_ERR_STATE. No translation
+ * crosses a set, and every set's values equal its own apply bit for bit.
+ *   hs      nsets >= 1 handles of one kernel (kind, kappa) and dim, built by
+ *           skel_build / skel_build_batch / skel_plan_import (not merged);
+ *           they stay valid and independent (the merged plan has its own
+ *           device copy of every operator)
+ *   opts    nrhs_max, store_tiles and host_only are read (NULL: 32, no
+ *           stored tiles, a device plan; host_only = 1 forms the merged
+ *           layout and its statistics only, and applies return SKEL_ERR_STATE)
+ *   out     receives the merged handle; untouched on error
+ * The upload goes to the current CUDA device.
+ * Errors: SKEL_ERR_ARG, SKEL_ERR_OOM, SKEL_ERR_CUDA.
+ */
+int skel_merge(const skel_handle* hs, int nsets, const skel_options* opts, skel_handle* out);
+
+/*
  * skel_free — release the handle and all the host and device memory that
  * skel_build (or skel_plan_import) allocated for it: the tree, the index sets
  * and every interpolation matrix T_B (the paper's M_proj, the memory of all

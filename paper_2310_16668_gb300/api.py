@@ -258,7 +258,20 @@ class SkelBatch:
         self.plans = [SkelFMM(None, kernel, tol, leaf_size, kappa=kappa, nrhs_max=nrhs_max,
                               _handle=ctypes.c_void_p(out[i])) for i in range(ns)]
         self.sizes = [f.n for f in self.plans]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.kernel, self.kappa, self.nrhs_max = kernel, float(kappa), int(nrhs_max)
         self._hs = (ctypes.c_void_p * len(self.plans))(*[f._h.value for f in self.plans])
+
+    def merged(self, nrhs_max: int | None = None, store_tiles: bool = False, host_only: bool = False) -> SkelFMM:
+        """One plan over every set (skel_merge): each phase of the apply is a
+        single launch over all sets. Its q and u are N x nrhs column-major with
+        the sets' points one after the other (set i: rows offsets[i] ..
+        offsets[i+1]); each set's values equal its own apply bit for bit."""
+        nm = int(nrhs_max or self.nrhs_max)
+        h = ctypes.c_void_p()
+        opts = _options(0, nm, host_only, 0, False, store_tiles)
+        check(self._lib.skel_merge(self._hs, len(self.plans), ctypes.byref(opts), ctypes.byref(h)))
+        return SkelFMM(None, self.kernel, kappa=self.kappa, nrhs_max=nm, _handle=h)
 
     def apply_into(self, qs, us, nrhs: int, precision: str = "fp32_tc", transpose: bool = False, stream=None):
         """qs[i], us[i]: device tensors holding set i's n_i x nrhs column-major buffers."""

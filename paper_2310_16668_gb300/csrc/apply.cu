@@ -225,6 +225,7 @@ NearArgs<Real, CPLX> near_args(DevicePlan* dp, DeviceBuffers* b, const WorkItem*
     a.partial = (typename Scal<Real, CPLX>::T*)b->partial;
     a.nrhs = nrhs;
     a.kappa = (Real)dp->kappa;
+    a.kappa_lo = (Real)(dp->kappa - (double)(Real)dp->kappa);
     return a;
 }
 

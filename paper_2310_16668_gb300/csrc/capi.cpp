@@ -27,6 +27,11 @@ struct skel_plan {
     double t_upload = 0;
     int64_t n_items = 0, pairs_direct = 0, pairs_far = 0;
     int64_t n_tc_items = 0, n_tc_tiles = 0, n_mix_items = 0, pairs_tc = 0;
+    // skel_merge: a plan over many point sets keeps only the device part and
+    // the sets' summed statistics (its host tree and IDs stay with the sets)
+    bool merged = false;
+    int n_sets = 1;
+    skel_stats mstats{};
 };
 
 namespace {
@@ -336,6 +341,102 @@ int skel_apply_batch(const skel_handle* hs, int nsets, const void* const* q, voi
     });
 }
 
+int skel_merge(const skel_handle* hs, int nsets, const skel_options* opts, skel_handle* out) {
+    return guarded([&] {
+        if (!hs || !out || nsets < 1) throw Error(SKEL_ERR_ARG, "NULL argument or nsets < 1");
+        for (int i = 0; i < nsets; ++i) {
+            if (!hs[i]) throw Error(SKEL_ERR_ARG, "handle " + std::to_string(i) + " is NULL");
+            if (hs[i]->merged) throw Error(SKEL_ERR_ARG, "handle " + std::to_string(i) + " is itself a merged plan");
+            const skel::Plan& a = hs[i]->plan;
+            const skel::Plan& b = hs[0]->plan;
+            if (a.kind != b.kind || a.kappa != b.kappa || a.tree.dim != b.tree.dim)
+                throw Error(SKEL_ERR_ARG, "plan " + std::to_string(i) + " has another kernel, kappa or dim");
+        }
+        const double t0 = now();
+        std::vector<skel::Layout> lays(nsets);
+        std::vector<int> codes(nsets, SKEL_OK);
+        std::vector<std::string> msgs(nsets);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int i = 0; i < nsets; ++i) {
+            try {
+                skel::build_layout(hs[i]->plan, lays[i]);
+            } catch (const Error& e) {
+                codes[i] = e.code;
+                msgs[i] = e.what();
+            } catch (const std::bad_alloc&) {
+                codes[i] = SKEL_ERR_OOM;
+                msgs[i] = "host allocation failed";
+            } catch (...) {
+                codes[i] = SKEL_ERR_ARG;
+                msgs[i] = "layout failed";
+            }
+        }
+        for (int i = 0; i < nsets; ++i)
+            if (codes[i] != SKEL_OK) throw Error(codes[i], "set " + std::to_string(i) + ": " + msgs[i]);
+        std::vector<const skel::Layout*> lp;
+        std::vector<int64_t> np, nb;
+        for (int i = 0; i < nsets; ++i) {
+            lp.push_back(&lays[i]);
+            np.push_back(hs[i]->plan.tree.n);
+            nb.push_back(hs[i]->plan.tree.nb);
+        }
+        const skel::Plan& P0 = hs[0]->plan;
+        skel::Layout m;
+        skel::merge_layouts(lp, np, nb, P0.sk.cplx ? 2 : 1, m);
+        lays.clear();
+        skel_plan* h = new skel_plan();
+        try {
+            h->merged = true;
+            h->n_sets = nsets;
+            h->plan.kind = P0.kind;
+            h->plan.kappa = P0.kappa;
+            h->plan.tree.dim = P0.tree.dim;
+            h->plan.sk.cplx = P0.sk.cplx;
+            skel_stats& st = h->mstats;
+            std::memset(&st, 0, sizeof(st));
+            st.dim = P0.tree.dim;
+            for (int i = 0; i < nsets; ++i) {
+                skel_stats si;
+                if (skel_info(hs[i], &si) != SKEL_OK) throw Error(SKEL_ERR_ARG, g_err);
+                st.n_points += si.n_points;
+                st.n_levels = std::max(st.n_levels, si.n_levels);
+                st.n_boxes += si.n_boxes;
+                st.n_leaves += si.n_leaves;
+                st.k_max = std::max(st.k_max, si.k_max);
+                st.n_index += si.n_index;
+                st.n_T += si.n_T;
+                st.n_colleague += si.n_colleague;
+                st.n_coarse += si.n_coarse;
+                st.n_fine += si.n_fine;
+                st.t_tree += si.t_tree;
+                st.t_skel += si.t_skel;
+                st.t_id_kernels += si.t_id_kernels;
+                st.id_gflop += si.id_gflop;
+                st.skel_on_device |= si.skel_on_device;
+                st.n_proxy = si.n_proxy;
+            }
+            h->plan.tree.n = st.n_points;
+            h->plan.tree.L = st.n_levels;
+            st.pairs_direct = h->pairs_direct = m.pairs_direct;
+            st.pairs_far = h->pairs_far = m.pairs_far;
+            st.n_work_items = h->n_items = (int64_t)m.items.size();
+            st.n_tc_items = h->n_tc_items = (int64_t)m.tc_items.size();
+            st.n_tc_tiles = h->n_tc_tiles = (int64_t)m.tc_tiles.size();
+            st.n_mix_items = h->n_mix_items = (int64_t)m.mix_items.size();
+            st.pairs_tc = h->pairs_tc = m.pairs_tc;
+            h->nrhs_max = (opts && opts->nrhs_max > 0) ? opts->nrhs_max : 32;
+            if (h->nrhs_max > 256) throw Error(SKEL_ERR_ARG, "nrhs_max must be <= 256");
+            h->host_only = opts && opts->host_only;
+            if (!h->host_only) h->dev = skel::device_plan_create(h->plan, m, h->nrhs_max, opts && opts->store_tiles);
+            h->t_upload = st.t_upload = now() - t0;
+        } catch (...) {
+            destroy(h);
+            throw;
+        }
+        *out = h;
+    });
+}
+
 void skel_free(skel_handle h) {
     if (!h) return;
     skel::device_plan_destroy(h->dev);
@@ -345,6 +446,12 @@ void skel_free(skel_handle h) {
 int skel_info(skel_handle h, skel_stats* s) {
     return guarded([&] {
         if (!h || !s) throw Error(SKEL_ERR_ARG, "NULL argument");
+        if (h->merged) {
+            *s = h->mstats;
+            s->device_bytes = h->dev ? h->dev->bytes : 0;
+            s->stored_tile_bytes = h->dev ? h->dev->stored_bytes : 0;
+            return;
+        }
         const skel::Plan& P = h->plan;
         const skel::Tree& t = P.tree;
         std::memset(s, 0, sizeof(*s));
@@ -385,6 +492,7 @@ const char* skel_last_error(void) { return g_err.c_str(); }
 int skel_plan_get_dims(skel_handle h, skel_plan_dims* d) {
     return guarded([&] {
         if (!h || !d) throw Error(SKEL_ERR_ARG, "NULL argument");
+        if (h->merged) throw Error(SKEL_ERR_STATE, "a merged plan has no single tree to export");
         const skel::Plan& P = h->plan;
         std::memset(d, 0, sizeof(*d));
         d->n_boxes = P.tree.nb;
@@ -401,6 +509,7 @@ int skel_plan_export(skel_handle h, int32_t* level, int32_t* coord, int64_t* par
                      int64_t* idx_ptr, int64_t* idx, int64_t* piv, int32_t* k, int64_t* T_ptr, double* T) {
     return guarded([&] {
         if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");
+        if (h->merged) throw Error(SKEL_ERR_STATE, "a merged plan has no single tree to export");
         const skel::Plan& P = h->plan;
         const skel::Tree& t = P.tree;
         const int64_t nb = t.nb;
@@ -574,6 +683,7 @@ int skel_plan_import(const double* points, int64_t n, int dim, skel_kernel kern,
 int skel_neighbors_export(skel_handle h, int which, int64_t* ptr, int64_t* list) {
     return guarded([&] {
         if (!h || !ptr) throw Error(SKEL_ERR_ARG, "NULL argument");
+        if (h->merged) throw Error(SKEL_ERR_STATE, "a merged plan has no single tree to export");
         const skel::Tree& t = h->plan.tree;
         const std::vector<int64_t>* p = nullptr;
         const std::vector<int64_t>* l = nullptr;

@@ -198,4 +198,10 @@ struct Layout {
 
 void build_layout(const Plan& p, Layout& lay);
 
+// One layout for many independent point sets (set s: n_points[s] points,
+// n_boxes[s] boxes; T_width = 1 for real, 2 for complex operators): each
+// phase of the apply then covers every set in one launch.
+void merge_layouts(const std::vector<const Layout*>& ls, const std::vector<int64_t>& n_points,
+                   const std::vector<int64_t>& n_boxes, int T_width, Layout& m);
+
 }  // namespace skel

@@ -367,3 +367,119 @@ void build_layout(const Plan& p, Layout& lay) {
 }
 
 }  // namespace skel
+
+namespace skel {
+
+// Concatenate the layouts of independent point sets into one: every index is
+// shifted by the entries, points, boxes, tasks, items, tiles, chunks and
+// operator entries of the sets before it, and the up/down boxes are grouped
+// by level across sets, so that each phase of the apply is one launch over
+// all sets. No task, item or box refers across sets, and every per-entry sum
+// keeps its order (the CSR lists are concatenated, not re-sorted), so each
+// set's result is the one its own layout gives.
+void merge_layouts(const std::vector<const Layout*>& ls, const std::vector<int64_t>& n_points,
+                   const std::vector<int64_t>& n_boxes, int T_width, Layout& m) {
+    m = Layout();
+    m.top = 1;
+    int Lmax = 0;
+    for (const Layout* l : ls) Lmax = std::max(Lmax, (int)l->up_level_ptr.size() - 2);
+    std::vector<int64_t> e0, p0, b0, k0, w0, mw0, t0, c0, T0;   // per-set offsets
+    int64_t eo = 0, po = 0, bo = 0, ko = 0, wo = 0, mwo = 0, to = 0, co = 0, To = 0;
+    for (size_t s = 0; s < ls.size(); ++s) {
+        const Layout& l = *ls[s];
+        e0.push_back(eo); p0.push_back(po); b0.push_back(bo); k0.push_back(ko);
+        w0.push_back(wo); mw0.push_back(mwo); t0.push_back(to); c0.push_back(co); T0.push_back(To);
+        eo += l.n_tot;
+        po += n_points[s];
+        bo += n_boxes[s];
+        ko += (int64_t)l.task_src.size();
+        wo += (int64_t)l.items.size();
+        mwo += (int64_t)l.mix_items.size();
+        to += (int64_t)l.tc_tiles.size();
+        co += (int64_t)l.chunk_start.size();
+        To += (int64_t)(l.T.size() / T_width);
+        if (l.top == 0) m.top = 0;
+    }
+    m.n_tot = eo;
+    auto shift_items = [](const std::vector<WorkItem>& in, int64_t bo_, int64_t ko_, std::vector<WorkItem>& out) {
+        for (WorkItem w : in) {
+            w.tgt_box += bo_;
+            w.task_lo = (int32_t)(w.task_lo + ko_);
+            w.task_hi = (int32_t)(w.task_hi + ko_);
+            out.push_back(w);
+        }
+    };
+    auto cat_csr = [&](const std::vector<int64_t>& ptr, const std::vector<int64_t>& idx, int64_t slot_off,
+                       std::vector<int64_t>& optr, std::vector<int64_t>& oidx) {
+        const int64_t base = (int64_t)oidx.size();
+        if (optr.empty()) optr.push_back(0);
+        for (size_t e = 1; e < ptr.size(); ++e) optr.push_back(base + ptr[e]);
+        for (int64_t v : idx) oidx.push_back(v + slot_off * kChunk);
+    };
+    for (size_t s = 0; s < ls.size(); ++s) {
+        const Layout& l = *ls[s];
+        for (int64_t v : l.box_off) m.box_off.push_back(v < 0 ? -1 : v + e0[s]);
+        m.box_n.insert(m.box_n.end(), l.box_n.begin(), l.box_n.end());
+        m.box_nslot.insert(m.box_nslot.end(), l.box_nslot.begin(), l.box_nslot.end());
+        m.slot_start.insert(m.slot_start.end(), l.slot_start.begin(), l.slot_start.end());
+        m.X.insert(m.X.end(), l.X.begin(), l.X.end());
+        for (int64_t v : l.perm_entry) m.perm_entry.push_back(v + e0[s]);
+        for (int64_t v : l.perm_point) m.perm_point.push_back(v + p0[s]);
+        m.pos.insert(m.pos.end(), l.pos.begin(), l.pos.end());
+        m.T.insert(m.T.end(), l.T.begin(), l.T.end());
+        for (int64_t v : l.task_src) m.task_src.push_back(v + b0[s]);
+        m.task_mask.insert(m.task_mask.end(), l.task_mask.begin(), l.task_mask.end());
+        m.task_flags.insert(m.task_flags.end(), l.task_flags.begin(), l.task_flags.end());
+        shift_items(l.items, b0[s], k0[s], m.items);
+        cat_csr(l.part_ptr, l.part_idx, w0[s], m.part_ptr, m.part_idx);
+        shift_items(l.mix_items, b0[s], k0[s], m.mix_items);
+        cat_csr(l.tc_part_ptr, l.tc_part_idx, mw0[s], m.tc_part_ptr, m.tc_part_idx);
+        for (SrcTile t : l.tc_tiles) {
+            t.start += e0[s];
+            t.chunk = (int32_t)(t.chunk + c0[s]);
+            m.tc_tiles.push_back(t);
+        }
+        for (TcItem it : l.tc_items) {
+            it.row_off += e0[s];
+            it.list_lo = (int32_t)(it.list_lo + t0[s]);
+            it.list_hi = (int32_t)(it.list_hi + t0[s]);
+            m.tc_items.push_back(it);
+        }
+        for (int64_t v : l.box_chunk0) m.box_chunk0.push_back(v < 0 ? -1 : v + c0[s]);
+        for (int64_t v : l.chunk_start) m.chunk_start.push_back(v + e0[s]);
+        m.chunk_cnt.insert(m.chunk_cnt.end(), l.chunk_cnt.begin(), l.chunk_cnt.end());
+        m.chunk_center.insert(m.chunk_center.end(), l.chunk_center.begin(), l.chunk_center.end());
+        m.pairs_direct += l.pairs_direct;
+        m.pairs_far += l.pairs_far;
+        m.pairs_tc += l.pairs_tc;
+    }
+    if (m.part_ptr.empty()) m.part_ptr.push_back(0);
+    if (m.tc_part_ptr.empty()) m.tc_part_ptr.push_back(0);
+    m.tc_n_slots = mwo;
+    if (eo > INT32_MAX || to > INT32_MAX || co > INT32_MAX || ko > INT32_MAX)
+        throw Error(-1, "merged plan too large (more than 2^31 entries, tasks, tiles or chunks)");
+    // up/down boxes grouped by level over all sets
+    m.up_level_ptr.assign(Lmax + 2, 0);
+    for (int lv = 0; lv <= Lmax; ++lv) {
+        m.up_level_ptr[lv] = (int64_t)m.up.size();
+        for (size_t s = 0; s < ls.size(); ++s) {
+            const Layout& l = *ls[s];
+            if (lv + 1 >= (int)l.up_level_ptr.size()) continue;
+            for (int64_t i = l.up_level_ptr[lv]; i < l.up_level_ptr[lv + 1]; ++i) {
+                UpBox u = l.up[i];
+                u.off += e0[s];
+                u.dst += e0[s];
+                u.T_off += T0[s];
+                m.up.push_back(u);
+            }
+        }
+    }
+    m.up_level_ptr[Lmax + 1] = (int64_t)m.up.size();
+    // the longest tile lists first over all sets (each item writes its own
+    // rows, so the order changes no result)
+    std::stable_sort(m.tc_items.begin(), m.tc_items.end(), [](const TcItem& a, const TcItem& c) {
+        return a.list_hi - a.list_lo > c.list_hi - c.list_lo;
+    });
+}
+
+}  // namespace skel

@@ -277,6 +277,7 @@ struct NearArgs {
     S* partial;
     int nrhs;
     Real kappa;
+    Real kappa_lo;        // kappa - (Real)kappa: the FP32 2D Helmholtz phase uses both
 };
 
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
@@ -323,6 +324,87 @@ template <class Real> struct Green<Real, 3> {
     }
     static __device__ __forceinline__ Cx<Real> zero_() { return {Real(0), Real(0)}; }
 };
+// ---- 2D Helmholtz in FP32 ---------------------------------------------------------------
+// FP32 cannot carry the phase kappa r of a far pair: one ulp of r is 6e-8 r,
+// so at kappa r ~ 100 the phase, and with it the kernel value, would be off by
+// ~1e-5. The FP32 path therefore forms the coordinate differences from the hi
+// and lo parts and the distance r = sqrt(dx^2 + dy^2) as double-float values
+// (an unevaluated sum h + l; Knuth's two-sum, FMA-exact products, one Newton
+// correction of the square root), and evaluates G without its factor 1/4:
+//   x = kappa r < 8:  (-Y_0(x), J_0(x)) from the CUDA math library's y0f /
+//                     j0f (at most 9 ulp on this range);
+//   x >= 8:           Hankel's asymptotic expansion (Abramowitz & Stegun
+//                     9.2.5, 9.2.9, 9.2.10) H_0^(1)(x) = sqrt(2 / (pi x))
+//                     (P(x) + i Q(x)) e^{i (x - pi/4)}, with
+//                     P = sum_k (-1)^k t_{2k} u^{2k}, Q = sum_k (-1)^{k+1}
+//                     t_{2k+1} u^{2k+1}, u = 1 / (2x), t_0 = 1,
+//                     t_m = t_{m-1} (2m - 1)^2 / (4m); six terms of each stay
+//                     within 4e-8 of |H_0^(1)| for x >= 8. The phase x - pi/4
+//                     is reduced modulo pi/2 by Cody and Waite's method (pi/2
+//                     as a sum of three floats) in double-float arithmetic.
+struct F2 {
+    float h, l;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, fmaf(a, b, -p)};
+}
+// (th + tl) - (sh + sl) as a double-float
+__device__ __forceinline__ F2 df_diff(float th, float sh, float tl, float sl) {
+    const F2 d = two_sum(th, -sh);
+    return two_sum(d.h, __fadd_rn(d.l, __fsub_rn(tl, sl)));
+}
+__host__ __device__ constexpr double hankel_t(int m) {
+    double v = 1.0;
+    for (int j = 1; j <= m; ++j) v *= (double)((2 * j - 1) * (2 * j - 1)) / (4.0 * j);
+    return v;
+}
+__device__ __forceinline__ Cx<float> helmholtz2d_f32(F2 dx, F2 dy, float kh, float kl) {
+    // r^2 and r as double-floats
+    const F2 px = two_prod(dx.h, dx.h), py = two_prod(dy.h, dy.h);
+    const F2 s = two_sum(px.h, py.h);
+    const float lo = s.l + px.l + py.l + 2.f * (dx.h * dx.l + dy.h * dy.l);
+    const F2 r2 = two_sum(s.h, lo);
+    if (!(r2.h > 0.f)) return {0.f, 0.f};
+    const float rh = sqrtf(r2.h);
+    const float rl = (fmaf(-rh, rh, r2.h) + r2.l) * (0.5f / rh);
+    F2 x = two_prod(kh, rh);
+    x.l += kh * rl + kl * rh;
+    if (x.h < 8.f) return {-y0f(x.h), j0f(x.h)};
+    constexpr double kPi = 3.14159265358979323846;
+    const float u = 0.5f / x.h, v = u * u;
+    const float P = 1.f + v * (-(float)hankel_t(2) + v * ((float)hankel_t(4) + v * (-(float)hankel_t(6) +
+                    v * ((float)hankel_t(8) + v * (-(float)hankel_t(10))))));
+    const float Q = u * (-(float)hankel_t(1) + v * ((float)hankel_t(3) + v * (-(float)hankel_t(5) +
+                    v * ((float)hankel_t(7) + v * (-(float)hankel_t(9) + v * (float)hankel_t(11))))));
+    const float amp = (float)0.79788456080286535588 * rsqrtf(x.h);     // sqrt(2 / pi) / sqrt(x)
+    // chi = x - pi/4 = w + n pi/2, |w| <= pi/4 (plus rounding)
+    constexpr float kP4h = (float)(kPi / 4);
+    constexpr float kP4l = (float)(kPi / 4 - (double)(float)(kPi / 4));
+    constexpr float kC1 = 1.5703125f;                                   // 8 significant bits: n C1 is exact
+    constexpr float kC2 = (float)(kPi / 2 - 1.5703125);
+    constexpr float kC3 = (float)(kPi / 2 - 1.5703125 - (double)(float)(kPi / 2 - 1.5703125));
+    const F2 z = two_sum(x.h, -kP4h);
+    const float zl = z.l + (x.l - kP4l);
+    const float n = rintf(z.h * (float)(2.0 / kPi));
+    float w = fmaf(-n, kC1, z.h);
+    w = fmaf(-n, kC2, w);
+    w = fmaf(-n, kC3, w);
+    w += zl;
+    float sw, cw;
+    sincosf(w, &sw, &cw);
+    const int qd = (int)n & 3;
+    const float sc = qd == 0 ? sw : qd == 1 ? cw : qd == 2 ? -sw : -cw;     // sin chi
+    const float cc = qd == 0 ? cw : qd == 1 ? -sw : qd == 2 ? -cw : sw;     // cos chi
+    const float J = amp * (P * cc - Q * sc), Y = amp * (P * sc + Q * cc);
+    return {-Y, J};
+}
+
 template <class G, class S> __device__ __forceinline__ void madd(S& acc, G g, S q);
 template <> __device__ __forceinline__ void madd<float, float>(float& a, float g, float q) { a = fmaf(g, q, a); }
 template <> __device__ __forceinline__ void madd<double, double>(double& a, double g, double q) { a = fma(g, q, a); }
@@ -350,7 +432,10 @@ __device__ __forceinline__ void near_slot(const NearArgs<Real, cplx_kind(KIND)>&
                                           typename Scal<Real, cplx_kind(KIND)>::T* part) {
     using S = typename Scal<Real, cplx_kind(KIND)>::T;
     using Gr = Green<Real, KIND>;
-    constexpr bool LO = ADJ && sizeof(Real) == 4;
+    // FP32 lo parts: touching leaves (arbitrarily close pairs), and every pair
+    // of the 2D Helmholtz kernel (its phase needs the distance to ~1e-9)
+    constexpr bool H2F = KIND == 3 && sizeof(Real) == 4;
+    constexpr bool LO = (ADJ || H2F) && sizeof(Real) == 4;
     for (int64_t b = s0; b < s1; b += 32) {
         const int cnt = (int)min((int64_t)32, s1 - b);
         if (lane < cnt) {
@@ -363,16 +448,23 @@ __device__ __forceinline__ void near_slot(const NearArgs<Real, cplx_kind(KIND)>&
         __syncwarp();
         for (int j = 0; j < cnt; ++j) {
             const typename RealT<Real>::V4 s = sx[j];
-            Real dx = tx.x - s.x, dy = tx.y - s.y, dz = tx.z - s.z;
-            if (LO) {
+            typename Gr::G g;
+            if constexpr (H2F) {
                 const typename RealT<Real>::V4 l = sl[j];
-                dx += tl.x - l.x;
-                dy += tl.y - l.y;
-                dz += tl.z - l.z;
+                g = helmholtz2d_f32(df_diff(tx.x, s.x, tl.x, l.x), df_diff(tx.y, s.y, tl.y, l.y), a.kappa,
+                                    a.kappa_lo);
+            } else {
+                Real dx = tx.x - s.x, dy = tx.y - s.y, dz = tx.z - s.z;
+                if (LO) {
+                    const typename RealT<Real>::V4 l = sl[j];
+                    dx += tl.x - l.x;
+                    dy += tl.y - l.y;
+                    dz += tl.z - l.z;
+                }
+                const Real r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                g = Gr::eval(r2, a.kappa);
+                if (ADJ && !(r2 > Real(0))) g = Gr::zero_();
             }
-            const Real r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            typename Gr::G g = Gr::eval(r2, a.kappa);
-            if (ADJ && !(r2 > Real(0))) g = Gr::zero_();
 #pragma unroll
             for (int r = 0; r < RT; ++r) madd(part[r], g, sq[j * RT + r]);
         }

@@ -177,6 +177,29 @@ def test_build_batch_equals_single_builds(threads):
             assert np.array_equal(np.asarray(pa[key]), np.asarray(pb[key])), key
 
 
+def test_merged_layout_sums_the_sets():
+    """skel_merge (host part): the merged layout holds exactly the sets' boxes,
+    entries, operators and translation work; plan export is refused."""
+    from paper_2310_16668_gb300 import SkelBatch
+    sets = [W.points_curve(n, 900 + i) for i, n in enumerate((700, 1500, 2600, 1100))]
+    b = SkelBatch(sets, "laplace2d", 1e-7, 16, nrhs_max=4, host_only=True)
+    m = b.merged(host_only=True)
+    mi, infos = m.info(), [f.info() for f in b.plans]
+    for k in ("n_points", "n_boxes", "n_leaves", "n_index", "n_T", "pairs_direct", "pairs_far", "pairs_tc",
+              "n_tc_items", "n_tc_tiles", "n_mix_items", "n_work_items", "n_colleague", "n_coarse", "n_fine"):
+        assert mi[k] == sum(i[k] for i in infos), k
+    assert mi["k_max"] == max(i["k_max"] for i in infos)
+    assert mi["n_levels"] == max(i["n_levels"] for i in infos)
+    _expect(-6, m.export_plan)
+    _expect(-6, m.apply, np.zeros(mi["n_points"]))
+    b3 = SkelBatch([W.points_uniform(500, 3, 1)], "laplace3d", 1e-6, 16, host_only=True)
+    lib = _lib.load()
+    hs = (ctypes.c_void_p * 2)(b.plans[0]._h.value, b3.plans[0]._h.value)
+    out = ctypes.c_void_p()
+    assert lib.skel_merge(hs, 2, None, ctypes.byref(out)) == -1          # kernels differ
+    assert out.value is None
+
+
 def test_build_batch_errors_name_the_set():
     from paper_2310_16668_gb300 import SkelBatch
     from paper_2310_16668_gb300._lib import SkelError

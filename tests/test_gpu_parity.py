@@ -246,6 +246,51 @@ def test_full_size_helmholtz_sampled():
     assert e64 < 10 * wl.tol and e32 < 10 * wl.tol
 
 
+def test_helmholtz2d_fp32_kernel_values():
+    """The FP32 2D Helmholtz kernel value by value, through the C-ABI: on a
+    single-leaf plan the apply is the direct sum, so unit charges return the
+    kernel matrix column by column. kappa = 100 and distances from 1e-6 to
+    1.41 put kappa r on both sides of 8 (the library's series / asymptotic
+    switch) up to 141; compared with the oracle's complex128 kernel (the
+    Bessel functions of scipy) relative to |G|."""
+    from oracle import kernels
+    n, kappa = 64, 100.0
+    t = np.concatenate([[0.0], np.geomspace(1e-6, 1.42, n - 1)])
+    th = np.linspace(0.0, 0.7, n)
+    x = np.stack([0.01 + t * np.cos(0.785 + 0.05 * th), 0.005 + t * np.sin(0.785 + 0.05 * th)], axis=1)
+    fmm = SkelFMM(x, "helmholtz2d", 1e-6, n, kappa=kappa, nrhs_max=n)
+    assert fmm.info()["n_levels"] == 0
+    G = fmm.apply(torch.eye(n, dtype=torch.complex64, device="cuda"), "fp32").cpu().numpy()
+    ref = kernels.kernel_matrix("helmholtz2d", x, x, kappa)
+    off = ~np.eye(n, dtype=bool)
+    kr = kappa * np.linalg.norm(x[:, None, :] - x[None, :, :], axis=2)
+    assert kr[off].min() < 1e-3 and kr.max() > 140 and np.any((kr > 8) & (kr < 20))
+    err = np.abs(G - ref)[off] / np.abs(ref)[off]
+    assert np.all(np.diag(G) == 0)
+    assert err.max() < 2e-6, (err.max(), kr[off][np.argmax(err)])
+
+
+@pytest.mark.slow
+def test_full_size_helmholtz2d_sampled():
+    """2D Helmholtz (kappa = 100, about 16 wavelengths across the square),
+    N = 2^20, leaf 64, tol 1e-6: complex64 and complex128 applies at 4096
+    sampled targets against the oracle's complex128 direct sum, within
+    10 tol (the FP32 path carries the phase kappa r as a double-float)."""
+    wl = W.HELMHOLTZ2D_1M
+    x = wl.make_points()
+    q = wl.make_charges(2)
+    fmm = SkelFMM(x, wl.kernel, wl.tol, wl.leaf, kappa=wl.kappa, nrhs_max=2)
+    tg = wl.make_sample()
+    ref = direct.direct_sum(wl.kernel, x, np.ascontiguousarray(q[:, 0]), targets=tg, kappa=wl.kappa)
+    qt = torch.from_numpy(q).cuda()
+    u64 = fmm.apply(qt, "fp64").cpu().numpy()[tg, 0]
+    u32 = fmm.apply(qt.to(torch.complex64), "fp32").cpu().numpy()[tg, 0]
+    fmm.device_status()
+    e64, e32 = relerr(u64, ref), relerr(u32, ref)
+    print(f"helmholtz2d: relerr complex128 {e64:.3e} complex64 {e32:.3e}")
+    assert e64 < 10 * wl.tol and e32 < 10 * wl.tol
+
+
 def test_batched_curve_sets_and_graph():
     """Several independent 2D point sets on closed curves: the batched apply
     equals each set's own apply, matches the oracle's direct sum within
@@ -282,6 +327,63 @@ def test_batched_curve_sets_and_graph():
         f.apply_into(gs[i], e2, nrhs, "fp32_tc", transpose=True)
         torch.cuda.synchronize()
         assert torch.equal(e1, us[i]) and torch.equal(e2, vs[i])
+    b.close()
+
+
+def test_merged_plan_equals_per_set_applies():
+    """skel_merge: one plan over several independent curve sets applies every
+    set in one pass (one launch per phase over all sets) and gives each set
+    exactly its own apply's values, for every precision and the transpose;
+    a CUDA graph of the merged forward and adjoint replays to the same."""
+    from paper_2310_16668_gb300 import SkelBatch
+    cs = W.CurveSets(n_sets=6, seed=21)
+    sets = [W.points_curve(n, 900 + i) for i, n in enumerate((700, 1500, 2600, 1100, 3300, 900))]
+    nrhs = 4
+    b = SkelBatch(sets, "laplace2d", cs.tol, 16, nrhs_max=nrhs)
+    m = b.merged()
+    assert m.n == sum(b.sizes)
+    off = b.offsets
+    for prec in ("fp64", "fp32", "fp32_tc"):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        qs = [torch.from_numpy(np.ascontiguousarray(cs.make_charges(i, len(x), nrhs).T)).cuda().to(dt)
+              for i, x in enumerate(sets)]
+        Q = torch.cat(qs, dim=1).contiguous()                   # (nrhs, N): N x nrhs column-major
+        for transpose in (False, True):
+            U = torch.empty_like(Q)
+            m.set_profiling(1)
+            m.apply_into(Q, U, nrhs, prec, transpose=transpose)
+            t = m.last_timings()
+            m.set_profiling(0)
+            m.device_status()
+            assert t["launches"] <= 16, t
+            for i, f in enumerate(b.plans):
+                one = torch.empty_like(qs[i])
+                f.apply_into(qs[i], one, nrhs, prec, transpose=transpose)
+                torch.cuda.synchronize()
+                assert torch.equal(one, U[:, off[i]:off[i + 1]]), (prec, transpose, i)
+    # graph of the merged forward and adjoint, replayed on new inputs
+    Q = torch.cat([torch.from_numpy(np.ascontiguousarray(cs.make_charges(i, len(x), nrhs).T)).cuda().float()
+                   for i, x in enumerate(sets)], dim=1).contiguous()
+    G = torch.randn_like(Q)
+    U, V = torch.empty_like(Q), torch.empty_like(Q)
+    m.apply_into(Q, U, nrhs, "fp32_tc")
+    m.apply_into(G, V, nrhs, "fp32_tc", transpose=True)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            m.apply_into(Q, U, nrhs, "fp32_tc")
+            m.apply_into(G, V, nrhs, "fp32_tc", transpose=True)
+    Q.mul_(-2.0)
+    g.replay()
+    torch.cuda.synchronize()
+    U2, V2 = torch.empty_like(Q), torch.empty_like(Q)
+    m.apply_into(Q, U2, nrhs, "fp32_tc")
+    m.apply_into(G, V2, nrhs, "fp32_tc", transpose=True)
+    torch.cuda.synchronize()
+    assert torch.equal(U, U2) and torch.equal(V, V2)
+    m.close()
     b.close()
 
 
