@@ -267,7 +267,7 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     t.B = dp->tc_b;
     t.U = (float*)b->U;
     t.A = dp->tc_a;
-    t.abase = dp->tc_abase;
+    t.stiles = (const StoredTile*)dp->tc_stiles;
     t.nrhs = nrhs;
     t.status = dp->status;
     t.wait_ns = dp->test_withhold ? dp->test_wait_ns : kWaitLimitNs;
@@ -386,10 +386,10 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
 void drop_tiles(DevicePlan* dp) {
     if (!dp->tc_a) return;
     cudaFree(dp->tc_a);
-    cudaFree(dp->tc_abase);
+    cudaFree(dp->tc_stiles);
     dp->tc_a = nullptr;
-    dp->tc_abase = nullptr;
-    dp->bytes -= dp->stored_bytes + (int64_t)(dp->tc_abase_host.size() * sizeof(int64_t));
+    dp->tc_stiles = nullptr;
+    dp->bytes -= dp->stored_bytes + (int64_t)dp->tc_stiles_host.size();
     dp->stored_bytes = 0;
 }
 
@@ -399,12 +399,12 @@ void drop_tiles(DevicePlan* dp) {
 void fill_tiles(DevicePlan* dp, cudaStream_t st) {
     if (dp->tc_a) return;
     int64_t bytes = 0;
-    dp->tc_abase = upload(dp->tc_abase_host, bytes);
+    dp->tc_stiles = upload(dp->tc_stiles_host, bytes);
     try {
         dp->tc_a = dalloc<float>((size_t)dp->store_floats, bytes);
     } catch (...) {
-        cudaFree(dp->tc_abase);
-        dp->tc_abase = nullptr;
+        cudaFree(dp->tc_stiles);
+        dp->tc_stiles = nullptr;
         throw;
     }
     dp->bytes += bytes;
@@ -425,7 +425,7 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st) {
         t.B = dp->tc_b;
         t.U = (float*)b->U;
         t.A = dp->tc_a;
-        t.abase = dp->tc_abase;
+        t.stiles = (const StoredTile*)dp->tc_stiles;
         t.nrhs = 1;
         t.r0 = 0;
         t.status = dp->status;
@@ -511,16 +511,27 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, b
         dp->p32 = new DeviceBuffers();
         make_buffers<float>(dp, lay, dp->p32);
         if (dp->n_tc > 0 && !dp->cplx) {
-            // where each item's stored tiles would go (its nrows rows only)
+            // where each tile's stored values would go: its item's rows x the
+            // columns some row of the item keeps (the others are zero in
+            // every row), padded to 4 floats
             dp->n_tc_tiles = (int64_t)lay.tc_tiles.size();
-            dp->tc_abase_host.resize(lay.tc_items.size());
+            std::vector<StoredTile> sd(lay.tc_tiles.size());
             int64_t nf = 0;
             for (size_t i = 0; i < lay.tc_items.size(); ++i) {
                 const TcItem& it = lay.tc_items[i];
                 if (it.nrows < 1 || it.nrows > kTcRows) throw Error(-5, "tensor-core item with no rows");
-                dp->tc_abase_host[i] = nf;
-                nf += (int64_t)(it.list_hi - it.list_lo) * it.nrows * 32;
+                for (int32_t t = it.list_lo; t < it.list_hi; ++t) {
+                    uint32_t cm = 0;
+                    for (int sl = 0; sl < it.nslot; ++sl)
+                        if (std::min(it.slot_start[sl + 1], it.nrows) > std::max(it.slot_start[sl], 0))
+                            cm |= lay.tc_tiles[t].keep[sl];
+                    const int64_t f = ((int64_t)__builtin_popcount(cm) * it.nrows + 3) & ~(int64_t)3;
+                    sd[t] = StoredTile{nf, cm, (uint32_t)f};
+                    nf += f;
+                }
             }
+            dp->tc_stiles_host.resize(sd.size() * sizeof(StoredTile));
+            std::memcpy(dp->tc_stiles_host.data(), sd.data(), dp->tc_stiles_host.size());
             dp->store_floats = nf;
             if (store_tiles) fill_tiles(dp, 0);
         }
@@ -540,7 +551,7 @@ void device_plan_destroy(DevicePlan* dp) {
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
                     dp->tc_items, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
-                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a, dp->tc_abase};
+                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a, dp->tc_stiles};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);
@@ -620,7 +631,7 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
     dp->prof_cap = 0;                                      // no profiling events while measuring
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float* keep_a = nullptr;                               // stored tiles hidden while timing
-    int64_t* keep_base = nullptr;
+    void* keep_base = nullptr;
     try {
         CUDA_CHECK(cudaEventCreate(&e0));
         CUDA_CHECK(cudaEventCreate(&e1));
@@ -669,12 +680,12 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
             int passes = 0;
             auto tc = [&] { run_tc<float, false>(dp, b, nrhs, st, passes); };
             keep_a = dp->tc_a;
-            keep_base = dp->tc_abase;
+            keep_base = dp->tc_stiles;
             dp->tc_a = nullptr;                            // time the on-the-fly kernel
-            dp->tc_abase = nullptr;
+            dp->tc_stiles = nullptr;
             rep.ms_onfly = time_ms(tc, 3);
             dp->tc_a = keep_a;
-            dp->tc_abase = keep_base;
+            dp->tc_stiles = keep_base;
             keep_a = nullptr;
             keep_base = nullptr;
             if (!dp->tc_a && allow_store) {
@@ -693,7 +704,7 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
         dp->prof_cap = saved_cap;
         if (keep_a) {
             dp->tc_a = keep_a;
-            dp->tc_abase = keep_base;
+            dp->tc_stiles = keep_base;
         }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);

@@ -51,8 +51,8 @@ struct DevicePlan {
     int64_t n_chunks = 0;
     float* tc_b = nullptr;                 // B operand per chunk for one 32-column pass (hi, lo)
     float* tc_a = nullptr;                 // stored-operator mode: every tile's kernel values
-    int64_t* tc_abase = nullptr;           // per tensor-core item: first float of its tiles in tc_a
-    std::vector<int64_t> tc_abase_host;    // the same offsets on the host (kept to fill later)
+    void* tc_stiles = nullptr;             // per tile: StoredTile (place, stored columns, size)
+    std::vector<unsigned char> tc_stiles_host;  // the same on the host (kept to fill later)
     int64_t store_floats = 0;              // floats the stored tiles take
     int64_t n_tc_tiles = 0;
     int64_t stored_bytes = 0;              // 0 unless the tiles are stored

@@ -96,6 +96,18 @@ struct TcShared {
 constexpr int kTcSmemRequest = 112 * 1024;    // at most two CTAs (2 x 256 TMEM columns) per SM
 static_assert(sizeof(TcShared) <= kTcSmemRequest, "shared memory plan");
 
+// Stored-operator mode, one per tensor-core tile: where its kernel values
+// start in the stored array, which of its 32 source columns are stored (the
+// columns some row of the item keeps; the others are zero for every row), and
+// how many floats the tile takes (kept columns x nrows, padded to a multiple
+// of 4 so that every tile starts and ends on a 16-byte boundary).
+struct StoredTile {
+    int64_t off;
+    uint32_t colmask;
+    uint32_t nfloats;
+};
+static_assert(sizeof(StoredTile) == 16, "StoredTile is one 16-byte bulk copy");
+
 struct TcArgs {
     const TcItem* items;
     const SrcTile* tiles;                      // item i's tiles: [list_lo, list_hi) of this array
@@ -104,7 +116,7 @@ struct TcArgs {
     const float* B;                            // per source chunk (kChunkFloats): B hi, B lo, coordinates
     float* U;                                  // entry rows of nrhs (this item's rows are written here)
     float* A;                                  // stored kernel tiles, or null
-    const int64_t* abase;                      // per item: first float of its stored tiles
+    const StoredTile* stiles;                  // per tile: its place in A (stored-operator mode)
     int nrhs;                                  // right-hand sides (row length of U)
     int r0;                                    // first right-hand side of this pass
     int* status;
@@ -335,14 +347,13 @@ __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict
     }
 }
 
-// Stored kernel tiles (the stored-operator mode): the u-th tile of an item
-// with nrows rows keeps its nrows x 32 kernel values (unscaled FP32, zero
-// where a row's slot skips the source; rows past nrows are not stored) at
-// A + abase[item] + u * nrows * 32, ordered so that compute thread (row,
-// half) reads its 16 values as four 16-byte words with consecutive rows
-// adjacent: value (row, j = 16 half + 4 q + e) at ((half * 4 + q) * nrows + row) * 4 + e.
+// Stored kernel tiles (the stored-operator mode): tile t of an item with
+// nrows rows keeps the kernel values of its stored columns (StoredTile
+// colmask, in column order) as unscaled FP32, zero where a row's slot skips
+// the source; column p of the packed tile holds its nrows values at
+// A + off + p * nrows + row, so that a warp's 32 consecutive rows read 32
+// consecutive floats.
 constexpr int kTileFloats = 128 * 32;          // the largest tile
-__device__ __forceinline__ int tile_word(int half, int q, int row, int nrows) { return (half * 4 + q) * nrows + row; }
 
 // RECORD: also write every tile's kernel values to a.A (the fill pass of the
 // stored-operator mode; the values are the ones the MMA consumes, hi + lo).
@@ -525,15 +536,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                 tmem_st16(acol + 16u * g, ghi);
                 tmem_st16(acol + 32u + 16u * g, glo);
                 if constexpr (RECORD) {
-                    float4* dst = reinterpret_cast<float4*>(a.A + a.abase[blockIdx.x] + (int64_t)u * nrows * 32);
+                    // the tile's stored columns, packed in column order
+                    const StoredTile sd = a.stiles[list_lo + u];
+                    const int jb = j0 + 16 * g;
+                    int p = __popc(sd.colmask & ((1u << jb) - 1u));
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int jj = 4 * q;
-                        if (valid) dst[tile_word(half, q, row, nrows)] =
-                            make_float4(__uint_as_float(ghi[jj]) + __uint_as_float(glo[jj]),
-                                        __uint_as_float(ghi[jj + 1]) + __uint_as_float(glo[jj + 1]),
-                                        __uint_as_float(ghi[jj + 2]) + __uint_as_float(glo[jj + 2]),
-                                        __uint_as_float(ghi[jj + 3]) + __uint_as_float(glo[jj + 3]));
+                    for (int jj = 0; jj < 16; ++jj) {
+                        if ((sd.colmask >> (jb + jj)) & 1u) {
+                            if (valid)
+                                a.A[sd.off + (int64_t)p * nrows + row] =
+                                    __uint_as_float(ghi[jj]) + __uint_as_float(glo[jj]);
+                            ++p;
+                        }
                     }
                 }
             }
@@ -565,16 +579,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
 // ---------------------------------------------------------------------------
 // Stored-operator mode: the same translations with the kernel values read
 // from the tiles a RECORD pass wrote, instead of evaluated. Per tile the
-// producer copies 24 KB (the chunk's B hi + lo and the 16 KB kernel tile);
-// the compute warps only split the values into TF32 hi + lo and write A to
-// tensor memory. The MMA issue, the accumulator drain and the two-level sum
-// are those of tc_near_kernel, so both modes give the same result bit for
-// bit. Bound: HBM, nrows x 128 bytes of kernel values per tile and pass.
+// producer copies the chunk's B hi + lo (8 KB), the tile's StoredTile and its
+// packed kernel values (stored columns x nrows floats); the compute warps
+// put every value back in its column (zero in the others), split it into
+// TF32 hi + lo and write A to tensor memory. The MMA issue, the accumulator
+// drain and the two-level sum are those of tc_near_kernel, so both modes give
+// the same result bit for bit. Bound: HBM, 4 bytes per stored value.
 static_assert(kSrcPerThread == 16, "stored tiles assume two compute threads per row");
 constexpr int kNSS = 3;                        // data stages (24 KB each)
 struct alignas(128) TcSStage {
     float b[2 * 1024];                         // B hi, B lo (the first 8 KB of the chunk block)
-    float4 ga[kTileFloats / 4];                // the tile's kernel values
+    float ga[kTileFloats];                     // the tile's packed kernel values
+    StoredTile desc;                           // its StoredTile (bulk-copied)
 };
 struct TcSShared {
     TcSStage st[kNSS];
@@ -616,23 +632,26 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
 
     if (warp == kTcCompute / 32) {
         // ---------------- producer warp ----------------
-        const float* tiles_src = a.A + a.abase[blockIdx.x];
-        const uint32_t tile_bytes = 128u * (uint32_t)nrows;    // nrows x 32 floats (1 <= nrows <= 128)
         for (int t0 = 0; t0 < ntile; t0 += 32) {
             const int d_chunk = t0 + lane < ntile ? a.tiles[list_lo + t0 + lane].chunk : 0;
+            StoredTile d_st{0, 0u, 0u};
+            if (t0 + lane < ntile) d_st = a.stiles[list_lo + t0 + lane];
             const int nb = min(32, ntile - t0);
             for (int i = 0; i < nb; ++i) {
                 const int t = t0 + i;
                 const int s = t % kNSS;
                 const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
+                const int64_t toff = __shfl_sync(0xffffffffu, d_st.off, i);
+                const uint32_t tile_bytes = 4u * __shfl_sync(0xffffffffu, d_st.nfloats, i);
                 if (t >= kNSS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1), a.wait_ns)) err = true;
                 const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
                 if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
                 if (lane == 0) {
                     const uint32_t bar = sm_addr(&S.full[s]);
-                    mbar_arrive_tx(bar, 4u * 2048u + tile_bytes);
+                    mbar_arrive_tx(bar, 4u * 2048u + 16u + tile_bytes);
                     bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
-                    bulk_g2s(sm_addr(S.st[s].ga), tiles_src + (int64_t)t * nrows * 32, tile_bytes, bar);
+                    bulk_g2s(sm_addr(&S.st[s].desc), a.stiles + list_lo + t, 16u, bar);
+                    if (tile_bytes > 0) bulk_g2s(sm_addr(S.st[s].ga), a.A + toff, tile_bytes, bar);
                     if (hold && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
                 }
                 __syncwarp();
@@ -697,21 +716,30 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             const int s = u % kNSS;
             if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNSS) & 1), a.wait_ns)) err = true;
             uint32_t ghi[16], glo[16];
+            // this thread's 16 columns: stored ones from their packed place
+            // (the mask is the same for the whole warp), the others zero
+            const uint32_t cm = S.st[s].desc.colmask;
+            const float* ga = S.st[s].ga;
+            int p = __popc(cm & ((1u << j0) - 1u));
+            float gv[16];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 g4 = valid ? S.st[s].ga[tile_word(half, q, row, nrows)] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float2 g = h ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
-                    const float2 t = __fmul2_rn(g, split);
-                    const float2 hi = __ffma2_rn(__ffma2_rn(g, m1, t), m1, t);
-                    const float2 lo = __ffma2_rn(hi, m1, g);
-                    const int jj = 4 * q + 2 * h;
-                    ghi[jj] = __float_as_uint(hi.x);
-                    ghi[jj + 1] = __float_as_uint(hi.y);
-                    glo[jj] = __float_as_uint(lo.x);
-                    glo[jj + 1] = __float_as_uint(lo.y);
+            for (int jj = 0; jj < 16; ++jj) {
+                gv[jj] = 0.f;
+                if ((cm >> (j0 + jj)) & 1u) {
+                    if (valid) gv[jj] = ga[p * nrows + row];
+                    ++p;
                 }
+            }
+#pragma unroll
+            for (int jj = 0; jj < 16; jj += 2) {
+                const float2 g = make_float2(gv[jj], gv[jj + 1]);
+                const float2 t = __fmul2_rn(g, split);
+                const float2 hi = __ffma2_rn(__ffma2_rn(g, m1, t), m1, t);
+                const float2 lo = __ffma2_rn(hi, m1, g);
+                ghi[jj] = __float_as_uint(hi.x);
+                ghi[jj + 1] = __float_as_uint(hi.y);
+                glo[jj] = __float_as_uint(lo.x);
+                glo[jj + 1] = __float_as_uint(lo.y);
             }
             if (u >= 2) drain(u - 2);
             const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + (uint32_t)j0;
