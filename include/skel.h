@@ -389,9 +389,10 @@ int skel_test_fail_alloc(int countdown);
 
 /*
  * skel_autotune — pick, by measurement on this plan and device, the variants
- * the FP32 applies of nrhs right-hand sides will use: per tree level the
- * up/down kernel (plain or with register prefetch of the next inner chunk),
- * and for the tensor-core translations (real kernels, nrhs >= 4) whether the
+ * the FP32 applies of nrhs right-hand sides will use: per tree level and
+ * direction the launch shape of the up/down kernel (1, 2, 4 or 8 warps per
+ * CTA sharing a 32-row block; every shape adds the same partial sums in the
+ * same order), and for the tensor-core translations (real kernels, nrhs >= 4) whether the
  * kernel values are evaluated on the fly or read from stored tiles (the
  * choice between operators stored and evaluated on the fly; stored only if
  * allow_store and the tiles fit the free device memory with 2 GB to spare;
@@ -408,7 +409,7 @@ typedef struct {
     double ms_onfly;          /* one tensor-core pass, kernel evaluated on the fly (-1: not timed) */
     double ms_stored;         /* the same reading stored tiles (-1: not timed)                   */
     int    stored;            /* 1 if the plan keeps stored tiles after tuning                  */
-    int    n_updown;          /* up/down level launches measured                                */
+    int    n_updown;          /* up/down level launches tuned (levels x 2 directions)           */
     int    n_changed;         /* of those, choices unlike the default rule                      */
     double ms_updown_default; /* their summed time with the default rule                        */
     double ms_updown_tuned;   /* and with the chosen variants                                   */

@@ -152,24 +152,65 @@ void free_buffers(DeviceBuffers* b) {
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
-// one level of the upward or downward pass
+// warps per CTA of the up/down kernel for a level whose inner index has nch
+// chunks of 32: the default rule (one warp per chunk, at most 4)
+inline int ud_default_warps(int nch) { return nch >= 4 ? 4 : nch >= 2 ? 2 : 1; }
+
+template <class S, bool DOWN, int W>
+void ud_launch(dim3 grid, const UpBox* up, const int32_t* pos, const S* T, S* X, int nrhs, bool conj_op,
+               cudaStream_t st) {
+    if constexpr (W <= ud_streams<S>())
+        updown_kernel<S, DOWN, W><<<grid, 32 * W, ud_smem<S>(W), st>>>(up, pos, T, X, nrhs, conj_op);
+    else
+        throw Error(-1, "up/down: more warps than streams");
+}
+
+template <class S, bool DOWN>
+void ud_set_attributes() {
+    CUDA_CHECK(cudaFuncSetAttribute(updown_kernel<S, DOWN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUdSmemMax));
+    CUDA_CHECK(cudaFuncSetAttribute(updown_kernel<S, DOWN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUdSmemMax));
+    if constexpr (ud_streams<S>() >= 4)
+        CUDA_CHECK(cudaFuncSetAttribute(updown_kernel<S, DOWN, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUdSmemMax));
+    if constexpr (ud_streams<S>() >= 8)
+        CUDA_CHECK(cudaFuncSetAttribute(updown_kernel<S, DOWN, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUdSmemMax));
+}
+
 template <class S>
-void up_down(bool down, const DevicePlan* dp, int l, const S* T, S* X, int nrhs, bool conj_op, cudaStream_t st) {
+void ud_attributes_once() {
+    static bool done = false;
+    if (done) return;
+    ud_set_attributes<S, false>();
+    ud_set_attributes<S, true>();
+    done = true;
+}
+
+// one level of the upward or downward pass; warps = 0: the level's setting
+// (autotuned for FP32, else the default rule)
+template <class S>
+void up_down(bool down, const DevicePlan* dp, int l, const S* T, S* X, int nrhs, bool conj_op, cudaStream_t st,
+             int warps = 0) {
+    ud_attributes_once<S>();
     const int64_t b0 = dp->up_level_ptr[l], b1 = dp->up_level_ptr[l + 1];
     const int nout = down ? dp->up_level_maxr[l] : dp->up_level_maxk[l];
-    const dim3 grid((unsigned)(b1 - b0), std::max(1u, ceil_div(nout, kGT)), ceil_div(nrhs, kGT));
     const int ninner = down ? dp->up_level_maxk[l] : dp->up_level_maxr[l];
-    bool pref = ninner > kGT;                              // the default rule
-    if (std::is_same<S, float>::value) {                   // FP32 levels the autotuner measured
-        const std::vector<int8_t>& t = down ? dp->pref_down : dp->pref_up;
-        if (l < (int)t.size() && t[l] >= 0) pref = t[l] != 0;
+    const dim3 grid((unsigned)(b1 - b0), std::max(1u, ceil_div(nout, kGT)), ceil_div(nrhs, kGT));
+    int W = warps;
+    if (W == 0 && std::is_same<S, float>::value) {
+        const std::vector<int8_t>& t = down ? dp->ud_warps_down : dp->ud_warps_up;
+        if (l < (int)t.size() && t[l] > 0) W = t[l];
     }
-    if (pref) {
-        if (down) updown_kernel<S, true, true><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
-        else updown_kernel<S, false, true><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
-    } else {
-        if (down) updown_kernel<S, true, false><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
-        else updown_kernel<S, false, false><<<grid, kGThreads, 0, st>>>(dp->up + b0, dp->pos, T, X, nrhs, conj_op);
+    if (W == 0) W = ud_default_warps((ninner + kGT - 1) / kGT);
+    W = std::min(W, ud_streams<S>());
+    const UpBox* up = dp->up + b0;
+    switch (W) {
+        case 1: down ? ud_launch<S, true, 1>(grid, up, dp->pos, T, X, nrhs, conj_op, st)
+                     : ud_launch<S, false, 1>(grid, up, dp->pos, T, X, nrhs, conj_op, st); break;
+        case 2: down ? ud_launch<S, true, 2>(grid, up, dp->pos, T, X, nrhs, conj_op, st)
+                     : ud_launch<S, false, 2>(grid, up, dp->pos, T, X, nrhs, conj_op, st); break;
+        case 4: down ? ud_launch<S, true, 4>(grid, up, dp->pos, T, X, nrhs, conj_op, st)
+                     : ud_launch<S, false, 4>(grid, up, dp->pos, T, X, nrhs, conj_op, st); break;
+        default: down ? ud_launch<S, true, 8>(grid, up, dp->pos, T, X, nrhs, conj_op, st)
+                      : ud_launch<S, false, 8>(grid, up, dp->pos, T, X, nrhs, conj_op, st); break;
     }
 }
 
@@ -650,27 +691,29 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
             CUDA_CHECK(cudaGetLastError());
             return (double)ms / reps;
         };
-        // 1. up/down variant per level
+        // 1. up/down launch shape per level: warps per CTA (every choice
+        //    adds the same partial sums in the same order)
         const int nl = (int)dp->up_level_ptr.size() - 1;
-        dp->pref_up.assign(std::max(nl, 0), -1);
-        dp->pref_down.assign(std::max(nl, 0), -1);
+        dp->ud_warps_up.assign(std::max(nl, 0), 0);
+        dp->ud_warps_down.assign(std::max(nl, 0), 0);
         for (int l = 2; l <= dp->L && l < nl; ++l) {
             if (dp->up_level_ptr[l + 1] == dp->up_level_ptr[l]) continue;
             for (int down = 0; down < 2; ++down) {
-                std::vector<int8_t>& t = down ? dp->pref_down : dp->pref_up;
+                std::vector<int8_t>& t = down ? dp->ud_warps_down : dp->ud_warps_up;
                 const float* T = (const float*)(down ? b->Tt : b->T);
-                double ms[2];
-                for (int v = 0; v < 2; ++v) {
-                    t[l] = (int8_t)v;
-                    ms[v] = time_ms([&] { up_down<float>(down != 0, dp, l, T, (float*)(down ? b->U : b->Q), nrhs,
-                                                         down != 0, st); }, 5);
-                }
                 const int ninner = down ? dp->up_level_maxk[l] : dp->up_level_maxr[l];
-                const int def = ninner > kGT ? 1 : 0;
-                const int best = ms[1] < ms[0] ? 1 : 0;
+                const int def = ud_default_warps((ninner + kGT - 1) / kGT);
+                double best_ms = 1e30, def_ms = 0;
+                int best = def;
+                for (int W : {1, 2, 4, 8}) {
+                    const double ms = time_ms([&] { up_down<float>(down != 0, dp, l, T, (float*)(down ? b->U : b->Q),
+                                                                   nrhs, down != 0, st, W); }, 5);
+                    if (W == def) def_ms = ms;
+                    if (ms < best_ms) best_ms = ms, best = W;
+                }
                 t[l] = (int8_t)best;
-                rep.ms_updown_default += ms[def];
-                rep.ms_updown_tuned += ms[best];
+                rep.ms_updown_default += def_ms;
+                rep.ms_updown_tuned += best_ms;
                 rep.n_changed += best != def;
                 ++rep.n_levels;
             }

@@ -56,9 +56,9 @@ struct DevicePlan {
     int64_t store_floats = 0;              // floats the stored tiles take
     int64_t n_tc_tiles = 0;
     int64_t stored_bytes = 0;              // 0 unless the tiles are stored
-    // FP32 up/down variant per level (-1: the default rule, 0: plain, 1:
-    // register prefetch), set by the autotuner
-    std::vector<int8_t> pref_up, pref_down;
+    // FP32 up/down launch shape per level: warps per CTA (0: the default
+    // rule), set by the autotuner
+    std::vector<int8_t> ud_warps_up, ud_warps_down;
     int* status = nullptr;                 // device word raised by a bounded wait that gave up
     // test hook: the next tensor-core pass withholds its first item's first
     // tile until the compute warps gave up, with every wait limited to

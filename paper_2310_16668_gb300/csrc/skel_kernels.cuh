@@ -103,122 +103,137 @@ __global__ void permute_out_narrow(const int64_t* __restrict__ eop, const S* __r
     u[g] = U[eop[p] * nrhs + r];
 }
 
-// ---- upward / downward passes: tiled small GEMMs ---------------------------------------
+// ---- upward / downward passes ------------------------------------------------------------
 // Upward (qhat_S = q_S + T q_R into the parent's slot): output rows i < k,
 // inner index j < r, A(i, j) = T[i + j k] (T column-major k x r), B row j =
 // the q row of R entry j. Downward (u_S += uhat, then u_R += T^* uhat): output
 // rows j < r, inner index i < k, A(j, i) = Tt[j + i r] (the transposed copy,
-// column-major r x k), B row i = uhat_i (the parent's slot). A CTA owns 32
-// output rows x 32 right-hand sides of one box (grid y, z) and stages the A
-// block (inner index major) and the gathered B rows through shared memory 32
-// inner indices at a time; a thread accumulates 4 rows x 4 right-hand sides
-// from one 4-row and one 4-column shared-memory vector per inner index.
-// conj_op applies the complex conjugate to A (T^* downward, conj(T) for the
-// transposed apply).
+// column-major r x k), B row i = uhat_i (the parent's slot). conj_op applies
+// the complex conjugate to A (T^* downward, conj(T) for the transposed apply).
+//
+// A CTA owns 32 output rows x 32 right-hand sides of one box (grid x: box,
+// y: row block, z: column block) and has W warps. The inner index runs in
+// chunks of 32 dealt round-robin to NS streams (stream s: chunks s, s + NS,
+// ...); warp w forms the partial sums of streams w, w + W, ... one after the
+// other, each over its chunks in order, and the stream partials are added in
+// stream order (through shared memory when W > 1, in registers when W = 1).
+// The result is therefore the same for every W, which the autotuner picks
+// per level. Within a warp, lane = right-hand side: per chunk the warp stages
+// its 32 x 32 block of A (inner-major; each load is one coalesced column of
+// 32 rows) and its 32 B rows (each load one coalesced row) in shared memory;
+// each inner index then costs 32 row FMAs per lane (paired in FP32), with the
+// A column read as broadcast 16-byte words.
 constexpr int kGT = 32;
-constexpr int kGThreads = 64;
+template <class S> __host__ __device__ constexpr int ud_streams() {
+    return sizeof(S) <= 4 ? 8 : sizeof(S) <= 8 ? 4 : 2;
+}
+// dynamic shared memory of a CTA with W warps: per warp its A and B blocks,
+// then (W > 1) the stream partials
+template <class S> __host__ __device__ constexpr int ud_smem(int W) {
+    return (W * 2 + (W > 1 ? ud_streams<S>() : 0)) * kGT * kGT * (int)sizeof(S);
+}
+constexpr int kUdSmemMax = 96 * 1024;
 
-template <class S> __device__ __forceinline__ void lds4(const S* p, S* v) {
+template <class S> __device__ __forceinline__ void ud_rows(S* acc, const S* a, S q) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = p[q];
+    for (int r = 0; r < kGT; ++r) acc[r] += a[r] * q;
 }
-template <> __device__ __forceinline__ void lds4<float>(const float* p, float* v) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+template <> __device__ __forceinline__ void ud_rows<float>(float* acc, const float* a, float q) {
+    const float2 q2 = make_float2(q, q);
+    float2* acc2 = reinterpret_cast<float2*>(acc);
+#pragma unroll
+    for (int r4 = 0; r4 < kGT / 4; ++r4) {
+        const float4 v = reinterpret_cast<const float4*>(a)[r4];
+        acc2[2 * r4] = __ffma2_rn(make_float2(v.x, v.y), q2, acc2[2 * r4]);
+        acc2[2 * r4 + 1] = __ffma2_rn(make_float2(v.z, v.w), q2, acc2[2 * r4 + 1]);
+    }
 }
 
-template <class S, bool DOWN, bool PREFETCH>
-__global__ void __launch_bounds__(kGThreads, sizeof(S) <= 4 ? (PREFETCH ? 12 : 16) : 4) updown_kernel(const UpBox* __restrict__ up,
-                                                           const int32_t* __restrict__ pos,
-                                                           const S* __restrict__ T, S* X, int nrhs, bool conj_op) {
-    constexpr int kPer = kGT * kGT / kGThreads;           // A and B elements per thread per chunk
-    constexpr int kRowStep = kGThreads / kGT;             // rows covered by one pass of the CTA
-    // register prefetch of the next chunk (levels with several chunks; element
-    // types up to 8 bytes); single-chunk levels save the registers instead
-    constexpr bool kPrefetch = PREFETCH && sizeof(S) <= 8;
-    __shared__ __align__(16) S As[kGT][kGT];              // As[inner][row]
-    __shared__ __align__(16) S Bs[kGT][kGT];              // Bs[inner][column]; the output tile at the end
+template <class S, bool DOWN, int W>
+__global__ void __launch_bounds__(32 * W) updown_kernel(const UpBox* __restrict__ up, const int32_t* __restrict__ pos,
+                                                        const S* __restrict__ T, S* X, int nrhs, bool conj_op) {
+    constexpr int NS = ud_streams<S>();
+    static_assert(W == 1 || W == 2 || W == 4 || W == 8, "warps per CTA");
+    static_assert(W <= NS, "at most one warp per stream");
+    extern __shared__ __align__(16) unsigned char ud_raw[];
+    S* sm = reinterpret_cast<S*>(ud_raw);
     const UpBox u = up[blockIdx.x];
     const int k = u.k, r = u.n - u.k;
     const int nout = DOWN ? r : k, ninner = DOWN ? k : r;
     const int row0 = blockIdx.y * kGT, c0 = blockIdx.z * kGT;
-    const int tid = threadIdx.x;
-    // every global access below: lane = a contiguous index (a row of T or a
-    // column of X), warp / pass = the other index
-    const int lx = tid % kGT, ly = tid / kGT;
-    if (DOWN && blockIdx.y == 0) {                        // u_S += uhat, this CTA's columns
-        if (c0 + lx < nrhs)
-            for (int i = ly; i < k; i += kRowStep)
-                X[(u.off + pos[u.off + i]) * nrhs + c0 + lx] += X[(u.dst + i) * nrhs + c0 + lx];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int col = c0 + lane;
+    const bool colok = col < nrhs;
+    if (DOWN && blockIdx.y == 0 && colok) {              // u_S += uhat, this CTA's columns
+        for (int i = warp; i < k; i += W) X[(u.off + pos[u.off + i]) * nrhs + col] += X[(u.dst + i) * nrhs + col];
     }
     if (row0 >= nout) return;
-    S ra[kPer], rb[kPer];
-    auto load = [&](int j0) {
-        const int jn = min(kGT, ninner - j0);
+    S* As = sm + warp * 2 * kGT * kGT;                     // this warp's A block [inner][row]
+    S* Bs = As + kGT * kGT;                                // and B block [inner][column]
+    S* Ps = sm + W * 2 * kGT * kGT;                        // stream partials [stream][row][column]
+    const int nch = (ninner + kGT - 1) / kGT;
+    const int nsum = nch < NS ? nch : NS;                  // streams that receive chunks
+    const bool rowok = row0 + lane < nout;
+    S acc[kGT];
+    S tot[W == 1 ? kGT : 1];
+    for (int st = warp; st < nsum; st += W) {
 #pragma unroll
-        for (int t = 0; t < kPer; ++t) {
-            const int b = ly + t * kRowStep;
-            S v = zero<S>();
-            if (row0 + lx < nout && b < jn) {
-                v = T[u.T_off + row0 + lx + (int64_t)(j0 + b) * nout];
-                if (conj_op) v = conj(v);
+        for (int i = 0; i < kGT; ++i) acc[i] = zero<S>();
+        for (int ch = st; ch < nch; ch += NS) {
+            const int j0 = ch * kGT, jn = min(kGT, ninner - j0);
+            // the B rows of this chunk: their entry indices, one per lane
+            int64_t ri = 0;
+            if (lane < jn) ri = DOWN ? (u.dst + j0 + lane) : (u.off + pos[u.off + k + j0 + lane]);
+#pragma unroll 8
+            for (int jj = 0; jj < kGT; ++jj) {
+                S a = zero<S>(), b = zero<S>();
+                const int64_t rj = __shfl_sync(0xffffffffu, ri, jj);
+                if (jj < jn) {
+                    if (rowok) {
+                        a = T[u.T_off + row0 + lane + (int64_t)(j0 + jj) * nout];
+                        if (conj_op) a = conj(a);
+                    }
+                    if (colok) b = X[rj * nrhs + col];
+                }
+                As[jj * kGT + lane] = a;
+                Bs[jj * kGT + lane] = b;
             }
-            ra[t] = v;
-        }
-#pragma unroll
-        for (int t = 0; t < kPer; ++t) {
-            const int b = ly + t * kRowStep;
-            S v = zero<S>();
-            if (b < jn && c0 + lx < nrhs) {
-                const int64_t row = DOWN ? (u.dst + j0 + b) : (u.off + pos[u.off + k + j0 + b]);
-                v = X[row * nrhs + c0 + lx];
-            }
-            rb[t] = v;
-        }
-    };
-    const int ti = tid >> 3, tc = tid & 7;                // rows 4ti .. 4ti+3; columns 4tc .. 4tc+3
-    S acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = zero<S>();
-    if (kPrefetch) load(0);
-    for (int j0 = 0; j0 < ninner; j0 += kGT) {
-        if (!kPrefetch) load(j0);
-        __syncthreads();                                  // the previous chunk's reads are done
-#pragma unroll
-        for (int t = 0; t < kPer; ++t) {
-            As[ly + t * kRowStep][lx] = ra[t];
-            Bs[ly + t * kRowStep][lx] = rb[t];
-        }
-        __syncthreads();
-        if (kPrefetch && j0 + kGT < ninner) load(j0 + kGT);   // next chunk in flight during the products
+            __syncwarp();
 #pragma unroll 4
-        for (int jj = 0; jj < kGT; ++jj) {
-            S av[4], bv[4];
-            lds4(&As[jj][4 * ti], av);
-            lds4(&Bs[jj][4 * tc], bv);
+            for (int jj = 0; jj < kGT; ++jj) ud_rows<S>(acc, As + jj * kGT, Bs[jj * kGT + lane]);
+            __syncwarp();                                  // before the next chunk overwrites the blocks
+        }
+        if constexpr (W == 1) {
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int i = 0; i < kGT; ++i) tot[i] = st == 0 ? acc[i] : tot[i] + acc[i];
+        } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[a][c] += av[a] * bv[c];
+            for (int i = 0; i < kGT; ++i) Ps[(st * kGT + i) * kGT + lane] = acc[i];
         }
     }
-    // the output tile goes through shared memory so that each row is written
-    // by consecutive lanes
-    __syncthreads();
+    if constexpr (W > 1) __syncthreads();
+    if (!colok) return;
+    // rows of this CTA: warp w writes rows w, w + W, ...
+    if constexpr (W == 1) {
+        if (nsum == 0) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) Bs[4 * ti + a][4 * tc + c] = acc[a][c];
-    __syncthreads();
-    if (c0 + lx < nrhs) {
-        for (int i = ly; i < kGT && row0 + i < nout; i += kRowStep) {
-            const int orow = row0 + i;
-            const S v = Bs[i][lx];
-            if (DOWN) X[(u.off + pos[u.off + k + orow]) * nrhs + c0 + lx] += v;
-            else X[(u.dst + orow) * nrhs + c0 + lx] = X[(u.off + pos[u.off + orow]) * nrhs + c0 + lx] + v;
+            for (int i = 0; i < kGT; ++i) tot[i] = zero<S>();
         }
+    }
+#pragma unroll
+    for (int i0 = 0; i0 < kGT; i0 += W) {
+        const int i = i0 + warp;
+        if (row0 + i >= nout) break;
+        S v;
+        if constexpr (W == 1) {
+            v = tot[i];
+        } else {
+            v = zero<S>();
+            for (int s2 = 0; s2 < nsum; ++s2) v = s2 == 0 ? Ps[i * kGT + lane] : v + Ps[(s2 * kGT + i) * kGT + lane];
+        }
+        const int orow = row0 + i;
+        if (DOWN) X[(u.off + pos[u.off + k + orow]) * nrhs + col] += v;
+        else X[(u.dst + orow) * nrhs + col] = X[(u.off + pos[u.off + orow]) * nrhs + col] + v;
     }
 }
 

@@ -73,7 +73,9 @@ def test_full_size_stored_tiles():
     print(f"stored tiles: {info['stored_tile_bytes'] / 1e9:.1f} GB (kept values {4 * info['pairs_tc'] / 1e9:.1f} GB), "
           f"device bytes {info['device_bytes'] / 1e9:.1f} GB, relerr fp32_tc {e:.3e}")
     assert e < 10 * wl.tol
-    assert info["stored_tile_bytes"] < 1.1 * 4 * info["pairs_tc"]      # only kept columns are stored
+    # only columns some row keeps are stored: the rest is entries masked for
+    # other rows of the item and the 16-byte padding of each tile
+    assert info["stored_tile_bytes"] < 1.15 * 4 * info["pairs_tc"]
 
 
 @pytest.mark.parametrize("kind,dim", [("laplace3d", 3), ("laplace2d", 2)])
