@@ -73,13 +73,15 @@ typedef struct {
                          CUDA device in FP64, one CTA per box; 0 = on the host. Same
                          ranks and operators up to rounding (ties in the pivot order
                          may resolve differently). Needs host_only = 0.               */
-    int store_tiles;  /* 1 = stored-operator mode: evaluate every tensor-core tile's
-                         kernel values (its item's rows x 32 sources) once at build
-                         and keep them on the device (at most n_tc_tiles x 16 KB;
-                         skel_stats.stored_tile_bytes); FP32_TC applies then read them
-                         instead of evaluating the kernel. Same results bit for bit.
-                         Real kernels only (ignored otherwise). SKEL_ERR_OOM if the
-                         tiles do not fit.                                            */
+    int store_tiles;  /* 1 = stored-operator mode: evaluate the kernel blocks of the
+                         tensor-core translations once at build and keep them on the
+                         device (skel_stats.stored_tile_bytes); FP32_TC applies then
+                         read them instead of evaluating the kernel. The real kernels
+                         are symmetric, so a block shared by two tiles is stored once
+                         and read transposed by one of them: results equal the
+                         on-the-fly apply's up to FP32 rounding of those values (a few
+                         ulp each). Real kernels only (ignored otherwise).
+                         SKEL_ERR_OOM if the blocks do not fit.                        */
 } skel_options;
 
 typedef struct {
@@ -109,6 +111,9 @@ typedef struct {
     double  id_gflop;        /* device build: GFLOP of the QR reflector updates (FP64)   */
     int64_t stored_tile_bytes; /* store_tiles: device bytes of the stored kernel tiles   */
     int     n_proxy;         /* proxy points per box (2D: 4p, 3D: 6p^2; Section 2.1)     */
+    int64_t pairs_stored;    /* FP32_TC stored-operator mode: kept kernel values the
+                                symmetric store holds once (of pairs_tc; the others are
+                                the same values read transposed)                          */
 } skel_stats;
 
 /*

@@ -47,7 +47,8 @@ class SkelStats(ctypes.Structure):
                 ("n_tc_tiles", ctypes.c_int64), ("n_mix_items", ctypes.c_int64),
                 ("pairs_tc", ctypes.c_int64), ("skel_on_device", ctypes.c_int),
                 ("t_id_kernels", ctypes.c_double), ("id_gflop", ctypes.c_double),
-                ("stored_tile_bytes", ctypes.c_int64), ("n_proxy", ctypes.c_int)]
+                ("stored_tile_bytes", ctypes.c_int64), ("n_proxy", ctypes.c_int),
+                ("pairs_stored", ctypes.c_int64)]
 
 
 class SkelPlanDims(ctypes.Structure):

@@ -308,7 +308,8 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     t.B = dp->tc_b;
     t.U = (float*)b->U;
     t.A = dp->tc_a;
-    t.stiles = (const StoredTile*)dp->tc_stiles;
+    t.refs = (const BlockRef*)dp->tc_refs;
+    t.isym = (const ItemSym*)dp->tc_isym;
     t.nrhs = nrhs;
     t.status = dp->status;
     t.wait_ns = dp->test_withhold ? dp->test_wait_ns : kWaitLimitNs;
@@ -423,29 +424,33 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
     }
 }
 
-// Free the stored tiles (the plan falls back to the on-the-fly kernel).
+// Free the stored blocks (the plan falls back to the on-the-fly kernel).
 void drop_tiles(DevicePlan* dp) {
     if (!dp->tc_a) return;
     cudaFree(dp->tc_a);
-    cudaFree(dp->tc_stiles);
+    cudaFree(dp->tc_refs);
+    cudaFree(dp->tc_isym);
     dp->tc_a = nullptr;
-    dp->tc_stiles = nullptr;
-    dp->bytes -= dp->stored_bytes + (int64_t)dp->tc_stiles_host.size();
+    dp->tc_refs = nullptr;
+    dp->tc_isym = nullptr;
+    dp->bytes -= dp->stored_bytes + (int64_t)(dp->tc_refs_host.size() + dp->tc_isym_host.size());
     dp->stored_bytes = 0;
 }
 
-// Stored-operator mode: evaluate every tile once (the on-the-fly kernel with
-// zero charges, recording the values it hands to the tensor core) into a
-// new allocation; synchronous. On any failure the tiles are freed again.
+// Stored-operator mode: evaluate every stored block once (the on-the-fly
+// kernel in its fill mode, which also runs the translations on zero charges)
+// into a new allocation; synchronous. On any failure the store is freed again.
 void fill_tiles(DevicePlan* dp, cudaStream_t st) {
     if (dp->tc_a) return;
     int64_t bytes = 0;
-    dp->tc_stiles = upload(dp->tc_stiles_host, bytes);
     try {
+        dp->tc_refs = upload(dp->tc_refs_host, bytes);
+        dp->tc_isym = upload(dp->tc_isym_host, bytes);
         dp->tc_a = dalloc<float>((size_t)dp->store_floats, bytes);
     } catch (...) {
-        cudaFree(dp->tc_stiles);
-        dp->tc_stiles = nullptr;
+        cudaFree(dp->tc_refs);
+        cudaFree(dp->tc_isym);
+        dp->tc_refs = dp->tc_isym = nullptr;
         throw;
     }
     dp->bytes += bytes;
@@ -466,7 +471,8 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st) {
         t.B = dp->tc_b;
         t.U = (float*)b->U;
         t.A = dp->tc_a;
-        t.stiles = (const StoredTile*)dp->tc_stiles;
+        t.refs = (const BlockRef*)dp->tc_refs;
+        t.isym = (const ItemSym*)dp->tc_isym;
         t.nrhs = 1;
         t.r0 = 0;
         t.status = dp->status;
@@ -485,6 +491,142 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st) {
     }
 }
 
+
+// The symmetric store of the stored-operator mode (tc_kernels.cuh): the row
+// chunks of every tensor-core item, and per (tile, row chunk) the stored
+// block it reads. A block G(a, c) that one tile reads as (rows a, sources c)
+// and another as (rows c, sources a), both with the same touching-leaf flag,
+// is stored once, as (min, max), written by the first of its direct readers
+// in the fill pass and read transposed by the others; every other block is
+// stored for its own reader(s). Fills dp->tc_isym_host, dp->tc_refs_host,
+// dp->store_floats and dp->pairs_stored.
+void plan_symmetric_store(const Layout& lay, DevicePlan* dp) {
+    const int64_t nch = (int64_t)lay.chunk_start.size();
+    const int64_t nitems = (int64_t)lay.tc_items.size();
+    std::vector<int32_t> chunk_of(lay.n_tot, -1);
+    for (int64_t c = 0; c < nch; ++c)
+        for (int32_t j = 0; j < lay.chunk_cnt[c]; ++j) chunk_of[lay.chunk_start[c] + j] = (int32_t)c;
+    std::vector<ItemSym> isym(nitems);
+    std::vector<int32_t> rc_chunk((size_t)nitems * kMaxRc, -1);
+    int64_t nref = 0;
+    for (int64_t i = 0; i < nitems; ++i) {
+        const TcItem& it = lay.tc_items[i];
+        ItemSym& is = isym[i];
+        std::memset(&is, 0, sizeof(is));
+        int r = 0, m = 0;
+        while (r < it.nrows) {
+            const int32_t c = chunk_of[it.row_off + r];
+            if (c < 0 || lay.chunk_start[c] != it.row_off + r || r + lay.chunk_cnt[c] > it.nrows || m == kMaxRc)
+                throw Error(-5, "symmetric store: an item's rows are not whole chunks");
+            is.ro[m] = (int16_t)r;
+            rc_chunk[(size_t)i * kMaxRc + m] = c;
+            r += lay.chunk_cnt[c];
+            ++m;
+        }
+        is.ro[m] = (int16_t)it.nrows;
+        is.m = m;
+        is.ref0 = nref;
+        nref += (int64_t)(it.list_hi - it.list_lo) * m;
+    }
+    if (nref >= ((int64_t)1 << 32)) throw Error(-1, "symmetric store: too many block references");
+    // one request per (tile, row chunk) whose rows keep any source of the tile
+    struct Req {
+        uint64_t key;       // (min chunk, max chunk)
+        uint32_t ref;       // its BlockRef
+        uint16_t kept;      // kept (row, source) pairs of its rows
+        uint8_t flags;      // 1: direct (rows = the min chunk), 2: touching leaves
+        uint8_t pad;
+    };
+    std::vector<Req> reqs;
+    reqs.reserve((size_t)nref);
+    std::vector<int32_t> ref_rows(nref, 0), ref_cols(nref, 0);   // chunks of a reference: rows, sources
+    for (int64_t i = 0; i < nitems; ++i) {
+        const TcItem& it = lay.tc_items[i];
+        const ItemSym& is = isym[i];
+        for (int32_t t = it.list_lo; t < it.list_hi; ++t) {
+            const SrcTile& tl = lay.tc_tiles[t];
+            const int32_t c = tl.chunk;
+            const uint32_t colbits = tl.cnt >= 32 ? 0xFFFFFFFFu : (1u << tl.cnt) - 1u;
+            for (int k = 0; k < is.m; ++k) {
+                const int32_t a = rc_chunk[(size_t)i * kMaxRc + k];
+                const int lo = is.ro[k], hi = is.ro[k + 1];
+                uint32_t need = 0;
+                int kept = 0;
+                for (int sl = 0; sl < it.nslot; ++sl) {
+                    const int r0 = std::max(lo, it.slot_start[sl]), r1 = std::min(hi, it.slot_start[sl + 1]);
+                    if (r1 <= r0) continue;
+                    const uint32_t kb = tl.keep[sl] & colbits;
+                    need |= kb;
+                    kept += (r1 - r0) * __builtin_popcount(kb);
+                }
+                const int64_t ref = is.ref0 + (int64_t)(t - it.list_lo) * is.m + k;
+                ref_rows[ref] = a;
+                ref_cols[ref] = c;
+                if (!need) continue;
+                const uint64_t lo_c = (uint64_t)std::min(a, c), hi_c = (uint64_t)std::max(a, c);
+                reqs.push_back(Req{(lo_c << 32) | hi_c, (uint32_t)ref, (uint16_t)kept,
+                                   (uint8_t)((a <= c ? 1 : 0) | ((tl.flags & TASK_ADJ) ? 2 : 0)), 0});
+            }
+        }
+    }
+    std::sort(reqs.begin(), reqs.end(), [](const Req& x, const Req& y) {
+        if (x.key != y.key) return x.key < y.key;
+        if ((x.flags & 2) != (y.flags & 2)) return (x.flags & 2) < (y.flags & 2);
+        if ((x.flags & 1) != (y.flags & 1)) return (x.flags & 1) > (y.flags & 1);   // direct readers first
+        return x.ref < y.ref;
+    });
+    std::vector<BlockRef> refs(nref, BlockRef{0, 0u, 0, 0, 0});
+    int64_t nf = 0, stored_pairs = 0;
+    auto new_block = [&](int32_t rows_chunk, int32_t cols_chunk, int64_t& off, int& P) {
+        P = lay.chunk_cnt[rows_chunk] | 1;
+        const int64_t f = ((int64_t)P * lay.chunk_cnt[cols_chunk] + 3) & ~(int64_t)3;
+        off = nf;
+        nf += f;
+        return f;
+    };
+    for (size_t g0 = 0; g0 < reqs.size();) {
+        // one (pair, touching flag) group: direct readers first, then the
+        // readers of the other orientation
+        size_t g1 = g0;
+        while (g1 < reqs.size() && reqs[g1].key == reqs[g0].key && (reqs[g1].flags & 2) == (reqs[g0].flags & 2)) ++g1;
+        size_t d1 = g0;
+        while (d1 < g1 && (reqs[d1].flags & 1)) ++d1;
+        const Req& first = reqs[g0];
+        int64_t off;
+        int P;
+        const int64_t f = new_block(ref_rows[first.ref], ref_cols[first.ref], off, P);
+        // the first reader records the block (it reads it directly)
+        for (size_t q = g0; q < g1; ++q) {
+            const Req& rq = reqs[q];
+            const bool same = ref_rows[rq.ref] == ref_rows[first.ref];    // same orientation as stored
+            refs[rq.ref] = BlockRef{off, (uint32_t)(4 * f), (uint16_t)P,
+                                    (uint8_t)((same ? 0 : kRefTransposed) | (q == g0 ? kRefRecord : 0)), 0};
+            if (same) stored_pairs += rq.kept;
+        }
+        (void)d1;
+        g0 = g1;
+    }
+    // every block fits the place of its reader's row chunk in a stage (rows
+    // ro_k .. ro_{k+1} at float (ro_k + k) * 32, up to the next chunk's place)
+    for (int64_t i = 0; i < nitems; ++i) {
+        const TcItem& it = lay.tc_items[i];
+        const ItemSym& is = isym[i];
+        for (int32_t t = it.list_lo; t < it.list_hi; ++t)
+            for (int k = 0; k < is.m; ++k) {
+                const BlockRef& rf = refs[is.ref0 + (int64_t)(t - it.list_lo) * is.m + k];
+                if (rf.bytes == 0) continue;
+                const int64_t cap = 4 * 32 * (int64_t)(is.ro[k + 1] - is.ro[k] + 1);
+                if ((int64_t)rf.bytes > cap || rf.bytes % 16 != 0 || rf.off % 4 != 0 || rf.off + rf.bytes / 4 > nf)
+                    throw Error(-5, "symmetric store: a block does not fit its row chunk's place");
+            }
+    }
+    dp->tc_isym_host.resize(isym.size() * sizeof(ItemSym));
+    std::memcpy(dp->tc_isym_host.data(), isym.data(), dp->tc_isym_host.size());
+    dp->tc_refs_host.resize(refs.size() * sizeof(BlockRef));
+    std::memcpy(dp->tc_refs_host.data(), refs.data(), dp->tc_refs_host.size());
+    dp->store_floats = nf;
+    dp->pairs_stored = stored_pairs;
+}
 
 }  // namespace
 
@@ -552,28 +694,10 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, b
         dp->p32 = new DeviceBuffers();
         make_buffers<float>(dp, lay, dp->p32);
         if (dp->n_tc > 0 && !dp->cplx) {
-            // where each tile's stored values would go: its item's rows x the
-            // columns some row of the item keeps (the others are zero in
-            // every row), padded to 4 floats
             dp->n_tc_tiles = (int64_t)lay.tc_tiles.size();
-            std::vector<StoredTile> sd(lay.tc_tiles.size());
-            int64_t nf = 0;
-            for (size_t i = 0; i < lay.tc_items.size(); ++i) {
-                const TcItem& it = lay.tc_items[i];
+            for (const TcItem& it : lay.tc_items)
                 if (it.nrows < 1 || it.nrows > kTcRows) throw Error(-5, "tensor-core item with no rows");
-                for (int32_t t = it.list_lo; t < it.list_hi; ++t) {
-                    uint32_t cm = 0;
-                    for (int sl = 0; sl < it.nslot; ++sl)
-                        if (std::min(it.slot_start[sl + 1], it.nrows) > std::max(it.slot_start[sl], 0))
-                            cm |= lay.tc_tiles[t].keep[sl];
-                    const int64_t f = ((int64_t)__builtin_popcount(cm) * it.nrows + 3) & ~(int64_t)3;
-                    sd[t] = StoredTile{nf, cm, (uint32_t)f};
-                    nf += f;
-                }
-            }
-            dp->tc_stiles_host.resize(sd.size() * sizeof(StoredTile));
-            std::memcpy(dp->tc_stiles_host.data(), sd.data(), dp->tc_stiles_host.size());
-            dp->store_floats = nf;
+            plan_symmetric_store(lay, dp);
             if (store_tiles) fill_tiles(dp, 0);
         }
         CUDA_CHECK(cudaDeviceSynchronize());
@@ -592,7 +716,7 @@ void device_plan_destroy(DevicePlan* dp) {
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
                     dp->tc_items, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
-                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a, dp->tc_stiles};
+                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a, dp->tc_refs, dp->tc_isym};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);
@@ -671,8 +795,7 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
     const int saved_cap = dp->prof_cap;
     dp->prof_cap = 0;                                      // no profiling events while measuring
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    float* keep_a = nullptr;                               // stored tiles hidden while timing
-    void* keep_base = nullptr;
+    float* keep_a = nullptr;                               // stored blocks hidden while timing
     try {
         CUDA_CHECK(cudaEventCreate(&e0));
         CUDA_CHECK(cudaEventCreate(&e1));
@@ -723,14 +846,10 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
             int passes = 0;
             auto tc = [&] { run_tc<float, false>(dp, b, nrhs, st, passes); };
             keep_a = dp->tc_a;
-            keep_base = dp->tc_stiles;
             dp->tc_a = nullptr;                            // time the on-the-fly kernel
-            dp->tc_stiles = nullptr;
             rep.ms_onfly = time_ms(tc, 3);
             dp->tc_a = keep_a;
-            dp->tc_stiles = keep_base;
             keep_a = nullptr;
-            keep_base = nullptr;
             if (!dp->tc_a && allow_store) {
                 size_t free_b = 0, total_b = 0;
                 CUDA_CHECK(cudaMemGetInfo(&free_b, &total_b));
@@ -745,10 +864,7 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
         }
     } catch (...) {
         dp->prof_cap = saved_cap;
-        if (keep_a) {
-            dp->tc_a = keep_a;
-            dp->tc_stiles = keep_base;
-        }
+        if (keep_a) dp->tc_a = keep_a;
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         throw;

@@ -450,6 +450,7 @@ int skel_info(skel_handle h, skel_stats* s) {
             *s = h->mstats;
             s->device_bytes = h->dev ? h->dev->bytes : 0;
             s->stored_tile_bytes = h->dev ? h->dev->stored_bytes : 0;
+            s->pairs_stored = h->dev ? h->dev->pairs_stored : 0;
             return;
         }
         const skel::Plan& P = h->plan;
@@ -484,6 +485,7 @@ int skel_info(skel_handle h, skel_stats* s) {
         s->id_gflop = P.id_flops * 1e-9;
         s->stored_tile_bytes = h->dev ? h->dev->stored_bytes : 0;
         s->n_proxy = t.dim == 2 ? 4 * P.proxy_p : 6 * P.proxy_p * P.proxy_p;
+        s->pairs_stored = h->dev ? h->dev->pairs_stored : 0;
     });
 }
 

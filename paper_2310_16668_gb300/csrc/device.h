@@ -50,10 +50,13 @@ struct DevicePlan {
     float* chunk_center = nullptr;         // 4 per chunk: its box's centre
     int64_t n_chunks = 0;
     float* tc_b = nullptr;                 // B operand per chunk for one 32-column pass (hi, lo)
-    float* tc_a = nullptr;                 // stored-operator mode: every tile's kernel values
-    void* tc_stiles = nullptr;             // per tile: StoredTile (place, stored columns, size)
-    std::vector<unsigned char> tc_stiles_host;  // the same on the host (kept to fill later)
-    int64_t store_floats = 0;              // floats the stored tiles take
+    float* tc_a = nullptr;                 // stored-operator mode: the symmetric store of kernel blocks
+    void* tc_refs = nullptr;               // per tile and row chunk: BlockRef (device, while stored)
+    void* tc_isym = nullptr;               // per tensor-core item: ItemSym (device, while stored)
+    std::vector<unsigned char> tc_refs_host, tc_isym_host;  // the same on the host (kept to fill later)
+    int64_t store_floats = 0;              // floats the store takes
+    int64_t pairs_stored = 0;              // kept kernel values the store holds once (the rest are
+                                           // read transposed)
     int64_t n_tc_tiles = 0;
     int64_t stored_bytes = 0;              // 0 unless the tiles are stored
     // FP32 up/down launch shape per level: warps per CTA (0: the default

@@ -96,17 +96,38 @@ struct TcShared {
 constexpr int kTcSmemRequest = 112 * 1024;    // at most two CTAs (2 x 256 TMEM columns) per SM
 static_assert(sizeof(TcShared) <= kTcSmemRequest, "shared memory plan");
 
-// Stored-operator mode, one per tensor-core tile: where its kernel values
-// start in the stored array, which of its 32 source columns are stored (the
-// columns some row of the item keeps; the others are zero for every row), and
-// how many floats the tile takes (kept columns x nrows, padded to a multiple
-// of 4 so that every tile starts and ends on a 16-byte boundary).
-struct StoredTile {
-    int64_t off;
-    uint32_t colmask;
-    uint32_t nfloats;
+// Stored-operator mode (symmetric store). The rows of every tensor-core item
+// are whole source chunks ("row chunks", at most kMaxRc of them); the values
+// a tile (item, source chunk c) needs are, for each row chunk a, the block
+// G(a, c) of the kernel between the entries of a and of c. For the real
+// kernels G(a, c) = G(c, a)^T and the near-field relation is symmetric, so a
+// block is stored once, in one orientation, and read directly by one tile and
+// transposed by the other. A stored block with R rows and C columns keeps its
+// values column by column with an odd pitch P >= R (value (r, j) at
+// off + j P + r), so that 32 consecutive rows read 32 consecutive floats and
+// the transposed read (r, j) -> off + r P + j, a stride of P, meets every
+// shared-memory bank once. Stored values are unmasked; each reader applies
+// its own keep mask.
+constexpr int kMaxRc = 12;                     // row chunks per item (<= 8 packed leaves + 128 / 32)
+constexpr int kSymFloats = (128 + kMaxRc) * 32;  // a stage's block area: row chunk k at (ro_k + k) * 32
+
+struct BlockRef {                              // 16 bytes: one row chunk of one tile
+    int64_t off;                               // first float of the stored block
+    uint32_t bytes;                            // bulk-copy size (0: no row of this chunk keeps a source)
+    uint16_t pitch;                            // P of the stored block
+    uint8_t flags;                             // kRefTransposed, kRefRecord
+    uint8_t pad;
 };
-static_assert(sizeof(StoredTile) == 16, "StoredTile is one 16-byte bulk copy");
+static_assert(sizeof(BlockRef) == 16, "BlockRef is 16 bytes");
+constexpr uint8_t kRefTransposed = 1;          // the block is stored as G(c, a): read it transposed
+constexpr uint8_t kRefRecord = 2;              // this tile's fill pass writes the block
+
+struct ItemSym {                               // 40 bytes per tensor-core item
+    int64_t ref0;                              // its tiles' BlockRefs: ref0 + t * m + k (t = tile of the item)
+    int32_t m;                                 // row chunks
+    int16_t ro[kMaxRc + 2];                    // first row of each row chunk; ro[m] = nrows
+};
+static_assert(sizeof(ItemSym) == 40, "ItemSym layout");
 
 struct TcArgs {
     const TcItem* items;
@@ -115,8 +136,9 @@ struct TcArgs {
     const float4* Xlo;
     const float* B;                            // per source chunk (kChunkFloats): B hi, B lo, coordinates
     float* U;                                  // entry rows of nrhs (this item's rows are written here)
-    float* A;                                  // stored kernel tiles, or null
-    const StoredTile* stiles;                  // per tile: its place in A (stored-operator mode)
+    float* A;                                  // stored kernel blocks, or null
+    const BlockRef* refs;                      // stored-operator mode: per tile and row chunk
+    const ItemSym* isym;                       // stored-operator mode: per item
     int nrhs;                                  // right-hand sides (row length of U)
     int r0;                                    // first right-hand side of this pass
     int* status;
@@ -467,6 +489,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         constexpr int kCols = kTcN / kTpr;                     // accumulator columns this thread owns
         constexpr uint32_t kKeepMask = kSrcPerThread == 32 ? 0xFFFFFFFFu : (1u << kSrcPerThread) - 1u;
         const int j0 = kSrcPerThread * half;
+        // fill pass: this row's row chunk and its row in it
+        int rk = 0, rl = row, rm = 1;
+        int64_t rref0 = 0;
+        if constexpr (RECORD) {
+            const ItemSym* is = a.isym + blockIdx.x;
+            rm = is->m;
+            rref0 = is->ref0;
+            for (int k = 1; k < rm; ++k)
+                if (row >= is->ro[k]) rk = k;
+            rl = row - is->ro[rk];
+        }
         // two-level FP32 sum: acc adds the tiles of a group of kTcGroup, the
         // shared-memory `outer` adds the groups (keeps long lists accurate)
         float acc[kCols];
@@ -510,7 +543,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             for (int p = lane; p < nsw * kSrcPerThread; p += 32) {
                 const int ls = p / kSrcPerThread, jj = p % kSrcPerThread;
                 const float4 v = st.xh[j0 + jj];
-                const bool kept = (st.tile.keep[s_lo + ls] >> (j0 + jj)) & 1u;
+                // (the fill pass records every source of the chunk, unmasked:
+                // each reader of a stored block applies its own keep mask)
+                const bool kept = RECORD ? (j0 + jj < st.tile.cnt) : ((st.tile.keep[s_lo + ls] >> (j0 + jj)) & 1u);
                 float* d = wc + ls * kWarpSlotFloats + jj;
                 d[0] = kept ? v.x : kFar;
                 d[kSrcPerThread] = kept ? v.y : kFar;
@@ -521,7 +556,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             // A buffer u % kNA was last read by MMA(u - kNA), complete since drain(u - 2)
             const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + (uint32_t)j0;
             const float* c = wc + myloc * kWarpSlotFloats;
-            const bool none = __all_sync(0xffffffffu, keep == 0);
+            const bool none = !RECORD && __all_sync(0xffffffffu, keep == 0);
 #pragma unroll
             for (int g = 0; g < kSrcPerThread / 16; ++g) {
                 uint32_t ghi[16], glo[16];
@@ -536,18 +571,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                 tmem_st16(acol + 16u * g, ghi);
                 tmem_st16(acol + 32u + 16u * g, glo);
                 if constexpr (RECORD) {
-                    // the tile's stored columns, packed in column order
-                    const StoredTile sd = a.stiles[list_lo + u];
-                    const int jb = j0 + 16 * g;
-                    int p = __popc(sd.colmask & ((1u << jb) - 1u));
+                    // this row's block of the tile, if this tile records it
+                    // (stored as this row chunk x the tile's chunk)
+                    const BlockRef rf = a.refs[rref0 + (int64_t)u * rm + rk];
+                    if (valid && (rf.flags & kRefRecord)) {
+                        const int jb = j0 + 16 * g;
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        if ((sd.colmask >> (jb + jj)) & 1u) {
-                            if (valid)
-                                a.A[sd.off + (int64_t)p * nrows + row] =
+                        for (int jj = 0; jj < 16; ++jj)
+                            if (jb + jj < st.tile.cnt)
+                                a.A[rf.off + (int64_t)(jb + jj) * rf.pitch + rl] =
                                     __uint_as_float(ghi[jj]) + __uint_as_float(glo[jj]);
-                            ++p;
-                        }
                     }
                 }
             }
@@ -578,19 +611,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
 
 // ---------------------------------------------------------------------------
 // Stored-operator mode: the same translations with the kernel values read
-// from the tiles a RECORD pass wrote, instead of evaluated. Per tile the
-// producer copies the chunk's B hi + lo (8 KB), the tile's StoredTile and its
-// packed kernel values (stored columns x nrows floats); the compute warps
-// put every value back in its column (zero in the others), split it into
-// TF32 hi + lo and write A to tensor memory. The MMA issue, the accumulator
-// drain and the two-level sum are those of tc_near_kernel, so both modes give
-// the same result bit for bit. Bound: HBM, 4 bytes per stored value.
+// from the symmetric store instead of evaluated. Per tile the producer copies
+// the chunk's B hi + lo (8 KB), the tile's SrcTile (its keep masks) and
+// BlockRefs, and each row chunk's stored block into that row chunk's fixed
+// place in the stage (rows ro_k .. ro_k + cnt_k at float (ro_k + k) * 32;
+// a block of R rows and C columns with pitch P <= R + 1 fits there in either
+// orientation). The compute warps read their row's 16 values directly or
+// transposed, apply the row's keep mask, split into TF32 hi + lo and write A
+// to tensor memory. The MMA issue, the accumulator drain and the two-level
+// sum are those of tc_near_kernel. Bound: HBM, 4 bytes per stored value.
 static_assert(kSrcPerThread == 16, "stored tiles assume two compute threads per row");
-constexpr int kNSS = 3;                        // data stages (24 KB each)
+constexpr int kNSS = 3;                        // data stages (~26 KB each)
 struct alignas(128) TcSStage {
     float b[2 * 1024];                         // B hi, B lo (the first 8 KB of the chunk block)
-    float ga[kTileFloats];                     // the tile's packed kernel values
-    StoredTile desc;                           // its StoredTile (bulk-copied)
+    float ga[kSymFloats];                      // the row chunks' stored blocks
+    SrcTile tile;                              // the tile's descriptor (keep masks, source count)
+    BlockRef refs[kMaxRc];                     // its row chunks' blocks
 };
 struct TcSShared {
     TcSStage st[kNSS];
@@ -607,9 +643,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
     TcSShared& S = *reinterpret_cast<TcSShared*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const TcItem* itp = a.items + blockIdx.x;
+    const ItemSym* isp = a.isym + blockIdx.x;
     const int64_t row_off = itp->row_off;
-    const int nrows = itp->nrows, list_lo = itp->list_lo;
+    const int nrows = itp->nrows, nslot = itp->nslot, list_lo = itp->list_lo;
     const int ntile = itp->list_hi - list_lo;
+    const int m = isp->m;
+    const int64_t ref0 = isp->ref0;
 
     if (tid == 0) {
         for (int s = 0; s < kNSS; ++s) {
@@ -632,30 +671,30 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
 
     if (warp == kTcCompute / 32) {
         // ---------------- producer warp ----------------
-        for (int t0 = 0; t0 < ntile; t0 += 32) {
-            const int d_chunk = t0 + lane < ntile ? a.tiles[list_lo + t0 + lane].chunk : 0;
-            StoredTile d_st{0, 0u, 0u};
-            if (t0 + lane < ntile) d_st = a.stiles[list_lo + t0 + lane];
-            const int nb = min(32, ntile - t0);
-            for (int i = 0; i < nb; ++i) {
-                const int t = t0 + i;
-                const int s = t % kNSS;
-                const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
-                const int64_t toff = __shfl_sync(0xffffffffu, d_st.off, i);
-                const uint32_t tile_bytes = 4u * __shfl_sync(0xffffffffu, d_st.nfloats, i);
-                if (t >= kNSS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1), a.wait_ns)) err = true;
-                const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
-                if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
-                if (lane == 0) {
-                    const uint32_t bar = sm_addr(&S.full[s]);
-                    mbar_arrive_tx(bar, 4u * 2048u + 16u + tile_bytes);
-                    bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
-                    bulk_g2s(sm_addr(&S.st[s].desc), a.stiles + list_lo + t, 16u, bar);
-                    if (tile_bytes > 0) bulk_g2s(sm_addr(S.st[s].ga), a.A + toff, tile_bytes, bar);
-                    if (hold && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
-                }
-                __syncwarp();
+        // lane k < m owns row chunk k: its place in the stage is fixed
+        const uint32_t slot_bytes_off = lane < m ? 4u * 32u * (uint32_t)(isp->ro[lane] + lane) : 0u;
+        for (int t = 0; t < ntile; ++t) {
+            const int s = t % kNSS;
+            BlockRef rf{0, 0u, 0, 0, 0};
+            if (lane < m) rf = a.refs[ref0 + (int64_t)t * m + lane];
+            uint32_t tot = rf.bytes;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            const int chunk = a.tiles[list_lo + t].chunk;
+            if (t >= kNSS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1), a.wait_ns)) err = true;
+            const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
+            if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
+            const uint32_t bar = sm_addr(&S.full[s]);
+            if (lane == 0) {
+                mbar_arrive_tx(bar, 4u * 2048u + 64u + 16u * (uint32_t)m + tot);
+                bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
+                bulk_g2s(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar);
+                bulk_g2s(sm_addr(S.st[s].refs), a.refs + ref0 + (int64_t)t * m, 16u * (uint32_t)m, bar);
             }
+            __syncwarp();                              // the byte count is armed before any block lands
+            if (rf.bytes > 0) bulk_g2s(sm_addr(S.st[s].ga) + slot_bytes_off, a.A + rf.off, rf.bytes, bar);
+            if (hold && lane == 0 && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
+            __syncwarp();
         }
         if (lane == 0) {
             for (int t = (ntile > kNSS ? ntile - kNSS : 0); t < ntile; ++t)
@@ -666,12 +705,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                                    ((128u >> 4) << 24);
-            for (int m = 0; m < ntile; ++m) {
-                const int s = m % kNSS, ab = m % kNA;
-                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kNSS) & 1), a.wait_ns)) err = true;
+            for (int mm = 0; mm < ntile; ++mm) {
+                const int s = mm % kNSS, ab = mm % kNA;
+                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((mm / kNSS) & 1), a.wait_ns)) err = true;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t bh = sm_addr(S.st[s].b), bl = bh + 4u * 1024u;
-                const uint32_t d = tbase + kColD + 32u * (m & 1);
+                const uint32_t d = tbase + kColD + 32u * (mm & 1);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const uint32_t ahi = tbase + kColA + 64u * ab + 8u * k, alo = ahi + 32u;
@@ -687,6 +726,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         // ---------------- compute warps ----------------
         const int row = tid & 127, half = tid >> 7;
         const bool valid = row < nrows;
+        int myslot = 0;
+        for (int c = 1; c < nslot; ++c)
+            if (row >= itp->slot_start[c]) myslot = c;
+        // this row's row chunk k, its row rl in it, and the chunk's place in a stage
+        int rk = 0;
+        for (int k = 1; k < m; ++k)
+            if (row >= isp->ro[k]) rk = k;
+        const int rl = row - isp->ro[rk];
+        const int slot_off = 32 * (isp->ro[rk] + rk);
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         constexpr int kCols = kTcN / kTpr;
         const int j0 = kSrcPerThread * half;
@@ -696,14 +744,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             acc[c] = 0.f;
             S.outer[c][tid] = 0.f;
         }
-        auto drain = [&](int m) {
-            if (!mbar_wait(sm_addr(&S.empty[m % kNSS]), (uint32_t)((m / kNSS) & 1), a.wait_ns)) err = true;
+        auto drain = [&](int mm) {
+            if (!mbar_wait(sm_addr(&S.empty[mm % kNSS]), (uint32_t)((mm / kNSS) & 1), a.wait_ns)) err = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t v[kCols];
-            tmem_ld16(tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kCols * half), v);
+            tmem_ld16(tbase + lane_off + kColD + 32u * (mm & 1) + (uint32_t)(kCols * half), v);
 #pragma unroll
             for (int c = 0; c < kCols; ++c) acc[c] += __uint_as_float(v[c]);
-            if (m % kTcGroup == kTcGroup - 1) {
+            if (mm % kTcGroup == kTcGroup - 1) {
 #pragma unroll
                 for (int c = 0; c < kCols; ++c) {
                     S.outer[c][tid] += acc[c];
@@ -715,21 +763,20 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         for (int u = 0; u < ntile; ++u) {
             const int s = u % kNSS;
             if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNSS) & 1), a.wait_ns)) err = true;
-            uint32_t ghi[16], glo[16];
-            // this thread's 16 columns: stored ones from their packed place
-            // (the mask is the same for the whole warp), the others zero
-            const uint32_t cm = S.st[s].desc.colmask;
-            const float* ga = S.st[s].ga;
-            int p = __popc(cm & ((1u << j0) - 1u));
+            const TcSStage& st = S.st[s];
+            // the row's kept sources of this tile, and where its block sits
+            const uint32_t keep = valid ? (st.tile.keep[myslot] >> j0) & 0xFFFFu : 0u;
+            const BlockRef rf = st.refs[rk];
+            const bool tr = (rf.flags & kRefTransposed) != 0;
+            const int P = rf.pitch;
+            const float* blk = st.ga + slot_off;
+            // direct: (rl, j) at j P + rl; transposed: at rl P + j
+            const int base = tr ? rl * P : rl;
+            const int step = tr ? 1 : P;
             float gv[16];
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-                gv[jj] = 0.f;
-                if ((cm >> (j0 + jj)) & 1u) {
-                    if (valid) gv[jj] = ga[p * nrows + row];
-                    ++p;
-                }
-            }
+            for (int jj = 0; jj < 16; ++jj) gv[jj] = ((keep >> jj) & 1u) ? blk[base + (j0 + jj) * step] : 0.f;
+            uint32_t ghi[16], glo[16];
 #pragma unroll
             for (int jj = 0; jj < 16; jj += 2) {
                 const float2 g = make_float2(gv[jj], gv[jj + 1]);
@@ -749,7 +796,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(sm_addr(&S.afull[s]));
         }
-        for (int m = (ntile >= 2 ? ntile - 2 : 0); m < ntile; ++m) drain(m);
+        for (int mm = (ntile >= 2 ? ntile - 2 : 0); mm < ntile; ++mm) drain(mm);
 #pragma unroll
         for (int c = 0; c < kCols; ++c) acc[c] += S.outer[c][tid];
         if (valid) {

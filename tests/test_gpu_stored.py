@@ -1,7 +1,9 @@
 """Stored-operator mode (``store_tiles``): the tensor-core apply reading kernel
-tiles evaluated once at build must equal the on-the-fly apply bit for bit
-(the stored values are exactly the ones the tensor core consumed), and so
-inherits its parity with the oracle."""
+blocks evaluated once at build. The real kernels are symmetric, so a block
+two tiles share is stored once and one of them reads it transposed: its
+values are the on-the-fly kernel's for the other orientation, equal up to
+FP32 rounding. The stored apply therefore matches the on-the-fly apply to
+FP32 rounding (1e-6 of max |u|), and the oracle's direct sum within 10 tol."""
 import numpy as np
 import pytest
 import torch
@@ -27,21 +29,23 @@ def _gpu():
                                                  ("laplace3d", 3, "clustered", 32, 1e-6),
                                                  ("laplace2d", 2, "clustered", 32, 1e-8)])
 @pytest.mark.parametrize("nrhs", [32, 64])
-def test_stored_tiles_equal_on_the_fly(kind, dim, dist, b, tol, nrhs):
+def test_stored_blocks_match_on_the_fly(kind, dim, dist, b, tol, nrhs):
     x = W.points_uniform(20000, dim, 31) if dist == "uniform" else clustered(12000, dim, 31)
     fs = SkelFMM(x, kind, tol, b, nrhs_max=nrhs, store_tiles=True)
     fo = SkelFMM(x, kind, tol, b, nrhs_max=nrhs)
     info = fs.info()
-    # every kept value is stored once, plus at most the masked entries of
-    # stored columns and the 4-float padding of each tile
-    assert 4 * info["pairs_tc"] <= info["stored_tile_bytes"] <= info["n_tc_tiles"] * 128 * 32 * 4
+    # every distinct kept value is stored once; shared blocks are read twice
+    assert 0 < info["pairs_stored"] < info["pairs_tc"]
+    assert 4 * info["pairs_stored"] <= info["stored_tile_bytes"] <= 4 * 2 * info["pairs_tc"]
     assert info["stored_tile_bytes"] % 16 == 0
     assert fo.info()["stored_tile_bytes"] == 0
     q = torch.from_numpy(W.charges_normal(x.shape[0], nrhs, 32)).cuda().float()
     us = fs.apply(q, "fp32_tc")
     uo = fo.apply(q, "fp32_tc")
     fs.device_status()
-    assert torch.equal(us, uo)
+    for r in (0, nrhs // 2, nrhs - 1):
+        assert relerr(us[:, r].cpu().numpy(), uo[:, r].cpu().numpy()) < 1e-6, r
+    assert torch.equal(fs.apply(q, "fp32_tc"), us)    # deterministic
     ut = fs.apply_transpose(q, "fp32_tc")
     assert torch.equal(ut, us)                         # real kernels: A~^T = A~
     # and against the direct sum (RHS 0)
@@ -70,18 +74,21 @@ def test_full_size_stored_tiles():
     ref = direct.direct_sum(wl.kernel, x, qall[:, 0].double().cpu().numpy(), targets=tg)
     e = relerr(us[:, 0].double().cpu().numpy()[tg], ref)
     info = fs.info()
-    print(f"stored tiles: {info['stored_tile_bytes'] / 1e9:.1f} GB (kept values {4 * info['pairs_tc'] / 1e9:.1f} GB), "
+    print(f"stored tiles: {info['stored_tile_bytes'] / 1e9:.1f} GB (distinct kept values {4 * info['pairs_stored'] / 1e9:.1f} GB"
+          f" of {4 * info['pairs_tc'] / 1e9:.1f} GB evaluated), "
           f"device bytes {info['device_bytes'] / 1e9:.1f} GB, relerr fp32_tc {e:.3e}")
     assert e < 10 * wl.tol
-    # only columns some row keeps are stored: the rest is entries masked for
-    # other rows of the item and the 16-byte padding of each tile
-    assert info["stored_tile_bytes"] < 1.15 * 4 * info["pairs_tc"]
+    # the symmetric store holds each shared block once: well under the
+    # 4 B per evaluation of a per-tile store
+    assert info["stored_tile_bytes"] < 0.7 * 4 * info["pairs_tc"]
 
 
 @pytest.mark.parametrize("kind,dim", [("laplace3d", 3), ("laplace2d", 2)])
 def test_autotune_keeps_results(kind, dim):
     """The autotuner only picks among variants that compute the same thing:
-    the FP32 and FP32_TC applies are bit for bit what they were before."""
+    the up/down launch shapes give the same FP32 result bit for bit; the
+    stored blocks, if chosen, the on-the-fly result up to FP32 rounding of the
+    shared blocks read transposed."""
     x = clustered(12000, dim, 35)
     f = SkelFMM(x, kind, 1e-6, 32, nrhs_max=32)
     q = torch.from_numpy(W.charges_normal(x.shape[0], 32, 36)).cuda().float()
@@ -94,7 +101,15 @@ def test_autotune_keeps_results(kind, dim):
         assert 0 < rep["ms_stored"] < rep["ms_onfly"]
     tc1, s1 = f.apply(q, "fp32_tc"), f.apply(q[:, :3].contiguous(), "fp32")
     f.device_status()
-    assert torch.equal(tc0, tc1) and torch.equal(s0, s1)
+    assert torch.equal(s0, s1)
+    if rep["stored"]:
+        assert relerr(tc1[:, 0].cpu().numpy(), tc0[:, 0].cpu().numpy()) < 1e-6
+    else:
+        assert torch.equal(tc0, tc1)
     rep2 = f.autotune(32, allow_store=False)          # tuning again is allowed
-    assert torch.equal(f.apply(q, "fp32_tc"), tc0)
+    tc2 = f.apply(q, "fp32_tc")
+    if rep2["stored"]:
+        assert relerr(tc2[:, 0].cpu().numpy(), tc0[:, 0].cpu().numpy()) < 1e-6
+    else:
+        assert torch.equal(tc2, tc0)
     assert rep2["n_updown"] == rep["n_updown"]
