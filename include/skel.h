@@ -397,7 +397,9 @@ int skel_test_fail_alloc(int countdown);
  * the FP32 applies of nrhs right-hand sides will use: per tree level and
  * direction the launch shape of the up/down kernel (1, 2, 4 or 8 warps per
  * CTA sharing a 32-row block; every shape adds the same partial sums in the
- * same order), and for the tensor-core translations (real kernels, nrhs >= 4) whether the
+ * same order), the pipeline depth of the on-the-fly tensor-core kernel (4, 6
+ * or 8 bulk-copy stages; same arithmetic), and for the tensor-core
+ * translations (real kernels, nrhs >= 4) whether the
  * kernel values are evaluated on the fly or read from stored tiles (the
  * choice between operators stored and evaluated on the fly; stored only if
  * allow_store and the tiles fit the free device memory with 2 GB to spare;
@@ -418,6 +420,8 @@ typedef struct {
     int    n_changed;         /* of those, choices unlike the default rule                      */
     double ms_updown_default; /* their summed time with the default rule                        */
     double ms_updown_tuned;   /* and with the chosen variants                                   */
+    int    tc_stages;         /* pipeline depth (bulk-copy stages) chosen for the on-the-fly
+                                 tensor-core kernel: 4, 6 or 8 (0: not tuned)                  */
 } skel_tuning;
 int skel_autotune(skel_handle h, int nrhs, int allow_store, void* stream, skel_tuning* out);
 

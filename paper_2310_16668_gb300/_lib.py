@@ -65,7 +65,8 @@ class SkelTimings(ctypes.Structure):
 class SkelTuning(ctypes.Structure):
     _fields_ = [("ms_onfly", ctypes.c_double), ("ms_stored", ctypes.c_double), ("stored", ctypes.c_int),
                 ("n_updown", ctypes.c_int), ("n_changed", ctypes.c_int),
-                ("ms_updown_default", ctypes.c_double), ("ms_updown_tuned", ctypes.c_double)]
+                ("ms_updown_default", ctypes.c_double), ("ms_updown_tuned", ctypes.c_double),
+                ("tc_stages", ctypes.c_int)]
 
 
 class SkelError(RuntimeError):

@@ -279,8 +279,12 @@ NearArgs<Real, CPLX> near_args(DevicePlan* dp, DeviceBuffers* b, const WorkItem*
 void set_tc_attributes() {
     static bool done = false;
     if (done) return;
-    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcsSmemRequest));
@@ -332,8 +336,16 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
             if (kidx == 0) tc_stored_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTcsSmemRequest, st>>>(t);
             else tc_stored_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTcsSmemRequest, st>>>(t);
         } else {
-            if (kidx == 0) tc_near_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
-            else tc_near_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+            // pipeline depth: the autotuner's choice (same arithmetic for every depth)
+            const unsigned g = (unsigned)dp->n_tc;
+            switch (dp->tc_stages) {
+                case 4: kidx == 0 ? tc_near_kernel<0, false, 4><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
+                                  : tc_near_kernel<1, false, 4><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
+                case 8: kidx == 0 ? tc_near_kernel<0, false, 8><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
+                                  : tc_near_kernel<1, false, 8><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
+                default: kidx == 0 ? tc_near_kernel<0, false, 6><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
+                                   : tc_near_kernel<1, false, 6><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
+            }
         }
         CUDA_CHECK(cudaGetLastError());
     }
@@ -847,7 +859,16 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
             auto tc = [&] { run_tc<float, false>(dp, b, nrhs, st, passes); };
             keep_a = dp->tc_a;
             dp->tc_a = nullptr;                            // time the on-the-fly kernel
-            rep.ms_onfly = time_ms(tc, 3);
+            // its pipeline depth (bulk-copy stages): the fastest of 4, 6, 8
+            rep.ms_onfly = 1e30;
+            int best_ns = kNS;
+            for (int ns : {4, 6, 8}) {
+                dp->tc_stages = ns;
+                const double ms = time_ms(tc, 3);
+                if (ms < rep.ms_onfly) rep.ms_onfly = ms, best_ns = ns;
+            }
+            dp->tc_stages = best_ns;
+            rep.tc_stages = best_ns;
             dp->tc_a = keep_a;
             keep_a = nullptr;
             if (!dp->tc_a && allow_store) {

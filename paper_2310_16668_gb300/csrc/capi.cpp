@@ -759,6 +759,7 @@ int skel_autotune(skel_handle h, int nrhs, int allow_store, void* stream, skel_t
             out->n_changed = r.n_changed;
             out->ms_updown_default = r.ms_updown_default;
             out->ms_updown_tuned = r.ms_updown_tuned;
+            out->tc_stages = r.tc_stages;
         }
     });
 }

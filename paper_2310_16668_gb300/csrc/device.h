@@ -62,6 +62,7 @@ struct DevicePlan {
     // FP32 up/down launch shape per level: warps per CTA (0: the default
     // rule), set by the autotuner
     std::vector<int8_t> ud_warps_up, ud_warps_down;
+    int tc_stages = 6;                     // bulk-copy stages of the on-the-fly tensor-core kernel (4, 6, 8)
     int* status = nullptr;                 // device word raised by a bounded wait that gave up
     // test hook: the next tensor-core pass withholds its first item's first
     // tile until the compute warps gave up, with every wait limited to
@@ -106,6 +107,7 @@ struct TuneReport {
     int stored = 0;                         // the plan keeps stored tiles after tuning
     int n_levels = 0, n_changed = 0;        // up/down launches timed, choices unlike the default rule
     double ms_updown_default = 0, ms_updown_tuned = 0;  // summed over the levels, one launch each
+    int tc_stages = 0;                      // chosen pipeline depth of the on-the-fly kernel (0: not tuned)
 };
 TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* stream);
 

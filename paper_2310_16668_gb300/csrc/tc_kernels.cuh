@@ -61,7 +61,8 @@ constexpr int kSrcPerThread = 32 / kTpr;       // sources of a tile each compute
 constexpr int kTcThreads = kTcCompute + 64;    // + the producer warp and the MMA warp
 constexpr int kTcN = 32;                       // right-hand sides per pass (MMA N)
 constexpr int kTcGroup = 128;                  // tiles summed in registers before the outer sum
-constexpr int kNS = 6;                         // data stages (bulk-copy destinations)
+constexpr int kNS = 6;                         // data stages (bulk-copy destinations) by default;
+                                               // the autotuner may pick 4 or 8 (same arithmetic)
 constexpr int kNA = 3;                         // A-operand buffers in tensor memory
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kColD = 0;                  // accumulators D0 [0,32), D1 [32,64)
@@ -85,16 +86,17 @@ static_assert(offsetof(TcStage, tile) == kChunkFloats * 4, "chunk blob is contig
 // slot skips sits at kFar
 constexpr int kWarpSlotFloats = 3 * kSrcPerThread;
 constexpr float kFar = 1e30f;                  // r^2 from here overflows to +inf: 1/r = 0
+template <int NS>
 struct TcShared {
-    TcStage st[kNS];
+    TcStage st[NS];
     float wc[kTcCompute / 32][kMaxSlots * kWarpSlotFloats];
     float outer[kTcN / kTpr][kTcCompute];      // per compute thread: the sum of its flushed tile groups
-    uint64_t full[kNS], afull[kNS], empty[kNS];  // per data stage
+    uint64_t full[NS], afull[NS], empty[NS];   // per data stage
     uint32_t tmem;
     uint32_t slots;
 };
 constexpr int kTcSmemRequest = 112 * 1024;    // at most two CTAs (2 x 256 TMEM columns) per SM
-static_assert(sizeof(TcShared) <= kTcSmemRequest, "shared memory plan");
+static_assert(sizeof(TcShared<8>) <= kTcSmemRequest, "shared memory plan");
 
 // Stored-operator mode (symmetric store). The rows of every tensor-core item
 // are whole source chunks ("row chunks", at most kMaxRc of them); the values
@@ -379,10 +381,10 @@ constexpr int kTileFloats = 128 * 32;          // the largest tile
 
 // RECORD: also write every tile's kernel values to a.A (the fill pass of the
 // stored-operator mode; the values are the ones the MMA consumes, hi + lo).
-template <int KIND, bool RECORD = false>
+template <int KIND, bool RECORD = false, int NS = kNS>
 __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcShared& S = *reinterpret_cast<TcShared*>(smem_raw);
+    TcShared<NS>& S = *reinterpret_cast<TcShared<NS>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const TcItem* itp = a.items + blockIdx.x;
     const int64_t row_off = itp->row_off;
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
 
     if (tid == 0) {
         S.slots = 0;
-        for (int s = 0; s < kNS; ++s) {
+        for (int s = 0; s < NS; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.full[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sm_addr(&S.afull[s])), "r"(kTcCompute));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.empty[s])));
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
     bool err = false;
 
     if (warp == kTcCompute / 32) {
-        // ---------------- producer warp: bulk copies up to kNS tiles ahead ----------------
+        // ---------------- producer warp: bulk copies up to NS tiles ahead ----------------
         // the lanes fetch the descriptors of 32 tiles at a time; lane 0
         // issues each tile's copies
         for (int t0 = 0; t0 < ntile; t0 += 32) {
@@ -418,9 +420,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             const int nb = min(32, ntile - t0);
             for (int i = 0; i < nb; ++i) {
                 const int t = t0 + i;
-                const int s = t % kNS;
+                const int s = t % NS;
                 const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
-                if (t >= kNS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNS) / kNS) & 1), a.wait_ns)) err = true;
+                if (t >= NS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - NS) / NS) & 1), a.wait_ns)) err = true;
                 const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
                 if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
                 if (lane == 0) {
@@ -437,8 +439,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         }
         if (lane == 0) {
             // all bulk copies have landed before the CTA may exit
-            for (int t = (ntile > kNS ? ntile - kNS : 0); t < ntile; ++t)
-                if (!mbar_wait(sm_addr(&S.full[t % kNS]), (uint32_t)((t / kNS) & 1), a.wait_ns)) err = true;
+            for (int t = (ntile > NS ? ntile - NS : 0); t < ntile; ++t)
+                if (!mbar_wait(sm_addr(&S.full[t % NS]), (uint32_t)((t / NS) & 1), a.wait_ns)) err = true;
         }
     } else if (warp == kTcCompute / 32 + 1) {
         // ---------------- MMA issuer (one thread) ----------------
@@ -446,8 +448,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                                    ((128u >> 4) << 24);
             for (int m = 0; m < ntile; ++m) {
-                const int s = m % kNS, ab = m % kNA;
-                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kNS) & 1), a.wait_ns)) err = true;
+                const int s = m % NS, ab = m % kNA;
+                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / NS) & 1), a.wait_ns)) err = true;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t bh = sm_addr(S.st[s].bhi), bl = sm_addr(S.st[s].blo);
                 const uint32_t d = tbase + kColD + 32u * (m & 1);
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             S.outer[c][tid] = 0.f;
         }
         auto drain = [&](int m) {                              // add tile m's accumulator
-            if (!mbar_wait(sm_addr(&S.empty[m % kNS]), (uint32_t)((m / kNS) & 1), a.wait_ns)) err = true;
+            if (!mbar_wait(sm_addr(&S.empty[m % NS]), (uint32_t)((m / NS) & 1), a.wait_ns)) err = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t v[kCols];
             const uint32_t col = tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kCols * half);
@@ -526,8 +528,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             }
         };
         for (int u = 0; u < ntile; ++u) {
-            const int s = u % kNS;
-            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNS) & 1), a.wait_ns)) err = true;
+            const int s = u % NS;
+            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / NS) & 1), a.wait_ns)) err = true;
             TcStage& st = S.st[s];
             const bool adj = (st.tile.flags & TASK_ADJ) != 0;
             // the target measured from the source box's centre (the frame of
