@@ -61,7 +61,7 @@ class SkelFMM:
     # ---- construction from an external plan --------------------------------------
     @classmethod
     def from_plan(cls, points, kernel: str, plan: dict, kappa: float = 0.0, nrhs_max: int = 32,
-                  host_only: bool = False):
+                  host_only: bool = False, store_tiles: bool = False):
         """Handle from a plan in the skel.h exchange format (dict of arrays)."""
         lib = _lib.load()
         pts = np.ascontiguousarray(points, dtype=np.float64)
@@ -82,7 +82,7 @@ class SkelFMM:
         center = np.ascontiguousarray(plan["center"], dtype=np.float64)
         nb = arr["level"].shape[0]
         h = ctypes.c_void_p()
-        opts = _options(0, nrhs_max, host_only, 0)
+        opts = _options(0, nrhs_max, host_only, 0, False, store_tiles)
         check(lib.skel_plan_import(pts.ctypes.data, n, dim, SkelKernel(_lib.KERNELS[kernel], float(kappa)),
                                    center.ctypes.data, float(plan["side"]), nb,
                                    *[arr[k].ctypes.data for k in ("level", "coord", "parent", "is_leaf",

@@ -770,14 +770,19 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             const uint32_t keep = valid ? (st.tile.keep[myslot] >> j0) & 0xFFFFu : 0u;
             const BlockRef rf = st.refs[rk];
             const bool tr = (rf.flags & kRefTransposed) != 0;
-            const int P = rf.pitch;
+            // a stored pitch is at most 33; the clamps keep every address in
+            // this stage's block area even when a bounded wait gave up and the
+            // descriptor is stale (the values are then invalid, never the addresses)
+            const int P = min((int)rf.pitch, 33);
             const float* blk = st.ga + slot_off;
+            const int lim = kSymFloats - 1 - slot_off;
             // direct: (rl, j) at j P + rl; transposed: at rl P + j
             const int base = tr ? rl * P : rl;
             const int step = tr ? 1 : P;
             float gv[16];
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) gv[jj] = ((keep >> jj) & 1u) ? blk[base + (j0 + jj) * step] : 0.f;
+            for (int jj = 0; jj < 16; ++jj)
+                gv[jj] = ((keep >> jj) & 1u) ? blk[min(base + (j0 + jj) * step, lim)] : 0.f;
             uint32_t ghi[16], glo[16];
 #pragma unroll
             for (int jj = 0; jj < 16; jj += 2) {
