@@ -412,7 +412,10 @@ def run_curves(args):
     g_sets = batch.capture(qs, us, nrhs, prec)
     ms_sets = timed(g_sets, args.steps)
     torch.cuda.synchronize()
-    same = all(torch.equal(us[i], U[:, off[i]:off[i + 1]]) for i in range(len(sets)))
+    # the merged plan against the per-set plans: bit for bit unless the
+    # merged plan keeps stored blocks (symmetric store: FP32 rounding)
+    diff = max(float((us[i] - U[:, off[i]:off[i + 1]]).abs().max() / us[i].abs().max())
+               for i in range(len(sets)))
     # end to end through the C-ABI: pinned host buffers, staged by the library
     qh = Q.cpu().pin_memory()
     uh = torch.empty_like(qh).pin_memory()
@@ -454,7 +457,7 @@ def run_curves(args):
                    "translations": ("stored kernel tiles" if info["stored_tile_bytes"] > 0 else "kernel on the fly")},
         "forward_and_adjoint_ms": ms_both,
         "per_set_graph_ms": ms_sets,
-        "merged_equals_per_set": same,
+        "merged_vs_per_set_maxrel": diff,
         "kernel_launches_per_apply": launches_per_apply,
         "relerr": max(errs.values()),
         "relerr_sets": errs,

@@ -165,7 +165,26 @@ __global__ void __launch_bounds__(32 * W) updown_kernel(const UpBox* __restrict_
     const int col = c0 + lane;
     const bool colok = col < nrhs;
     if (DOWN && blockIdx.y == 0 && colok) {              // u_S += uhat, this CTA's columns
-        for (int i = warp; i < k; i += W) X[(u.off + pos[u.off + i]) * nrhs + col] += X[(u.dst + i) * nrhs + col];
+        // batches of 8 rows: every load of a batch is issued before its stores
+        // (X is read and written through the same pointer, so the compiler
+        // would otherwise keep each load behind the previous row's store)
+        for (int i0 = warp; i0 < k; i0 += 8 * W) {
+            S uh[8], us[8];
+            int64_t at[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q * W;
+                at[q] = -1;
+                if (i < k) {
+                    at[q] = (u.off + pos[u.off + i]) * nrhs + col;
+                    uh[q] = X[(u.dst + i) * nrhs + col];
+                    us[q] = X[at[q]];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (at[q] >= 0) X[at[q]] = us[q] + uh[q];
+        }
     }
     if (row0 >= nout) return;
     S* As = sm + warp * 2 * kGT * kGT;                     // this warp's A block [inner][row]
@@ -184,19 +203,28 @@ __global__ void __launch_bounds__(32 * W) updown_kernel(const UpBox* __restrict_
             // the B rows of this chunk: their entry indices, one per lane
             int64_t ri = 0;
             if (lane < jn) ri = DOWN ? (u.dst + j0 + lane) : (u.off + pos[u.off + k + j0 + lane]);
-#pragma unroll 8
-            for (int jj = 0; jj < kGT; ++jj) {
-                S a = zero<S>(), b = zero<S>();
-                const int64_t rj = __shfl_sync(0xffffffffu, ri, jj);
-                if (jj < jn) {
-                    if (rowok) {
-                        a = T[u.T_off + row0 + lane + (int64_t)(j0 + jj) * nout];
-                        if (conj_op) a = conj(a);
+            // stage the A and B blocks: a group's loads all go out before its
+            // stores to shared memory (one memory latency per group)
+            constexpr int G = sizeof(S) <= 4 ? 32 : sizeof(S) <= 8 ? 16 : 8;
+#pragma unroll
+            for (int g0 = 0; g0 < kGT; g0 += G) {
+                S ra[G], rb[G];
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    const int jj = g0 + q;
+                    const int64_t rj = __shfl_sync(0xffffffffu, ri, jj);
+                    ra[q] = zero<S>();
+                    rb[q] = zero<S>();
+                    if (jj < jn) {
+                        if (rowok) ra[q] = T[u.T_off + row0 + lane + (int64_t)(j0 + jj) * nout];
+                        if (colok) rb[q] = X[rj * nrhs + col];
                     }
-                    if (colok) b = X[rj * nrhs + col];
                 }
-                As[jj * kGT + lane] = a;
-                Bs[jj * kGT + lane] = b;
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    As[(g0 + q) * kGT + lane] = conj_op ? conj(ra[q]) : ra[q];
+                    Bs[(g0 + q) * kGT + lane] = rb[q];
+                }
             }
             __syncwarp();
 #pragma unroll 4
@@ -220,10 +248,25 @@ __global__ void __launch_bounds__(32 * W) updown_kernel(const UpBox* __restrict_
             for (int i = 0; i < kGT; ++i) tot[i] = zero<S>();
         }
     }
+    // the rows this warp writes (w, w + W, ...): all their old values are
+    // loaded before any store
+    constexpr int R = kGT / W;
+    S old[R];
+    int64_t src[R], dst[R];
 #pragma unroll
-    for (int i0 = 0; i0 < kGT; i0 += W) {
-        const int i = i0 + warp;
-        if (row0 + i >= nout) break;
+    for (int q = 0; q < R; ++q) {
+        const int orow = row0 + q * W + warp;
+        dst[q] = -1;
+        if (orow < nout) {
+            src[q] = DOWN ? (u.off + pos[u.off + k + orow]) * nrhs + col : (u.off + pos[u.off + orow]) * nrhs + col;
+            dst[q] = DOWN ? src[q] : (u.dst + orow) * nrhs + col;
+            old[q] = X[src[q]];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        if (dst[q] < 0) continue;
+        const int i = q * W + warp;
         S v;
         if constexpr (W == 1) {
             v = tot[i];
@@ -231,9 +274,7 @@ __global__ void __launch_bounds__(32 * W) updown_kernel(const UpBox* __restrict_
             v = zero<S>();
             for (int s2 = 0; s2 < nsum; ++s2) v = s2 == 0 ? Ps[i * kGT + lane] : v + Ps[(s2 * kGT + i) * kGT + lane];
         }
-        const int orow = row0 + i;
-        if (DOWN) X[(u.off + pos[u.off + k + orow]) * nrhs + col] += v;
-        else X[(u.dst + orow) * nrhs + col] = X[(u.off + pos[u.off + orow]) * nrhs + col] + v;
+        X[dst[q]] = old[q] + v;
     }
 }
 

@@ -673,30 +673,58 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
 
     if (warp == kTcCompute / 32) {
         // ---------------- producer warp ----------------
-        // lane k < m owns row chunk k: its place in the stage is fixed
+        // lane k < m owns row chunk k: its place in the stage is fixed. The
+        // descriptors come in batches of per = 32 / m tiles (lane l holds
+        // reference l % m of tile t0 + l / m, and the chunk of tile t0 + l),
+        // the next batch loading while this one is issued
         const uint32_t slot_bytes_off = lane < m ? 4u * 32u * (uint32_t)(isp->ro[lane] + lane) : 0u;
-        for (int t = 0; t < ntile; ++t) {
-            const int s = t % kNSS;
-            BlockRef rf{0, 0u, 0, 0, 0};
-            if (lane < m) rf = a.refs[ref0 + (int64_t)t * m + lane];
-            uint32_t tot = rf.bytes;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-            const int chunk = a.tiles[list_lo + t].chunk;
-            if (t >= kNSS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1), a.wait_ns)) err = true;
-            const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
-            if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
-            const uint32_t bar = sm_addr(&S.full[s]);
-            if (lane == 0) {
-                mbar_arrive_tx(bar, 4u * 2048u + 64u + 16u * (uint32_t)m + tot);
-                bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
-                bulk_g2s(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar);
-                bulk_g2s(sm_addr(S.st[s].refs), a.refs + ref0 + (int64_t)t * m, 16u * (uint32_t)m, bar);
+        const int per = 32 / m;
+        auto fetch = [&](int t0, int64_t& roff, uint32_t& rbytes, int& ch) {
+            roff = 0;
+            rbytes = 0u;
+            if (lane < per * m && t0 + lane / m < ntile) {
+                const BlockRef r = a.refs[ref0 + (int64_t)t0 * m + lane];
+                roff = r.off;
+                rbytes = r.bytes;
             }
-            __syncwarp();                              // the byte count is armed before any block lands
-            if (rf.bytes > 0) bulk_g2s(sm_addr(S.st[s].ga) + slot_bytes_off, a.A + rf.off, rf.bytes, bar);
-            if (hold && lane == 0 && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
-            __syncwarp();
+            ch = (lane < per && t0 + lane < ntile) ? a.tiles[list_lo + t0 + lane].chunk : 0;
+        };
+        int64_t c_off, n_off = 0;
+        uint32_t c_bytes, n_bytes = 0u;
+        int c_ch, n_ch = 0;
+        fetch(0, c_off, c_bytes, c_ch);
+        for (int t0 = 0; t0 < ntile; t0 += per) {
+            if (t0 + per < ntile) fetch(t0 + per, n_off, n_bytes, n_ch);
+            const int nb = min(per, ntile - t0);
+            for (int i = 0; i < nb; ++i) {
+                const int t = t0 + i;
+                const int s = t % kNSS;
+                const int src = i * m + (lane < m ? lane : 0);
+                const int64_t roff = __shfl_sync(0xffffffffu, c_off, src);
+                uint32_t rbytes = __shfl_sync(0xffffffffu, c_bytes, src);
+                if (lane >= m) rbytes = 0u;
+                const int chunk = __shfl_sync(0xffffffffu, c_ch, i);
+                uint32_t tot = rbytes;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                if (t >= kNSS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1), a.wait_ns)) err = true;
+                const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
+                if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
+                const uint32_t bar = sm_addr(&S.full[s]);
+                if (lane == 0) {
+                    mbar_arrive_tx(bar, 4u * 2048u + 64u + 16u * (uint32_t)m + tot);
+                    bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
+                    bulk_g2s(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar);
+                    bulk_g2s(sm_addr(S.st[s].refs), a.refs + ref0 + (int64_t)t * m, 16u * (uint32_t)m, bar);
+                }
+                __syncwarp();                          // the byte count is armed before any block lands
+                if (rbytes > 0) bulk_g2s(sm_addr(S.st[s].ga) + slot_bytes_off, a.A + roff, rbytes, bar);
+                if (hold && lane == 0 && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
+                __syncwarp();
+            }
+            c_off = n_off;
+            c_bytes = n_bytes;
+            c_ch = n_ch;
         }
         if (lane == 0) {
             for (int t = (ntile > kNSS ? ntile - kNSS : 0); t < ntile; ++t)
