@@ -614,29 +614,34 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
 // ---------------------------------------------------------------------------
 // Stored-operator mode: the same translations with the kernel values read
 // from the symmetric store instead of evaluated. Per tile the producer copies
-// the chunk's B hi + lo (8 KB), the tile's SrcTile (its keep masks) and
-// BlockRefs, and each row chunk's stored block into that row chunk's fixed
-// place in the stage (rows ro_k .. ro_k + cnt_k at float (ro_k + k) * 32;
-// a block of R rows and C columns with pitch P <= R + 1 fits there in either
-// orientation). The compute warps read their row's 16 values directly or
-// transposed, apply the row's keep mask, split into TF32 hi + lo and write A
-// to tensor memory. The MMA issue, the accumulator drain and the two-level
-// sum are those of tc_near_kernel. Bound: HBM, 4 bytes per stored value.
+// into a stage the chunk's B hi + lo (8 KB), the tile's SrcTile (its keep
+// masks) and BlockRefs, and the row chunks' stored blocks, one after the
+// other, into a ring of shared memory (a tile's blocks take 6 KB on average
+// and at most 18 KB, so a ring holds several times more tiles in flight than
+// fixed per-stage areas would). The compute warps find their row chunk's
+// block from the ring base the producer recorded and the sizes of the blocks
+// before it, read their row's 16 values directly or transposed, apply the
+// row's keep mask, split into TF32 hi + lo and write A to tensor memory. The
+// MMA issue, the accumulator drain and the two-level sum are those of
+// tc_near_kernel. Bound: HBM, 4 bytes per stored value.
 static_assert(kSrcPerThread == 16, "stored tiles assume two compute threads per row");
-constexpr int kNSS = 3;                        // data stages (~26 KB each)
+constexpr int kNSS = 6;                        // stages (B operand, descriptors)
+constexpr int kRing = 10240;                   // floats of the block ring (40 KB)
+static_assert(kSymFloats <= kRing, "a tile's blocks fit the ring");
 struct alignas(128) TcSStage {
     float b[2 * 1024];                         // B hi, B lo (the first 8 KB of the chunk block)
-    float ga[kSymFloats];                      // the row chunks' stored blocks
     SrcTile tile;                              // the tile's descriptor (keep masks, source count)
     BlockRef refs[kMaxRc];                     // its row chunks' blocks
+    int32_t rbase;                             // ring float of its first block
 };
 struct TcSShared {
     TcSStage st[kNSS];
+    float ring[kRing];
     float outer[kTcN / kTpr][kTcCompute];
     uint64_t full[kNSS], afull[kNSS], empty[kNSS];
     uint32_t tmem;
 };
-constexpr int kTcsSmemRequest = 100 * 1024;   // two CTAs per SM
+constexpr int kTcsSmemRequest = 112 * 1024;   // two CTAs per SM
 static_assert(sizeof(TcSShared) <= kTcsSmemRequest, "shared memory plan (stored mode)");
 
 template <int KIND>
@@ -673,11 +678,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
 
     if (warp == kTcCompute / 32) {
         // ---------------- producer warp ----------------
-        // lane k < m owns row chunk k: its place in the stage is fixed. The
-        // descriptors come in batches of per = 32 / m tiles (lane l holds
-        // reference l % m of tile t0 + l / m, and the chunk of tile t0 + l),
-        // the next batch loading while this one is issued
-        const uint32_t slot_bytes_off = lane < m ? 4u * 32u * (uint32_t)(isp->ro[lane] + lane) : 0u;
+        // lane k < m copies row chunk k's block. The descriptors come in
+        // batches of per = 32 / m tiles (lane l holds reference l % m of tile
+        // t0 + l / m, and the chunk of tile t0 + l), the next batch loading
+        // while this one is issued. Ring space is handed out in tile order:
+        // a tile's blocks go contiguously at the head (to the start of the
+        // ring if they would wrap), after the oldest tiles whose space that
+        // needs have been consumed (their "empty" barrier); lane s % kNSS
+        // remembers where tile s's blocks start.
         const int per = 32 / m;
         auto fetch = [&](int t0, int64_t& roff, uint32_t& rbytes, int& ch) {
             roff = 0;
@@ -692,6 +700,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         int64_t c_off, n_off = 0;
         uint32_t c_bytes, n_bytes = 0u;
         int c_ch, n_ch = 0;
+        int64_t head = 0, my_start = 0;
+        int tail = 0;
         fetch(0, c_off, c_bytes, c_ch);
         for (int t0 = 0; t0 < ntile; t0 += per) {
             if (t0 + per < ntile) fetch(t0 + per, n_off, n_bytes, n_ch);
@@ -701,24 +711,44 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
                 const int s = t % kNSS;
                 const int src = i * m + (lane < m ? lane : 0);
                 const int64_t roff = __shfl_sync(0xffffffffu, c_off, src);
-                uint32_t rbytes = __shfl_sync(0xffffffffu, c_bytes, src);
-                if (lane >= m) rbytes = 0u;
+                uint32_t rfl = __shfl_sync(0xffffffffu, c_bytes, src) >> 2;     // floats
+                if (lane >= m) rfl = 0u;
                 const int chunk = __shfl_sync(0xffffffffu, c_ch, i);
-                uint32_t tot = rbytes;
+                // this lane's block goes pre floats after the tile's first one
+                uint32_t incl = rfl;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                if (t >= kNSS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1), a.wait_ns)) err = true;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const uint32_t pre = incl - rfl;
+                const uint32_t totf = __shfl_sync(0xffffffffu, incl, 31);
+                if (t >= kNSS) {
+                    if (!mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1), a.wait_ns)) err = true;
+                    tail = max(tail, t - kNSS + 1);        // every tile up to t - kNSS is consumed
+                }
+                int64_t start = head;
+                if (start % kRing + totf > (uint32_t)kRing) start += kRing - start % kRing;
+                const int64_t end = start + totf;
+                while (tail < t && end - __shfl_sync(0xffffffffu, my_start, tail % kNSS) > kRing) {
+                    if (!mbar_wait(sm_addr(&S.empty[tail % kNSS]), (uint32_t)((tail / kNSS) & 1), a.wait_ns)) err = true;
+                    ++tail;
+                }
+                head = end;
+                if (lane == s) my_start = start;
                 const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
                 if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
                 const uint32_t bar = sm_addr(&S.full[s]);
+                const int rb = (int)(start % kRing);
                 if (lane == 0) {
-                    mbar_arrive_tx(bar, 4u * 2048u + 64u + 16u * (uint32_t)m + tot);
+                    S.st[s].rbase = rb;
+                    mbar_arrive_tx(bar, 4u * 2048u + 64u + 16u * (uint32_t)m + 4u * totf);
                     bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
                     bulk_g2s(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar);
                     bulk_g2s(sm_addr(S.st[s].refs), a.refs + ref0 + (int64_t)t * m, 16u * (uint32_t)m, bar);
                 }
                 __syncwarp();                          // the byte count is armed before any block lands
-                if (rbytes > 0) bulk_g2s(sm_addr(S.st[s].ga) + slot_bytes_off, a.A + roff, rbytes, bar);
+                if (rfl > 0) bulk_g2s(sm_addr(S.ring) + 4u * (uint32_t)(rb + pre), a.A + roff, 4u * rfl, bar);
                 if (hold && lane == 0 && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
                 __syncwarp();
             }
@@ -759,12 +789,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         int myslot = 0;
         for (int c = 1; c < nslot; ++c)
             if (row >= itp->slot_start[c]) myslot = c;
-        // this row's row chunk k, its row rl in it, and the chunk's place in a stage
+        // this row's row chunk k and its row rl in it
         int rk = 0;
         for (int k = 1; k < m; ++k)
             if (row >= isp->ro[k]) rk = k;
         const int rl = row - isp->ro[rk];
-        const int slot_off = 32 * (isp->ro[rk] + rk);
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         constexpr int kCols = kTcN / kTpr;
         const int j0 = kSrcPerThread * half;
@@ -796,21 +825,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             const TcSStage& st = S.st[s];
             // the row's kept sources of this tile, and where its block sits
             const uint32_t keep = valid ? (st.tile.keep[myslot] >> j0) & 0xFFFFu : 0u;
+            // this row chunk's block: after the tile's earlier blocks in the ring
+            int boff = st.rbase;
+            for (int k = 0; k < rk; ++k) boff += (int)(st.refs[k].bytes >> 2);
             const BlockRef rf = st.refs[rk];
             const bool tr = (rf.flags & kRefTransposed) != 0;
             // a stored pitch is at most 33; the clamps keep every address in
-            // this stage's block area even when a bounded wait gave up and the
-            // descriptor is stale (the values are then invalid, never the addresses)
+            // the ring even when a bounded wait gave up and the descriptors are
+            // stale (the values are then invalid, never the addresses)
             const int P = min((int)rf.pitch, 33);
-            const float* blk = st.ga + slot_off;
-            const int lim = kSymFloats - 1 - slot_off;
             // direct: (rl, j) at j P + rl; transposed: at rl P + j
-            const int base = tr ? rl * P : rl;
+            const int base = boff + (tr ? rl * P : rl);
             const int step = tr ? 1 : P;
             float gv[16];
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj)
-                gv[jj] = ((keep >> jj) & 1u) ? blk[min(base + (j0 + jj) * step, lim)] : 0.f;
+                gv[jj] = ((keep >> jj) & 1u) ? S.ring[min(max(base + (j0 + jj) * step, 0), kRing - 1)] : 0.f;
             uint32_t ghi[16], glo[16];
 #pragma unroll
             for (int jj = 0; jj < 16; jj += 2) {
