@@ -212,6 +212,25 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
+// L2 cache policies for the bulk copies: data read once (stored kernel
+// blocks, tile descriptors) is evicted first, so that the source chunks' B
+// blocks, which every neighbouring item reads again, stay in L2
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
+                                              uint64_t policy) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(bar), "l"(policy) : "memory");
+}
+
 // B operand layout (K-major, no swizzle): core matrix = 8 right-hand sides x
 // 4 sources (16 bytes per row); the 4 groups of 8 right-hand sides of one
 // 4-source slab are contiguous (SBO = 128 B) and slabs follow along K
@@ -430,8 +449,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                     // the tile's descriptor
                     const uint32_t bar = sm_addr(&S.full[s]);
                     mbar_arrive_tx(bar, 4u * kChunkFloats + 64u);
-                    bulk_g2s(sm_addr(S.st[s].bhi), a.B + (int64_t)chunk * kChunkFloats, 4u * kChunkFloats, bar);
-                    bulk_g2s(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar);
+                    bulk_g2s_hint(sm_addr(S.st[s].bhi), a.B + (int64_t)chunk * kChunkFloats, 4u * kChunkFloats, bar,
+                                  l2_evict_last());
+                    bulk_g2s_hint(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar, l2_evict_first());
                     if (hold && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
                 }
                 __syncwarp();
@@ -687,6 +707,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         // needs have been consumed (their "empty" barrier); lane s % kNSS
         // remembers where tile s's blocks start.
         const int per = 32 / m;
+        const uint64_t pol_once = l2_evict_first(), pol_keep = l2_evict_last();
         auto fetch = [&](int t0, int64_t& roff, uint32_t& rbytes, int& ch) {
             roff = 0;
             rbytes = 0u;
@@ -743,12 +764,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
                 if (lane == 0) {
                     S.st[s].rbase = rb;
                     mbar_arrive_tx(bar, 4u * 2048u + 64u + 16u * (uint32_t)m + 4u * totf);
-                    bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
-                    bulk_g2s(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar);
-                    bulk_g2s(sm_addr(S.st[s].refs), a.refs + ref0 + (int64_t)t * m, 16u * (uint32_t)m, bar);
+                    bulk_g2s_hint(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar, pol_keep);
+                    bulk_g2s_hint(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar, pol_once);
+                    bulk_g2s_hint(sm_addr(S.st[s].refs), a.refs + ref0 + (int64_t)t * m, 16u * (uint32_t)m, bar,
+                                  pol_once);
                 }
                 __syncwarp();                          // the byte count is armed before any block lands
-                if (rfl > 0) bulk_g2s(sm_addr(S.ring) + 4u * (uint32_t)(rb + pre), a.A + roff, 4u * rfl, bar);
+                if (rfl > 0)
+                    bulk_g2s_hint(sm_addr(S.ring) + 4u * (uint32_t)(rb + pre), a.A + roff, 4u * rfl, bar, pol_once);
                 if (hold && lane == 0 && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
                 __syncwarp();
             }
@@ -821,26 +844,33 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
         for (int u = 0; u < ntile; ++u) {
             const int s = u % kNSS;
-            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNSS) & 1), a.wait_ns)) err = true;
+            const bool landed = mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNSS) & 1), a.wait_ns);
+            if (!landed) err = true;
             const TcSStage& st = S.st[s];
             // the row's kept sources of this tile, and where its block sits
-            const uint32_t keep = valid ? (st.tile.keep[myslot] >> j0) & 0xFFFFu : 0u;
+            uint32_t keep = valid ? (st.tile.keep[myslot] >> j0) & 0xFFFFu : 0u;
             // this row chunk's block: after the tile's earlier blocks in the ring
             int boff = st.rbase;
             for (int k = 0; k < rk; ++k) boff += (int)(st.refs[k].bytes >> 2);
             const BlockRef rf = st.refs[rk];
             const bool tr = (rf.flags & kRefTransposed) != 0;
-            // a stored pitch is at most 33; the clamps keep every address in
-            // the ring even when a bounded wait gave up and the descriptors are
-            // stale (the values are then invalid, never the addresses)
-            const int P = min((int)rf.pitch, 33);
+            const int P = rf.pitch;
+            // only a stage whose copies landed is read, and only inside its
+            // block (a stored pitch is at most 33, a block lies in the ring):
+            // after a bounded wait gave up the descriptors may be stale, and
+            // the row then contributes zeros
+            if (!landed || P > 33 || boff < 0 || boff + (int)(rf.bytes >> 2) > kRing) keep = 0u;
             // direct: (rl, j) at j P + rl; transposed: at rl P + j
-            const int base = boff + (tr ? rl * P : rl);
+            const float* blk = S.ring + boff + (tr ? rl * P : rl);
             const int step = tr ? 1 : P;
             float gv[16];
+            if (__all_sync(0xffffffffu, keep == 0u)) {
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj)
-                gv[jj] = ((keep >> jj) & 1u) ? S.ring[min(max(base + (j0 + jj) * step, 0), kRing - 1)] : 0.f;
+                for (int jj = 0; jj < 16; ++jj) gv[jj] = 0.f;
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) gv[jj] = ((keep >> jj) & 1u) ? blk[(j0 + jj) * step] : 0.f;
+            }
             uint32_t ghi[16], glo[16];
 #pragma unroll
             for (int jj = 0; jj < 16; jj += 2) {
