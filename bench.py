@@ -65,8 +65,9 @@ def parse_args():
     p.add_argument("--n", type=int, default=None, help="override N (testing only)")
     p.add_argument("--build", default="host", choices=["host", "device"],
                    help="where Algorithm 1 runs (outside the timed region either way)")
-    p.add_argument("--store-tiles", action="store_true",
-                   help="stored-operator mode: kernel tiles evaluated once at build, read by every apply")
+    p.add_argument("--store-tiles", type=int, default=0, choices=[0, 1, 2],
+                   help="stored-operator mode at build: 1 every tile's kernel values, 2 the symmetric store "
+                        "(shared blocks once); read by every apply")
     p.add_argument("--tune", default="auto", choices=["auto", "none"],
                    help="auto: skel_autotune after the build (per-level up/down variants; stored or on-the-fly "
                         "kernel tiles, chosen by measurement); none: the default rules, tiles on the fly")
@@ -230,7 +231,28 @@ def roofline(info, phases, clk, prec, pairs):
             "per_launch_ms": near_ms_per_launch, "launches_per_step": n_near,
             "algorithmic_units": f"{units} kernel evaluations per launch ({unit_note})"}
     stored = prec == "fp32_tc" and info["stored_tile_bytes"] > 0
-    if stored:
+    if stored and info["store_mode"] == 1:
+        # per-tile store, HBM-bound: the algorithmic bytes are 4 B per kept
+        # kernel evaluation (pairs_tc, each value read once per 32-column
+        # pass) plus the rows of U the launch writes; the stored bytes beyond
+        # that (zero padding of ragged tiles, masked entries) and the chunks'
+        # B blocks (8 KB per tile, mostly L2 hits) are overhead, reported
+        # beside the figure
+        kname = "tc_stored_kernel"
+        alg_bytes = 4 * info["pairs_tc"] + info["n_index"] * 32 * 4
+        traffic = ncu_traffic(kname, prec)
+        roof.update({"kernel": kname, "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                     "achieved": alg_bytes / (near_ms_per_launch * 1e-3) / 1e9,
+                     "traffic": traffic,
+                     "peak_basis": f"{peaks_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_units": f"{alg_bytes} bytes per launch (4 B x pairs_tc {info['pairs_tc']} "
+                                          f"+ U rows {info['n_index']} x 32 x 4)",
+                     "stored_tile_bytes": info["stored_tile_bytes"],
+                     "stored_over_algorithmic": info["stored_tile_bytes"] / (4 * info["pairs_tc"]),
+                     "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None,
+                     "evaluation_rate_gpair_s": achieved})
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    elif stored:
         # stored-operator mode, HBM-bound: the algorithmic bytes are 4 B per
         # kept kernel evaluation (pairs_tc, each value read once per 32-column
         # pass) plus the rows of U the launch writes; the stored bytes beyond
@@ -240,7 +262,7 @@ def roofline(info, phases, clk, prec, pairs):
         # symmetric store: a kernel value shared by two tiles (G(e, f) =
         # G(f, e)) is held and read once, so the minimum is 4 B per distinct
         # kept value (skel_info pairs_stored), not per evaluation
-        kname = "tc_stored_kernel"
+        kname = "tc_sym_kernel"
         alg_bytes = 4 * info["pairs_stored"] + info["n_index"] * 32 * 4
         traffic = ncu_traffic(kname, prec)
         roof.update({"kernel": kname, "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
@@ -454,7 +476,7 @@ def run_curves(args):
                    "N_max": int(max(batch.sizes)), "nrhs": nrhs, "leaf": cs.leaf, "tol": tol,
                    "precision": prec, "t_build_s": t_build, "t_merge_s": t_merge,
                    "l2": f"inputs larger than L2: merged plan {info['device_bytes'] / 1e9:.2f} GB resident",
-                   "translations": ("stored kernel tiles" if info["stored_tile_bytes"] > 0 else "kernel on the fly")},
+                   "translations": ({1: "per-tile store", 2: "symmetric store"}.get(info["store_mode"], "kernel on the fly"))},
         "forward_and_adjoint_ms": ms_both,
         "per_set_graph_ms": ms_sets,
         "merged_vs_per_set_maxrel": diff,
@@ -654,7 +676,7 @@ def run_ours(args):
                          f"{info['device_bytes'] / 1e9:.2f} GB resident",
                    "k_max": info["k_max"], "levels": info["n_levels"], "t_build_s": t_build,
                    "pairs_per_apply": pairs,
-                   "translations": ("stored kernel tiles" if info["stored_tile_bytes"] > 0 else "kernel on the fly")
+                   "translations": ({1: "per-tile store", 2: "symmetric store"}.get(info["store_mode"], "kernel on the fly"))
                                    + (", chosen by skel_autotune" if tuning and "error" not in tuning else "")},
         "relerr": out.get("relerr"),
         "relerr_l2": out.get("relerr_l2"),

@@ -73,15 +73,18 @@ typedef struct {
                          CUDA device in FP64, one CTA per box; 0 = on the host. Same
                          ranks and operators up to rounding (ties in the pivot order
                          may resolve differently). Needs host_only = 0.               */
-    int store_tiles;  /* 1 = stored-operator mode: evaluate the kernel blocks of the
+    int store_tiles;  /* stored-operator mode: evaluate the kernel values of the
                          tensor-core translations once at build and keep them on the
                          device (skel_stats.stored_tile_bytes); FP32_TC applies then
-                         read them instead of evaluating the kernel. The real kernels
-                         are symmetric, so a block shared by two tiles is stored once
-                         and read transposed by one of them: results equal the
-                         on-the-fly apply's up to FP32 rounding of those values (a few
-                         ulp each). Real kernels only (ignored otherwise).
-                         SKEL_ERR_OOM if the blocks do not fit.                        */
+                         read them instead of evaluating the kernel.
+                         1 = per-tile store: every tile's rows x 32 values; results
+                             equal the on-the-fly apply bit for bit.
+                         2 = symmetric store: the real kernels are symmetric, so a
+                             block two tiles share is stored once (about half the
+                             bytes) and read transposed by one of them; results equal
+                             the on-the-fly apply up to FP32 rounding of those values.
+                         0 = none. Real kernels only (ignored otherwise).
+                         SKEL_ERR_OOM if the values do not fit.                         */
 } skel_options;
 
 typedef struct {
@@ -111,9 +114,11 @@ typedef struct {
     double  id_gflop;        /* device build: GFLOP of the QR reflector updates (FP64)   */
     int64_t stored_tile_bytes; /* store_tiles: device bytes of the stored kernel tiles   */
     int     n_proxy;         /* proxy points per box (2D: 4p, 3D: 6p^2; Section 2.1)     */
-    int64_t pairs_stored;    /* FP32_TC stored-operator mode: kept kernel values the
-                                symmetric store holds once (of pairs_tc; the others are
-                                the same values read transposed)                          */
+    int64_t pairs_stored;    /* FP32_TC: kept kernel values the symmetric store holds
+                                once (of pairs_tc; the others are the same values read
+                                transposed)                                              */
+    int     store_mode;      /* stored-operator mode the plan holds: 0 none, 1 per-tile,
+                                2 symmetric                                              */
 } skel_stats;
 
 /*
@@ -400,11 +405,13 @@ int skel_test_fail_alloc(int countdown);
  * same order), the pipeline depth of the on-the-fly tensor-core kernel (4, 6
  * or 8 bulk-copy stages; same arithmetic), and for the tensor-core
  * translations (real kernels, nrhs >= 4) whether the
- * kernel values are evaluated on the fly or read from stored tiles (the
- * choice between operators stored and evaluated on the fly; stored only if
- * allow_store and the tiles fit the free device memory with 2 GB to spare;
- * tiles that lose are freed). Every variant computes the same result, so
- * tuning changes speed and memory only. Synchronous on `stream`, uses the
+ * kernel values are evaluated on the fly or read from a store (the choice
+ * between operators stored and evaluated on the fly: the per-tile and the
+ * symmetric store are each tried if allow_store and they fit the free device
+ * memory with 2 GB to spare; the fastest of the three is kept, stores that
+ * lose are freed). Every launch shape computes the same result; the
+ * symmetric store differs from the others by FP32 rounding only, so tuning
+ * changes speed and memory, not accuracy. Synchronous on `stream`, uses the
  * plan's own buffers (no concurrent apply on the handle; not capturable).
  *   h            plan with a device part; real kernels only
  *   nrhs         1 .. nrhs_max
@@ -414,14 +421,16 @@ int skel_test_fail_alloc(int countdown);
  */
 typedef struct {
     double ms_onfly;          /* one tensor-core pass, kernel evaluated on the fly (-1: not timed) */
-    double ms_stored;         /* the same reading stored tiles (-1: not timed)                   */
-    int    stored;            /* 1 if the plan keeps stored tiles after tuning                  */
+    double ms_stored;         /* the same reading the per-tile store (-1: not timed)            */
+    int    stored;            /* store mode the plan keeps after tuning: 0 none, 1 per-tile,
+                                 2 symmetric                                                     */
     int    n_updown;          /* up/down level launches tuned (levels x 2 directions)           */
     int    n_changed;         /* of those, choices unlike the default rule                      */
     double ms_updown_default; /* their summed time with the default rule                        */
     double ms_updown_tuned;   /* and with the chosen variants                                   */
     int    tc_stages;         /* pipeline depth (bulk-copy stages) chosen for the on-the-fly
                                  tensor-core kernel: 4, 6 or 8 (0: not tuned)                  */
+    double ms_sym;            /* one tensor-core pass reading the symmetric store (-1: not timed) */
 } skel_tuning;
 int skel_autotune(skel_handle h, int nrhs, int allow_store, void* stream, skel_tuning* out);
 

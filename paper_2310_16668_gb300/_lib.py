@@ -48,7 +48,7 @@ class SkelStats(ctypes.Structure):
                 ("pairs_tc", ctypes.c_int64), ("skel_on_device", ctypes.c_int),
                 ("t_id_kernels", ctypes.c_double), ("id_gflop", ctypes.c_double),
                 ("stored_tile_bytes", ctypes.c_int64), ("n_proxy", ctypes.c_int),
-                ("pairs_stored", ctypes.c_int64)]
+                ("pairs_stored", ctypes.c_int64), ("store_mode", ctypes.c_int)]
 
 
 class SkelPlanDims(ctypes.Structure):
@@ -66,7 +66,7 @@ class SkelTuning(ctypes.Structure):
     _fields_ = [("ms_onfly", ctypes.c_double), ("ms_stored", ctypes.c_double), ("stored", ctypes.c_int),
                 ("n_updown", ctypes.c_int), ("n_changed", ctypes.c_int),
                 ("ms_updown_default", ctypes.c_double), ("ms_updown_tuned", ctypes.c_double),
-                ("tc_stages", ctypes.c_int)]
+                ("tc_stages", ctypes.c_int), ("ms_sym", ctypes.c_double)]
 
 
 class SkelError(RuntimeError):

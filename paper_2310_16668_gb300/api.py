@@ -26,16 +26,18 @@ _DTYPES = {("fp64", False): torch.float64, ("fp64", True): torch.complex128,
 
 def _options(proxy_p, nrhs_max, host_only, num_threads, device_build=False, store_tiles=False):
     return SkelOptions(int(proxy_p), int(nrhs_max), int(bool(host_only)), int(num_threads), int(bool(device_build)),
-                       int(bool(store_tiles)))
+                       int(store_tiles))
 
 
 class SkelFMM:
     """One skeletonized-FMM plan (Algorithm 1 done, ready for Algorithm 2).
 
     ``device_build=True`` runs Algorithm 1 (proxy matrices, pivoted QR, T) on
-    the current CUDA device instead of the host cores. ``store_tiles=True``
-    keeps every tensor-core tile's kernel values on the device (16 KB per
-    tile) so that FP32_TC applies read them instead of evaluating the kernel.
+    the current CUDA device instead of the host cores. ``store_tiles`` keeps
+    the tensor-core translations' kernel values on the device so that FP32_TC
+    applies read them instead of evaluating the kernel: 1 (or True) every
+    tile's values (same result bit for bit), 2 the symmetric store (each
+    block two tiles share held once; same result up to FP32 rounding).
     """
 
     def __init__(self, points, kernel: str = "laplace3d", tol: float = 1e-6, leaf_size: int = 128,

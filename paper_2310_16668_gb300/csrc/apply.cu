@@ -279,16 +279,20 @@ NearArgs<Real, CPLX> near_args(DevicePlan* dp, DeviceBuffers* b, const WorkItem*
 void set_tc_attributes() {
     static bool done = false;
     if (done) return;
-    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, kRecNone, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, kRecNone, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, kRecNone, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, kRecNone, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, kRecNone, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, kRecNone, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, kRecTiles>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, kRecTiles>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, kRecSym>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, kRecSym>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcsSmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcsSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_sym_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTsySmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_sym_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTsySmemRequest));
     done = true;
 }
 
@@ -312,6 +316,7 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     t.B = dp->tc_b;
     t.U = (float*)b->U;
     t.A = dp->tc_a;
+    t.abase = dp->tc_abase;
     t.refs = (const BlockRef*)dp->tc_refs;
     t.isym = (const ItemSym*)dp->tc_isym;
     t.nrhs = nrhs;
@@ -332,19 +337,22 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
         CUDA_CHECK(cudaGetLastError());
         ++launches;
         if (r0 == 0) mark(dp, kMainEvent, st);
-        if (stored) {
+        if (stored && dp->store_mode == 2) {
+            if (kidx == 0) tc_sym_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTsySmemRequest, st>>>(t);
+            else tc_sym_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTsySmemRequest, st>>>(t);
+        } else if (stored) {
             if (kidx == 0) tc_stored_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTcsSmemRequest, st>>>(t);
             else tc_stored_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTcsSmemRequest, st>>>(t);
         } else {
             // pipeline depth: the autotuner's choice (same arithmetic for every depth)
             const unsigned g = (unsigned)dp->n_tc;
             switch (dp->tc_stages) {
-                case 4: kidx == 0 ? tc_near_kernel<0, false, 4><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
-                                  : tc_near_kernel<1, false, 4><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
-                case 8: kidx == 0 ? tc_near_kernel<0, false, 8><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
-                                  : tc_near_kernel<1, false, 8><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
-                default: kidx == 0 ? tc_near_kernel<0, false, 6><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
-                                   : tc_near_kernel<1, false, 6><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
+                case 4: kidx == 0 ? tc_near_kernel<0, kRecNone, 4><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
+                                  : tc_near_kernel<1, kRecNone, 4><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
+                case 8: kidx == 0 ? tc_near_kernel<0, kRecNone, 8><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
+                                  : tc_near_kernel<1, kRecNone, 8><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
+                default: kidx == 0 ? tc_near_kernel<0, kRecNone, 6><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
+                                   : tc_near_kernel<1, kRecNone, 6><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
             }
         }
         CUDA_CHECK(cudaGetLastError());
@@ -436,37 +444,50 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
     }
 }
 
-// Free the stored blocks (the plan falls back to the on-the-fly kernel).
+// Free the stored kernel values (the plan falls back to the on-the-fly kernel).
 void drop_tiles(DevicePlan* dp) {
     if (!dp->tc_a) return;
     cudaFree(dp->tc_a);
+    cudaFree(dp->tc_abase);
     cudaFree(dp->tc_refs);
     cudaFree(dp->tc_isym);
     dp->tc_a = nullptr;
+    dp->tc_abase = nullptr;
     dp->tc_refs = nullptr;
     dp->tc_isym = nullptr;
-    dp->bytes -= dp->stored_bytes + (int64_t)(dp->tc_refs_host.size() + dp->tc_isym_host.size());
+    dp->bytes -= dp->stored_bytes + (dp->store_mode == 2 ? (int64_t)(dp->tc_refs_host.size() + dp->tc_isym_host.size())
+                                                          : (int64_t)(dp->tc_abase_host.size() * sizeof(int64_t)));
     dp->stored_bytes = 0;
+    dp->store_mode = 0;
 }
 
-// Stored-operator mode: evaluate every stored block once (the on-the-fly
-// kernel in its fill mode, which also runs the translations on zero charges)
-// into a new allocation; synchronous. On any failure the store is freed again.
-void fill_tiles(DevicePlan* dp, cudaStream_t st) {
+// Stored-operator mode `mode` (1: per-tile store, 2: symmetric store):
+// evaluate the values once (the on-the-fly kernel in its fill mode, which
+// also runs the translations on zero charges) into a new allocation;
+// synchronous. On any failure the store is freed again.
+void fill_tiles(DevicePlan* dp, cudaStream_t st, int mode) {
     if (dp->tc_a) return;
     int64_t bytes = 0;
+    const int64_t floats = mode == 2 ? dp->sym_floats : dp->tile_floats;
     try {
-        dp->tc_refs = upload(dp->tc_refs_host, bytes);
-        dp->tc_isym = upload(dp->tc_isym_host, bytes);
-        dp->tc_a = dalloc<float>((size_t)dp->store_floats, bytes);
+        if (mode == 2) {
+            dp->tc_refs = upload(dp->tc_refs_host, bytes);
+            dp->tc_isym = upload(dp->tc_isym_host, bytes);
+        } else {
+            dp->tc_abase = upload(dp->tc_abase_host, bytes);
+        }
+        dp->tc_a = dalloc<float>((size_t)floats, bytes);
     } catch (...) {
+        cudaFree(dp->tc_abase);
         cudaFree(dp->tc_refs);
         cudaFree(dp->tc_isym);
+        dp->tc_abase = nullptr;
         dp->tc_refs = dp->tc_isym = nullptr;
         throw;
     }
+    dp->store_mode = mode;
     dp->bytes += bytes;
-    dp->stored_bytes = dp->store_floats * (int64_t)sizeof(float);
+    dp->stored_bytes = floats * (int64_t)sizeof(float);
     try {
         DeviceBuffers* b = dp->p32;
         CUDA_CHECK(cudaMemsetAsync(b->Q, 0, (size_t)dp->n_tot * sizeof(float), st));
@@ -483,6 +504,7 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st) {
         t.B = dp->tc_b;
         t.U = (float*)b->U;
         t.A = dp->tc_a;
+        t.abase = dp->tc_abase;
         t.refs = (const BlockRef*)dp->tc_refs;
         t.isym = (const ItemSym*)dp->tc_isym;
         t.nrhs = 1;
@@ -490,8 +512,14 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st) {
         t.status = dp->status;
         t.wait_ns = kWaitLimitNs;
         t.withhold_item = -1;
-        if (dp->kind == 0) tc_near_kernel<0, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
-        else tc_near_kernel<1, true><<<(unsigned)dp->n_tc, kTcThreads, kTcSmemRequest, st>>>(t);
+        const unsigned g = (unsigned)dp->n_tc;
+        if (mode == 2) {
+            if (dp->kind == 0) tc_near_kernel<0, kRecSym><<<g, kTcThreads, kTcSmemRequest, st>>>(t);
+            else tc_near_kernel<1, kRecSym><<<g, kTcThreads, kTcSmemRequest, st>>>(t);
+        } else {
+            if (dp->kind == 0) tc_near_kernel<0, kRecTiles><<<g, kTcThreads, kTcSmemRequest, st>>>(t);
+            else tc_near_kernel<1, kRecTiles><<<g, kTcThreads, kTcSmemRequest, st>>>(t);
+        }
         CUDA_CHECK(cudaGetLastError());
         CUDA_CHECK(cudaStreamSynchronize(st));
         int stv = 0;
@@ -511,7 +539,7 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st) {
 // is stored once, as (min, max), written by the first of its direct readers
 // in the fill pass and read transposed by the others; every other block is
 // stored for its own reader(s). Fills dp->tc_isym_host, dp->tc_refs_host,
-// dp->store_floats and dp->pairs_stored.
+// dp->sym_floats and dp->pairs_stored.
 void plan_symmetric_store(const Layout& lay, DevicePlan* dp) {
     const int64_t nch = (int64_t)lay.chunk_start.size();
     const int64_t nitems = (int64_t)lay.tc_items.size();
@@ -636,13 +664,13 @@ void plan_symmetric_store(const Layout& lay, DevicePlan* dp) {
     std::memcpy(dp->tc_isym_host.data(), isym.data(), dp->tc_isym_host.size());
     dp->tc_refs_host.resize(refs.size() * sizeof(BlockRef));
     std::memcpy(dp->tc_refs_host.data(), refs.data(), dp->tc_refs_host.size());
-    dp->store_floats = nf;
+    dp->sym_floats = nf;
     dp->pairs_stored = stored_pairs;
 }
 
 }  // namespace
 
-DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, bool store_tiles) {
+DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles) {
     DevicePlan* dp = new DevicePlan();
     try {
         CUDA_CHECK(cudaGetDevice(&dp->device));
@@ -709,8 +737,17 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, b
             dp->n_tc_tiles = (int64_t)lay.tc_tiles.size();
             for (const TcItem& it : lay.tc_items)
                 if (it.nrows < 1 || it.nrows > kTcRows) throw Error(-5, "tensor-core item with no rows");
+            // per-tile store: each item's tiles back to back, nrows x 32 floats each
+            dp->tc_abase_host.resize(lay.tc_items.size());
+            int64_t nf = 0;
+            for (size_t i = 0; i < lay.tc_items.size(); ++i) {
+                const TcItem& it = lay.tc_items[i];
+                dp->tc_abase_host[i] = nf;
+                nf += (int64_t)(it.list_hi - it.list_lo) * it.nrows * 32;
+            }
+            dp->tile_floats = nf;
             plan_symmetric_store(lay, dp);
-            if (store_tiles) fill_tiles(dp, 0);
+            if (store_tiles) fill_tiles(dp, 0, store_tiles == 2 ? 2 : 1);
         }
         CUDA_CHECK(cudaDeviceSynchronize());
     } catch (...) {
@@ -871,17 +908,30 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
             rep.tc_stages = best_ns;
             dp->tc_a = keep_a;
             keep_a = nullptr;
-            if (!dp->tc_a && allow_store) {
-                size_t free_b = 0, total_b = 0;
-                CUDA_CHECK(cudaMemGetInfo(&free_b, &total_b));
-                const size_t need = (size_t)dp->store_floats * sizeof(float) + ((size_t)2 << 30);
-                if (free_b > need) fill_tiles(dp, st);
+            // the stores: the one the plan holds, and (allow_store) each one
+            // that fits the free memory with 2 GB to spare, timed in turn; the
+            // fastest of on the fly, per-tile and symmetric is kept
+            double best = rep.ms_onfly;
+            int best_mode = 0;
+            for (int mode : {1, 2}) {
+                if (!(dp->tc_a && dp->store_mode == mode)) {
+                    if (!allow_store) continue;
+                    drop_tiles(dp);
+                    size_t free_b = 0, total_b = 0;
+                    CUDA_CHECK(cudaMemGetInfo(&free_b, &total_b));
+                    const int64_t floats = mode == 2 ? dp->sym_floats : dp->tile_floats;
+                    if (free_b <= (size_t)floats * sizeof(float) + ((size_t)2 << 30)) continue;
+                    fill_tiles(dp, st, mode);
+                }
+                const double ms = time_ms(tc, 3);
+                (mode == 2 ? rep.ms_sym : rep.ms_stored) = ms;
+                if (ms < best) best = ms, best_mode = mode;
             }
-            if (dp->tc_a) {
-                rep.ms_stored = time_ms(tc, 3);
-                if (rep.ms_stored >= rep.ms_onfly) drop_tiles(dp);
+            if (dp->store_mode != best_mode) {
+                drop_tiles(dp);
+                if (best_mode) fill_tiles(dp, st, best_mode);
             }
-            rep.stored = dp->tc_a != nullptr;
+            rep.stored = dp->store_mode;
         }
     } catch (...) {
         dp->prof_cap = saved_cap;

@@ -91,7 +91,8 @@ void finalize(skel_plan* h, const skel_options* opts) {
     h->n_tc_tiles = (int64_t)lay.tc_tiles.size();
     h->n_mix_items = (int64_t)lay.mix_items.size();
     h->pairs_tc = lay.pairs_tc;
-    if (!h->host_only) h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max, opts && opts->store_tiles);
+    if (opts && (opts->store_tiles < 0 || opts->store_tiles > 2)) throw Error(SKEL_ERR_ARG, "store_tiles must be 0, 1 or 2");
+    if (!h->host_only) h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max, opts ? opts->store_tiles : 0);
     h->t_upload = now() - t0;
 }
 
@@ -427,7 +428,9 @@ int skel_merge(const skel_handle* hs, int nsets, const skel_options* opts, skel_
             h->nrhs_max = (opts && opts->nrhs_max > 0) ? opts->nrhs_max : 32;
             if (h->nrhs_max > 256) throw Error(SKEL_ERR_ARG, "nrhs_max must be <= 256");
             h->host_only = opts && opts->host_only;
-            if (!h->host_only) h->dev = skel::device_plan_create(h->plan, m, h->nrhs_max, opts && opts->store_tiles);
+            if (opts && (opts->store_tiles < 0 || opts->store_tiles > 2))
+                throw Error(SKEL_ERR_ARG, "store_tiles must be 0, 1 or 2");
+            if (!h->host_only) h->dev = skel::device_plan_create(h->plan, m, h->nrhs_max, opts ? opts->store_tiles : 0);
             h->t_upload = st.t_upload = now() - t0;
         } catch (...) {
             destroy(h);
@@ -451,6 +454,7 @@ int skel_info(skel_handle h, skel_stats* s) {
             s->device_bytes = h->dev ? h->dev->bytes : 0;
             s->stored_tile_bytes = h->dev ? h->dev->stored_bytes : 0;
             s->pairs_stored = h->dev ? h->dev->pairs_stored : 0;
+            s->store_mode = h->dev ? h->dev->store_mode : 0;
             return;
         }
         const skel::Plan& P = h->plan;
@@ -486,6 +490,7 @@ int skel_info(skel_handle h, skel_stats* s) {
         s->stored_tile_bytes = h->dev ? h->dev->stored_bytes : 0;
         s->n_proxy = t.dim == 2 ? 4 * P.proxy_p : 6 * P.proxy_p * P.proxy_p;
         s->pairs_stored = h->dev ? h->dev->pairs_stored : 0;
+        s->store_mode = h->dev ? h->dev->store_mode : 0;
     });
 }
 
@@ -760,6 +765,7 @@ int skel_autotune(skel_handle h, int nrhs, int allow_store, void* stream, skel_t
             out->ms_updown_default = r.ms_updown_default;
             out->ms_updown_tuned = r.ms_updown_tuned;
             out->tc_stages = r.tc_stages;
+            out->ms_sym = r.ms_sym;
         }
     });
 }

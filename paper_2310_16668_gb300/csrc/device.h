@@ -50,13 +50,19 @@ struct DevicePlan {
     float* chunk_center = nullptr;         // 4 per chunk: its box's centre
     int64_t n_chunks = 0;
     float* tc_b = nullptr;                 // B operand per chunk for one 32-column pass (hi, lo)
-    float* tc_a = nullptr;                 // stored-operator mode: the symmetric store of kernel blocks
-    void* tc_refs = nullptr;               // per tile and row chunk: BlockRef (device, while stored)
-    void* tc_isym = nullptr;               // per tensor-core item: ItemSym (device, while stored)
+    // stored-operator mode: store_mode 1 = per-tile store (every tile's
+    // nrows x 32 values), 2 = symmetric store (shared blocks once); 0 = none
+    int store_mode = 0;
+    float* tc_a = nullptr;                 // the stored kernel values (either mode)
+    int64_t* tc_abase = nullptr;           // per-tile store: per item, first float of its tiles
+    std::vector<int64_t> tc_abase_host;
+    int64_t tile_floats = 0;               // floats the per-tile store takes
+    void* tc_refs = nullptr;               // symmetric store: per tile and row chunk, BlockRef
+    void* tc_isym = nullptr;               // symmetric store: per tensor-core item, ItemSym
     std::vector<unsigned char> tc_refs_host, tc_isym_host;  // the same on the host (kept to fill later)
-    int64_t store_floats = 0;              // floats the store takes
-    int64_t pairs_stored = 0;              // kept kernel values the store holds once (the rest are
-                                           // read transposed)
+    int64_t sym_floats = 0;                // floats the symmetric store takes
+    int64_t pairs_stored = 0;              // kept kernel values the symmetric store holds once
+                                           // (the rest are read transposed)
     int64_t n_tc_tiles = 0;
     int64_t stored_bytes = 0;              // 0 unless the tiles are stored
     // FP32 up/down launch shape per level: warps per CTA (0: the default
@@ -87,7 +93,7 @@ struct DevicePlan {
 // Upload a layout; throws Error on failure. store_tiles: also evaluate every
 // tensor-core tile's kernel values once and keep them (nrows x 128 B per tile), so
 // that FP32_TC applies read them instead of evaluating (real kernels).
-DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, bool store_tiles = false);
+DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles = 0);
 void device_plan_destroy(DevicePlan* dp);
 // capture the phases of the next max_applies applies (0 = off)
 void device_set_profiling(DevicePlan* dp, int max_applies);
@@ -104,7 +110,8 @@ void device_last_timings(DevicePlan* dp, double* ms6, int* launches, int* n_appl
 // uses the plan's own buffers.
 struct TuneReport {
     double ms_onfly = -1, ms_stored = -1;  // one tensor-core pass (bprep + translations)
-    int stored = 0;                         // the plan keeps stored tiles after tuning
+    double ms_sym = -1;                     // the same reading the symmetric store (-1: not timed)
+    int stored = 0;                         // store mode the plan keeps after tuning (0, 1, 2)
     int n_levels = 0, n_changed = 0;        // up/down launches timed, choices unlike the default rule
     double ms_updown_default = 0, ms_updown_tuned = 0;  // summed over the levels, one launch each
     int tc_stages = 0;                      // chosen pipeline depth of the on-the-fly kernel (0: not tuned)

@@ -198,6 +198,10 @@ struct Layout {
 
 void build_layout(const Plan& p, Layout& lay);
 
+// class of a tensor-core item's tile-list length (lengths within a factor
+// 1.25 share a class); items run longest class first
+int length_class(int n);
+
 // One layout for many independent point sets (set s: n_points[s] points,
 // n_boxes[s] boxes; T_width = 1 for real, 2 for complex operators): each
 // phase of the apply then covers every set in one launch.

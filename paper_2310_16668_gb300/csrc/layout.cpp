@@ -32,6 +32,13 @@ namespace {
 constexpr int64_t kItemCost = 2048;   // source entries per warp work item
 }
 
+// class of a tile-list length: lengths within a factor 1.25 share a class
+int length_class(int n) {
+    int c = 0;
+    for (double v = 1.0; v * 1.25 <= (double)n; v *= 1.25) ++c;
+    return c;
+}
+
 void build_layout(const Plan& p, Layout& lay) {
     const Tree& t = p.tree;
     const Skel& sk = p.sk;
@@ -356,9 +363,12 @@ void build_layout(const Plan& p, Layout& lay) {
         sst[tg.size()] = rows;
         emit(row_off, rows, (int)tg.size(), sst, tg);
     }
-    // longest lists first, so that the long items start early
+    // longest lists first, so that the long items start early, by classes of
+    // lengths within 25% of each other; within a class the items keep their
+    // order (boxes in level and Morton order), so that items running at the
+    // same time read the same neighbouring source chunks (L2 reuse)
     std::stable_sort(lay.tc_items.begin(), lay.tc_items.end(), [](const TcItem& a, const TcItem& c) {
-        return a.list_hi - a.list_lo > c.list_hi - c.list_lo;
+        return length_class(a.list_hi - a.list_lo) > length_class(c.list_hi - c.list_lo);
     });
     // the partial sums of the CUDA-core items (small non-leaf boxes) only;
     // tensor-core items write their rows of U directly
@@ -475,10 +485,11 @@ void merge_layouts(const std::vector<const Layout*>& ls, const std::vector<int64
         }
     }
     m.up_level_ptr[Lmax + 1] = (int64_t)m.up.size();
-    // the longest tile lists first over all sets (each item writes its own
-    // rows, so the order changes no result)
+    // the longest tile lists first over all sets, by length classes as in
+    // build_layout (each item writes its own rows, so the order changes no
+    // result)
     std::stable_sort(m.tc_items.begin(), m.tc_items.end(), [](const TcItem& a, const TcItem& c) {
-        return a.list_hi - a.list_lo > c.list_hi - c.list_lo;
+        return length_class(a.list_hi - a.list_lo) > length_class(c.list_hi - c.list_lo);
     });
 }
 

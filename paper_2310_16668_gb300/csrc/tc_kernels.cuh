@@ -138,8 +138,9 @@ struct TcArgs {
     const float4* Xlo;
     const float* B;                            // per source chunk (kChunkFloats): B hi, B lo, coordinates
     float* U;                                  // entry rows of nrhs (this item's rows are written here)
-    float* A;                                  // stored kernel blocks, or null
-    const BlockRef* refs;                      // stored-operator mode: per tile and row chunk
+    float* A;                                  // stored kernel values, or null
+    const int64_t* abase;                      // per-tile store: per item, first float of its tiles
+    const BlockRef* refs;                      // symmetric store: per tile and row chunk
     const ItemSym* isym;                       // stored-operator mode: per item
     int nrhs;                                  // right-hand sides (row length of U)
     int r0;                                    // first right-hand side of this pass
@@ -390,17 +391,20 @@ __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict
     }
 }
 
-// Stored kernel tiles (the stored-operator mode): tile t of an item with
-// nrows rows keeps the kernel values of its stored columns (StoredTile
-// colmask, in column order) as unscaled FP32, zero where a row's slot skips
-// the source; column p of the packed tile holds its nrows values at
-// A + off + p * nrows + row, so that a warp's 32 consecutive rows read 32
-// consecutive floats.
+// Stored-operator mode, per-tile store: tile u of an item with nrows rows
+// keeps its nrows x 32 kernel values (unscaled FP32, zero where a row's slot
+// skips the source) at A + abase[item] + u * nrows * 32.
 constexpr int kTileFloats = 128 * 32;          // the largest tile
+// per-tile store: value (row, j = 16 half + 4 q + e) of a tile at float4
+// (half * 4 + q) * nrows + row
+__device__ __forceinline__ int tile_word(int half, int q, int row, int nrows) { return (half * 4 + q) * nrows + row; }
 
-// RECORD: also write every tile's kernel values to a.A (the fill pass of the
-// stored-operator mode; the values are the ones the MMA consumes, hi + lo).
-template <int KIND, bool RECORD = false, int NS = kNS>
+// REC: the fill pass of a stored-operator mode also writes the kernel values
+// it evaluates to a.A: kRecTiles every tile's values as the MMA consumes them
+// (hi + lo, masked), kRecSym the blocks this tile records for the symmetric
+// store (every source of the chunk, unmasked).
+constexpr int kRecNone = 0, kRecTiles = 1, kRecSym = 2;
+template <int KIND, int REC = kRecNone, int NS = kNS>
 __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcShared<NS>& S = *reinterpret_cast<TcShared<NS>*>(smem_raw);
@@ -514,7 +518,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         // fill pass: this row's row chunk and its row in it
         int rk = 0, rl = row, rm = 1;
         int64_t rref0 = 0;
-        if constexpr (RECORD) {
+        if constexpr (REC == kRecSym) {
             const ItemSym* is = a.isym + blockIdx.x;
             rm = is->m;
             rref0 = is->ref0;
@@ -567,7 +571,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                 const float4 v = st.xh[j0 + jj];
                 // (the fill pass records every source of the chunk, unmasked:
                 // each reader of a stored block applies its own keep mask)
-                const bool kept = RECORD ? (j0 + jj < st.tile.cnt) : ((st.tile.keep[s_lo + ls] >> (j0 + jj)) & 1u);
+                const bool kept = REC == kRecSym ? (j0 + jj < st.tile.cnt)
+                                                 : ((st.tile.keep[s_lo + ls] >> (j0 + jj)) & 1u) != 0u;
                 float* d = wc + ls * kWarpSlotFloats + jj;
                 d[0] = kept ? v.x : kFar;
                 d[kSrcPerThread] = kept ? v.y : kFar;
@@ -578,7 +583,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
             // A buffer u % kNA was last read by MMA(u - kNA), complete since drain(u - 2)
             const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + (uint32_t)j0;
             const float* c = wc + myloc * kWarpSlotFloats;
-            const bool none = !RECORD && __all_sync(0xffffffffu, keep == 0);
+            const bool none = REC != kRecSym && __all_sync(0xffffffffu, keep == 0);
 #pragma unroll
             for (int g = 0; g < kSrcPerThread / 16; ++g) {
                 uint32_t ghi[16], glo[16];
@@ -592,7 +597,19 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                 }
                 tmem_st16(acol + 16u * g, ghi);
                 tmem_st16(acol + 32u + 16u * g, glo);
-                if constexpr (RECORD) {
+                if constexpr (REC == kRecTiles) {
+                    float4* dst = reinterpret_cast<float4*>(a.A + a.abase[blockIdx.x] + (int64_t)u * nrows * 32);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int jj = 4 * q;
+                        if (valid) dst[tile_word(half, q, row, nrows)] =
+                            make_float4(__uint_as_float(ghi[jj]) + __uint_as_float(glo[jj]),
+                                        __uint_as_float(ghi[jj + 1]) + __uint_as_float(glo[jj + 1]),
+                                        __uint_as_float(ghi[jj + 2]) + __uint_as_float(glo[jj + 2]),
+                                        __uint_as_float(ghi[jj + 3]) + __uint_as_float(glo[jj + 3]));
+                    }
+                }
+                if constexpr (REC == kRecSym) {
                     // this row's block of the tile, if this tile records it
                     // (stored as this row chunk x the tile's chunk)
                     const BlockRef rf = a.refs[rref0 + (int64_t)u * rm + rk];
@@ -632,7 +649,194 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
 }
 
 // ---------------------------------------------------------------------------
-// Stored-operator mode: the same translations with the kernel values read
+// Stored-operator mode, per-tile store: the same translations with every
+// tile's kernel values read from the tiles the fill pass (tc_near_kernel with
+// REC = kRecTiles) wrote, instead of evaluated. Tile u of an item with nrows
+// rows keeps its nrows x 32 values (unscaled FP32, zero where a row's slot
+// skips the source) at A + abase[item] + u * nrows * 32, ordered so that
+// compute thread (row, half) reads its 16 values as four 16-byte words with
+// consecutive rows adjacent: value (row, j = 16 half + 4 q + e) at
+// ((half * 4 + q) * nrows + row) * 4 + e. Per tile the producer copies 24 KB
+// at most (the chunk's B hi + lo and the kernel tile); the compute warps only
+// split the values into TF32 hi + lo and write A to tensor memory. The MMA
+// issue, the accumulator drain and the two-level sum are those of
+// tc_near_kernel, so both give the same result bit for bit. Bound: HBM,
+// nrows x 128 bytes of kernel values per tile.
+static_assert(kSrcPerThread == 16, "stored tiles assume two compute threads per row");
+constexpr int kNST = 3;                        // data stages (24 KB each)
+struct alignas(128) TcTileStage {
+    float b[2 * 1024];                         // B hi, B lo (the first 8 KB of the chunk block)
+    float4 ga[kTileFloats / 4];                // the tile's kernel values
+};
+struct TcTileShared {
+    TcTileStage st[kNST];
+    float outer[kTcN / kTpr][kTcCompute];
+    uint64_t full[kNST], afull[kNST], empty[kNST];
+    uint32_t tmem;
+};
+constexpr int kTcsSmemRequest = 100 * 1024;   // two CTAs per SM
+static_assert(sizeof(TcTileShared) <= kTcsSmemRequest, "shared memory plan (per-tile store)");
+
+template <int KIND>
+__global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcTileShared& S = *reinterpret_cast<TcTileShared*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const TcItem* itp = a.items + blockIdx.x;
+    const int64_t row_off = itp->row_off;
+    const int nrows = itp->nrows, list_lo = itp->list_lo;
+    const int ntile = itp->list_hi - list_lo;
+
+    if (tid == 0) {
+        for (int s = 0; s < kNST; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sm_addr(&S.afull[s])), "r"(kTcCompute));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.empty[s])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(sm_addr(&S.tmem)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = S.tmem;
+    bool err = false;
+
+    if (warp == kTcCompute / 32) {
+        // ---------------- producer warp ----------------
+        const float* tiles_src = a.A + a.abase[blockIdx.x];
+        const uint32_t tile_bytes = 128u * (uint32_t)nrows;    // nrows x 32 floats (1 <= nrows <= 128)
+        for (int t0 = 0; t0 < ntile; t0 += 32) {
+            const int d_chunk = t0 + lane < ntile ? a.tiles[list_lo + t0 + lane].chunk : 0;
+            const int nb = min(32, ntile - t0);
+            for (int i = 0; i < nb; ++i) {
+                const int t = t0 + i;
+                const int s = t % kNST;
+                const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
+                if (t >= kNST && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNST) / kNST) & 1), a.wait_ns))
+                    err = true;
+                const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
+                if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
+                if (lane == 0) {
+                    const uint32_t bar = sm_addr(&S.full[s]);
+                    mbar_arrive_tx(bar, 4u * 2048u + tile_bytes);
+                    bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
+                    bulk_g2s(sm_addr(S.st[s].ga), tiles_src + (int64_t)t * nrows * 32, tile_bytes, bar);
+                    if (hold && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0) {
+            for (int t = (ntile > kNST ? ntile - kNST : 0); t < ntile; ++t)
+                if (!mbar_wait(sm_addr(&S.full[t % kNST]), (uint32_t)((t / kNST) & 1), a.wait_ns)) err = true;
+        }
+    } else if (warp == kTcCompute / 32 + 1) {
+        // ---------------- MMA issuer (one thread) ----------------
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                                   ((128u >> 4) << 24);
+            for (int m = 0; m < ntile; ++m) {
+                const int s = m % kNST, ab = m % kNA;
+                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kNST) & 1), a.wait_ns)) err = true;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t bh = sm_addr(S.st[s].b), bl = bh + 4u * 1024u;
+                const uint32_t d = tbase + kColD + 32u * (m & 1);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t ahi = tbase + kColA + 64u * ab + 8u * k, alo = ahi + 32u;
+                    mma_tf32(d, ahi, smem_desc(bh + 2u * kBLbo * k), idesc, k > 0 ? 1u : 0u);
+                    mma_tf32(d, ahi, smem_desc(bl + 2u * kBLbo * k), idesc, 1u);
+                    mma_tf32(d, alo, smem_desc(bh + 2u * kBLbo * k), idesc, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(sm_addr(&S.empty[s])) : "memory");
+            }
+        }
+    } else {
+        // ---------------- compute warps ----------------
+        const int row = tid & 127, half = tid >> 7;
+        const bool valid = row < nrows;
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        constexpr int kCols = kTcN / kTpr;
+        const int j0 = kSrcPerThread * half;
+        float acc[kCols];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+            acc[c] = 0.f;
+            S.outer[c][tid] = 0.f;
+        }
+        auto drain = [&](int m) {
+            if (!mbar_wait(sm_addr(&S.empty[m % kNST]), (uint32_t)((m / kNST) & 1), a.wait_ns)) err = true;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t v[kCols];
+            tmem_ld16(tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kCols * half), v);
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) acc[c] += __uint_as_float(v[c]);
+            if (m % kTcGroup == kTcGroup - 1) {
+#pragma unroll
+                for (int c = 0; c < kCols; ++c) {
+                    S.outer[c][tid] += acc[c];
+                    acc[c] = 0.f;
+                }
+            }
+        };
+        const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
+        for (int u = 0; u < ntile; ++u) {
+            const int s = u % kNST;
+            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNST) & 1), a.wait_ns)) err = true;
+            uint32_t ghi[16], glo[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 g4 = valid ? S.st[s].ga[tile_word(half, q, row, nrows)] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 g = h ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
+                    const float2 t = __fmul2_rn(g, split);
+                    const float2 hi = __ffma2_rn(__ffma2_rn(g, m1, t), m1, t);
+                    const float2 lo = __ffma2_rn(hi, m1, g);
+                    const int jj = 4 * q + 2 * h;
+                    ghi[jj] = __float_as_uint(hi.x);
+                    ghi[jj + 1] = __float_as_uint(hi.y);
+                    glo[jj] = __float_as_uint(lo.x);
+                    glo[jj + 1] = __float_as_uint(lo.y);
+                }
+            }
+            if (u >= 2) drain(u - 2);
+            const uint32_t acol = tbase + lane_off + kColA + 64u * (u % kNA) + (uint32_t)j0;
+            tmem_st16(acol, ghi);
+            tmem_st16(acol + 32u, glo);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(sm_addr(&S.afull[s]));
+        }
+        for (int m = (ntile >= 2 ? ntile - 2 : 0); m < ntile; ++m) drain(m);
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) acc[c] += S.outer[c][tid];
+        if (valid) {
+            const float scale = (float)green_scale<KIND>();
+            const int64_t base = (row_off + row) * a.nrhs;
+            const int c0 = a.r0 + kCols * half;
+#pragma unroll
+            for (int c = 0; c < kCols; ++c)
+                if (c0 + c < a.nrhs) a.U[base + c0 + c] = scale * acc[c];
+        }
+    }
+    if (err) atomicExch(a.status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(kTmemCols));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stored-operator mode, symmetric store: the same translations with the kernel values read
 // from the symmetric store instead of evaluated. Per tile the producer copies
 // into a stage the chunk's B hi + lo (8 KB), the tile's SrcTile (its keep
 // masks) and BlockRefs, and the row chunks' stored blocks, one after the
@@ -645,29 +849,29 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
 // MMA issue, the accumulator drain and the two-level sum are those of
 // tc_near_kernel. Bound: HBM, 4 bytes per stored value.
 static_assert(kSrcPerThread == 16, "stored tiles assume two compute threads per row");
-constexpr int kNSS = 6;                        // stages (B operand, descriptors)
+constexpr int kNSY = 6;                        // stages (B operand, descriptors)
 constexpr int kRing = 10240;                   // floats of the block ring (40 KB)
 static_assert(kSymFloats <= kRing, "a tile's blocks fit the ring");
-struct alignas(128) TcSStage {
+struct alignas(128) TcSymStage {
     float b[2 * 1024];                         // B hi, B lo (the first 8 KB of the chunk block)
     SrcTile tile;                              // the tile's descriptor (keep masks, source count)
     BlockRef refs[kMaxRc];                     // its row chunks' blocks
     int32_t rbase;                             // ring float of its first block
 };
-struct TcSShared {
-    TcSStage st[kNSS];
+struct TcSymShared {
+    TcSymStage st[kNSY];
     float ring[kRing];
     float outer[kTcN / kTpr][kTcCompute];
-    uint64_t full[kNSS], afull[kNSS], empty[kNSS];
+    uint64_t full[kNSY], afull[kNSY], empty[kNSY];
     uint32_t tmem;
 };
-constexpr int kTcsSmemRequest = 112 * 1024;   // two CTAs per SM
-static_assert(sizeof(TcSShared) <= kTcsSmemRequest, "shared memory plan (stored mode)");
+constexpr int kTsySmemRequest = 112 * 1024;   // two CTAs per SM
+static_assert(sizeof(TcSymShared) <= kTsySmemRequest, "shared memory plan (symmetric store)");
 
 template <int KIND>
-__global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 2) tc_sym_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcSShared& S = *reinterpret_cast<TcSShared*>(smem_raw);
+    TcSymShared& S = *reinterpret_cast<TcSymShared*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const TcItem* itp = a.items + blockIdx.x;
     const ItemSym* isp = a.isym + blockIdx.x;
@@ -678,7 +882,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
     const int64_t ref0 = isp->ref0;
 
     if (tid == 0) {
-        for (int s = 0; s < kNSS; ++s) {
+        for (int s = 0; s < kNSY; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.full[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sm_addr(&S.afull[s])), "r"(kTcCompute));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.empty[s])));
@@ -704,7 +908,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         // while this one is issued. Ring space is handed out in tile order:
         // a tile's blocks go contiguously at the head (to the start of the
         // ring if they would wrap), after the oldest tiles whose space that
-        // needs have been consumed (their "empty" barrier); lane s % kNSS
+        // needs have been consumed (their "empty" barrier); lane s % kNSY
         // remembers where tile s's blocks start.
         const int per = 32 / m;
         const uint64_t pol_once = l2_evict_first(), pol_keep = l2_evict_last();
@@ -729,7 +933,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             const int nb = min(per, ntile - t0);
             for (int i = 0; i < nb; ++i) {
                 const int t = t0 + i;
-                const int s = t % kNSS;
+                const int s = t % kNSY;
                 const int src = i * m + (lane < m ? lane : 0);
                 const int64_t roff = __shfl_sync(0xffffffffu, c_off, src);
                 uint32_t rfl = __shfl_sync(0xffffffffu, c_bytes, src) >> 2;     // floats
@@ -744,15 +948,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
                 }
                 const uint32_t pre = incl - rfl;
                 const uint32_t totf = __shfl_sync(0xffffffffu, incl, 31);
-                if (t >= kNSS) {
-                    if (!mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSS) / kNSS) & 1), a.wait_ns)) err = true;
-                    tail = max(tail, t - kNSS + 1);        // every tile up to t - kNSS is consumed
+                if (t >= kNSY) {
+                    if (!mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNSY) / kNSY) & 1), a.wait_ns)) err = true;
+                    tail = max(tail, t - kNSY + 1);        // every tile up to t - kNSY is consumed
                 }
                 int64_t start = head;
                 if (start % kRing + totf > (uint32_t)kRing) start += kRing - start % kRing;
                 const int64_t end = start + totf;
-                while (tail < t && end - __shfl_sync(0xffffffffu, my_start, tail % kNSS) > kRing) {
-                    if (!mbar_wait(sm_addr(&S.empty[tail % kNSS]), (uint32_t)((tail / kNSS) & 1), a.wait_ns)) err = true;
+                while (tail < t && end - __shfl_sync(0xffffffffu, my_start, tail % kNSY) > kRing) {
+                    if (!mbar_wait(sm_addr(&S.empty[tail % kNSY]), (uint32_t)((tail / kNSY) & 1), a.wait_ns)) err = true;
                     ++tail;
                 }
                 head = end;
@@ -780,8 +984,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             c_ch = n_ch;
         }
         if (lane == 0) {
-            for (int t = (ntile > kNSS ? ntile - kNSS : 0); t < ntile; ++t)
-                if (!mbar_wait(sm_addr(&S.full[t % kNSS]), (uint32_t)((t / kNSS) & 1), a.wait_ns)) err = true;
+            for (int t = (ntile > kNSY ? ntile - kNSY : 0); t < ntile; ++t)
+                if (!mbar_wait(sm_addr(&S.full[t % kNSY]), (uint32_t)((t / kNSY) & 1), a.wait_ns)) err = true;
         }
     } else if (warp == kTcCompute / 32 + 1) {
         // ---------------- MMA issuer (one thread) ----------------
@@ -789,8 +993,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                                    ((128u >> 4) << 24);
             for (int mm = 0; mm < ntile; ++mm) {
-                const int s = mm % kNSS, ab = mm % kNA;
-                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((mm / kNSS) & 1), a.wait_ns)) err = true;
+                const int s = mm % kNSY, ab = mm % kNA;
+                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((mm / kNSY) & 1), a.wait_ns)) err = true;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t bh = sm_addr(S.st[s].b), bl = bh + 4u * 1024u;
                 const uint32_t d = tbase + kColD + 32u * (mm & 1);
@@ -827,7 +1031,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             S.outer[c][tid] = 0.f;
         }
         auto drain = [&](int mm) {
-            if (!mbar_wait(sm_addr(&S.empty[mm % kNSS]), (uint32_t)((mm / kNSS) & 1), a.wait_ns)) err = true;
+            if (!mbar_wait(sm_addr(&S.empty[mm % kNSY]), (uint32_t)((mm / kNSY) & 1), a.wait_ns)) err = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t v[kCols];
             tmem_ld16(tbase + lane_off + kColD + 32u * (mm & 1) + (uint32_t)(kCols * half), v);
@@ -843,10 +1047,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         };
         const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
         for (int u = 0; u < ntile; ++u) {
-            const int s = u % kNSS;
-            const bool landed = mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNSS) & 1), a.wait_ns);
+            const int s = u % kNSY;
+            const bool landed = mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNSY) & 1), a.wait_ns);
             if (!landed) err = true;
-            const TcSStage& st = S.st[s];
+            const TcSymStage& st = S.st[s];
             // the row's kept sources of this tile, and where its block sits
             uint32_t keep = valid ? (st.tile.keep[myslot] >> j0) & 0xFFFFu : 0u;
             // this row chunk's block: after the tile's earlier blocks in the ring

@@ -1,10 +1,16 @@
-"""Stored-operator mode (``store_tiles``): the tensor-core apply reading kernel
-blocks evaluated once at build. The real kernels are symmetric, so a block
-two tiles share is stored once and one of them reads it transposed: its
-values are the on-the-fly kernel's for the other orientation, equal up to
-FP32 rounding. The stored apply therefore matches the on-the-fly apply within
-the FP32 parity tolerance (1e-5 of max |u|; measured about 1e-6), and the
-oracle's direct sum within 10 tol."""
+"""Stored-operator mode (``store_tiles``): the tensor-core apply reading
+kernel values evaluated once at build.
+
+* Per-tile store (mode 1): every tile's values exactly as the tensor core
+  consumed them, so the apply equals the on-the-fly apply bit for bit.
+* Symmetric store (mode 2): the real kernels are symmetric, so a block two
+  tiles share is stored once and one of them reads it transposed; those
+  values come from the other tile's frame and equal its own evaluation up to
+  FP32 rounding. The apply matches the on-the-fly apply within the FP32
+  parity tolerance (1e-5 of max |u|; measured about 1e-6).
+
+Both match the oracle's direct sum within 10 tol.
+"""
 import numpy as np
 import pytest
 import torch
@@ -30,23 +36,31 @@ def _gpu():
                                                  ("laplace3d", 3, "clustered", 32, 1e-6),
                                                  ("laplace2d", 2, "clustered", 32, 1e-8)])
 @pytest.mark.parametrize("nrhs", [32, 64])
-def test_stored_blocks_match_on_the_fly(kind, dim, dist, b, tol, nrhs):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_stored_match_on_the_fly(kind, dim, dist, b, tol, nrhs, mode):
     x = W.points_uniform(20000, dim, 31) if dist == "uniform" else clustered(12000, dim, 31)
-    fs = SkelFMM(x, kind, tol, b, nrhs_max=nrhs, store_tiles=True)
+    fs = SkelFMM(x, kind, tol, b, nrhs_max=nrhs, store_tiles=mode)
     fo = SkelFMM(x, kind, tol, b, nrhs_max=nrhs)
     info = fs.info()
-    # every distinct kept value is stored once; shared blocks are read twice
-    assert 0 < info["pairs_stored"] < info["pairs_tc"]
-    assert 4 * info["pairs_stored"] <= info["stored_tile_bytes"] <= 4 * 2 * info["pairs_tc"]
-    assert info["stored_tile_bytes"] % 16 == 0
-    assert fo.info()["stored_tile_bytes"] == 0
+    assert info["store_mode"] == mode and fo.info()["store_mode"] == 0
+    assert info["stored_tile_bytes"] % 16 == 0 and fo.info()["stored_tile_bytes"] == 0
+    if mode == 1:
+        # every tile's rows x 32 values: all kept values plus masked / ragged zeros
+        assert 4 * info["pairs_tc"] <= info["stored_tile_bytes"] <= info["n_tc_tiles"] * 128 * 32 * 4
+    else:
+        # every distinct kept value once; shared blocks are read twice
+        assert 0 < info["pairs_stored"] < info["pairs_tc"]
+        assert 4 * info["pairs_stored"] <= info["stored_tile_bytes"] <= 4 * 2 * info["pairs_tc"]
     q = torch.from_numpy(W.charges_normal(x.shape[0], nrhs, 32)).cuda().float()
     us = fs.apply(q, "fp32_tc")
     uo = fo.apply(q, "fp32_tc")
     fs.device_status()
-    for r in (0, nrhs // 2, nrhs - 1):
-        assert relerr(us[:, r].cpu().numpy(), uo[:, r].cpu().numpy()) < 1e-5, r
-    assert torch.equal(fs.apply(q, "fp32_tc"), us)    # deterministic
+    if mode == 1:
+        assert torch.equal(us, uo)
+    else:
+        for r in (0, nrhs // 2, nrhs - 1):
+            assert relerr(us[:, r].cpu().numpy(), uo[:, r].cpu().numpy()) < 1e-5, r
+        assert torch.equal(fs.apply(q, "fp32_tc"), us)    # deterministic
     ut = fs.apply_transpose(q, "fp32_tc")
     assert torch.equal(ut, us)                         # real kernels: A~^T = A~
     # and against the direct sum (RHS 0)
@@ -64,32 +78,34 @@ def test_stored_tiles_ignored_for_complex_kernels():
 
 
 @pytest.mark.slow
-def test_full_size_stored_tiles():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_full_size_stored(mode):
     wl = W.LAPLACE3D_1M
     x = wl.make_points()
     qall = torch.from_numpy(wl.make_charges(32)).cuda().float()
-    fs = SkelFMM(x, wl.kernel, wl.tol, wl.leaf, nrhs_max=32, store_tiles=True, device_build=True)
+    fs = SkelFMM(x, wl.kernel, wl.tol, wl.leaf, nrhs_max=32, store_tiles=mode, device_build=True)
     us = fs.apply(qall, "fp32_tc")
     fs.device_status()
     tg = wl.make_sample()
     ref = direct.direct_sum(wl.kernel, x, qall[:, 0].double().cpu().numpy(), targets=tg)
     e = relerr(us[:, 0].double().cpu().numpy()[tg], ref)
     info = fs.info()
-    print(f"stored tiles: {info['stored_tile_bytes'] / 1e9:.1f} GB (distinct kept values {4 * info['pairs_stored'] / 1e9:.1f} GB"
-          f" of {4 * info['pairs_tc'] / 1e9:.1f} GB evaluated), "
+    print(f"store mode {mode}: {info['stored_tile_bytes'] / 1e9:.1f} GB (distinct kept values "
+          f"{4 * info['pairs_stored'] / 1e9:.1f} GB of {4 * info['pairs_tc'] / 1e9:.1f} GB evaluated), "
           f"device bytes {info['device_bytes'] / 1e9:.1f} GB, relerr fp32_tc {e:.3e}")
     assert e < 10 * wl.tol
-    # the symmetric store holds each shared block once: well under the
-    # 4 B per evaluation of a per-tile store
-    assert info["stored_tile_bytes"] < 0.7 * 4 * info["pairs_tc"]
+    if mode == 2:
+        # the symmetric store holds each shared block once
+        assert info["stored_tile_bytes"] < 0.7 * 4 * info["pairs_tc"]
+    fs.close()
 
 
 @pytest.mark.parametrize("kind,dim", [("laplace3d", 3), ("laplace2d", 2)])
 def test_autotune_keeps_results(kind, dim):
     """The autotuner only picks among variants that compute the same thing:
-    the up/down launch shapes give the same FP32 result bit for bit; the
-    stored blocks, if chosen, the on-the-fly result up to FP32 rounding of the
-    shared blocks read transposed."""
+    the up/down launch shapes and the per-tile store give the same FP32
+    result bit for bit; the symmetric store, if chosen, the on-the-fly result
+    up to FP32 rounding of the shared blocks read transposed."""
     x = clustered(12000, dim, 35)
     f = SkelFMM(x, kind, 1e-6, 32, nrhs_max=32)
     q = torch.from_numpy(W.charges_normal(x.shape[0], 32, 36)).cuda().float()
@@ -97,19 +113,22 @@ def test_autotune_keeps_results(kind, dim):
     rep = f.autotune(32, allow_store=True)
     assert rep["ms_onfly"] > 0 and rep["n_updown"] > 0
     assert rep["ms_updown_tuned"] <= rep["ms_updown_default"] + 1e-9
-    assert (rep["stored"] == 1) == (f.info()["stored_tile_bytes"] > 0)
-    if rep["stored"]:
+    assert rep["stored"] == f.info()["store_mode"]
+    assert (rep["stored"] > 0) == (f.info()["stored_tile_bytes"] > 0)
+    if rep["stored"] == 1:
         assert 0 < rep["ms_stored"] < rep["ms_onfly"]
+    if rep["stored"] == 2:
+        assert 0 < rep["ms_sym"] < rep["ms_onfly"]
     tc1, s1 = f.apply(q, "fp32_tc"), f.apply(q[:, :3].contiguous(), "fp32")
     f.device_status()
     assert torch.equal(s0, s1)
-    if rep["stored"]:
+    if rep["stored"] == 2:
         assert relerr(tc1[:, 0].cpu().numpy(), tc0[:, 0].cpu().numpy()) < 1e-5
     else:
         assert torch.equal(tc0, tc1)
     rep2 = f.autotune(32, allow_store=False)          # tuning again is allowed
     tc2 = f.apply(q, "fp32_tc")
-    if rep2["stored"]:
+    if rep2["stored"] == 2:
         assert relerr(tc2[:, 0].cpu().numpy(), tc0[:, 0].cpu().numpy()) < 1e-5
     else:
         assert torch.equal(tc2, tc0)
