@@ -317,6 +317,7 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     t.U = (float*)b->U;
     t.A = dp->tc_a;
     t.abase = dp->tc_abase;
+    t.qmask = dp->tc_qmask;
     t.refs = (const BlockRef*)dp->tc_refs;
     t.isym = (const ItemSym*)dp->tc_isym;
     t.nrhs = nrhs;
@@ -449,14 +450,17 @@ void drop_tiles(DevicePlan* dp) {
     if (!dp->tc_a) return;
     cudaFree(dp->tc_a);
     cudaFree(dp->tc_abase);
+    cudaFree(dp->tc_qmask);
     cudaFree(dp->tc_refs);
     cudaFree(dp->tc_isym);
     dp->tc_a = nullptr;
     dp->tc_abase = nullptr;
+    dp->tc_qmask = nullptr;
     dp->tc_refs = nullptr;
     dp->tc_isym = nullptr;
     dp->bytes -= dp->stored_bytes + (dp->store_mode == 2 ? (int64_t)(dp->tc_refs_host.size() + dp->tc_isym_host.size())
-                                                          : (int64_t)(dp->tc_abase_host.size() * sizeof(int64_t)));
+                                                          : (int64_t)(dp->tc_abase_host.size() * sizeof(int64_t) +
+                                                                      dp->tc_qmask_host.size()));
     dp->stored_bytes = 0;
     dp->store_mode = 0;
 }
@@ -475,13 +479,16 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st, int mode) {
             dp->tc_isym = upload(dp->tc_isym_host, bytes);
         } else {
             dp->tc_abase = upload(dp->tc_abase_host, bytes);
+            dp->tc_qmask = upload(dp->tc_qmask_host, bytes);
         }
         dp->tc_a = dalloc<float>((size_t)floats, bytes);
     } catch (...) {
         cudaFree(dp->tc_abase);
+        cudaFree(dp->tc_qmask);
         cudaFree(dp->tc_refs);
         cudaFree(dp->tc_isym);
         dp->tc_abase = nullptr;
+        dp->tc_qmask = nullptr;
         dp->tc_refs = dp->tc_isym = nullptr;
         throw;
     }
@@ -505,6 +512,7 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st, int mode) {
         t.U = (float*)b->U;
         t.A = dp->tc_a;
         t.abase = dp->tc_abase;
+        t.qmask = dp->tc_qmask;
         t.refs = (const BlockRef*)dp->tc_refs;
         t.isym = (const ItemSym*)dp->tc_isym;
         t.nrhs = 1;
@@ -737,13 +745,26 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, i
             dp->n_tc_tiles = (int64_t)lay.tc_tiles.size();
             for (const TcItem& it : lay.tc_items)
                 if (it.nrows < 1 || it.nrows > kTcRows) throw Error(-5, "tensor-core item with no rows");
-            // per-tile store: each item's tiles back to back, nrows x 32 floats each
+            // per-tile store: each item's tiles back to back; a tile keeps the
+            // 4-column quads in which some row of its item keeps a source
+            // (the others are zero in every row), nrows float4 each
             dp->tc_abase_host.resize(lay.tc_items.size());
+            dp->tc_qmask_host.assign(lay.tc_tiles.size(), 0);
             int64_t nf = 0;
             for (size_t i = 0; i < lay.tc_items.size(); ++i) {
                 const TcItem& it = lay.tc_items[i];
                 dp->tc_abase_host[i] = nf;
-                nf += (int64_t)(it.list_hi - it.list_lo) * it.nrows * 32;
+                for (int32_t t = it.list_lo; t < it.list_hi; ++t) {
+                    uint32_t cm = 0;
+                    for (int sl = 0; sl < it.nslot; ++sl)
+                        if (std::min(it.slot_start[sl + 1], it.nrows) > std::max(it.slot_start[sl], 0))
+                            cm |= lay.tc_tiles[t].keep[sl];
+                    uint32_t qm = 0;
+                    for (int q = 0; q < 8; ++q)
+                        if ((cm >> (4 * q)) & 0xFu) qm |= 1u << q;
+                    dp->tc_qmask_host[t] = (uint8_t)qm;
+                    nf += (int64_t)__builtin_popcount(qm) * it.nrows * 4;
+                }
             }
             dp->tile_floats = nf;
             plan_symmetric_store(lay, dp);
@@ -765,7 +786,8 @@ void device_plan_destroy(DevicePlan* dp) {
     void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
                     dp->tc_items, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
-                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a, dp->tc_refs, dp->tc_isym};
+                    dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a, dp->tc_abase,
+                    dp->tc_qmask, dp->tc_refs, dp->tc_isym};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);

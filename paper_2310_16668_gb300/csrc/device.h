@@ -56,6 +56,8 @@ struct DevicePlan {
     float* tc_a = nullptr;                 // the stored kernel values (either mode)
     int64_t* tc_abase = nullptr;           // per-tile store: per item, first float of its tiles
     std::vector<int64_t> tc_abase_host;
+    uint8_t* tc_qmask = nullptr;           // per-tile store: per tile, the 4-column quads it keeps
+    std::vector<uint8_t> tc_qmask_host;
     int64_t tile_floats = 0;               // floats the per-tile store takes
     void* tc_refs = nullptr;               // symmetric store: per tile and row chunk, BlockRef
     void* tc_isym = nullptr;               // symmetric store: per tensor-core item, ItemSym

@@ -140,6 +140,7 @@ struct TcArgs {
     float* U;                                  // entry rows of nrhs (this item's rows are written here)
     float* A;                                  // stored kernel values, or null
     const int64_t* abase;                      // per-tile store: per item, first float of its tiles
+    const uint8_t* qmask;                      // per-tile store: per tile, the quads it keeps
     const BlockRef* refs;                      // symmetric store: per tile and row chunk
     const ItemSym* isym;                       // stored-operator mode: per item
     int nrhs;                                  // right-hand sides (row length of U)
@@ -391,13 +392,17 @@ __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict
     }
 }
 
-// Stored-operator mode, per-tile store: tile u of an item with nrows rows
-// keeps its nrows x 32 kernel values (unscaled FP32, zero where a row's slot
-// skips the source) at A + abase[item] + u * nrows * 32.
+// Stored-operator mode, per-tile store: a tile's 32 columns come in 8 quads
+// of 4 (quad h * 4 + q holds columns 16 h + 4 q .. + 3); the tile keeps the
+// quads some row of its item keeps a source in (bit of qmask[tile]), each as
+// nrows float4 (unscaled FP32, zero where a row's slot skips the source), so
+// that compute thread (row, half) reads its quads as 16-byte words with
+// consecutive rows adjacent. Tiles follow each other from A + abase[item].
 constexpr int kTileFloats = 128 * 32;          // the largest tile
-// per-tile store: value (row, j = 16 half + 4 q + e) of a tile at float4
-// (half * 4 + q) * nrows + row
-__device__ __forceinline__ int tile_word(int half, int q, int row, int nrows) { return (half * 4 + q) * nrows + row; }
+// float4 index of (row, quad) in a tile with quad mask qm
+__device__ __forceinline__ int tile_word(uint32_t qm, int quad, int row, int nrows) {
+    return __popc(qm & ((1u << quad) - 1u)) * nrows + row;
+}
 
 // REC: the fill pass of a stored-operator mode also writes the kernel values
 // it evaluates to a.A: kRecTiles every tile's values as the MMA consumes them
@@ -515,6 +520,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
         constexpr int kCols = kTcN / kTpr;                     // accumulator columns this thread owns
         constexpr uint32_t kKeepMask = kSrcPerThread == 32 ? 0xFFFFFFFFu : (1u << kSrcPerThread) - 1u;
         const int j0 = kSrcPerThread * half;
+        int64_t tfill = 0;                                     // per-tile fill: floats of the tiles before
         // fill pass: this row's row chunk and its row in it
         int rk = 0, rl = row, rm = 1;
         int64_t rref0 = 0;
@@ -598,16 +604,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
                 tmem_st16(acol + 16u * g, ghi);
                 tmem_st16(acol + 32u + 16u * g, glo);
                 if constexpr (REC == kRecTiles) {
-                    float4* dst = reinterpret_cast<float4*>(a.A + a.abase[blockIdx.x] + (int64_t)u * nrows * 32);
+                    const uint32_t qm = a.qmask[list_lo + u];
+                    float4* dst = reinterpret_cast<float4*>(a.A + a.abase[blockIdx.x] + tfill);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int jj = 4 * q;
-                        if (valid) dst[tile_word(half, q, row, nrows)] =
+                        const int jj = 4 * q, quad = 4 * half + q;
+                        if (valid && ((qm >> quad) & 1u)) dst[tile_word(qm, quad, row, nrows)] =
                             make_float4(__uint_as_float(ghi[jj]) + __uint_as_float(glo[jj]),
                                         __uint_as_float(ghi[jj + 1]) + __uint_as_float(glo[jj + 1]),
                                         __uint_as_float(ghi[jj + 2]) + __uint_as_float(glo[jj + 2]),
                                         __uint_as_float(ghi[jj + 3]) + __uint_as_float(glo[jj + 3]));
                     }
+                    tfill += (int64_t)__popc(qm) * nrows * 4;
                 }
                 if constexpr (REC == kRecSym) {
                     // this row's block of the tile, if this tile records it
@@ -666,7 +674,8 @@ static_assert(kSrcPerThread == 16, "stored tiles assume two compute threads per 
 constexpr int kNST = 3;                        // data stages (24 KB each)
 struct alignas(128) TcTileStage {
     float b[2 * 1024];                         // B hi, B lo (the first 8 KB of the chunk block)
-    float4 ga[kTileFloats / 4];                // the tile's kernel values
+    float4 ga[kTileFloats / 4];                // the tile's kept quads
+    uint32_t qm;                               // which quads (written by the producer)
 };
 struct TcTileShared {
     TcTileStage st[kNST];
@@ -709,25 +718,30 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
     if (warp == kTcCompute / 32) {
         // ---------------- producer warp ----------------
         const float* tiles_src = a.A + a.abase[blockIdx.x];
-        const uint32_t tile_bytes = 128u * (uint32_t)nrows;    // nrows x 32 floats (1 <= nrows <= 128)
+        int64_t toff = 0;                                      // floats of the tiles before
         for (int t0 = 0; t0 < ntile; t0 += 32) {
             const int d_chunk = t0 + lane < ntile ? a.tiles[list_lo + t0 + lane].chunk : 0;
+            const uint32_t d_qm = t0 + lane < ntile ? a.qmask[list_lo + t0 + lane] : 0u;
             const int nb = min(32, ntile - t0);
             for (int i = 0; i < nb; ++i) {
                 const int t = t0 + i;
                 const int s = t % kNST;
                 const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
+                const uint32_t qm = __shfl_sync(0xffffffffu, d_qm, i);
+                const uint32_t tile_bytes = 16u * (uint32_t)__popc(qm) * (uint32_t)nrows;
                 if (t >= kNST && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNST) / kNST) & 1), a.wait_ns))
                     err = true;
                 const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
                 if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
                 if (lane == 0) {
                     const uint32_t bar = sm_addr(&S.full[s]);
+                    S.st[s].qm = qm;
                     mbar_arrive_tx(bar, 4u * 2048u + tile_bytes);
                     bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
-                    bulk_g2s(sm_addr(S.st[s].ga), tiles_src + (int64_t)t * nrows * 32, tile_bytes, bar);
+                    if (tile_bytes > 0) bulk_g2s(sm_addr(S.st[s].ga), tiles_src + toff, tile_bytes, bar);
                     if (hold && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
                 }
+                toff += (int64_t)__popc(qm) * nrows * 4;
                 __syncwarp();
             }
         }
@@ -790,9 +804,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             const int s = u % kNST;
             if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNST) & 1), a.wait_ns)) err = true;
             uint32_t ghi[16], glo[16];
+            // a stale mask after a bounded wait gave up can only pick a quad
+            // inside the 16 KB area (at most 8 quads of nrows <= 128 rows)
+            const uint32_t qm = S.st[s].qm & 0xFFu;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 g4 = valid ? S.st[s].ga[tile_word(half, q, row, nrows)] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int quad = 4 * half + q;
+                const float4 g4 = (valid && ((qm >> quad) & 1u)) ? S.st[s].ga[tile_word(qm, quad, row, nrows)]
+                                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const float2 g = h ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
