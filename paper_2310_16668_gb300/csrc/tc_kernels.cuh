@@ -737,8 +737,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
                     const uint32_t bar = sm_addr(&S.full[s]);
                     S.st[s].qm = qm;
                     mbar_arrive_tx(bar, 4u * 2048u + tile_bytes);
-                    bulk_g2s(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar);
-                    if (tile_bytes > 0) bulk_g2s(sm_addr(S.st[s].ga), tiles_src + toff, tile_bytes, bar);
+                    bulk_g2s_hint(sm_addr(S.st[s].b), a.B + (int64_t)chunk * kChunkFloats, 4u * 2048u, bar,
+                                  l2_evict_last());
+                    if (tile_bytes > 0)
+                        bulk_g2s_hint(sm_addr(S.st[s].ga), tiles_src + toff, tile_bytes, bar, l2_evict_first());
                     if (hold && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
                 }
                 toff += (int64_t)__popc(qm) * nrows * 4;
