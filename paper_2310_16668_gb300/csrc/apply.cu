@@ -157,10 +157,10 @@ inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) /
 inline int ud_default_warps(int nch) { return nch >= 4 ? 4 : nch >= 2 ? 2 : 1; }
 
 template <class S, bool DOWN, int W>
-void ud_launch(dim3 grid, int nch, const UpBox* up, const int32_t* pos, const S* T, S* X, int nrhs, bool conj_op,
+void ud_launch(dim3 grid, const UpBox* up, const int32_t* pos, const S* T, S* X, int nrhs, bool conj_op,
                cudaStream_t st) {
     if constexpr (W <= ud_streams<S>())
-        updown_kernel<S, DOWN, W><<<grid, 32 * W, ud_smem<S>(W, nch), st>>>(up, pos, T, X, nrhs, conj_op);
+        updown_kernel<S, DOWN, W><<<grid, 32 * W, ud_smem<S>(W), st>>>(up, pos, T, X, nrhs, conj_op);
     else
         throw Error(-1, "up/down: more warps than streams");
 }
@@ -193,9 +193,7 @@ void up_down(bool down, const DevicePlan* dp, int l, const S* T, S* X, int nrhs,
     const int64_t b0 = dp->up_level_ptr[l], b1 = dp->up_level_ptr[l + 1];
     const int nout = down ? dp->up_level_maxr[l] : dp->up_level_maxk[l];
     const int ninner = down ? dp->up_level_maxk[l] : dp->up_level_maxr[l];
-    // downward, the row blocks also cover the skeleton rows (u_S += uhat)
-    const int nrow = down ? std::max(nout, dp->up_level_maxk[l]) : nout;
-    const dim3 grid((unsigned)(b1 - b0), std::max(1u, ceil_div(nrow, kGT)), ceil_div(nrhs, kGT));
+    const dim3 grid((unsigned)(b1 - b0), std::max(1u, ceil_div(nout, kGT)), ceil_div(nrhs, kGT));
     int W = warps;
     if (W == 0 && std::is_same<S, float>::value) {
         const std::vector<int8_t>& t = down ? dp->ud_warps_down : dp->ud_warps_up;
@@ -204,16 +202,15 @@ void up_down(bool down, const DevicePlan* dp, int l, const S* T, S* X, int nrhs,
     if (W == 0) W = ud_default_warps((ninner + kGT - 1) / kGT);
     W = std::min(W, ud_streams<S>());
     const UpBox* up = dp->up + b0;
-    const int nch = (ninner + kGT - 1) / kGT;
     switch (W) {
-        case 1: down ? ud_launch<S, true, 1>(grid, nch, up, dp->pos, T, X, nrhs, conj_op, st)
-                     : ud_launch<S, false, 1>(grid, nch, up, dp->pos, T, X, nrhs, conj_op, st); break;
-        case 2: down ? ud_launch<S, true, 2>(grid, nch, up, dp->pos, T, X, nrhs, conj_op, st)
-                     : ud_launch<S, false, 2>(grid, nch, up, dp->pos, T, X, nrhs, conj_op, st); break;
-        case 4: down ? ud_launch<S, true, 4>(grid, nch, up, dp->pos, T, X, nrhs, conj_op, st)
-                     : ud_launch<S, false, 4>(grid, nch, up, dp->pos, T, X, nrhs, conj_op, st); break;
-        default: down ? ud_launch<S, true, 8>(grid, nch, up, dp->pos, T, X, nrhs, conj_op, st)
-                      : ud_launch<S, false, 8>(grid, nch, up, dp->pos, T, X, nrhs, conj_op, st); break;
+        case 1: down ? ud_launch<S, true, 1>(grid, up, dp->pos, T, X, nrhs, conj_op, st)
+                     : ud_launch<S, false, 1>(grid, up, dp->pos, T, X, nrhs, conj_op, st); break;
+        case 2: down ? ud_launch<S, true, 2>(grid, up, dp->pos, T, X, nrhs, conj_op, st)
+                     : ud_launch<S, false, 2>(grid, up, dp->pos, T, X, nrhs, conj_op, st); break;
+        case 4: down ? ud_launch<S, true, 4>(grid, up, dp->pos, T, X, nrhs, conj_op, st)
+                     : ud_launch<S, false, 4>(grid, up, dp->pos, T, X, nrhs, conj_op, st); break;
+        default: down ? ud_launch<S, true, 8>(grid, up, dp->pos, T, X, nrhs, conj_op, st)
+                      : ud_launch<S, false, 8>(grid, up, dp->pos, T, X, nrhs, conj_op, st); break;
     }
 }
 
@@ -334,7 +331,7 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
         t.r0 = r0;
         t.withhold_item = (dp->test_withhold && r0 == 0) ? 0 : -1;
         // the pass's B operand blocks, then the translations
-        tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q,
+        tc_bprep_kernel<false><<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q,
                                                                nrhs, r0, (const float4*)b->X,
                                                                (const float4*)b->Xlo,
                                                                (const float4*)dp->chunk_center, dp->tc_b);
@@ -502,7 +499,7 @@ void fill_tiles(DevicePlan* dp, cudaStream_t st, int mode) {
         DeviceBuffers* b = dp->p32;
         CUDA_CHECK(cudaMemsetAsync(b->Q, 0, (size_t)dp->n_tot * sizeof(float), st));
         set_tc_attributes();
-        tc_bprep_kernel<<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q, 1, 0,
+        tc_bprep_kernel<false><<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q, 1, 0,
                                                                (const float4*)b->X, (const float4*)b->Xlo,
                                                                (const float4*)dp->chunk_center, dp->tc_b);
         CUDA_CHECK(cudaGetLastError());

@@ -115,25 +115,22 @@ __global__ void permute_out_narrow(const int64_t* __restrict__ eop, const S* __r
 // y: row block, z: column block) and has W warps. The inner index runs in
 // chunks of 32 dealt round-robin to NS streams (stream s: chunks s, s + NS,
 // ...); warp w forms the partial sums of streams w, w + W, ... one after the
-// other, each over its chunks in order. With one warp and one stream its
-// sum is the result; otherwise the stream partials go to shared memory and
-// are added in stream order. The result is therefore the same for every W, which
-// the autotuner picks per level. Within a warp, lane = right-hand side: per
-// chunk the warp stages its 32 x 32 block of A (inner-major; each load is one
-// coalesced column of 32 rows) and its 32 B rows (each load one coalesced
-// row) in shared memory; each inner index then costs 32 row FMAs per lane
-// (paired in FP32), with the A column read as broadcast 16-byte words.
-// Downward, the CTAs of a box also add uhat to u_S, 32 skeleton rows each.
+// other, each over its chunks in order, and the stream partials are added in
+// stream order (through shared memory when W > 1, in registers when W = 1).
+// The result is therefore the same for every W, which the autotuner picks
+// per level. Within a warp, lane = right-hand side: per chunk the warp stages
+// its 32 x 32 block of A (inner-major; each load is one coalesced column of
+// 32 rows) and its 32 B rows (each load one coalesced row) in shared memory;
+// each inner index then costs 32 row FMAs per lane (paired in FP32), with the
+// A column read as broadcast 16-byte words.
 constexpr int kGT = 32;
 template <class S> __host__ __device__ constexpr int ud_streams() {
     return sizeof(S) <= 4 ? 8 : sizeof(S) <= 8 ? 4 : 2;
 }
-// dynamic shared memory of a CTA with W warps on a level whose inner index
-// has at most nch chunks: per warp its A and B blocks, then the stream
-// partials when there is more than one stream
-template <class S> __host__ __device__ constexpr int ud_smem(int W, int nch) {
-    const int ns = nch < ud_streams<S>() ? nch : ud_streams<S>();
-    return (W * 2 + ((W > 1 || ns > 1) ? ns : 0)) * kGT * kGT * (int)sizeof(S);
+// dynamic shared memory of a CTA with W warps: per warp its A and B blocks,
+// then (W > 1) the stream partials
+template <class S> __host__ __device__ constexpr int ud_smem(int W) {
+    return (W * 2 + (W > 1 ? ud_streams<S>() : 0)) * kGT * kGT * (int)sizeof(S);
 }
 constexpr int kUdSmemMax = 96 * 1024;
 
@@ -152,35 +149,6 @@ template <> __device__ __forceinline__ void ud_rows<float>(float* acc, const flo
     }
 }
 
-// rows i = i0, i0 + step, ... (< lim, at most R of them) of column col:
-// X[dst_i] = X[src_i] + v[q], entries src_i = se(i), dst_i = same ? src_i :
-// de(i), every load issued before any store (X is read and written through
-// one pointer, so the compiler would otherwise keep each load behind the
-// previous row's store)
-template <class S, int R, class SE, class DE>
-__device__ __forceinline__ void ud_update_rows(S* X, int nrhs, int col, int i0, int step, int lim, SE se, DE de,
-                                               bool same, const S* v) {
-    constexpr int B = R < 16 ? R : 16;                     // rows per batch (registers)
-#pragma unroll
-    for (int b0 = 0; b0 < R; b0 += B) {
-        S old[B];
-        int32_t e[B];
-#pragma unroll
-        for (int q = 0; q < B; ++q) {
-            const int i = i0 + (b0 + q) * step;
-            if (i < lim) {
-                e[q] = se(i);
-                old[q] = X[(int64_t)e[q] * nrhs + col];
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < B; ++q) {
-            const int i = i0 + (b0 + q) * step;
-            if (i < lim) X[(int64_t)(same ? e[q] : de(i)) * nrhs + col] = old[q] + v[b0 + q];
-        }
-    }
-}
-
 template <class S, bool DOWN, int W>
 __global__ void __launch_bounds__(32 * W) updown_kernel(const UpBox* __restrict__ up, const int32_t* __restrict__ pos,
                                                         const S* __restrict__ T, S* X, int nrhs, bool conj_op) {
@@ -196,19 +164,26 @@ __global__ void __launch_bounds__(32 * W) updown_kernel(const UpBox* __restrict_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int col = c0 + lane;
     const bool colok = col < nrhs;
-    if (DOWN && colok && row0 < k) {
-        // u_S += uhat on this CTA's 32 skeleton rows and columns
-        constexpr int R = kGT / W, B = R < 16 ? R : 16;
-        auto at = [&](int i) { return (int32_t)(u.off + pos[u.off + i]); };
+    if (DOWN && blockIdx.y == 0 && colok) {              // u_S += uhat, this CTA's columns
+        // batches of 8 rows: every load of a batch is issued before its stores
+        // (X is read and written through the same pointer, so the compiler
+        // would otherwise keep each load behind the previous row's store)
+        for (int i0 = warp; i0 < k; i0 += 8 * W) {
+            S uh[8], us[8];
+            int64_t at[8];
 #pragma unroll
-        for (int b0 = 0; b0 < R; b0 += B) {
-            S uh[B];
-#pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const int i = row0 + warp + (b0 + q) * W;
-                if (i < k) uh[q] = X[(u.dst + i) * nrhs + col];
+            for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q * W;
+                at[q] = -1;
+                if (i < k) {
+                    at[q] = (u.off + pos[u.off + i]) * nrhs + col;
+                    uh[q] = X[(u.dst + i) * nrhs + col];
+                    us[q] = X[at[q]];
+                }
             }
-            ud_update_rows<S, B>(X, nrhs, col, row0 + warp + b0 * W, W, min(k, row0 + kGT), at, at, true, uh);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (at[q] >= 0) X[at[q]] = us[q] + uh[q];
         }
     }
     if (row0 >= nout) return;
@@ -219,13 +194,10 @@ __global__ void __launch_bounds__(32 * W) updown_kernel(const UpBox* __restrict_
     const int nsum = nch < NS ? nch : NS;                  // streams that receive chunks
     const bool rowok = row0 + lane < nout;
     S acc[kGT];
-#pragma unroll
-    for (int i = 0; i < kGT; ++i) acc[i] = zero<S>();
+    S tot[W == 1 ? kGT : 1];
     for (int st = warp; st < nsum; st += W) {
-        if (st != warp) {
 #pragma unroll
-            for (int i = 0; i < kGT; ++i) acc[i] = zero<S>();
-        }
+        for (int i = 0; i < kGT; ++i) acc[i] = zero<S>();
         for (int ch = st; ch < nch; ch += NS) {
             const int j0 = ch * kGT, jn = min(kGT, ninner - j0);
             // the B rows of this chunk: their entry indices, one per lane
@@ -233,7 +205,7 @@ __global__ void __launch_bounds__(32 * W) updown_kernel(const UpBox* __restrict_
             if (lane < jn) ri = DOWN ? (u.dst + j0 + lane) : (u.off + pos[u.off + k + j0 + lane]);
             // stage the A and B blocks: a group's loads all go out before its
             // stores to shared memory (one memory latency per group)
-            constexpr int G = sizeof(S) <= 4 ? 16 : 8;
+            constexpr int G = sizeof(S) <= 4 ? 32 : sizeof(S) <= 8 ? 16 : 8;
 #pragma unroll
             for (int g0 = 0; g0 < kGT; g0 += G) {
                 S ra[G], rb[G];
@@ -259,35 +231,51 @@ __global__ void __launch_bounds__(32 * W) updown_kernel(const UpBox* __restrict_
             for (int jj = 0; jj < kGT; ++jj) ud_rows<S>(acc, As + jj * kGT, Bs[jj * kGT + lane]);
             __syncwarp();                                  // before the next chunk overwrites the blocks
         }
-        if (W > 1 || nsum > 1) {
+        if constexpr (W == 1) {
+#pragma unroll
+            for (int i = 0; i < kGT; ++i) tot[i] = st == 0 ? acc[i] : tot[i] + acc[i];
+        } else {
 #pragma unroll
             for (int i = 0; i < kGT; ++i) Ps[(st * kGT + i) * kGT + lane] = acc[i];
         }
     }
-    auto se = [&](int i) {
-        return (int32_t)(DOWN ? u.off + pos[u.off + k + row0 + i] : u.off + pos[u.off + row0 + i]);
-    };
-    auto de = [&](int i) { return (int32_t)(u.dst + row0 + i); };
-    const int lim = min(kGT, nout - row0);
-    if (W == 1 && nsum <= 1) {
-        // one warp, one stream (or none): its sums are the result
-        if (colok) ud_update_rows<S, kGT>(X, nrhs, col, 0, 1, lim, se, de, DOWN, acc);
-        return;
-    }
-    if (W > 1) __syncthreads();
-    else __syncwarp();
+    if constexpr (W > 1) __syncthreads();
     if (!colok) return;
-    // rows of this CTA: warp w adds rows w, w + W, ... from the stream
-    // partials, in stream order
+    // rows of this CTA: warp w writes rows w, w + W, ...
+    if constexpr (W == 1) {
+        if (nsum == 0) {
+#pragma unroll
+            for (int i = 0; i < kGT; ++i) tot[i] = zero<S>();
+        }
+    }
+    // the rows this warp writes (w, w + W, ...): all their old values are
+    // loaded before any store
     constexpr int R = kGT / W;
-    S v[R];
+    S old[R];
+    int64_t src[R], dst[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-        const int i = warp + q * W;
-        v[q] = zero<S>();
-        for (int s2 = 0; s2 < nsum; ++s2) v[q] = s2 == 0 ? Ps[i * kGT + lane] : v[q] + Ps[(s2 * kGT + i) * kGT + lane];
+        const int orow = row0 + q * W + warp;
+        dst[q] = -1;
+        if (orow < nout) {
+            src[q] = DOWN ? (u.off + pos[u.off + k + orow]) * nrhs + col : (u.off + pos[u.off + orow]) * nrhs + col;
+            dst[q] = DOWN ? src[q] : (u.dst + orow) * nrhs + col;
+            old[q] = X[src[q]];
+        }
     }
-    ud_update_rows<S, R>(X, nrhs, col, warp, W, lim, se, de, DOWN, v);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        if (dst[q] < 0) continue;
+        const int i = q * W + warp;
+        S v;
+        if constexpr (W == 1) {
+            v = tot[i];
+        } else {
+            v = zero<S>();
+            for (int s2 = 0; s2 < nsum; ++s2) v = s2 == 0 ? Ps[i * kGT + lane] : v + Ps[(s2 * kGT + i) * kGT + lane];
+        }
+        X[dst[q]] = old[q] + v;
+    }
 }
 
 // ---- reduction of near-field partial sums ------------------------------------------

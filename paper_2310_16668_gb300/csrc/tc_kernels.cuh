@@ -350,7 +350,10 @@ __device__ __forceinline__ void tc_eval16(const float* c, const float4* xl, int 
 // minus the box centre: FP32 then resolves them to the box size, not to the
 // domain size) and their lo parts; entries past the chunk and columns past
 // nrhs are zero.
+// Complex charges (CPLX): column n < 16 holds the real part of right-hand
+// side r0 + n, column 16 + n its imaginary part (Q interleaved (re, im)).
 // Thread: n = tid % 32, sources 4 (tid / 32) .. +3.
+template <bool CPLX = false>
 __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict__ chunk_start,
                                                        const int32_t* __restrict__ chunk_cnt,
                                                        const float* __restrict__ Q, int nrhs, int r0,
@@ -360,11 +363,13 @@ __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict
     const int n = threadIdx.x & 31, jq = threadIdx.x >> 5;
     const int64_t start = chunk_start[ch];
     const int cnt = chunk_cnt[ch];
+    const int rr = CPLX ? r0 + (n & 15) : r0 + n;         // the right-hand side of column n
     float v[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const int j = 4 * jq + c;
-        v[c] = (j < cnt && r0 + n < nrhs) ? Q[(start + j) * nrhs + r0 + n] : 0.f;
+        v[c] = 0.f;
+        if (j < cnt && rr < nrhs) v[c] = CPLX ? Q[2 * ((start + j) * nrhs + rr) + (n >> 4)] : Q[(start + j) * nrhs + rr];
     }
     float4 h, l;
     h.x = __uint_as_float(to_tf32(v[0]));
@@ -656,6 +661,90 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
     }
 }
 
+// ---------------------------------------------------------------------------
+// 3D Helmholtz (complex64) on the tensor cores. The B operand of a chunk holds
+// 16 complex right-hand sides as 32 real columns (real parts, then imaginary
+// parts; tc_bprep_kernel<true>), in the layout of the real path; the A
+// operand of a tile is the kernel block's real and imaginary parts G_r, G_i
+// (each split into TF32 hi + lo). Per tile the MMA issuer forms
+// D_r = G_r B and D_i = G_i B (12 MMAs each), and the drain combines
+// u_r += D_r[re] - D_i[im], u_i += D_r[im] + D_i[re]. Tensor memory: D_r, D_i
+// of two tiles (128 columns) and three A buffers of G_r hi, lo, G_i hi, lo
+// (3 x 128 columns): all 512 columns, one CTA per SM.
+constexpr int kTcNc = 16;                      // complex right-hand sides per pass
+constexpr uint32_t kColAc = 128;               // A[b]: G_r hi, G_r lo, G_i hi, G_i lo at 128 + 128 b
+constexpr uint32_t kTmemColsC = 512;
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr) : "memory");
+}
+
+// e^{i kappa r} / r without its 1/(4 pi), for 16 sources (as tc_eval16): the
+// reciprocal square root as in the real path (0 for masked sources and, on
+// touching leaves, for r^2 <= FLT_MIN), r = r^2 / r corrected by one Newton
+// step, the phase kappa r reduced to [-pi, pi] by Cody and Waite's method
+// (2 pi as a sum of two floats) and then the hardware sine and cosine
+// (absolute error below 2^-21.4 on [-pi, pi]). Masked sources get kappa r = 0,
+// so their value is exactly 0.
+template <bool ADJ>
+__device__ __forceinline__ void tc_ceval16(const float* c, const float4* xl, int j0, float4 nt, float4 nl,
+                                           float kappa, uint32_t* grh, uint32_t* grl, uint32_t* gih, uint32_t* gil) {
+    constexpr int AX = kSrcPerThread;
+    constexpr float kTwoPiHi = 6.28125f;
+    constexpr float kTwoPiLo = (float)(6.283185307179586476925 - 6.28125);
+    constexpr float kInvTwoPi = (float)(1.0 / 6.283185307179586476925);
+    const float2 ntx = make_float2(nt.x, nt.x), nty = make_float2(nt.y, nt.y), ntz = make_float2(nt.z, nt.z);
+    float2 nlx, nly, nlz;
+    if (ADJ) nlx = make_float2(nl.x, nl.x), nly = make_float2(nl.y, nl.y), nlz = make_float2(nl.z, nl.z);
+    const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 X = *reinterpret_cast<const float4*>(&c[4 * q]);
+        const float4 Y = *reinterpret_cast<const float4*>(&c[AX + 4 * q]);
+        const float4 Z = *reinterpret_cast<const float4*>(&c[2 * AX + 4 * q]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jj = 4 * q + 2 * h;
+            float2 dx = __fadd2_rn(h ? make_float2(X.z, X.w) : make_float2(X.x, X.y), ntx);
+            float2 dy = __fadd2_rn(h ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y), nty);
+            float2 dz = __fadd2_rn(h ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y), ntz);
+            if (ADJ) {
+                const float4 l0 = xl[j0 + jj], l1 = xl[j0 + jj + 1];
+                dx = __fadd2_rn(dx, __fadd2_rn(make_float2(l0.x, l1.x), nlx));
+                dy = __fadd2_rn(dy, __fadd2_rn(make_float2(l0.y, l1.y), nly));
+                dz = __fadd2_rn(dz, __fadd2_rn(make_float2(l0.z, l1.z), nlz));
+            }
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            float gr[2], gi[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float rr = e ? r2.y : r2.x;
+                const float ri = tc_green<1, ADJ>(rr);
+                float r = rr * ri;
+                r = fmaf(0.5f * ri, fmaf(-r, r, rr), r);      // one Newton step: r = sqrt(r^2)
+                const float kr = ri > 0.f ? kappa * r : 0.f;
+                const float n = rintf(kr * kInvTwoPi);
+                const float y = fmaf(-n, kTwoPiLo, fmaf(-n, kTwoPiHi, kr));
+                gr[e] = __cosf(y) * ri;
+                gi[e] = __sinf(y) * ri;
+            }
+            const float2 gR = make_float2(gr[0], gr[1]), gI = make_float2(gi[0], gi[1]);
+            const float2 tR = __fmul2_rn(gR, split), tI = __fmul2_rn(gI, split);
+            const float2 hR = __ffma2_rn(__ffma2_rn(gR, m1, tR), m1, tR), hI = __ffma2_rn(__ffma2_rn(gI, m1, tI), m1, tI);
+            const float2 lR = __ffma2_rn(hR, m1, gR), lI = __ffma2_rn(hI, m1, gI);
+            grh[jj] = __float_as_uint(hR.x), grh[jj + 1] = __float_as_uint(hR.y);
+            grl[jj] = __float_as_uint(lR.x), grl[jj + 1] = __float_as_uint(lR.y);
+            gih[jj] = __float_as_uint(hI.x), gih[jj + 1] = __float_as_uint(hI.y);
+            gil[jj] = __float_as_uint(lI.x), gil[jj + 1] = __float_as_uint(lI.y);
+        }
+    }
+}
+
+//CNEAR
 // ---------------------------------------------------------------------------
 // Stored-operator mode, per-tile store: the same translations with every
 // tile's kernel values read from the tiles the fill pass (tc_near_kernel with
