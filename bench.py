@@ -39,6 +39,12 @@ METRIC = "Mpts·RHS/s, 3D Laplace apply N=1M, err≤1e-6: batched FP32 TC vs pla
 UNIT = "Mpts·RHS/s"
 SM_COUNT = 152
 MUFU_PER_SM_CLK = 16      # MUFU (rsqrt) results per SM per clock
+FP32_PER_SM_CLK = 128     # FP32 lane operations per SM per clock (a paired instruction counts as two)
+# FP32 operations per complex kernel evaluation in tc_cnear_kernel, counted
+# from its source (tc_ceval16 + tc_sincos2): differences 3, r^2 3, r with one
+# Newton step 5, kappa r 1, reduction 3 + 2, z 1, sin 5, cos 5, G_r / G_i 2,
+# TF32 split 8 (touching-leaf tiles add 9, not counted)
+FP32_OPS_HELMHOLTZ_TC = 38
 
 
 # --workload name -> workload in paper_2310_16668_gb300.workloads
@@ -59,7 +65,7 @@ def parse_args():
                         "laplace2d: N = 16384; curves2d: 256 independent 2D point sets on closed curves, "
                         "applied as one CUDA graph; helmholtz2d: kappa = 100, N = 2^20 uniform in 2D")
     p.add_argument("--precision", default=None, choices=["fp32_tc", "fp32", "fp64"],
-                   help="default: fp32_tc for the Laplace kernels, fp32 (complex64) for Helmholtz")
+                   help="default: fp32_tc, fp32 (complex64) for 2D Helmholtz")
     p.add_argument("--nrhs", type=int, default=None, help="default 32 (curves2d: 4)")
     p.add_argument("--tol", type=float, default=None)
     p.add_argument("--n", type=int, default=None, help="override N (testing only)")
@@ -203,14 +209,17 @@ def oracle_direct_sample(kind, x, q0, targets, kappa=0.0):
     return u, time.perf_counter() - t0, direct.num_threads()
 
 
-def roofline(info, phases, clk, prec, pairs):
+def roofline(info, phases, clk, prec, pairs, kind="laplace3d"):
     """The dominant kernel against its roofline: the main translation kernel,
     timed by the plan's own CUDA events on the launching stream inside the
     timed region (skel_set_profiling); the CUDA-core launch for the small
     non-leaf boxes is outside that span. On the fly it is bound by the MUFU
     unit (one operation per kernel evaluation); reading stored tiles, by
     HBM."""
-    if prec == "fp32_tc":
+    if prec == "fp32_tc" and kind == "helmholtz3d":
+        kname, units = "tc_cnear_kernel", info["pairs_tc"]
+        unit_note = "skel_info pairs_tc: kept complex kernel evaluations of the tensor-core items"
+    elif prec == "fp32_tc":
         kname, units = "tc_near_kernel", info["pairs_tc"]
         unit_note = "skel_info pairs_tc: kept kernel evaluations of the tensor-core items"
     else:
@@ -230,6 +239,13 @@ def roofline(info, phases, clk, prec, pairs):
                           f"({sm_mhz:.0f} MHz), one MUFU op per kernel evaluation",
             "per_launch_ms": near_ms_per_launch, "launches_per_step": n_near,
             "algorithmic_units": f"{units} kernel evaluations per launch ({unit_note})"}
+    if kname == "tc_cnear_kernel":
+        # complex: one MUFU operation but ~38 FP32 operations per evaluation
+        # (the sine and cosine are polynomials): the FP32 pipe is the bound
+        peak = SM_COUNT * FP32_PER_SM_CLK * sm_mhz * 1e6 / FP32_OPS_HELMHOLTZ_TC / 1e9
+        roof.update({"peak": peak, "frac": achieved / peak,
+                     "peak_basis": f"{SM_COUNT} SMs x {FP32_PER_SM_CLK} FP32 ops/clk x median SM clock under load "
+                                   f"({sm_mhz:.0f} MHz) / {FP32_OPS_HELMHOLTZ_TC} FP32 ops per complex evaluation"})
     stored = prec == "fp32_tc" and info["stored_tile_bytes"] > 0
     if stored and info["store_mode"] == 1:
         # per-tile store, HBM-bound: the algorithmic bytes are 4 B per kept
@@ -281,8 +297,11 @@ def roofline(info, phases, clk, prec, pairs):
         # the same launch against the tensor pipe: algorithmic 2 flops per
         # evaluation and right-hand side (32 per launch); the pipe issues 3
         # TF32 products (hi.hi + hi.lo + lo.hi) over full 128 x 32 tiles
+        # (complex: 8 real flops per evaluation and complex right-hand side,
+        # 16 per launch, the same 2 x 32 real flops; 6 products issued)
         tc_tflops = units * 2 * 32 / (near_ms_per_launch * 1e-3) / 1e12
-        issued = info["n_tc_tiles"] * 128 * 32 * 32 * 2 * 3 / (near_ms_per_launch * 1e-3) / 1e12
+        n_prod = 6 if kname == "tc_cnear_kernel" else 3
+        issued = info["n_tc_tiles"] * 128 * 32 * 32 * 2 * n_prod / (near_ms_per_launch * 1e-3) / 1e12
         tf32_peak = peaks["bf16_tflops"] * 0.5
         roof["tensor"] = {"achieved": tc_tflops, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc_tflops / tf32_peak,
                           "issued_tflops": issued,
@@ -528,7 +547,9 @@ def run_ours(args):
     fmm = SkelFMM(x, wl.kernel, tol, wl.leaf, kappa=wl.kappa, nrhs_max=nrhs, num_threads=threads,
                   device_build=args.build == "device", store_tiles=args.store_tiles)
     t_build = time.perf_counter() - t0
-    prec = args.precision or ("fp32" if cplx else "fp32_tc")
+    # the tensor-core path covers the 3D kernels and 2D Laplace; 2D Helmholtz
+    # (Bessel functions) runs on the CUDA cores
+    prec = args.precision or ("fp32" if wl.kernel == "helmholtz2d" else "fp32_tc")
     tuning = None
     if args.tune == "auto" and not cplx and prec != "fp64":
         # outside the timed region, like the build: measure the variants on
@@ -662,7 +683,7 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    roof = roofline(info, phases, clk, prec, pairs)
+    roof = roofline(info, phases, clk, prec, pairs, wl.kernel)
     _, peaks_kind = measured_peaks()
     metric = METRIC if args.workload == "laplace3d" else f"Mpts·RHS/s, {wl0.name} apply: {prec} vs plain FP64"
     line = {

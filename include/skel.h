@@ -54,7 +54,9 @@ extern "C" {
 #define SKEL_FP32     1   /* FP32 arithmetic on the CUDA cores, float in/out       */
 #define SKEL_FP32_TC  2   /* FP32 kernel evaluation, tensor-core contractions over
                              right-hand sides (3-pass TF32 split, FP32 accumulate)
-                             in passes of 32 columns; real kernels with nrhs >= 4 —
+                             in passes of 32 columns (3D Helmholtz: 16 complex
+                             columns, [u_r | u_i] = G_r [q_r | q_i] + G_i [-q_i | q_r]);
+                             2D / 3D Laplace and 3D Helmholtz with nrhs >= 4 —
                              otherwise the FP32 CUDA-core path runs */
 
 typedef struct skel_plan* skel_handle;

@@ -293,6 +293,7 @@ void set_tc_attributes() {
     CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcsSmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_sym_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTsySmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_sym_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTsySmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_cnear_kernel<kNSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTccSmemRequest));
     done = true;
 }
 
@@ -323,10 +324,29 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
     t.nrhs = nrhs;
     t.status = dp->status;
     t.wait_ns = dp->test_withhold ? dp->test_wait_ns : kWaitLimitNs;
+    t.kappa = (float)dp->kappa;
     const int kidx = dp->kind == 0 ? 0 : 1;
     const bool stored = dp->tc_a != nullptr;
     set_tc_attributes();
     tc_launches = 0;
+    if constexpr (CPLX) {
+        // 3D Helmholtz: 16 complex right-hand sides per pass
+        for (int r0 = 0; r0 < nrhs; r0 += kTcNc, ++launches, ++tc_launches) {
+            t.r0 = r0;
+            t.withhold_item = (dp->test_withhold && r0 == 0) ? 0 : -1;
+            tc_bprep_kernel<true><<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt,
+                                                                          (const float*)b->Q, nrhs, r0,
+                                                                          (const float4*)b->X, (const float4*)b->Xlo,
+                                                                          (const float4*)dp->chunk_center, dp->tc_b);
+            CUDA_CHECK(cudaGetLastError());
+            ++launches;
+            if (r0 == 0) mark(dp, kMainEvent, st);
+            tc_cnear_kernel<kNSC><<<(unsigned)dp->n_tc, kTcThreads, kTccSmemRequest, st>>>(t);
+            CUDA_CHECK(cudaGetLastError());
+        }
+        dp->test_withhold = false;
+        return launches;
+    }
     for (int r0 = 0; r0 < nrhs; r0 += kTcN, ++launches, ++tc_launches) {
         t.r0 = r0;
         t.withhold_item = (dp->test_withhold && r0 == 0) ? 0 : -1;
@@ -398,7 +418,7 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
     int main_launches = 0;
     {
         Range r("translations");
-        const bool tc = use_tc && !CPLX && sizeof(Real) == 4 && dp->n_tc > 0;
+        const bool tc = use_tc && (!CPLX || dp->kind == 2) && sizeof(Real) == 4 && dp->n_tc > 0;
         if (tc) {
             launches += run_tc<Real, CPLX>(dp, b, nrhs, st, main_launches);
             mark(dp, 3, st);
@@ -725,12 +745,12 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, i
         dp->tc_tiles = upload(lay.tc_tiles, dp->bytes);
         dp->tc_items = upload(lay.tc_items, dp->bytes);
         dp->n_tc = (int64_t)lay.tc_items.size();
-        if (dp->n_tc > 0 && !dp->cplx) {
+        if (dp->n_tc > 0 && (!dp->cplx || dp->kind == 2)) {
             dp->chunk_start = upload(lay.chunk_start, dp->bytes);
             dp->chunk_cnt = upload(lay.chunk_cnt, dp->bytes);
             dp->chunk_center = upload(lay.chunk_center, dp->bytes);
             dp->n_chunks = (int64_t)lay.chunk_start.size();
-            dp->tc_b = dalloc<float>((size_t)dp->n_chunks * kChunkFloats, dp->bytes);
+            dp->tc_b = dalloc<float>((size_t)dp->n_chunks * (dp->cplx ? kChunkFloatsC : kChunkFloats), dp->bytes);
         }
         dp->tc_n_slots = lay.tc_n_slots;
         dp->tc_part_ptr = upload(lay.tc_part_ptr, dp->bytes);
@@ -849,7 +869,9 @@ void device_apply(DevicePlan* dp, const void* q, void* u, int nrhs, int precisio
         if (dp->cplx) run_apply<double, true>(dp, dp->p64, q, u, nrhs, transpose, false, st);
         else run_apply<double, false>(dp, dp->p64, q, u, nrhs, transpose, false, st);
     } else if (dp->cplx) {
-        run_apply<float, true>(dp, dp->p32, q, u, nrhs, transpose, false, st);
+        // tensor-core translations for 3D Helmholtz, one pass per 16 right-hand sides
+        const bool tc = precision == 2 && nrhs >= 4 && dp->kind == 2;
+        run_apply<float, true>(dp, dp->p32, q, u, nrhs, transpose, tc, st);
     } else if (precision == 2 && nrhs >= 4) {
         // tensor-core translations, one pass per 32 right-hand sides
         run_apply<float, false>(dp, dp->p32, q, u, nrhs, transpose, true, st);

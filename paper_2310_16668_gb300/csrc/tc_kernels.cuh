@@ -145,6 +145,7 @@ struct TcArgs {
     const ItemSym* isym;                       // stored-operator mode: per item
     int nrhs;                                  // right-hand sides (row length of U)
     int r0;                                    // first right-hand side of this pass
+    float kappa;                               // Helmholtz wavenumber (complex path)
     int* status;
     uint64_t wait_ns;                          // limit of every bounded wait (kWaitLimitNs)
     int withhold_item;                         // test hook: this item's first tile is copied only
@@ -350,8 +351,10 @@ __device__ __forceinline__ void tc_eval16(const float* c, const float4* xl, int 
 // minus the box centre: FP32 then resolves them to the box size, not to the
 // domain size) and their lo parts; entries past the chunk and columns past
 // nrhs are zero.
-// Complex charges (CPLX): column n < 16 holds the real part of right-hand
-// side r0 + n, column 16 + n its imaginary part (Q interleaved (re, im)).
+// Complex charges (CPLX, the blob of tc_cnear_kernel): B column n < 16 holds
+// the real part of right-hand side r0 + n, column 16 + n its imaginary part
+// (Q interleaved (re, im)); B' = [-imaginary | real] follows B; then the
+// coordinates.
 // Thread: n = tid % 32, sources 4 (tid / 32) .. +3.
 template <bool CPLX = false>
 __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict__ chunk_start,
@@ -359,27 +362,41 @@ __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict
                                                        const float* __restrict__ Q, int nrhs, int r0,
                                                        const float4* __restrict__ X, const float4* __restrict__ Xlo,
                                                        const float4* __restrict__ center, float* __restrict__ B) {
+    constexpr int kBlob = CPLX ? 4 * 1024 + 2 * 128 : kChunkFloats;
+    constexpr int kXoff = CPLX ? 4096 : 2048;
     const int64_t ch = blockIdx.x;
     const int n = threadIdx.x & 31, jq = threadIdx.x >> 5;
     const int64_t start = chunk_start[ch];
     const int cnt = chunk_cnt[ch];
     const int rr = CPLX ? r0 + (n & 15) : r0 + n;         // the right-hand side of column n
-    float v[4];
+    float v[4], w[4];                                      // B and (CPLX) B' of column n
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const int j = 4 * jq + c;
-        v[c] = 0.f;
-        if (j < cnt && rr < nrhs) v[c] = CPLX ? Q[2 * ((start + j) * nrhs + rr) + (n >> 4)] : Q[(start + j) * nrhs + rr];
+        v[c] = w[c] = 0.f;
+        if (j < cnt && rr < nrhs) {
+            if constexpr (CPLX) {
+                const float2 z = reinterpret_cast<const float2*>(Q)[(start + j) * nrhs + rr];
+                v[c] = n < 16 ? z.x : z.y;
+                w[c] = n < 16 ? -z.y : z.x;
+            } else {
+                v[c] = Q[(start + j) * nrhs + rr];
+            }
+        }
     }
-    float4 h, l;
-    h.x = __uint_as_float(to_tf32(v[0]));
-    h.y = __uint_as_float(to_tf32(v[1]));
-    h.z = __uint_as_float(to_tf32(v[2]));
-    h.w = __uint_as_float(to_tf32(v[3]));
-    l = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
-    float* blob = B + ch * kChunkFloats;
-    *reinterpret_cast<float4*>(blob + jq * 128 + n * 4) = h;
-    *reinterpret_cast<float4*>(blob + 1024 + jq * 128 + n * 4) = l;
+    float* blob = B + ch * kBlob;
+#pragma unroll
+    for (int part = 0; part < (CPLX ? 2 : 1); ++part) {
+        const float* x = part ? w : v;
+        float4 h, l;
+        h.x = __uint_as_float(to_tf32(x[0]));
+        h.y = __uint_as_float(to_tf32(x[1]));
+        h.z = __uint_as_float(to_tf32(x[2]));
+        h.w = __uint_as_float(to_tf32(x[3]));
+        l = make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w);
+        *reinterpret_cast<float4*>(blob + 2048 * part + jq * 128 + n * 4) = h;
+        *reinterpret_cast<float4*>(blob + 2048 * part + 1024 + jq * 128 + n * 4) = l;
+    }
     // the chunk's coordinates: hi parts measured from the box centre, then
     // the lo parts (zero past cnt)
     if (threadIdx.x < 64) {
@@ -393,7 +410,7 @@ __global__ void __launch_bounds__(256) tc_bprep_kernel(const int64_t* __restrict
                 c = Xlo[start + j];
             }
         }
-        reinterpret_cast<float4*>(blob + 2048)[threadIdx.x] = c;
+        reinterpret_cast<float4*>(blob + kXoff)[threadIdx.x] = c;
     }
 }
 
@@ -662,43 +679,94 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
 }
 
 // ---------------------------------------------------------------------------
-// 3D Helmholtz (complex64) on the tensor cores. The B operand of a chunk holds
-// 16 complex right-hand sides as 32 real columns (real parts, then imaginary
-// parts; tc_bprep_kernel<true>), in the layout of the real path; the A
-// operand of a tile is the kernel block's real and imaginary parts G_r, G_i
-// (each split into TF32 hi + lo). Per tile the MMA issuer forms
-// D_r = G_r B and D_i = G_i B (12 MMAs each), and the drain combines
-// u_r += D_r[re] - D_i[im], u_i += D_r[im] + D_i[re]. Tensor memory: D_r, D_i
-// of two tiles (128 columns) and three A buffers of G_r hi, lo, G_i hi, lo
-// (3 x 128 columns): all 512 columns, one CTA per SM.
+// 3D Helmholtz (complex64) on the tensor cores: u = G q with G = G_r + i G_i
+// and q = q_r + i q_i is u_r = G_r q_r - G_i q_i, u_i = G_r q_i + G_i q_r, so
+// one real accumulator of 32 columns holds [u_r | u_i] of 16 right-hand sides
+// as G_r B + G_i B' with B = [q_r | q_i] and B' = [-q_i | q_r]
+// (tc_bprep_kernel<true> writes both, TF32 hi + lo). Per tile the MMA issuer
+// adds 12 MMAs of G_r (hi, lo) against B and 12 of G_i against B'. Tensor
+// memory: the accumulators of two tiles (64 columns) and three A buffers of
+// G_r hi, G_r lo, G_i hi, G_i lo (3 x 128 columns): 512 columns, one CTA per SM.
 constexpr int kTcNc = 16;                      // complex right-hand sides per pass
-constexpr uint32_t kColAc = 128;               // A[b]: G_r hi, G_r lo, G_i hi, G_i lo at 128 + 128 b
 constexpr uint32_t kTmemColsC = 512;
+constexpr uint32_t kColAc = 64;                // A[b]: G_r hi, G_r lo, G_i hi, G_i lo at 64 + 128 b (+0/32/64/96)
+constexpr int kChunkFloatsC = 4 * 1024 + 2 * 128;
+struct alignas(128) TcStageC {
+    float bhi[32 * 32];                        // B = [q_r | q_i], TF32 hi
+    float blo[32 * 32];                        //   lo
+    float bphi[32 * 32];                       // B' = [-q_i | q_r], TF32 hi
+    float bplo[32 * 32];                       //   lo
+    float4 xh[32];                             // source coordinates (hi)
+    float4 xl[32];                             // lo parts (touching-leaf tiles)
+    SrcTile tile;                              // the tile's descriptor (its own copy)
+};
+static_assert(offsetof(TcStageC, tile) == kChunkFloatsC * 4, "chunk blob is contiguous in the stage");
+constexpr int kNSC = 6;                        // data stages
+template <int NS>
+struct TcSharedC {
+    TcStageC st[NS];
+    float wc[kTcCompute / 32][kMaxSlots * kWarpSlotFloats];
+    float outer[kTcN / kTpr][kTcCompute];
+    uint64_t full[NS], afull[NS], empty[NS];
+    uint32_t tmem;
+};
+constexpr int kTccSmemRequest = 144 * 1024;   // one CTA per SM (512 TMEM columns)
+static_assert(sizeof(TcSharedC<kNSC>) <= kTccSmemRequest, "shared memory plan");
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                 : "r"(taddr) : "memory");
+__device__ __forceinline__ float2 tc_f2(float x) { return make_float2(x, x); }
+
+// sin and cos of two non-negative arguments x below ~1e4: x = n pi/2 + y with
+// |y| <= pi/4 (Cody and Waite's reduction, pi/2 as a sum of three floats, the
+// first with 8 significant bits so that n C1 is exact), the Taylor series of
+// sin y to the y^9 term and of cos y to the y^10 term (truncation error below
+// 2e-9 on |y| <= pi/4), then the quadrant n mod 4 (sin, cos) -> (cos, -sin)
+// -> (-sin, -cos) -> (-cos, sin). FP32 FMA pipe only, two arguments per
+// paired instruction.
+__device__ __forceinline__ void tc_sincos2(float2 x, float2& s, float2& c) {
+    constexpr double kHalfPi = 1.57079632679489661923132169163975;
+    constexpr float kC1 = 1.5703125f;
+    constexpr float kC2 = (float)(kHalfPi - 1.5703125);
+    constexpr float kC3 = (float)(kHalfPi - 1.5703125 - (double)kC2);
+    constexpr float kTwoOverPi = (float)(1.0 / kHalfPi);
+    const float nx = rintf(x.x * kTwoOverPi), ny = rintf(x.y * kTwoOverPi);
+    const float2 mn = make_float2(-nx, -ny);
+    float2 y = __ffma2_rn(mn, tc_f2(kC1), x);
+    y = __ffma2_rn(mn, tc_f2(kC2), y);
+    y = __ffma2_rn(mn, tc_f2(kC3), y);
+    const float2 z = __fmul2_rn(y, y);
+    float2 ps = __ffma2_rn(z, tc_f2((float)(1.0 / 362880.0)), tc_f2((float)(-1.0 / 5040.0)));
+    ps = __ffma2_rn(z, ps, tc_f2((float)(1.0 / 120.0)));
+    ps = __ffma2_rn(z, ps, tc_f2((float)(-1.0 / 6.0)));
+    const float2 sy = __ffma2_rn(__fmul2_rn(y, z), ps, y);
+    float2 pc = __ffma2_rn(z, tc_f2((float)(-1.0 / 3628800.0)), tc_f2((float)(1.0 / 40320.0)));
+    pc = __ffma2_rn(z, pc, tc_f2((float)(-1.0 / 720.0)));
+    pc = __ffma2_rn(z, pc, tc_f2((float)(1.0 / 24.0)));
+    pc = __ffma2_rn(z, pc, tc_f2(-0.5f));
+    const float2 cy = __ffma2_rn(z, pc, tc_f2(1.0f));
+    const int qx = (int)nx & 3, qy = (int)ny & 3;
+    s.x = (qx & 1) ? cy.x : sy.x;
+    c.x = (qx & 1) ? sy.x : cy.x;
+    s.y = (qy & 1) ? cy.y : sy.y;
+    c.y = (qy & 1) ? sy.y : cy.y;
+    if (qx & 2) s.x = -s.x;
+    if ((qx + 1) & 2) c.x = -c.x;
+    if (qy & 2) s.y = -s.y;
+    if ((qy + 1) & 2) c.y = -c.y;
 }
 
 // e^{i kappa r} / r without its 1/(4 pi), for 16 sources (as tc_eval16): the
 // reciprocal square root as in the real path (0 for masked sources and, on
 // touching leaves, for r^2 <= FLT_MIN), r = r^2 / r corrected by one Newton
-// step, the phase kappa r reduced to [-pi, pi] by Cody and Waite's method
-// (2 pi as a sum of two floats) and then the hardware sine and cosine
-// (absolute error below 2^-21.4 on [-pi, pi]). Masked sources get kappa r = 0,
-// so their value is exactly 0.
+// step, then tc_sincos2 of kappa r. A zero reciprocal gives kappa r = 0 (not
+// the NaN of +inf * 0), so masked sources have the value 0 exactly.
 template <bool ADJ>
 __device__ __forceinline__ void tc_ceval16(const float* c, const float4* xl, int j0, float4 nt, float4 nl,
                                            float kappa, uint32_t* grh, uint32_t* grl, uint32_t* gih, uint32_t* gil) {
     constexpr int AX = kSrcPerThread;
-    constexpr float kTwoPiHi = 6.28125f;
-    constexpr float kTwoPiLo = (float)(6.283185307179586476925 - 6.28125);
-    constexpr float kInvTwoPi = (float)(1.0 / 6.283185307179586476925);
-    const float2 ntx = make_float2(nt.x, nt.x), nty = make_float2(nt.y, nt.y), ntz = make_float2(nt.z, nt.z);
+    const float2 ntx = tc_f2(nt.x), nty = tc_f2(nt.y), ntz = tc_f2(nt.z);
     float2 nlx, nly, nlz;
-    if (ADJ) nlx = make_float2(nl.x, nl.x), nly = make_float2(nl.y, nl.y), nlz = make_float2(nl.z, nl.z);
-    const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
+    if (ADJ) nlx = tc_f2(nl.x), nly = tc_f2(nl.y), nlz = tc_f2(nl.z);
+    const float2 m1 = tc_f2(-1.f), split = tc_f2(8193.f), kap = tc_f2(kappa), half = tc_f2(0.5f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const float4 X = *reinterpret_cast<const float4*>(&c[4 * q]);
@@ -719,22 +787,19 @@ __device__ __forceinline__ void tc_ceval16(const float* c, const float4* xl, int
             float2 r2 = __fmul2_rn(dx, dx);
             r2 = __ffma2_rn(dy, dy, r2);
             r2 = __ffma2_rn(dz, dz, r2);
-            float gr[2], gi[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const float rr = e ? r2.y : r2.x;
-                const float ri = tc_green<1, ADJ>(rr);
-                float r = rr * ri;
-                r = fmaf(0.5f * ri, fmaf(-r, r, rr), r);      // one Newton step: r = sqrt(r^2)
-                const float kr = ri > 0.f ? kappa * r : 0.f;
-                const float n = rintf(kr * kInvTwoPi);
-                const float y = fmaf(-n, kTwoPiLo, fmaf(-n, kTwoPiHi, kr));
-                gr[e] = __cosf(y) * ri;
-                gi[e] = __sinf(y) * ri;
-            }
-            const float2 gR = make_float2(gr[0], gr[1]), gI = make_float2(gi[0], gi[1]);
+            const float2 ri = make_float2(tc_green<1, ADJ>(r2.x), tc_green<1, ADJ>(r2.y));
+            float2 r = __fmul2_rn(r2, ri);
+            r = __ffma2_rn(__fmul2_rn(half, ri), __ffma2_rn(__fmul2_rn(r, m1), r, r2), r);
+            float2 kr = __fmul2_rn(kap, r);
+            kr.x = ri.x > 0.f ? kr.x : 0.f;
+            kr.y = ri.y > 0.f ? kr.y : 0.f;
+            float2 sn, cs;
+            tc_sincos2(kr, sn, cs);
+            const float2 gR = __fmul2_rn(cs, ri), gI = __fmul2_rn(sn, ri);
+            // Veltkamp's split of both parts (as tc_eval16)
             const float2 tR = __fmul2_rn(gR, split), tI = __fmul2_rn(gI, split);
-            const float2 hR = __ffma2_rn(__ffma2_rn(gR, m1, tR), m1, tR), hI = __ffma2_rn(__ffma2_rn(gI, m1, tI), m1, tI);
+            const float2 hR = __ffma2_rn(__ffma2_rn(gR, m1, tR), m1, tR);
+            const float2 hI = __ffma2_rn(__ffma2_rn(gI, m1, tI), m1, tI);
             const float2 lR = __ffma2_rn(hR, m1, gR), lI = __ffma2_rn(hI, m1, gI);
             grh[jj] = __float_as_uint(hR.x), grh[jj + 1] = __float_as_uint(hR.y);
             grl[jj] = __float_as_uint(lR.x), grl[jj + 1] = __float_as_uint(lR.y);
@@ -744,7 +809,201 @@ __device__ __forceinline__ void tc_ceval16(const float* c, const float4* xl, int
     }
 }
 
-//CNEAR
+// One CTA per tensor-core item, the roles and barriers of tc_near_kernel;
+// 16 complex right-hand sides per pass (a.r0 .. a.r0 + 15), U complex64 rows.
+template <int NS = kNSC>
+__global__ void __launch_bounds__(kTcThreads, 1) tc_cnear_kernel(const TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSharedC<NS>& S = *reinterpret_cast<TcSharedC<NS>*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const TcItem* itp = a.items + blockIdx.x;
+    const int64_t row_off = itp->row_off;
+    const int nrows = itp->nrows, nslot = itp->nslot, list_lo = itp->list_lo;
+    const int ntile = itp->list_hi - list_lo;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sm_addr(&S.afull[s])), "r"(kTcCompute));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.empty[s])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(sm_addr(&S.tmem)), "r"(kTmemColsC));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = S.tmem;
+    bool err = false;
+
+    if (warp == kTcCompute / 32) {
+        // ---------------- producer warp ----------------
+        for (int t0 = 0; t0 < ntile; t0 += 32) {
+            const int d_chunk = t0 + lane < ntile ? a.tiles[list_lo + t0 + lane].chunk : 0;
+            const int nb = min(32, ntile - t0);
+            for (int i = 0; i < nb; ++i) {
+                const int t = t0 + i;
+                const int s = t % NS;
+                const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
+                if (t >= NS && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - NS) / NS) & 1), a.wait_ns)) err = true;
+                const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
+                if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
+                if (lane == 0) {
+                    const uint32_t bar = sm_addr(&S.full[s]);
+                    mbar_arrive_tx(bar, 4u * kChunkFloatsC + 64u);
+                    bulk_g2s_hint(sm_addr(S.st[s].bhi), a.B + (int64_t)chunk * kChunkFloatsC, 4u * kChunkFloatsC, bar,
+                                  l2_evict_last());
+                    bulk_g2s_hint(sm_addr(&S.st[s].tile), a.tiles + list_lo + t, 64u, bar, l2_evict_first());
+                    if (hold && !mbar_wait(bar, 0u, a.wait_ns)) err = true;
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0) {
+            for (int t = (ntile > NS ? ntile - NS : 0); t < ntile; ++t)
+                if (!mbar_wait(sm_addr(&S.full[t % NS]), (uint32_t)((t / NS) & 1), a.wait_ns)) err = true;
+        }
+    } else if (warp == kTcCompute / 32 + 1) {
+        // ---------------- MMA issuer (one thread) ----------------
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                                   ((128u >> 4) << 24);
+            for (int m = 0; m < ntile; ++m) {
+                const int s = m % NS, ab = m % kNA;
+                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / NS) & 1), a.wait_ns)) err = true;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t bh = sm_addr(S.st[s].bhi), bl = sm_addr(S.st[s].blo);
+                const uint32_t bph = sm_addr(S.st[s].bphi), bpl = sm_addr(S.st[s].bplo);
+                const uint32_t d = tbase + kColD + 32u * (m & 1);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t arh = tbase + kColAc + 128u * ab + 8u * k, arl = arh + 32u;
+                    const uint32_t aih = arh + 64u, ail = arh + 96u;
+                    const uint32_t ko = 2u * kBLbo * k;
+                    mma_tf32(d, arh, smem_desc(bh + ko), idesc, k > 0 ? 1u : 0u);
+                    mma_tf32(d, arh, smem_desc(bl + ko), idesc, 1u);
+                    mma_tf32(d, arl, smem_desc(bh + ko), idesc, 1u);
+                    mma_tf32(d, aih, smem_desc(bph + ko), idesc, 1u);
+                    mma_tf32(d, aih, smem_desc(bpl + ko), idesc, 1u);
+                    mma_tf32(d, ail, smem_desc(bph + ko), idesc, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(sm_addr(&S.empty[s])) : "memory");
+            }
+        }
+    } else {
+        // ---------------- compute warps ----------------
+        const int row = tid & 127, half = tid >> 7;
+        const bool valid = row < nrows;
+        int myslot = 0;
+        for (int c = 1; c < nslot; ++c)
+            if (row >= itp->slot_start[c]) myslot = c;
+        float4 tx = make_float4(0.f, 0.f, 0.f, 0.f), tl = tx;
+        if (valid) {
+            tx = a.X[row_off + row];
+            tl = a.Xlo[row_off + row];
+        }
+        const float4 nl = make_float4(-tl.x, -tl.y, -tl.z, 0.f);
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        const int r_first = 32 * (warp & 3), r_last = min(r_first + 31, nrows - 1);
+        int s_lo = 0, s_hi = 0;
+        for (int c = 1; c < nslot; ++c) {
+            if (r_first >= itp->slot_start[c]) s_lo = c;
+            if (r_last >= itp->slot_start[c]) s_hi = c;
+        }
+        const int nsw = max(1, s_hi - s_lo + 1);
+        const int myloc = min(max(myslot - s_lo, 0), kMaxSlots - 1);
+        float* wc = S.wc[warp];
+        constexpr int kCols = kTcN / kTpr;                     // half 0: u_r, half 1: u_i of 16 right-hand sides
+        constexpr uint32_t kKeepMask = kSrcPerThread == 32 ? 0xFFFFFFFFu : (1u << kSrcPerThread) - 1u;
+        const int j0 = kSrcPerThread * half;
+        float acc[kCols];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+            acc[c] = 0.f;
+            S.outer[c][tid] = 0.f;
+        }
+        auto drain = [&](int m) {
+            if (!mbar_wait(sm_addr(&S.empty[m % NS]), (uint32_t)((m / NS) & 1), a.wait_ns)) err = true;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t v[kCols];
+            tmem_ld16(tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kCols * half), v);
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) acc[c] += __uint_as_float(v[c]);
+            if (m % kTcGroup == kTcGroup - 1) {
+#pragma unroll
+                for (int c = 0; c < kCols; ++c) {
+                    S.outer[c][tid] += acc[c];
+                    acc[c] = 0.f;
+                }
+            }
+        };
+        for (int u = 0; u < ntile; ++u) {
+            const int s = u % NS;
+            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / NS) & 1), a.wait_ns)) err = true;
+            TcStageC& st = S.st[s];
+            const bool adj = (st.tile.flags & TASK_ADJ) != 0;
+            const float cx = st.tile.cen[0], cy = st.tile.cen[1], cz = st.tile.cen[2];
+            const float4 nt = adj ? make_float4(cx - tx.x, cy - tx.y, cz - tx.z, 0.f)
+                                  : make_float4((cx - tx.x) - tl.x, (cy - tx.y) - tl.y, (cz - tx.z) - tl.z, 0.f);
+            const uint32_t keep = valid ? (st.tile.keep[myslot] >> j0) & kKeepMask : 0u;
+            __syncwarp();
+            for (int p = lane; p < nsw * kSrcPerThread; p += 32) {
+                const int ls = p / kSrcPerThread, jj = p % kSrcPerThread;
+                const float4 v = st.xh[j0 + jj];
+                const bool kept = ((st.tile.keep[s_lo + ls] >> (j0 + jj)) & 1u) != 0u;
+                float* d = wc + ls * kWarpSlotFloats + jj;
+                d[0] = kept ? v.x : kFar;
+                d[kSrcPerThread] = kept ? v.y : kFar;
+                d[2 * kSrcPerThread] = kept ? v.z : kFar;
+            }
+            __syncwarp();
+            if (u >= 2) drain(u - 2);
+            const uint32_t acol = tbase + lane_off + kColAc + 128u * (u % kNA) + (uint32_t)j0;
+            const float* c = wc + myloc * kWarpSlotFloats;
+            const bool none = __all_sync(0xffffffffu, keep == 0);
+            static_assert(kSrcPerThread == 16, "one group of 16 sources per thread");
+            uint32_t grh[16], grl[16], gih[16], gil[16];
+            if (none) {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) grh[jj] = grl[jj] = gih[jj] = gil[jj] = 0u;
+            } else if (adj) {
+                tc_ceval16<true>(c, st.xl, j0, nt, nl, a.kappa, grh, grl, gih, gil);
+            } else {
+                tc_ceval16<false>(c, st.xl, j0, nt, nl, a.kappa, grh, grl, gih, gil);
+            }
+            tmem_st16(acol, grh);
+            tmem_st16(acol + 32u, grl);
+            tmem_st16(acol + 64u, gih);
+            tmem_st16(acol + 96u, gil);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(sm_addr(&S.afull[s]));
+        }
+        for (int m = (ntile >= 2 ? ntile - 2 : 0); m < ntile; ++m) drain(m);
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) acc[c] += S.outer[c][tid];
+        if (valid) {
+            const float scale = (float)green_scale<2>();
+            const int64_t base = (row_off + row) * a.nrhs;
+#pragma unroll
+            for (int c = 0; c < kCols; ++c)
+                if (a.r0 + c < a.nrhs) a.U[2 * (base + a.r0 + c) + half] = scale * acc[c];
+        }
+    }
+    if (err) atomicExch(a.status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(kTmemColsC));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Stored-operator mode, per-tile store: the same translations with every
 // tile's kernel values read from the tiles the fill pass (tc_near_kernel with

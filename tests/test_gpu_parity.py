@@ -95,6 +95,30 @@ def test_tensor_core_many_rhs(nrhs, b):
         assert relerr(u64[:, r], oap.skeleton_apply(sk, q[:, r])) < 1e-12
 
 
+@pytest.mark.parametrize("nrhs,b", [(16, 64), (21, 64), (16, 128)])
+def test_tensor_core_helmholtz_many_rhs(nrhs, b):
+    """Complex tensor-core translations (3D Helmholtz, kappa = 25): 21
+    right-hand sides = one full pass of 16 and a ragged one; leaf size 128
+    puts touching leaves (coincident-free close pairs) on the tensor cores.
+    Every column against the FP64 apply, and the transposed apply."""
+    x = W.points_uniform(30000, 3, 33)
+    sk = osk.Skeletons(otree.Tree(x, b), "helmholtz3d", 1e-6, kappa=KAPPA)
+    fmm = SkelFMM.from_plan(x, "helmholtz3d", oplan.to_exchange(sk), kappa=KAPPA, nrhs_max=32)
+    assert fmm.info()["n_tc_items"] > 0
+    q = W.charges_complex(x.shape[0], nrhs, 34)
+    qt = torch.from_numpy(q).cuda()
+    utc = fmm.apply(qt.to(torch.complex64), "fp32_tc").cpu().numpy()
+    fmm.device_status()
+    u64 = fmm.apply(qt, "fp64").cpu().numpy()
+    for r in range(nrhs):
+        assert relerr(utc[:, r], u64[:, r]) < 1e-5, r
+    assert relerr(u64[:, nrhs - 1], oap.skeleton_apply(sk, q[:, nrhs - 1])) < 1e-12
+    vtc = fmm.apply_transpose(qt.to(torch.complex64), "fp32_tc").cpu().numpy()
+    v64 = fmm.apply_transpose(qt, "fp64").cpu().numpy()
+    for r in (0, nrhs - 1):
+        assert relerr(vtc[:, r], v64[:, r]) < 1e-5, r
+
+
 def test_transpose_matches_oracle(oracle_case):
     kind, x, sk, fmm = oracle_case
     q = _charges(kind, x.shape[0], 4, 12)
@@ -229,8 +253,9 @@ def test_full_size_sphere_cluster_sampled():
 
 @pytest.mark.slow
 def test_full_size_helmholtz_sampled():
-    """3D Helmholtz (kappa = 25), N = 2^20: complex64 and complex128 applies
-    at sampled targets against the oracle's complex128 direct sum."""
+    """3D Helmholtz (kappa = 25), N = 2^20: complex128, complex64 and the
+    complex64 tensor-core applies at sampled targets against the oracle's
+    complex128 direct sum."""
     wl = W.HELMHOLTZ3D_1M
     x = wl.make_points()
     q = wl.make_charges(4)
@@ -240,10 +265,11 @@ def test_full_size_helmholtz_sampled():
     qt = torch.from_numpy(q).cuda()
     u64 = fmm.apply(qt, "fp64").cpu().numpy()[tg, 1]
     u32 = fmm.apply(qt.to(torch.complex64), "fp32").cpu().numpy()[tg, 1]
+    utc = fmm.apply(qt.to(torch.complex64), "fp32_tc").cpu().numpy()[tg, 1]
     fmm.device_status()
-    e64, e32 = relerr(u64, ref), relerr(u32, ref)
-    print(f"helmholtz: relerr complex128 {e64:.3e} complex64 {e32:.3e}")
-    assert e64 < 10 * wl.tol and e32 < 10 * wl.tol
+    e64, e32, etc = relerr(u64, ref), relerr(u32, ref), relerr(utc, ref)
+    print(f"helmholtz: relerr complex128 {e64:.3e} complex64 {e32:.3e} complex64 tensor cores {etc:.3e}")
+    assert e64 < 10 * wl.tol and e32 < 10 * wl.tol and etc < 10 * wl.tol
 
 
 def test_helmholtz2d_fp32_kernel_values():
