@@ -384,7 +384,7 @@ int skel_device_status(skel_handle h);
  * so every barrier phase still completes once per tile and nothing faults
  * or hangs; that apply's result is invalid and the next skel_device_status
  * returns SKEL_ERR_TIMEOUT. Later applies are unaffected.
- * Errors: SKEL_ERR_ARG, SKEL_ERR_STATE (host-only plan, complex kernel, or
+ * Errors: SKEL_ERR_ARG, SKEL_ERR_STATE (host-only plan, 2D Helmholtz, or
  * no tensor-core items).
  */
 int skel_test_withhold_tile(skel_handle h, double wait_limit_ms);

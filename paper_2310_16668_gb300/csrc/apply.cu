@@ -341,7 +341,7 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
             CUDA_CHECK(cudaGetLastError());
             ++launches;
             if (r0 == 0) mark(dp, kMainEvent, st);
-            tc_cnear_kernel<kNSC><<<(unsigned)dp->n_tc, kTcThreads, kTccSmemRequest, st>>>(t);
+            tc_cnear_kernel<kNSC><<<(unsigned)dp->n_tc, kThreadsC, kTccSmemRequest, st>>>(t);
             CUDA_CHECK(cudaGetLastError());
         }
         dp->test_withhold = false;

@@ -736,7 +736,8 @@ int skel_test_withhold_tile(skel_handle h, double wait_limit_ms) {
         if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");
         if (!h->dev) throw Error(SKEL_ERR_STATE, "plan was built host-only");
         if (!(wait_limit_ms > 0 && wait_limit_ms <= 2000)) throw Error(SKEL_ERR_ARG, "wait_limit_ms must be in (0, 2000]");
-        if (h->dev->cplx || h->dev->n_tc == 0) throw Error(SKEL_ERR_STATE, "the plan has no tensor-core items");
+        if ((h->dev->cplx && h->dev->kind != SKEL_HELMHOLTZ_3D) || h->dev->n_tc == 0)
+            throw Error(SKEL_ERR_STATE, "the plan has no tensor-core items");
         h->dev->test_wait_ns = (uint64_t)(wait_limit_ms * 1e6);
         h->dev->test_withhold = true;
     });

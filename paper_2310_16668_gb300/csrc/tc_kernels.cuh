@@ -686,11 +686,19 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_near_kernel(const TcArgs a) 
 // (tc_bprep_kernel<true> writes both, TF32 hi + lo). Per tile the MMA issuer
 // adds 12 MMAs of G_r (hi, lo) against B and 12 of G_i against B'. Tensor
 // memory: the accumulators of two tiles (64 columns) and three A buffers of
-// G_r hi, G_r lo, G_i hi, G_i lo (3 x 128 columns): 512 columns, one CTA per SM.
+// G_r hi, G_r lo, G_i hi, G_i lo (3 x 128 columns): 512 columns, one CTA per
+// SM, so the CTA brings its own latency hiding: 4 compute threads per row
+// (16 compute warps), 8 sources of a tile each.
 constexpr int kTcNc = 16;                      // complex right-hand sides per pass
 constexpr uint32_t kTmemColsC = 512;
 constexpr uint32_t kColAc = 64;                // A[b]: G_r hi, G_r lo, G_i hi, G_i lo at 64 + 128 b (+0/32/64/96)
 constexpr int kChunkFloatsC = 4 * 1024 + 2 * 128;
+constexpr int kTprC = 4;                       // compute threads per target row
+constexpr int kComputeC = 128 * kTprC;         // compute threads
+constexpr int kSrcC = 32 / kTprC;              // sources of a tile per compute thread
+constexpr int kColsC = kTcN / kTprC;           // accumulator columns per compute thread
+constexpr int kThreadsC = kComputeC + 64;      // + the producer warp and the MMA warp
+constexpr int kSlotFloatsC = 3 * kSrcC;
 struct alignas(128) TcStageC {
     float bhi[32 * 32];                        // B = [q_r | q_i], TF32 hi
     float blo[32 * 32];                        //   lo
@@ -705,8 +713,8 @@ constexpr int kNSC = 6;                        // data stages
 template <int NS>
 struct TcSharedC {
     TcStageC st[NS];
-    float wc[kTcCompute / 32][kMaxSlots * kWarpSlotFloats];
-    float outer[kTcN / kTpr][kTcCompute];
+    float wc[kComputeC / 32][kMaxSlots * kSlotFloatsC];
+    float outer[kColsC][kComputeC];
     uint64_t full[NS], afull[NS], empty[NS];
     uint32_t tmem;
 };
@@ -715,21 +723,37 @@ static_assert(sizeof(TcSharedC<kNSC>) <= kTccSmemRequest, "shared memory plan");
 
 __device__ __forceinline__ float2 tc_f2(float x) { return make_float2(x, x); }
 
-// sin and cos of two non-negative arguments x below ~1e4: x = n pi/2 + y with
-// |y| <= pi/4 (Cody and Waite's reduction, pi/2 as a sum of three floats, the
-// first with 8 significant bits so that n C1 is exact), the Taylor series of
-// sin y to the y^9 term and of cos y to the y^10 term (truncation error below
-// 2e-9 on |y| <= pi/4), then the quadrant n mod 4 (sin, cos) -> (cos, -sin)
-// -> (-sin, -cos) -> (-cos, sin). FP32 FMA pipe only, two arguments per
-// paired instruction.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                    "r"(v[7]) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// sin and cos of two non-negative arguments x below 2^21: x = n pi/2 + y with
+// |y| <= pi/4. n is rounded to nearest by adding 1.5 * 2^23 (the sum's low
+// mantissa bits are then n, so n mod 4 is read from its bits: no conversion
+// instruction); Cody and Waite's reduction with pi/2 as a sum of three floats,
+// the first with 8 significant bits so that n C1 is exact; the Taylor series
+// of sin y to the y^9 term and of cos y to the y^10 term (truncation error
+// below 2e-9 on |y| <= pi/4); then the quadrant n mod 4 maps (sin, cos) to
+// (sin, cos), (cos, -sin), (-sin, -cos), (-cos, sin), the signs as bit flips.
+// FP32 pipe and integer logic only, two arguments per paired instruction.
 __device__ __forceinline__ void tc_sincos2(float2 x, float2& s, float2& c) {
     constexpr double kHalfPi = 1.57079632679489661923132169163975;
     constexpr float kC1 = 1.5703125f;
     constexpr float kC2 = (float)(kHalfPi - 1.5703125);
     constexpr float kC3 = (float)(kHalfPi - 1.5703125 - (double)kC2);
     constexpr float kTwoOverPi = (float)(1.0 / kHalfPi);
-    const float nx = rintf(x.x * kTwoOverPi), ny = rintf(x.y * kTwoOverPi);
-    const float2 mn = make_float2(-nx, -ny);
+    constexpr float kRound = 12582912.0f;      // 1.5 * 2^23
+    const float2 t = __ffma2_rn(x, tc_f2(kTwoOverPi), tc_f2(kRound));
+    const float2 mn = __ffma2_rn(t, tc_f2(-1.f), tc_f2(kRound));   // -n (exact)
     float2 y = __ffma2_rn(mn, tc_f2(kC1), x);
     y = __ffma2_rn(mn, tc_f2(kC2), y);
     y = __ffma2_rn(mn, tc_f2(kC3), y);
@@ -743,32 +767,30 @@ __device__ __forceinline__ void tc_sincos2(float2 x, float2& s, float2& c) {
     pc = __ffma2_rn(z, pc, tc_f2((float)(1.0 / 24.0)));
     pc = __ffma2_rn(z, pc, tc_f2(-0.5f));
     const float2 cy = __ffma2_rn(z, pc, tc_f2(1.0f));
-    const int qx = (int)nx & 3, qy = (int)ny & 3;
-    s.x = (qx & 1) ? cy.x : sy.x;
-    c.x = (qx & 1) ? sy.x : cy.x;
-    s.y = (qy & 1) ? cy.y : sy.y;
-    c.y = (qy & 1) ? sy.y : cy.y;
-    if (qx & 2) s.x = -s.x;
-    if ((qx + 1) & 2) c.x = -c.x;
-    if (qy & 2) s.y = -s.y;
-    if ((qy + 1) & 2) c.y = -c.y;
+    const uint32_t qx = __float_as_uint(t.x), qy = __float_as_uint(t.y);
+    // sign of sin: bit 1 of n; sign of cos: bit 1 of n + 1
+    const uint32_t ssx = (qx << 30) & 0x80000000u, ssy = (qy << 30) & 0x80000000u;
+    const uint32_t csx = ((qx + 1u) << 30) & 0x80000000u, csy = ((qy + 1u) << 30) & 0x80000000u;
+    s.x = __uint_as_float(__float_as_uint((qx & 1u) ? cy.x : sy.x) ^ ssx);
+    c.x = __uint_as_float(__float_as_uint((qx & 1u) ? sy.x : cy.x) ^ csx);
+    s.y = __uint_as_float(__float_as_uint((qy & 1u) ? cy.y : sy.y) ^ ssy);
+    c.y = __uint_as_float(__float_as_uint((qy & 1u) ? sy.y : cy.y) ^ csy);
 }
 
-// e^{i kappa r} / r without its 1/(4 pi), for 16 sources (as tc_eval16): the
-// reciprocal square root as in the real path (0 for masked sources and, on
-// touching leaves, for r^2 <= FLT_MIN), r = r^2 / r corrected by one Newton
-// step, then tc_sincos2 of kappa r. A zero reciprocal gives kappa r = 0 (not
-// the NaN of +inf * 0), so masked sources have the value 0 exactly.
-template <bool ADJ>
-__device__ __forceinline__ void tc_ceval16(const float* c, const float4* xl, int j0, float4 nt, float4 nl,
-                                           float kappa, uint32_t* grh, uint32_t* grl, uint32_t* gih, uint32_t* gil) {
-    constexpr int AX = kSrcPerThread;
+// e^{i kappa r} / r without its 1/(4 pi), for CNT sources (as tc_eval16):
+// the reciprocal square root as in the real path (0 for masked sources and,
+// on touching leaves, for r^2 <= FLT_MIN), r = r^2 / r corrected by one
+// Newton step, then tc_sincos2 of kappa r. A zero reciprocal gives
+// kappa r = 0 (not the NaN of +inf * 0), so masked sources have the value 0.
+template <bool ADJ, int CNT, int AX>
+__device__ __forceinline__ void tc_ceval(const float* c, const float4* xl, int j0, float4 nt, float4 nl,
+                                         float kappa, uint32_t* grh, uint32_t* grl, uint32_t* gih, uint32_t* gil) {
     const float2 ntx = tc_f2(nt.x), nty = tc_f2(nt.y), ntz = tc_f2(nt.z);
     float2 nlx, nly, nlz;
     if (ADJ) nlx = tc_f2(nl.x), nly = tc_f2(nl.y), nlz = tc_f2(nl.z);
     const float2 m1 = tc_f2(-1.f), split = tc_f2(8193.f), kap = tc_f2(kappa), half = tc_f2(0.5f);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < CNT / 4; ++q) {
         const float4 X = *reinterpret_cast<const float4*>(&c[4 * q]);
         const float4 Y = *reinterpret_cast<const float4*>(&c[AX + 4 * q]);
         const float4 Z = *reinterpret_cast<const float4*>(&c[2 * AX + 4 * q]);
@@ -809,10 +831,11 @@ __device__ __forceinline__ void tc_ceval16(const float* c, const float4* xl, int
     }
 }
 
-// One CTA per tensor-core item, the roles and barriers of tc_near_kernel;
-// 16 complex right-hand sides per pass (a.r0 .. a.r0 + 15), U complex64 rows.
+// One CTA per tensor-core item, the roles and barriers of tc_near_kernel
+// (kComputeC compute threads); 16 complex right-hand sides per pass
+// (a.r0 .. a.r0 + 15), U complex64 rows.
 template <int NS = kNSC>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_cnear_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kThreadsC, 1) tc_cnear_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSharedC<NS>& S = *reinterpret_cast<TcSharedC<NS>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -824,7 +847,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_cnear_kernel(const TcArgs a)
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sm_addr(&S.afull[s])), "r"(kTcCompute));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sm_addr(&S.afull[s])), "r"(kComputeC));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.empty[s])));
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -840,7 +863,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_cnear_kernel(const TcArgs a)
     const uint32_t tbase = S.tmem;
     bool err = false;
 
-    if (warp == kTcCompute / 32) {
+    if (warp == kComputeC / 32) {
         // ---------------- producer warp ----------------
         for (int t0 = 0; t0 < ntile; t0 += 32) {
             const int d_chunk = t0 + lane < ntile ? a.tiles[list_lo + t0 + lane].chunk : 0;
@@ -867,7 +890,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_cnear_kernel(const TcArgs a)
             for (int t = (ntile > NS ? ntile - NS : 0); t < ntile; ++t)
                 if (!mbar_wait(sm_addr(&S.full[t % NS]), (uint32_t)((t / NS) & 1), a.wait_ns)) err = true;
         }
-    } else if (warp == kTcCompute / 32 + 1) {
+    } else if (warp == kComputeC / 32 + 1) {
         // ---------------- MMA issuer (one thread) ----------------
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
@@ -896,8 +919,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_cnear_kernel(const TcArgs a)
             }
         }
     } else {
-        // ---------------- compute warps ----------------
-        const int row = tid & 127, half = tid >> 7;
+        // ---------------- compute warps: thread (row, quarter) ----------------
+        const int row = tid & 127, quarter = tid >> 7;
         const bool valid = row < nrows;
         int myslot = 0;
         for (int c = 1; c < nslot; ++c)
@@ -918,25 +941,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_cnear_kernel(const TcArgs a)
         const int nsw = max(1, s_hi - s_lo + 1);
         const int myloc = min(max(myslot - s_lo, 0), kMaxSlots - 1);
         float* wc = S.wc[warp];
-        constexpr int kCols = kTcN / kTpr;                     // half 0: u_r, half 1: u_i of 16 right-hand sides
-        constexpr uint32_t kKeepMask = kSrcPerThread == 32 ? 0xFFFFFFFFu : (1u << kSrcPerThread) - 1u;
-        const int j0 = kSrcPerThread * half;
-        float acc[kCols];
+        constexpr uint32_t kKeepMask = (1u << kSrcC) - 1u;
+        const int j0 = kSrcC * quarter;
+        float acc[kColsC];
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) {
+        for (int c = 0; c < kColsC; ++c) {
             acc[c] = 0.f;
             S.outer[c][tid] = 0.f;
         }
         auto drain = [&](int m) {
             if (!mbar_wait(sm_addr(&S.empty[m % NS]), (uint32_t)((m / NS) & 1), a.wait_ns)) err = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint32_t v[kCols];
-            tmem_ld16(tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kCols * half), v);
+            uint32_t v[kColsC];
+            tmem_ld8(tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kColsC * quarter), v);
 #pragma unroll
-            for (int c = 0; c < kCols; ++c) acc[c] += __uint_as_float(v[c]);
+            for (int c = 0; c < kColsC; ++c) acc[c] += __uint_as_float(v[c]);
             if (m % kTcGroup == kTcGroup - 1) {
 #pragma unroll
-                for (int c = 0; c < kCols; ++c) {
+                for (int c = 0; c < kColsC; ++c) {
                     S.outer[c][tid] += acc[c];
                     acc[c] = 0.f;
                 }
@@ -952,47 +974,49 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_cnear_kernel(const TcArgs a)
                                   : make_float4((cx - tx.x) - tl.x, (cy - tx.y) - tl.y, (cz - tx.z) - tl.z, 0.f);
             const uint32_t keep = valid ? (st.tile.keep[myslot] >> j0) & kKeepMask : 0u;
             __syncwarp();
-            for (int p = lane; p < nsw * kSrcPerThread; p += 32) {
-                const int ls = p / kSrcPerThread, jj = p % kSrcPerThread;
+            for (int p = lane; p < nsw * kSrcC; p += 32) {
+                const int ls = p / kSrcC, jj = p % kSrcC;
                 const float4 v = st.xh[j0 + jj];
                 const bool kept = ((st.tile.keep[s_lo + ls] >> (j0 + jj)) & 1u) != 0u;
-                float* d = wc + ls * kWarpSlotFloats + jj;
+                float* d = wc + ls * kSlotFloatsC + jj;
                 d[0] = kept ? v.x : kFar;
-                d[kSrcPerThread] = kept ? v.y : kFar;
-                d[2 * kSrcPerThread] = kept ? v.z : kFar;
+                d[kSrcC] = kept ? v.y : kFar;
+                d[2 * kSrcC] = kept ? v.z : kFar;
             }
             __syncwarp();
             if (u >= 2) drain(u - 2);
             const uint32_t acol = tbase + lane_off + kColAc + 128u * (u % kNA) + (uint32_t)j0;
-            const float* c = wc + myloc * kWarpSlotFloats;
+            const float* c = wc + myloc * kSlotFloatsC;
             const bool none = __all_sync(0xffffffffu, keep == 0);
-            static_assert(kSrcPerThread == 16, "one group of 16 sources per thread");
-            uint32_t grh[16], grl[16], gih[16], gil[16];
+            uint32_t grh[kSrcC], grl[kSrcC], gih[kSrcC], gil[kSrcC];
             if (none) {
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) grh[jj] = grl[jj] = gih[jj] = gil[jj] = 0u;
+                for (int jj = 0; jj < kSrcC; ++jj) grh[jj] = grl[jj] = gih[jj] = gil[jj] = 0u;
             } else if (adj) {
-                tc_ceval16<true>(c, st.xl, j0, nt, nl, a.kappa, grh, grl, gih, gil);
+                tc_ceval<true, kSrcC, kSrcC>(c, st.xl, j0, nt, nl, a.kappa, grh, grl, gih, gil);
             } else {
-                tc_ceval16<false>(c, st.xl, j0, nt, nl, a.kappa, grh, grl, gih, gil);
+                tc_ceval<false, kSrcC, kSrcC>(c, st.xl, j0, nt, nl, a.kappa, grh, grl, gih, gil);
             }
-            tmem_st16(acol, grh);
-            tmem_st16(acol + 32u, grl);
-            tmem_st16(acol + 64u, gih);
-            tmem_st16(acol + 96u, gil);
+            tmem_st8(acol, grh);
+            tmem_st8(acol + 32u, grl);
+            tmem_st8(acol + 64u, gih);
+            tmem_st8(acol + 96u, gil);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(sm_addr(&S.afull[s]));
         }
         for (int m = (ntile >= 2 ? ntile - 2 : 0); m < ntile; ++m) drain(m);
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) acc[c] += S.outer[c][tid];
+        for (int c = 0; c < kColsC; ++c) acc[c] += S.outer[c][tid];
         if (valid) {
+            // quarter q holds columns 8q .. 8q + 7: real parts of right-hand
+            // sides r0 + 8 (q & 1) .. + 7 (q < 2), their imaginary parts (q >= 2)
             const float scale = (float)green_scale<2>();
             const int64_t base = (row_off + row) * a.nrhs;
+            const int c0 = a.r0 + kColsC * (quarter & 1), part = quarter >> 1;
 #pragma unroll
-            for (int c = 0; c < kCols; ++c)
-                if (a.r0 + c < a.nrhs) a.U[2 * (base + a.r0 + c) + half] = scale * acc[c];
+            for (int c = 0; c < kColsC; ++c)
+                if (c0 + c < a.nrhs) a.U[2 * (base + c0 + c) + part] = scale * acc[c];
         }
     }
     if (err) atomicExch(a.status, 1);

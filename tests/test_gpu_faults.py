@@ -37,13 +37,17 @@ def _gpu():
     _lib.load().skel_test_fail_alloc(0)
 
 
-@pytest.mark.parametrize("stored", [0, 1, 2])
-def test_bounded_wait_runs_out(stored):
-    """On every tensor-core kernel: on the fly, per-tile store, symmetric store."""
+@pytest.mark.parametrize("kind,stored", [("laplace3d", 0), ("laplace3d", 1), ("laplace3d", 2), ("helmholtz3d", 0)])
+def test_bounded_wait_runs_out(kind, stored):
+    """On every tensor-core kernel: on the fly, per-tile store, symmetric
+    store, and the complex (3D Helmholtz) kernel."""
     x = W.points_uniform(20000, 3, 61)
-    fmm = SkelFMM(x, "laplace3d", 1e-6, 64, nrhs_max=32, store_tiles=stored)
+    fmm = SkelFMM(x, kind, 1e-6, 64, nrhs_max=32, store_tiles=stored, kappa=25.0 if kind == "helmholtz3d" else 0.0)
     assert fmm.info()["n_tc_items"] > 0 and fmm.info()["store_mode"] == stored
-    q = torch.from_numpy(W.charges_normal(x.shape[0], 32, 62)).cuda().float()
+    if kind == "helmholtz3d":
+        q = torch.from_numpy(W.charges_complex(x.shape[0], 32, 62)).cuda().to(torch.complex64)
+    else:
+        q = torch.from_numpy(W.charges_normal(x.shape[0], 32, 62)).cuda().float()
     ref = fmm.apply(q, "fp32_tc")
     fmm.device_status()                                          # clean before the hook
     lib = _lib.load()
