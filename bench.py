@@ -143,12 +143,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_sha() -> str:
-    """Hash of the files that define the device kernels' code (the kernels and
-    the structures they read); a committed traffic figure counts only while
-    it matches."""
+def kernel_source_sha(kernel: str = "") -> str:
+    """Hash of the files that define a device kernel's code (the kernels and
+    the structures they read; the complex tensor-core kernel adds its own
+    header); a committed traffic figure counts only while it matches."""
     h = hashlib.sha256()
-    for f in ("skel_kernels.cuh", "tc_kernels.cuh", "host.h"):
+    files = ("skel_kernels.cuh", "tc_kernels.cuh", "host.h")
+    if kernel == "tc_cnear_kernel":
+        files += ("tc_complex.cuh",)
+    for f in files:
         p = os.path.join(ROOT, "paper_2310_16668_gb300", "csrc", f)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
@@ -158,7 +161,7 @@ def kernel_source_sha() -> str:
 def ncu_traffic(kernel: str, precision: str):
     """DRAM bytes per launch of `kernel` from a committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    sha = kernel_source_sha()
+    sha = kernel_source_sha(kernel)
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None

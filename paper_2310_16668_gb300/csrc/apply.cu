@@ -40,6 +40,7 @@
 #include "device.h"
 #include "skel_kernels.cuh"
 #include "tc_kernels.cuh"
+#include "tc_complex.cuh"
 
 namespace skel {
 
