@@ -32,7 +32,7 @@ class SkelKernel(ctypes.Structure):
 class SkelOptions(ctypes.Structure):
     _fields_ = [("proxy_p", ctypes.c_int), ("nrhs_max", ctypes.c_int),
                 ("host_only", ctypes.c_int), ("num_threads", ctypes.c_int), ("device_build", ctypes.c_int),
-                ("store_tiles", ctypes.c_int)]
+                ("store_tiles", ctypes.c_int), ("store_stages", ctypes.c_int)]
 
 
 class SkelStats(ctypes.Structure):
@@ -66,7 +66,7 @@ class SkelTuning(ctypes.Structure):
     _fields_ = [("ms_onfly", ctypes.c_double), ("ms_stored", ctypes.c_double), ("stored", ctypes.c_int),
                 ("n_updown", ctypes.c_int), ("n_changed", ctypes.c_int),
                 ("ms_updown_default", ctypes.c_double), ("ms_updown_tuned", ctypes.c_double),
-                ("tc_stages", ctypes.c_int), ("ms_sym", ctypes.c_double)]
+                ("tc_stages", ctypes.c_int), ("ms_sym", ctypes.c_double), ("tcs_stages", ctypes.c_int)]
 
 
 class SkelError(RuntimeError):

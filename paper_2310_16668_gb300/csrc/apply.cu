@@ -290,8 +290,10 @@ void set_tc_attributes() {
     CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, kRecTiles>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<0, kRecSym>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_near_kernel<1, kRecSym>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemRequest));
-    CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcsSmemRequest));
-    CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcsSmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<0, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcs_smem_request<4>()));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcs_smem_request<4>()));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<0, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcs_smem_request<8>()));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcs_smem_request<8>()));
     CUDA_CHECK(cudaFuncSetAttribute(tc_sym_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTsySmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_sym_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTsySmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_cnear_kernel<kNSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTccSmemRequest));
@@ -363,8 +365,15 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
             if (kidx == 0) tc_sym_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTsySmemRequest, st>>>(t);
             else tc_sym_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTsySmemRequest, st>>>(t);
         } else if (stored) {
-            if (kidx == 0) tc_stored_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTcsSmemRequest, st>>>(t);
-            else tc_stored_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTcsSmemRequest, st>>>(t);
+            // stages per CTA: the autotuner's choice (same arithmetic)
+            const unsigned g = (unsigned)dp->n_tc;
+            if (dp->tcs_stages == 8) {
+                kidx == 0 ? tc_stored_kernel<0, 8><<<g, kTcThreads, tcs_smem_request<8>(), st>>>(t)
+                          : tc_stored_kernel<1, 8><<<g, kTcThreads, tcs_smem_request<8>(), st>>>(t);
+            } else {
+                kidx == 0 ? tc_stored_kernel<0, 4><<<g, kTcThreads, tcs_smem_request<4>(), st>>>(t)
+                          : tc_stored_kernel<1, 4><<<g, kTcThreads, tcs_smem_request<4>(), st>>>(t);
+            }
         } else {
             // pipeline depth: the autotuner's choice (same arithmetic for every depth)
             const unsigned g = (unsigned)dp->n_tc;
@@ -699,8 +708,9 @@ void plan_symmetric_store(const Layout& lay, DevicePlan* dp) {
 
 }  // namespace
 
-DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles) {
+DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles, int store_stages) {
     DevicePlan* dp = new DevicePlan();
+    dp->tcs_stages = store_stages == 8 ? 8 : 4;
     try {
         CUDA_CHECK(cudaGetDevice(&dp->device));
         dp->dim = p.tree.dim;
@@ -968,7 +978,16 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
                     if (free_b <= (size_t)floats * sizeof(float) + ((size_t)2 << 30)) continue;
                     fill_tiles(dp, st, mode);
                 }
-                const double ms = time_ms(tc, 3);
+                double ms = time_ms(tc, 3);
+                if (mode == 1) {
+                    // the per-tile store's stages per CTA: 4 (two CTAs per SM) or 8 (one)
+                    const int keep_stages = dp->tcs_stages;
+                    dp->tcs_stages = keep_stages == 8 ? 4 : 8;
+                    const double ms2 = time_ms(tc, 3);
+                    if (ms2 < ms) ms = ms2;
+                    else dp->tcs_stages = keep_stages;
+                    rep.tcs_stages = dp->tcs_stages;
+                }
                 (mode == 2 ? rep.ms_sym : rep.ms_stored) = ms;
                 if (ms < best) best = ms, best_mode = mode;
             }

@@ -71,6 +71,7 @@ struct DevicePlan {
     // rule), set by the autotuner
     std::vector<int8_t> ud_warps_up, ud_warps_down;
     int tc_stages = 6;                     // bulk-copy stages of the on-the-fly tensor-core kernel (4, 6, 8)
+    int tcs_stages = 4;                    // stages per CTA of the per-tile stored kernel (4 or 8)
     int* status = nullptr;                 // device word raised by a bounded wait that gave up
     // test hook: the next tensor-core pass withholds its first item's first
     // tile until the compute warps gave up, with every wait limited to
@@ -95,7 +96,8 @@ struct DevicePlan {
 // Upload a layout; throws Error on failure. store_tiles: also evaluate every
 // tensor-core tile's kernel values once and keep them (nrows x 128 B per tile), so
 // that FP32_TC applies read them instead of evaluating (real kernels).
-DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles = 0);
+DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles = 0,
+                               int store_stages = 4);
 void device_plan_destroy(DevicePlan* dp);
 // capture the phases of the next max_applies applies (0 = off)
 void device_set_profiling(DevicePlan* dp, int max_applies);
@@ -117,6 +119,7 @@ struct TuneReport {
     int n_levels = 0, n_changed = 0;        // up/down launches timed, choices unlike the default rule
     double ms_updown_default = 0, ms_updown_tuned = 0;  // summed over the levels, one launch each
     int tc_stages = 0;                      // chosen pipeline depth of the on-the-fly kernel (0: not tuned)
+    int tcs_stages = 0;                     // chosen stages per CTA of the per-tile stored kernel (0: not tuned)
 };
 TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* stream);
 

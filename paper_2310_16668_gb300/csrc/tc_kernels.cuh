@@ -699,7 +699,8 @@ static_assert(kSrcPerThread == 16, "stored tiles assume two compute threads per 
 // the outer sums at [192, 224). Two A buffers suffice: the buffer of tile u
 // was last read by MMA(u - 2), which drain(u - 2) has waited for before tile
 // u is written.
-constexpr int kNST = 4;                        // data stages (24 KB each)
+// NST data stages (24 KB each): 4 with two CTAs per SM, or 8 with one CTA
+// per SM (the autotuner times both).
 constexpr int kNAS = 2;                        // A buffers
 constexpr uint32_t kColOuter = 192;
 struct alignas(128) TcTileStage {
@@ -707,18 +708,21 @@ struct alignas(128) TcTileStage {
     float4 ga[kTileFloats / 4];                // the tile's kept quads
     uint32_t qm;                               // which quads (written by the producer)
 };
+template <int NST>
 struct TcTileShared {
-    TcTileStage st[kNST];
-    uint64_t full[kNST], afull[kNST], empty[kNST];
+    TcTileStage st[NST];
+    uint64_t full[NST], afull[NST], empty[NST];
     uint32_t tmem;
 };
-constexpr int kTcsSmemRequest = 100 * 1024;   // two CTAs per SM
-static_assert(sizeof(TcTileShared) <= kTcsSmemRequest, "shared memory plan (per-tile store)");
+template <int NST>
+constexpr int tcs_smem_request() { return NST <= 4 ? 100 * 1024 : 200 * 1024; }
+static_assert(sizeof(TcTileShared<4>) <= tcs_smem_request<4>(), "shared memory plan (per-tile store)");
+static_assert(sizeof(TcTileShared<8>) <= tcs_smem_request<8>(), "shared memory plan (per-tile store)");
 
-template <int KIND>
-__global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a) {
+template <int KIND, int NST>
+__global__ void __launch_bounds__(kTcThreads, NST <= 4 ? 2 : 1) tc_stored_kernel(const TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcTileShared& S = *reinterpret_cast<TcTileShared*>(smem_raw);
+    TcTileShared<NST>& S = *reinterpret_cast<TcTileShared<NST>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const TcItem* itp = a.items + blockIdx.x;
     const int64_t row_off = itp->row_off;
@@ -726,7 +730,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
     const int ntile = itp->list_hi - list_lo;
 
     if (tid == 0) {
-        for (int s = 0; s < kNST; ++s) {
+        for (int s = 0; s < NST; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.full[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sm_addr(&S.afull[s])), "r"(kTcCompute));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.empty[s])));
@@ -754,11 +758,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             const int nb = min(32, ntile - t0);
             for (int i = 0; i < nb; ++i) {
                 const int t = t0 + i;
-                const int s = t % kNST;
+                const int s = t % NST;
                 const int chunk = __shfl_sync(0xffffffffu, d_chunk, i);
                 const uint32_t qm = __shfl_sync(0xffffffffu, d_qm, i);
                 const uint32_t tile_bytes = 16u * (uint32_t)__popc(qm) * (uint32_t)nrows;
-                if (t >= kNST && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kNST) / kNST) & 1), a.wait_ns))
+                if (t >= NST && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - NST) / NST) & 1), a.wait_ns))
                     err = true;
                 const bool hold = t == 0 && (int)blockIdx.x == a.withhold_item;
                 if (hold && !withhold_first_tile(sm_addr(&S.afull[0]), a.wait_ns)) err = true;
@@ -777,8 +781,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             }
         }
         if (lane == 0) {
-            for (int t = (ntile > kNST ? ntile - kNST : 0); t < ntile; ++t)
-                if (!mbar_wait(sm_addr(&S.full[t % kNST]), (uint32_t)((t / kNST) & 1), a.wait_ns)) err = true;
+            for (int t = (ntile > NST ? ntile - NST : 0); t < ntile; ++t)
+                if (!mbar_wait(sm_addr(&S.full[t % NST]), (uint32_t)((t / NST) & 1), a.wait_ns)) err = true;
         }
     } else if (warp == kTcCompute / 32 + 1) {
         // ---------------- MMA issuer (one thread) ----------------
@@ -786,8 +790,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                                    ((128u >> 4) << 24);
             for (int m = 0; m < ntile; ++m) {
-                const int s = m % kNST, ab = m % kNAS;
-                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kNST) & 1), a.wait_ns)) err = true;
+                const int s = m % NST, ab = m % kNAS;
+                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / NST) & 1), a.wait_ns)) err = true;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t bh = sm_addr(S.st[s].b), bl = bh + 4u * 1024u;
                 const uint32_t d = tbase + kColD + 32u * (m & 1);
@@ -834,7 +838,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         };
         auto drain = [&](int m) {
-            if (!mbar_wait(sm_addr(&S.empty[m % kNST]), (uint32_t)((m / kNST) & 1), a.wait_ns)) err = true;
+            if (!mbar_wait(sm_addr(&S.empty[m % NST]), (uint32_t)((m / NST) & 1), a.wait_ns)) err = true;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t v[kCols];
             tmem_ld16(tbase + lane_off + kColD + 32u * (m & 1) + (uint32_t)(kCols * half), v);
@@ -844,8 +848,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_stored_kernel(const TcArgs a
         };
         const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
         for (int u = 0; u < ntile; ++u) {
-            const int s = u % kNST;
-            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / kNST) & 1), a.wait_ns)) err = true;
+            const int s = u % NST;
+            if (!mbar_wait(sm_addr(&S.full[s]), (uint32_t)((u / NST) & 1), a.wait_ns)) err = true;
             uint32_t ghi[16], glo[16];
             // a stale mask after a bounded wait gave up can only pick a quad
             // inside the 16 KB area (at most 8 quads of nrows <= 128 rows)
