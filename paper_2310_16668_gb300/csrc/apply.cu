@@ -232,12 +232,12 @@ void permute(bool out, const DevicePlan* dp, const S* src, S* dst, int nrhs, cud
     const int64_t N = dp->N;
     if (nrhs >= 8) {
         const dim3 grid(ceil_div(N, kPermTile), ceil_div(nrhs, kPermTile));
-        if (out) permute_out<S><<<grid, kPermThreads, 0, st>>>(dp->eop, src, dst, N, nrhs);
-        else permute_in<S><<<grid, kPermThreads, 0, st>>>(dp->eop, src, dst, N, nrhs);
+        if (out) permute_out<S><<<grid, kPermThreads, 0, st>>>(dp->eop, dp->eop2, src, dst, N, nrhs);
+        else permute_in<S><<<grid, kPermThreads, 0, st>>>(dp->eop, dp->eop2, src, dst, N, nrhs);
     } else {
         const int64_t n = N * nrhs;
-        if (out) permute_out_narrow<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->eop, src, dst, N, nrhs);
-        else permute_in_narrow<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->eop, src, dst, N, nrhs);
+        if (out) permute_out_narrow<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->eop, dp->eop2, src, dst, N, nrhs);
+        else permute_in_narrow<S><<<ceil_div(n, 256), 256, 0, st>>>(dp->eop, dp->eop2, src, dst, N, nrhs);
     }
 }
 
@@ -734,15 +734,43 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, i
                 if (v < 0) throw Error(-5, "a point has no leaf entry");
             dp->eop = upload(eop, dp->bytes);
         }
-        dp->up = upload(lay.up, dp->bytes);
-        dp->up_level_ptr = lay.up_level_ptr;
-        const int nl = (int)lay.up_level_ptr.size() - 1;
+        // leaf boxes with no redundant index (k = |I_B|): their upward and
+        // downward steps move to the permutations (eop2, see permute_in);
+        // the level launches get the other boxes
+        std::vector<UpBox> up;
+        dp->up_level_ptr.assign(lay.up_level_ptr.size(), 0);
+        {
+            std::vector<int64_t> point_of(lay.n_tot, -1), eop2(dp->N, -1);
+            for (size_t i = 0; i < lay.perm_entry.size(); ++i) point_of[lay.perm_entry[i]] = lay.perm_point[i];
+            int64_t fused = 0;
+            for (size_t l = 0; l + 1 < lay.up_level_ptr.size(); ++l) {
+                dp->up_level_ptr[l] = (int64_t)up.size();
+                for (int64_t i = lay.up_level_ptr[l]; i < lay.up_level_ptr[l + 1]; ++i) {
+                    const UpBox& u = lay.up[i];
+                    bool fuse = u.k == u.n && i < (int64_t)lay.up_leaf.size() && lay.up_leaf[i];
+                    for (int j = 0; fuse && j < u.k; ++j) {
+                        const int64_t p = point_of[u.off + lay.pos[u.off + j]];
+                        fuse = p >= 0 && eop2[p] < 0;
+                    }
+                    if (!fuse) {
+                        up.push_back(u);
+                        continue;
+                    }
+                    for (int j = 0; j < u.k; ++j) eop2[point_of[u.off + lay.pos[u.off + j]]] = u.dst + j;
+                    ++fused;
+                }
+            }
+            dp->up_level_ptr.back() = (int64_t)up.size();
+            if (fused > 0) dp->eop2 = upload(eop2, dp->bytes);
+        }
+        dp->up = upload(up, dp->bytes);
+        const int nl = (int)dp->up_level_ptr.size() - 1;
         dp->up_level_maxk.assign(std::max(nl, 0), 0);
         dp->up_level_maxr.assign(std::max(nl, 0), 0);
         for (int l = 0; l < nl; ++l)
-            for (int64_t i = lay.up_level_ptr[l]; i < lay.up_level_ptr[l + 1]; ++i) {
-                dp->up_level_maxk[l] = std::max(dp->up_level_maxk[l], lay.up[i].k);
-                dp->up_level_maxr[l] = std::max(dp->up_level_maxr[l], lay.up[i].n - lay.up[i].k);
+            for (int64_t i = dp->up_level_ptr[l]; i < dp->up_level_ptr[l + 1]; ++i) {
+                dp->up_level_maxk[l] = std::max(dp->up_level_maxk[l], up[i].k);
+                dp->up_level_maxr[l] = std::max(dp->up_level_maxr[l], up[i].n - up[i].k);
             }
         dp->task_src = upload(lay.task_src, dp->bytes);
         dp->task_mask = upload(lay.task_mask, dp->bytes);
@@ -814,7 +842,7 @@ void device_plan_destroy(DevicePlan* dp) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(dp->device);
-    void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
+    void* ptrs[] = {dp->box_off, dp->box_n, dp->box_nslot, dp->slot_start, dp->pos, dp->eop, dp->eop2, dp->up, dp->task_src, dp->task_mask, dp->task_flags, dp->items,
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
                     dp->tc_items, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
                     dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a, dp->tc_abase,

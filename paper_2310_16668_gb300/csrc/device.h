@@ -26,6 +26,9 @@ struct DevicePlan {
     int32_t* slot_start = nullptr;
     int32_t* pos = nullptr;
     int64_t* eop = nullptr;                // user point -> its leaf entry
+    int64_t* eop2 = nullptr;               // user point -> its skeleton row in the parent's slot, for
+                                           // leaf boxes whose up/down steps the permutations do (-1: none;
+                                           // null if no box qualifies)
     UpBox* up = nullptr;
     std::vector<int64_t> up_level_ptr;     // host copy
     std::vector<int32_t> up_level_maxk, up_level_maxr;   // per level: largest k, |I| - k

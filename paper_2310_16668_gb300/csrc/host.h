@@ -168,6 +168,7 @@ struct Layout {
     std::vector<int64_t> perm_entry, perm_point;  // leaf entries <-> user points
     std::vector<int32_t> pos;           // n_tot: piv of the owning box
     std::vector<UpBox> up;              // boxes of levels >= max(2, top+1)
+    std::vector<uint8_t> up_leaf;       // per up[] box: 1 if it is a leaf
     std::vector<int64_t> up_level_ptr;  // up[] ranges, index = level
     std::vector<double> T;              // all T, column-major per box
     // near field

@@ -97,6 +97,7 @@ void build_layout(const Plan& p, Layout& lay) {
     // ---- upward / downward boxes -----------------------------------------
     const int lo_up = std::max(2, lay.top + 1);
     lay.up.clear();
+    lay.up_leaf.clear();
     lay.up_level_ptr.assign(t.L + 2, 0);
     for (int l = 0; l <= t.L; ++l) {
         lay.up_level_ptr[l] = (int64_t)lay.up.size();
@@ -113,6 +114,7 @@ void build_layout(const Plan& p, Layout& lay) {
             u.n = lay.box_n[b];
             u.k = sk.k[b];
             lay.up.push_back(u);
+            lay.up_leaf.push_back(t.is_leaf[b] ? 1 : 0);
         }
     }
     lay.up_level_ptr[t.L + 1] = (int64_t)lay.up.size();
@@ -481,6 +483,7 @@ void merge_layouts(const std::vector<const Layout*>& ls, const std::vector<int64
                 u.dst += e0[s];
                 u.T_off += T0[s];
                 m.up.push_back(u);
+                m.up_leaf.push_back(l.up_leaf[i]);
             }
         }
     }

@@ -52,11 +52,18 @@ template <class S> __device__ __forceinline__ S warp_sum(S v) {
 // one row of nrhs per entry). eop[p] = the leaf entry of user point p. A tile
 // of 32 points x 32 right-hand sides goes through shared memory, so the
 // column reads and the row writes are both contiguous.
+// eop2 (may be null): for a point of a leaf box that keeps all its points as
+// skeletons (k = |I_B|, no redundant index), the entry of its skeleton row in
+// the parent's slot, else -1. Such a box's upward step is the copy
+// qhat_S = q_S into that slot and its downward step the sum u_S + uhat_S;
+// permute_in writes the second copy and permute_out adds the slot's value,
+// so the level launches skip the box.
 constexpr int kPermTile = 32;
 constexpr int kPermThreads = 256;
 
 template <class S>
-__global__ void __launch_bounds__(kPermThreads) permute_in(const int64_t* __restrict__ eop, const S* __restrict__ q,
+__global__ void __launch_bounds__(kPermThreads) permute_in(const int64_t* __restrict__ eop,
+                                                           const int64_t* __restrict__ eop2, const S* __restrict__ q,
                                                            S* __restrict__ Q, int64_t N, int nrhs) {
     __shared__ S t[kPermTile][kPermTile + 1];
     const int64_t p0 = (int64_t)blockIdx.x * kPermTile;
@@ -66,18 +73,33 @@ __global__ void __launch_bounds__(kPermThreads) permute_in(const int64_t* __rest
         if (r0 + k < nrhs && p0 + tx < N) t[k][tx] = q[(int64_t)(r0 + k) * N + p0 + tx];
     __syncthreads();
     for (int k = ty; k < kPermTile; k += kPermThreads / kPermTile)
-        if (p0 + k < N && r0 + tx < nrhs) Q[eop[p0 + k] * nrhs + r0 + tx] = t[tx][k];
+        if (p0 + k < N && r0 + tx < nrhs) {
+            const S v = t[tx][k];
+            Q[eop[p0 + k] * nrhs + r0 + tx] = v;
+            if (eop2) {
+                const int64_t e2 = eop2[p0 + k];
+                if (e2 >= 0) Q[e2 * nrhs + r0 + tx] = v;
+            }
+        }
 }
 
 template <class S>
-__global__ void __launch_bounds__(kPermThreads) permute_out(const int64_t* __restrict__ eop, const S* __restrict__ U,
+__global__ void __launch_bounds__(kPermThreads) permute_out(const int64_t* __restrict__ eop,
+                                                            const int64_t* __restrict__ eop2, const S* __restrict__ U,
                                                             S* __restrict__ u, int64_t N, int nrhs) {
     __shared__ S t[kPermTile][kPermTile + 1];
     const int64_t p0 = (int64_t)blockIdx.x * kPermTile;
     const int r0 = blockIdx.y * kPermTile;
     const int tx = threadIdx.x % kPermTile, ty = threadIdx.x / kPermTile;
     for (int k = ty; k < kPermTile; k += kPermThreads / kPermTile)
-        if (p0 + k < N && r0 + tx < nrhs) t[k][tx] = U[eop[p0 + k] * nrhs + r0 + tx];
+        if (p0 + k < N && r0 + tx < nrhs) {
+            S v = U[eop[p0 + k] * nrhs + r0 + tx];
+            if (eop2) {
+                const int64_t e2 = eop2[p0 + k];
+                if (e2 >= 0) v = v + U[e2 * nrhs + r0 + tx];
+            }
+            t[k][tx] = v;
+        }
     __syncthreads();
     for (int k = ty; k < kPermTile; k += kPermThreads / kPermTile)
         if (r0 + k < nrhs && p0 + tx < N) u[(int64_t)(r0 + k) * N + p0 + tx] = t[tx][k];
@@ -86,21 +108,31 @@ __global__ void __launch_bounds__(kPermThreads) permute_out(const int64_t* __res
 // few right-hand sides: one element per thread, points fastest (contiguous
 // column reads / writes on the user side)
 template <class S>
-__global__ void permute_in_narrow(const int64_t* __restrict__ eop, const S* __restrict__ q, S* __restrict__ Q,
-                                  int64_t N, int nrhs) {
+__global__ void permute_in_narrow(const int64_t* __restrict__ eop, const int64_t* __restrict__ eop2,
+                                  const S* __restrict__ q, S* __restrict__ Q, int64_t N, int nrhs) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N * nrhs) return;
     const int64_t p = g % N, r = g / N;
-    Q[eop[p] * nrhs + r] = q[g];
+    const S v = q[g];
+    Q[eop[p] * nrhs + r] = v;
+    if (eop2) {
+        const int64_t e2 = eop2[p];
+        if (e2 >= 0) Q[e2 * nrhs + r] = v;
+    }
 }
 
 template <class S>
-__global__ void permute_out_narrow(const int64_t* __restrict__ eop, const S* __restrict__ U, S* __restrict__ u,
-                                   int64_t N, int nrhs) {
+__global__ void permute_out_narrow(const int64_t* __restrict__ eop, const int64_t* __restrict__ eop2,
+                                   const S* __restrict__ U, S* __restrict__ u, int64_t N, int nrhs) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N * nrhs) return;
     const int64_t p = g % N, r = g / N;
-    u[g] = U[eop[p] * nrhs + r];
+    S v = U[eop[p] * nrhs + r];
+    if (eop2) {
+        const int64_t e2 = eop2[p];
+        if (e2 >= 0) v = v + U[e2 * nrhs + r];
+    }
+    u[g] = v;
 }
 
 // ---- upward / downward passes ------------------------------------------------------------
