@@ -41,6 +41,7 @@
 #include "skel_kernels.cuh"
 #include "tc_kernels.cuh"
 #include "tc_complex.cuh"
+#include "tc_updown.cuh"
 
 namespace skel {
 
@@ -183,6 +184,37 @@ void ud_attributes_once() {
     ud_set_attributes<S, false>();
     ud_set_attributes<S, true>();
     done = true;
+}
+
+// one level of the upward or downward pass on the tensor cores (FP32_TC,
+// real kernels): one launch per 32 right-hand sides; returns the launches
+int up_down_tc(bool down, DevicePlan* dp, int l, float* X, int nrhs, cudaStream_t st) {
+    static std::atomic<bool> attr{false};
+    if (!attr.exchange(true)) {
+        CUDA_CHECK(cudaFuncSetAttribute(tc_ud_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUdSmemRequest));
+        CUDA_CHECK(cudaFuncSetAttribute(tc_ud_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUdSmemRequest));
+    }
+    const std::vector<int64_t>& ptr = down ? dp->ud_ptr_down : dp->ud_ptr_up;
+    const int64_t i0 = ptr[l], i1 = ptr[l + 1];
+    if (i1 <= i0) return 0;
+    UdArgs a;
+    a.items = static_cast<const UdItem*>(down ? dp->ud_items_down : dp->ud_items_up) + i0;
+    a.up = dp->up;
+    a.pos = dp->pos;
+    a.A = down ? dp->ud_a_down : dp->ud_a_up;
+    a.X = X;
+    a.n_tot = dp->n_tot;
+    a.nrhs = nrhs;
+    a.status = dp->status;
+    a.wait_ns = kWaitLimitNs;
+    int launches = 0;
+    for (int r0 = 0; r0 < nrhs; r0 += kTcN, ++launches) {
+        a.r0 = r0;
+        if (down) tc_ud_kernel<true><<<(unsigned)(i1 - i0), kTcThreads, kUdSmemRequest, st>>>(a);
+        else tc_ud_kernel<false><<<(unsigned)(i1 - i0), kTcThreads, kUdSmemRequest, st>>>(a);
+        CUDA_CHECK(cudaGetLastError());
+    }
+    return launches;
 }
 
 // one level of the upward or downward pass; warps = 0: the level's setting
@@ -411,14 +443,21 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
         permute<S>(false, dp, (const S*)q, Q, nrhs, st);
         CUDA_CHECK(cudaGetLastError());
     }
-    // 2. upward pass, levels L .. 2
+    // 2. upward pass, levels L .. 2 (FP32_TC, real kernels: the skeleton
+    // GEMMs on the tensor cores; T is real, so the transposed apply is the
+    // same pass)
+    const bool tc_ud = use_tc && !CPLX && sizeof(Real) == 4 && dp->ud_a_up != nullptr;
     mark(dp, 1, st);
     {
         Range r("upward pass");
         for (int l = dp->L; l >= 2; --l) {
             if (dp->up_level_ptr[l + 1] > dp->up_level_ptr[l]) {
-                ++launches;
-                up_down<S>(false, dp, l, T, Q, nrhs, transpose, st);
+                if (tc_ud) {
+                    launches += up_down_tc(false, dp, l, reinterpret_cast<float*>(Q), nrhs, st);
+                } else {
+                    ++launches;
+                    up_down<S>(false, dp, l, T, Q, nrhs, transpose, st);
+                }
                 CUDA_CHECK(cudaGetLastError());
             }
         }
@@ -454,8 +493,12 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
         Range r("downward pass");
         for (int l = 2; l <= dp->L; ++l) {
             if (dp->up_level_ptr[l + 1] > dp->up_level_ptr[l]) {
-                ++launches;
-                up_down<S>(true, dp, l, Tt, U, nrhs, !transpose, st);
+                if (tc_ud) {
+                    launches += up_down_tc(true, dp, l, reinterpret_cast<float*>(U), nrhs, st);
+                } else {
+                    ++launches;
+                    up_down<S>(true, dp, l, Tt, U, nrhs, !transpose, st);
+                }
                 CUDA_CHECK(cudaGetLastError());
             }
         }
@@ -708,6 +751,52 @@ void plan_symmetric_store(const Layout& lay, DevicePlan* dp) {
 
 }  // namespace
 
+// The tensor-core up/down work items of one direction and their A blobs (see
+// tc_updown.cuh): per level, per box, per 128 output rows; upward A(i, j) =
+// T(i, j), downward A(j, i) = T(i, j) (real T, column-major k x (n - k)).
+// A downward box without redundant rows still gets one item (no rows, no
+// tiles) for its u_S += uhat.
+void build_ud_items(bool down, const std::vector<UpBox>& up, const std::vector<int64_t>& level_ptr, const Layout& lay,
+                    std::vector<UdItem>& items, std::vector<int64_t>& ptr, std::vector<float>& A) {
+    ptr.assign(level_ptr.size(), 0);
+    for (size_t l = 0; l + 1 < level_ptr.size(); ++l) {
+        ptr[l] = (int64_t)items.size();
+        for (int64_t b = level_ptr[l]; b < level_ptr[l + 1]; ++b) {
+            const UpBox& u = up[b];
+            const int k = u.k, r = u.n - u.k;
+            const int nout = down ? r : k, ninner = down ? k : r;
+            const int ntile = (ninner + 31) / 32;
+            if (nout == 0) {
+                if (down) items.push_back(UdItem{(int64_t)A.size(), (int32_t)b, 0, 0, 0});
+                continue;
+            }
+            for (int row0 = 0; row0 < nout; row0 += 128) {
+                const int nrows = std::min(128, nout - row0);
+                items.push_back(UdItem{(int64_t)A.size(), (int32_t)b, row0, nrows, ntile});
+                for (int t = 0; t < ntile; ++t) {
+                    const size_t base = A.size();
+                    A.resize(base + (size_t)ud_blob_floats(nrows), 0.f);
+                    for (int jj = 0; jj < 32; ++jj) {
+                        const int j = 32 * t + jj;                     // inner index
+                        int32_t e = -1;
+                        if (j < ninner) {
+                            e = (int32_t)(down ? u.dst + j : u.off + lay.pos[u.off + k + j]);
+                            for (int row = 0; row < nrows; ++row) {
+                                const int o = row0 + row;              // output index
+                                const double v = down ? lay.T[u.T_off + j + (int64_t)o * k]
+                                                      : lay.T[u.T_off + o + (int64_t)j * k];
+                                A[base + ((size_t)(jj / 4) * nrows + row) * 4 + jj % 4] = (float)v;
+                            }
+                        }
+                        std::memcpy(&A[base + (size_t)nrows * 32 + jj], &e, sizeof(e));
+                    }
+                }
+            }
+        }
+    }
+    ptr.back() = (int64_t)items.size();
+}
+
 DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles, int store_stages) {
     DevicePlan* dp = new DevicePlan();
     dp->tcs_stages = store_stages == 8 ? 8 : 4;
@@ -764,6 +853,15 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, i
             if (fused > 0) dp->eop2 = upload(eop2, dp->bytes);
         }
         dp->up = upload(up, dp->bytes);
+        if (!dp->cplx) {
+            for (int down = 0; down < 2; ++down) {
+                std::vector<UdItem> items;
+                std::vector<float> A;
+                build_ud_items(down != 0, up, dp->up_level_ptr, lay, items, down ? dp->ud_ptr_down : dp->ud_ptr_up, A);
+                (down ? dp->ud_items_down : dp->ud_items_up) = upload(items, dp->bytes);
+                (down ? dp->ud_a_down : dp->ud_a_up) = upload(A, dp->bytes);
+            }
+        }
         const int nl = (int)dp->up_level_ptr.size() - 1;
         dp->up_level_maxk.assign(std::max(nl, 0), 0);
         dp->up_level_maxr.assign(std::max(nl, 0), 0);
@@ -846,7 +944,8 @@ void device_plan_destroy(DevicePlan* dp) {
                     dp->part_ptr, dp->part_idx, dp->stage_in, dp->stage_out, dp->mix_items, dp->tc_tiles,
                     dp->tc_items, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
                     dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a, dp->tc_abase,
-                    dp->tc_qmask, dp->tc_refs, dp->tc_isym};
+                    dp->tc_qmask, dp->tc_refs, dp->tc_isym, dp->ud_items_up, dp->ud_items_down,
+                    dp->ud_a_up, dp->ud_a_down};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);

@@ -75,6 +75,13 @@ struct DevicePlan {
     std::vector<int8_t> ud_warps_up, ud_warps_down;
     int tc_stages = 6;                     // bulk-copy stages of the on-the-fly tensor-core kernel (4, 6, 8)
     int tcs_stages = 4;                    // stages per CTA of the per-tile stored kernel (4 or 8)
+    // tensor-core upward / downward passes (FP32_TC, real kernels): per
+    // direction the work items (UdItem) grouped by level and their A blobs
+    void* ud_items_up = nullptr;
+    void* ud_items_down = nullptr;
+    float* ud_a_up = nullptr;
+    float* ud_a_down = nullptr;
+    std::vector<int64_t> ud_ptr_up, ud_ptr_down;   // items of level l: [ptr[l], ptr[l + 1])
     int* status = nullptr;                 // device word raised by a bounded wait that gave up
     // test hook: the next tensor-core pass withholds its first item's first
     // tile until the compute warps gave up, with every wait limited to

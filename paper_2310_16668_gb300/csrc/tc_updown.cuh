@@ -1,0 +1,270 @@
+// Upward and downward passes of Algorithm 2 on the tensor cores (FP32_TC,
+// real kernels): the skeleton GEMMs qhat_S = q_S + T q_R and u_R += T^* uhat
+// of a level as 3-pass TF32 MMAs (tcgen05, kind::tf32) over 32 right-hand
+// sides at a time.
+//
+// Work item: one box of the level and up to 128 of its output rows (upward:
+// skeleton rows i < k; downward: redundant rows j < |I_B| - k). The inner
+// index (upward j < |I_B| - k, downward i < k) runs in tiles of 32. T is
+// static, so the plan keeps each item's A operand in tile order, one blob
+// per tile: its nrows x 32 values in the quad layout of the per-tile store
+// (value (row, 4 q + e) of column half h at float ((4 h + q) nrows + row) * 4
+// + e; zero past the inner size), then the 32 entry indices whose rows of X
+// form the tile's B operand (-1 past the inner size). The producer warp
+// bulk-copies a tile's blob into a stage; the compute warps read their row's
+// 16 values, split them into TF32 hi + lo and write A to tensor memory, and
+// build the B operand (the tile's 32 rows of X for this pass's 32 columns,
+// hi + lo, in the shared-memory layout of the MMA) from the entries; the MMA
+// warp accumulates all tiles of the item in one tensor-memory accumulator
+// (12 MMAs per tile). The epilogue writes qhat_S = q_S + D into the parent's
+// slot (upward) or adds D to u_R (downward); the downward items of row 0
+// also add uhat to u_S.
+//
+// Every wait is bounded (the globaltimer limit of the translations): on
+// timeout the kernel raises the status word and finishes the protocol; entry
+// indices read from a stage are range-checked before use, so a stage that
+// never landed can only give wrong values, not a wrong address.
+#pragma once
+
+#include "tc_kernels.cuh"
+
+namespace skel {
+
+struct UdItem {                                // 24 bytes
+    int64_t a_off;                             // float offset of its first tile blob
+    int32_t box;                               // index into the level's UpBox array (dp->up)
+    int32_t row0;                              // first output row
+    int32_t nrows;                             // output rows (0..128)
+    int32_t ntile;                             // inner tiles of 32
+};
+static_assert(sizeof(UdItem) == 24, "UdItem layout");
+
+struct UdArgs {
+    const UdItem* items;
+    const UpBox* up;
+    const int32_t* pos;
+    const float* A;                            // the tile blobs
+    float* X;                                  // Q (upward) or U (downward), rows of nrhs
+    int64_t n_tot;                             // entries (range check of the blob indices)
+    int nrhs;
+    int r0;                                    // first right-hand side of this pass
+    int* status;
+    uint64_t wait_ns;
+};
+
+// blob of a tile with nrows output rows: nrows x 32 floats, then 32 int32
+__host__ __device__ constexpr int64_t ud_blob_floats(int nrows) { return (int64_t)nrows * 32 + 32; }
+
+constexpr int kUdNST = 4;                      // stages
+struct alignas(128) UdStage {
+    float4 ga[kTileFloats / 4 + 8];            // the tile blob (values, then entry indices)
+    float b[2 * 1024];                         // B hi, B lo (written by the compute warps)
+};
+static_assert(sizeof(float4) * (kTileFloats / 4 + 8) % 128 == 0, "B area 128-byte aligned");
+struct UdShared {
+    UdStage st[kUdNST];
+    uint64_t full[kUdNST], afull[kUdNST], empty[kUdNST];
+    uint32_t tmem;
+};
+constexpr int kUdSmemRequest = 100 * 1024;    // two CTAs per SM
+static_assert(sizeof(UdShared) <= kUdSmemRequest, "shared memory plan (up/down)");
+// tensor memory: the accumulator D at [0, 32), A[b] hi at 64 + 64 b, lo at 96 + 64 b (b < 2)
+
+template <bool DOWN>
+__global__ void __launch_bounds__(kTcThreads, 2) tc_ud_kernel(const UdArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    UdShared& S = *reinterpret_cast<UdShared*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const UdItem it = a.items[blockIdx.x];
+    const UpBox u = a.up[it.box];
+    const int k = u.k;
+    const int nrows = it.nrows, ntile = it.ntile;
+    const int64_t blob = ud_blob_floats(nrows);
+
+    if (tid == 0) {
+        for (int s = 0; s < kUdNST; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sm_addr(&S.afull[s])), "r"(kTcCompute));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sm_addr(&S.empty[s])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(sm_addr(&S.tmem)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = S.tmem;
+    bool err = false;
+
+    if (warp == kTcCompute / 32) {
+        // ---------------- producer warp: the tile blobs, kUdNST ahead ----------------
+        if (lane == 0) {
+            const float* src = a.A + it.a_off;
+            const uint32_t bytes = (uint32_t)(blob * 4);
+            for (int t = 0; t < ntile; ++t) {
+                const int s = t % kUdNST;
+                if (t >= kUdNST && !mbar_wait(sm_addr(&S.empty[s]), (uint32_t)(((t - kUdNST) / kUdNST) & 1), a.wait_ns))
+                    err = true;
+                const uint32_t bar = sm_addr(&S.full[s]);
+                mbar_arrive_tx(bar, bytes);
+                bulk_g2s_hint(sm_addr(S.st[s].ga), src + (int64_t)t * blob, bytes, bar, l2_evict_first());
+            }
+            // every copy has landed before the CTA may exit
+            for (int t = (ntile > kUdNST ? ntile - kUdNST : 0); t < ntile; ++t)
+                if (!mbar_wait(sm_addr(&S.full[t % kUdNST]), (uint32_t)((t / kUdNST) & 1), a.wait_ns)) err = true;
+        }
+    } else if (warp == kTcCompute / 32 + 1) {
+        // ---------------- MMA issuer: all tiles into one accumulator ----------------
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                                   ((128u >> 4) << 24);
+            for (int m = 0; m < ntile; ++m) {
+                const int s = m % kUdNST;
+                if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kUdNST) & 1), a.wait_ns)) err = true;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t bh = sm_addr(S.st[s].b), bl = bh + 4u * 1024u;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t ahi = tbase + kColA + 64u * (m & 1) + 8u * kk, alo = ahi + 32u;
+                    mma_tf32(tbase + kColD, ahi, smem_desc(bh + 2u * kBLbo * kk), idesc, (m > 0 || kk > 0) ? 1u : 0u);
+                    mma_tf32(tbase + kColD, ahi, smem_desc(bl + 2u * kBLbo * kk), idesc, 1u);
+                    mma_tf32(tbase + kColD, alo, smem_desc(bh + 2u * kBLbo * kk), idesc, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(sm_addr(&S.empty[s])) : "memory");
+            }
+        }
+    } else {
+        // ---------------- compute warps ----------------
+        const int row = tid & 127, half = tid >> 7;          // A: thread (row, column half)
+        const int n = tid & 31, jq = tid >> 5;               // B: column n, inner rows 4 jq .. 4 jq + 3
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        const bool valid = row < nrows;
+        const int bcol = a.r0 + n;
+        // this thread's four B values of tile t (its stage has landed)
+        auto load_b = [&](int t, float* x) {
+            const int* ids = reinterpret_cast<const int*>(S.st[t % kUdNST].ga) + nrows * 32;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int e = ids[4 * jq + c];
+                x[c] = (e >= 0 && e < a.n_tot && bcol < a.nrhs) ? a.X[(int64_t)e * a.nrhs + bcol] : 0.f;
+            }
+        };
+        float xc[4] = {0.f, 0.f, 0.f, 0.f}, xn[4] = {0.f, 0.f, 0.f, 0.f};
+        if (ntile > 0) {
+            if (!mbar_wait(sm_addr(&S.full[0]), 0u, a.wait_ns)) err = true;
+            load_b(0, xc);
+        }
+        const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
+        for (int t = 0; t < ntile; ++t) {
+            const int s = t % kUdNST;
+            // the next tile's B rows go out now and arrive while this one is processed
+            if (t + 1 < ntile) {
+                if (!mbar_wait(sm_addr(&S.full[(t + 1) % kUdNST]), (uint32_t)(((t + 1) / kUdNST) & 1), a.wait_ns))
+                    err = true;
+                load_b(t + 1, xn);
+            }
+            // B of tile t: hi (rounded to nearest) and lo = x - hi, as tc_bprep_kernel lays them out
+            {
+                float4 h, l;
+                h.x = __uint_as_float(to_tf32(xc[0]));
+                h.y = __uint_as_float(to_tf32(xc[1]));
+                h.z = __uint_as_float(to_tf32(xc[2]));
+                h.w = __uint_as_float(to_tf32(xc[3]));
+                l = make_float4(xc[0] - h.x, xc[1] - h.y, xc[2] - h.z, xc[3] - h.w);
+                *reinterpret_cast<float4*>(S.st[s].b + jq * 128 + n * 4) = h;
+                *reinterpret_cast<float4*>(S.st[s].b + 1024 + jq * 128 + n * 4) = l;
+            }
+            // A of tile t: this row's 16 values of column half `half`
+            uint32_t ghi[16], glo[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int quad = 4 * half + q;
+                const float4 g4 = valid ? S.st[s].ga[quad * nrows + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 g = h ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
+                    const float2 tt = __fmul2_rn(g, split);
+                    const float2 hi = __ffma2_rn(__ffma2_rn(g, m1, tt), m1, tt);
+                    const float2 lo = __ffma2_rn(hi, m1, g);
+                    const int jj = 4 * q + 2 * h;
+                    ghi[jj] = __float_as_uint(hi.x);
+                    ghi[jj + 1] = __float_as_uint(hi.y);
+                    glo[jj] = __float_as_uint(lo.x);
+                    glo[jj + 1] = __float_as_uint(lo.y);
+                }
+            }
+            // A buffer t & 1 was last read by MMA(t - 2)
+            if (t >= 2 && !mbar_wait(sm_addr(&S.empty[(t - 2) % kUdNST]), (uint32_t)(((t - 2) / kUdNST) & 1), a.wait_ns))
+                err = true;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acol = tbase + lane_off + kColA + 64u * (t & 1) + 16u * half;
+            tmem_st16(acol, ghi);
+            tmem_st16(acol + 32u, glo);
+            // the B stores are generic-proxy writes that the tensor core reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(sm_addr(&S.afull[s]));
+#pragma unroll
+            for (int c = 0; c < 4; ++c) xc[c] = xn[c];
+        }
+        // the accumulator is complete once the last tile's MMAs are
+        uint32_t v[16];
+        if (ntile > 0) {
+            if (!mbar_wait(sm_addr(&S.empty[(ntile - 1) % kUdNST]), (uint32_t)(((ntile - 1) / kUdNST) & 1), a.wait_ns))
+                err = true;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tmem_ld16(tbase + lane_off + kColD + 16u * half, v);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = 0u;
+        }
+        const int c0 = a.r0 + 16 * half;
+        if (valid) {
+            const int i = it.row0 + row;
+            if (!DOWN) {
+                // qhat_S = q_S + T q_R into the parent's slot
+                const int64_t es = (u.off + a.pos[u.off + i]) * a.nrhs, ed = (u.dst + i) * a.nrhs;
+                float qs[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) qs[c] = c0 + c < a.nrhs ? a.X[es + c0 + c] : 0.f;
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    if (c0 + c < a.nrhs) a.X[ed + c0 + c] = qs[c] + __uint_as_float(v[c]);
+            } else {
+                // u_R += T^* uhat
+                const int64_t ed = (u.off + a.pos[u.off + k + i]) * a.nrhs;
+                float ur[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) ur[c] = c0 + c < a.nrhs ? a.X[ed + c0 + c] : 0.f;
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    if (c0 + c < a.nrhs) a.X[ed + c0 + c] = ur[c] + __uint_as_float(v[c]);
+            }
+        }
+        if (DOWN && it.row0 == 0) {
+            // u_S += uhat (this pass's columns), once per box
+            for (int g = tid; g < k * 32; g += kTcCompute) {
+                const int i = g >> 5, c = a.r0 + (g & 31);
+                if (c < a.nrhs) {
+                    const int64_t es = (u.off + a.pos[u.off + i]) * a.nrhs + c;
+                    a.X[es] = a.X[es] + a.X[(u.dst + i) * a.nrhs + c];
+                }
+            }
+        }
+    }
+    if (err) atomicExch(a.status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(kTmemCols));
+    }
+}
+
+}  // namespace skel
