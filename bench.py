@@ -77,6 +77,8 @@ def parse_args():
     p.add_argument("--tune", default="auto", choices=["auto", "none"],
                    help="auto: skel_autotune after the build (per-level up/down variants; stored or on-the-fly "
                         "kernel tiles, chosen by measurement); none: the default rules, tiles on the fly")
+    p.add_argument("--updown-tc", action="store_true",
+                   help="upward / downward skeleton GEMMs on the tensor cores (skel_options.updown_tc)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -548,7 +550,7 @@ def run_ours(args):
     threads = max(1, (os.cpu_count() or 1) // max(1, int(os.environ.get("LOCAL_WORLD_SIZE", world))))
     t0 = time.perf_counter()
     fmm = SkelFMM(x, wl.kernel, tol, wl.leaf, kappa=wl.kappa, nrhs_max=nrhs, num_threads=threads,
-                  device_build=args.build == "device", store_tiles=args.store_tiles)
+                  device_build=args.build == "device", store_tiles=args.store_tiles, updown_tc=args.updown_tc)
     t_build = time.perf_counter() - t0
     # the tensor-core path covers the 3D kernels and 2D Laplace; 2D Helmholtz
     # (Bessel functions) runs on the CUDA cores
@@ -700,6 +702,7 @@ def run_ours(args):
                          f"{info['device_bytes'] / 1e9:.2f} GB resident",
                    "k_max": info["k_max"], "levels": info["n_levels"], "t_build_s": t_build,
                    "pairs_per_apply": pairs,
+                   "updown": "tensor cores" if args.updown_tc and prec == "fp32_tc" else "CUDA cores",
                    "translations": ({1: "per-tile store", 2: "symmetric store"}.get(info["store_mode"], "kernel on the fly"))
                                    + (", chosen by skel_autotune" if tuning and "error" not in tuning else "")},
         "relerr": out.get("relerr"),

@@ -90,6 +90,13 @@ typedef struct {
     int store_stages; /* per-tile store: bulk-copy stages per CTA of its apply kernel,
                          4 (two CTAs per SM) or 8 (one CTA per SM); 0 = 4. Same result
                          either way; skel_autotune may change it.                       */
+    int updown_tc;    /* 1 = FP32_TC applies of a real kernel also run the upward and
+                         downward skeleton GEMMs on the tensor cores (three-part TF32
+                         split, 6 products); the plan keeps T in tile order (about the
+                         size of T twice). The tensor core's accumulation is less
+                         accurate than FP32 FMAs on these cancelling sums (relative error
+                         1.3e-6 instead of 7.8e-7 at N = 2^20, tol 1e-6), so the default
+                         0 keeps them on the CUDA cores.                               */
 } skel_options;
 
 typedef struct {

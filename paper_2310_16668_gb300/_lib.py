@@ -32,7 +32,7 @@ class SkelKernel(ctypes.Structure):
 class SkelOptions(ctypes.Structure):
     _fields_ = [("proxy_p", ctypes.c_int), ("nrhs_max", ctypes.c_int),
                 ("host_only", ctypes.c_int), ("num_threads", ctypes.c_int), ("device_build", ctypes.c_int),
-                ("store_tiles", ctypes.c_int), ("store_stages", ctypes.c_int)]
+                ("store_tiles", ctypes.c_int), ("store_stages", ctypes.c_int), ("updown_tc", ctypes.c_int)]
 
 
 class SkelStats(ctypes.Structure):

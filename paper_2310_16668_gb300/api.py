@@ -24,9 +24,10 @@ _DTYPES = {("fp64", False): torch.float64, ("fp64", True): torch.complex128,
            ("fp32_tc", False): torch.float32, ("fp32_tc", True): torch.complex64}
 
 
-def _options(proxy_p, nrhs_max, host_only, num_threads, device_build=False, store_tiles=False, store_stages=0):
+def _options(proxy_p, nrhs_max, host_only, num_threads, device_build=False, store_tiles=False, store_stages=0,
+             updown_tc=False):
     return SkelOptions(int(proxy_p), int(nrhs_max), int(bool(host_only)), int(num_threads), int(bool(device_build)),
-                       int(store_tiles), int(store_stages))
+                       int(store_tiles), int(store_stages), int(bool(updown_tc)))
 
 
 class SkelFMM:
@@ -40,12 +41,15 @@ class SkelFMM:
     block two tiles share held once; same result up to FP32 rounding).
     ``store_stages`` (4 or 8, 0 = 4): bulk-copy stages per CTA of the
     per-tile store's kernel (same result; the autotuner may change it).
+    ``updown_tc``: FP32_TC applies also run the upward / downward skeleton
+    GEMMs on the tensor cores (less accurate than the CUDA-core default on
+    these cancelling sums; see skel_options.updown_tc).
     """
 
     def __init__(self, points, kernel: str = "laplace3d", tol: float = 1e-6, leaf_size: int = 128,
                  kappa: float = 0.0, proxy_p: int = 0, nrhs_max: int = 32, host_only: bool = False,
                  num_threads: int = 0, device_build: bool = False, store_tiles: bool = False, store_stages: int = 0,
-                 _handle=None):
+                 updown_tc: bool = False, _handle=None):
         self._lib = _lib.load()
         self.kernel = kernel
         self.kappa = float(kappa)
@@ -57,7 +61,8 @@ class SkelFMM:
             pts = np.ascontiguousarray(points, dtype=np.float64)
             n, dim = pts.shape
             h = ctypes.c_void_p()
-            opts = _options(proxy_p, nrhs_max, host_only, num_threads, device_build, store_tiles, store_stages)
+            opts = _options(proxy_p, nrhs_max, host_only, num_threads, device_build, store_tiles, store_stages,
+                            updown_tc)
             check(self._lib.skel_build(pts.ctypes.data, n, dim, SkelKernel(_lib.KERNELS[kernel], self.kappa),
                                        float(tol), int(leaf_size), ctypes.byref(opts), ctypes.byref(h)))
             self._h = h
@@ -66,7 +71,8 @@ class SkelFMM:
     # ---- construction from an external plan --------------------------------------
     @classmethod
     def from_plan(cls, points, kernel: str, plan: dict, kappa: float = 0.0, nrhs_max: int = 32,
-                  host_only: bool = False, store_tiles: bool = False, store_stages: int = 0):
+                  host_only: bool = False, store_tiles: bool = False, store_stages: int = 0,
+                  updown_tc: bool = False):
         """Handle from a plan in the skel.h exchange format (dict of arrays)."""
         lib = _lib.load()
         pts = np.ascontiguousarray(points, dtype=np.float64)
@@ -87,7 +93,7 @@ class SkelFMM:
         center = np.ascontiguousarray(plan["center"], dtype=np.float64)
         nb = arr["level"].shape[0]
         h = ctypes.c_void_p()
-        opts = _options(0, nrhs_max, host_only, 0, False, store_tiles, store_stages)
+        opts = _options(0, nrhs_max, host_only, 0, False, store_tiles, store_stages, updown_tc)
         check(lib.skel_plan_import(pts.ctypes.data, n, dim, SkelKernel(_lib.KERNELS[kernel], float(kappa)),
                                    center.ctypes.data, float(plan["side"]), nb,
                                    *[arr[k].ctypes.data for k in ("level", "coord", "parent", "is_leaf",

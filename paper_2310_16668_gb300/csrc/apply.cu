@@ -443,9 +443,9 @@ void run_apply(DevicePlan* dp, DeviceBuffers* b, const void* q, void* u, int nrh
         permute<S>(false, dp, (const S*)q, Q, nrhs, st);
         CUDA_CHECK(cudaGetLastError());
     }
-    // 2. upward pass, levels L .. 2 (FP32_TC, real kernels: the skeleton
-    // GEMMs on the tensor cores; T is real, so the transposed apply is the
-    // same pass)
+    // 2. upward pass, levels L .. 2 (FP32_TC of a real kernel with
+    // skel_options.updown_tc: the skeleton GEMMs on the tensor cores; T is
+    // real, so the transposed apply is the same pass)
     const bool tc_ud = use_tc && !CPLX && sizeof(Real) == 4 && dp->ud_a_up != nullptr;
     mark(dp, 1, st);
     {
@@ -797,7 +797,8 @@ void build_ud_items(bool down, const std::vector<UpBox>& up, const std::vector<i
     ptr.back() = (int64_t)items.size();
 }
 
-DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles, int store_stages) {
+DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles, int store_stages,
+                               bool updown_tc) {
     DevicePlan* dp = new DevicePlan();
     dp->tcs_stages = store_stages == 8 ? 8 : 4;
     try {
@@ -853,7 +854,7 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, i
             if (fused > 0) dp->eop2 = upload(eop2, dp->bytes);
         }
         dp->up = upload(up, dp->bytes);
-        if (!dp->cplx) {
+        if (!dp->cplx && updown_tc) {
             for (int down = 0; down < 2; ++down) {
                 std::vector<UdItem> items;
                 std::vector<float> A;

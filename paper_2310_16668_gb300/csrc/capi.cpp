@@ -96,7 +96,8 @@ void finalize(skel_plan* h, const skel_options* opts) {
         throw Error(SKEL_ERR_ARG, "store_stages must be 0, 4 or 8");
     if (!h->host_only)
         h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max, opts ? opts->store_tiles : 0,
-                                          opts && opts->store_stages ? opts->store_stages : 4);
+                                          opts && opts->store_stages ? opts->store_stages : 4,
+                                          opts && opts->updown_tc);
     h->t_upload = now() - t0;
 }
 
@@ -438,7 +439,8 @@ int skel_merge(const skel_handle* hs, int nsets, const skel_options* opts, skel_
                 throw Error(SKEL_ERR_ARG, "store_stages must be 0, 4 or 8");
             if (!h->host_only)
                 h->dev = skel::device_plan_create(h->plan, m, h->nrhs_max, opts ? opts->store_tiles : 0,
-                                                  opts && opts->store_stages ? opts->store_stages : 4);
+                                                  opts && opts->store_stages ? opts->store_stages : 4,
+                                          opts && opts->updown_tc);
             h->t_upload = st.t_upload = now() - t0;
         } catch (...) {
             destroy(h);

@@ -107,7 +107,7 @@ struct DevicePlan {
 // tensor-core tile's kernel values once and keep them (nrows x 128 B per tile), so
 // that FP32_TC applies read them instead of evaluating (real kernels).
 DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles = 0,
-                               int store_stages = 4);
+                               int store_stages = 4, bool updown_tc = false);
 void device_plan_destroy(DevicePlan* dp);
 // capture the phases of the next max_applies applies (0 = off)
 void device_set_profiling(DevicePlan* dp, int max_applies);

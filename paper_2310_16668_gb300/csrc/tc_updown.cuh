@@ -12,13 +12,19 @@
 // + e; zero past the inner size), then the 32 entry indices whose rows of X
 // form the tile's B operand (-1 past the inner size). The producer warp
 // bulk-copies a tile's blob into a stage; the compute warps read their row's
-// 16 values, split them into TF32 hi + lo and write A to tensor memory, and
-// build the B operand (the tile's 32 rows of X for this pass's 32 columns,
-// hi + lo, in the shared-memory layout of the MMA) from the entries; the MMA
-// warp accumulates all tiles of the item in one tensor-memory accumulator
-// (12 MMAs per tile). The epilogue writes qhat_S = q_S + D into the parent's
-// slot (upward) or adds D to u_R (downward); the downward items of row 0
-// also add uhat to u_S.
+// 16 values, split them into three TF32 parts and write A to tensor memory,
+// and build the B operand (the tile's 32 rows of X for this pass's 32
+// columns, three parts, in the shared-memory layout of the MMA) from the
+// entries; the MMA warp forms each tile's product in one of two tensor-memory
+// accumulators and the compute warps add the tiles in FP32 registers.
+// Accuracy: the skeleton sums cancel (T mixes signs), so the two-part split of
+// the translations (3 products, each exact to about 2^-22) measured 5x the
+// FP32 error here. x = hi + mid + lo with hi = tf32(x), mid = tf32(x - hi)
+// (both rounded to nearest) and lo = x - hi - mid (at most 2 significant bits,
+// exact in TF32), and the 6 products hh, hm, mh, hl, lh, mm (24 MMAs per
+// tile) leave out terms below 2^-33 of the product. The epilogue writes
+// qhat_S = q_S + D into the parent's slot (upward) or adds D to u_R
+// (downward); the downward items of row 0 also add uhat to u_S.
 //
 // Every wait is bounded (the globaltimer limit of the translations): on
 // timeout the kernel raises the status word and finishes the protocol; entry
@@ -55,10 +61,18 @@ struct UdArgs {
 // blob of a tile with nrows output rows: nrows x 32 floats, then 32 int32
 __host__ __device__ constexpr int64_t ud_blob_floats(int nrows) { return (int64_t)nrows * 32 + 32; }
 
-constexpr int kUdNST = 4;                      // stages
+// x = hi + mid + lo, each a TF32 value (see above)
+__device__ __forceinline__ void tf32_split3(float x, float& hi, float& mid, float& lo) {
+    hi = __uint_as_float(to_tf32(x));
+    const float r = x - hi;
+    mid = __uint_as_float(to_tf32(r));
+    lo = r - mid;
+}
+
+constexpr int kUdNST = 3;                      // stages
 struct alignas(128) UdStage {
     float4 ga[kTileFloats / 4 + 8];            // the tile blob (values, then entry indices)
-    float b[2 * 1024];                         // B hi, B lo (written by the compute warps)
+    float b[3 * 1024];                         // B hi, mid, lo (written by the compute warps)
 };
 static_assert(sizeof(float4) * (kTileFloats / 4 + 8) % 128 == 0, "B area 128-byte aligned");
 struct UdShared {
@@ -68,7 +82,8 @@ struct UdShared {
 };
 constexpr int kUdSmemRequest = 100 * 1024;    // two CTAs per SM
 static_assert(sizeof(UdShared) <= kUdSmemRequest, "shared memory plan (up/down)");
-// tensor memory: the accumulator D at [0, 32), A[b] hi at 64 + 64 b, lo at 96 + 64 b (b < 2)
+// tensor memory: accumulators D0, D1 at [0, 64), A[b] hi, mid, lo at 64 + 96 b + 0 / 32 / 64 (b < 2)
+constexpr uint32_t kUdColA = 64;
 
 template <bool DOWN>
 __global__ void __launch_bounds__(kTcThreads, 2) tc_ud_kernel(const UdArgs a) {
@@ -118,7 +133,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_ud_kernel(const UdArgs a) {
                 if (!mbar_wait(sm_addr(&S.full[t % kUdNST]), (uint32_t)((t / kUdNST) & 1), a.wait_ns)) err = true;
         }
     } else if (warp == kTcCompute / 32 + 1) {
-        // ---------------- MMA issuer: all tiles into one accumulator ----------------
+        // ---------------- MMA issuer: tile m into accumulator m & 1 ----------------
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                                    ((128u >> 4) << 24);
@@ -126,13 +141,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_ud_kernel(const UdArgs a) {
                 const int s = m % kUdNST;
                 if (!mbar_wait(sm_addr(&S.afull[s]), (uint32_t)((m / kUdNST) & 1), a.wait_ns)) err = true;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t bh = sm_addr(S.st[s].b), bl = bh + 4u * 1024u;
+                const uint32_t bh = sm_addr(S.st[s].b), bm = bh + 4u * 1024u, bl = bh + 8u * 1024u;
+                const uint32_t d = tbase + kColD + 32u * (m & 1);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t ahi = tbase + kColA + 64u * (m & 1) + 8u * kk, alo = ahi + 32u;
-                    mma_tf32(tbase + kColD, ahi, smem_desc(bh + 2u * kBLbo * kk), idesc, (m > 0 || kk > 0) ? 1u : 0u);
-                    mma_tf32(tbase + kColD, ahi, smem_desc(bl + 2u * kBLbo * kk), idesc, 1u);
-                    mma_tf32(tbase + kColD, alo, smem_desc(bh + 2u * kBLbo * kk), idesc, 1u);
+                    const uint32_t ah = tbase + kUdColA + 96u * (m & 1) + 8u * kk, am = ah + 32u, al = ah + 64u;
+                    const uint32_t ko = 2u * kBLbo * kk;
+                    mma_tf32(d, ah, smem_desc(bh + ko), idesc, kk > 0 ? 1u : 0u);
+                    mma_tf32(d, ah, smem_desc(bm + ko), idesc, 1u);
+                    mma_tf32(d, am, smem_desc(bh + ko), idesc, 1u);
+                    mma_tf32(d, ah, smem_desc(bl + ko), idesc, 1u);
+                    mma_tf32(d, al, smem_desc(bh + ko), idesc, 1u);
+                    mma_tf32(d, am, smem_desc(bm + ko), idesc, 1u);
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              :: "r"(sm_addr(&S.empty[s])) : "memory");
@@ -154,12 +174,41 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_ud_kernel(const UdArgs a) {
                 x[c] = (e >= 0 && e < a.n_tot && bcol < a.nrhs) ? a.X[(int64_t)e * a.nrhs + bcol] : 0.f;
             }
         };
+        const int c0 = a.r0 + 16 * half;
+        if (DOWN && it.row0 == 0) {
+            // u_S += uhat (this pass's columns), once per box: thread (row,
+            // half) takes rows row, row + 128, ... and its 16 columns, every
+            // load of a row issued before its stores
+            for (int i = row; i < k; i += 128) {
+                const int64_t es = (u.off + a.pos[u.off + i]) * a.nrhs, eh = (u.dst + i) * a.nrhs;
+                float us[16], uh[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const bool ok = c0 + c < a.nrhs;
+                    us[c] = ok ? a.X[es + c0 + c] : 0.f;
+                    uh[c] = ok ? a.X[eh + c0 + c] : 0.f;
+                }
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    if (c0 + c < a.nrhs) a.X[es + c0 + c] = us[c] + uh[c];
+            }
+        }
+        float acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+        auto drain = [&](int m) {                            // add tile m's product (its MMAs are done)
+            if (!mbar_wait(sm_addr(&S.empty[m % kUdNST]), (uint32_t)((m / kUdNST) & 1), a.wait_ns)) err = true;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t v[16];
+            tmem_ld16(tbase + lane_off + kColD + 32u * (m & 1) + 16u * half, v);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] += __uint_as_float(v[c]);
+        };
         float xc[4] = {0.f, 0.f, 0.f, 0.f}, xn[4] = {0.f, 0.f, 0.f, 0.f};
         if (ntile > 0) {
             if (!mbar_wait(sm_addr(&S.full[0]), 0u, a.wait_ns)) err = true;
             load_b(0, xc);
         }
-        const float2 m1 = make_float2(-1.f, -1.f), split = make_float2(8193.f, 8193.f);
         for (int t = 0; t < ntile; ++t) {
             const int s = t % kUdNST;
             // the next tile's B rows go out now and arrive while this one is processed
@@ -168,43 +217,40 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_ud_kernel(const UdArgs a) {
                     err = true;
                 load_b(t + 1, xn);
             }
-            // B of tile t: hi (rounded to nearest) and lo = x - hi, as tc_bprep_kernel lays them out
+            // B of tile t in three parts, in the layout of tc_bprep_kernel
             {
-                float4 h, l;
-                h.x = __uint_as_float(to_tf32(xc[0]));
-                h.y = __uint_as_float(to_tf32(xc[1]));
-                h.z = __uint_as_float(to_tf32(xc[2]));
-                h.w = __uint_as_float(to_tf32(xc[3]));
-                l = make_float4(xc[0] - h.x, xc[1] - h.y, xc[2] - h.z, xc[3] - h.w);
-                *reinterpret_cast<float4*>(S.st[s].b + jq * 128 + n * 4) = h;
-                *reinterpret_cast<float4*>(S.st[s].b + 1024 + jq * 128 + n * 4) = l;
+                float4 h, m, l;
+                tf32_split3(xc[0], h.x, m.x, l.x);
+                tf32_split3(xc[1], h.y, m.y, l.y);
+                tf32_split3(xc[2], h.z, m.z, l.z);
+                tf32_split3(xc[3], h.w, m.w, l.w);
+                float* bb = S.st[s].b + jq * 128 + n * 4;
+                *reinterpret_cast<float4*>(bb) = h;
+                *reinterpret_cast<float4*>(bb + 1024) = m;
+                *reinterpret_cast<float4*>(bb + 2048) = l;
             }
             // A of tile t: this row's 16 values of column half `half`
-            uint32_t ghi[16], glo[16];
+            uint32_t gh[16], gm[16], gl[16];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int quad = 4 * half + q;
                 const float4 g4 = valid ? S.st[s].ga[quad * nrows + row] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float2 g = h ? make_float2(g4.z, g4.w) : make_float2(g4.x, g4.y);
-                    const float2 tt = __fmul2_rn(g, split);
-                    const float2 hi = __ffma2_rn(__ffma2_rn(g, m1, tt), m1, tt);
-                    const float2 lo = __ffma2_rn(hi, m1, g);
-                    const int jj = 4 * q + 2 * h;
-                    ghi[jj] = __float_as_uint(hi.x);
-                    ghi[jj + 1] = __float_as_uint(hi.y);
-                    glo[jj] = __float_as_uint(lo.x);
-                    glo[jj + 1] = __float_as_uint(lo.y);
+                for (int e = 0; e < 4; ++e) {
+                    float h, m, l;
+                    tf32_split3(gv[e], h, m, l);
+                    gh[4 * q + e] = __float_as_uint(h);
+                    gm[4 * q + e] = __float_as_uint(m);
+                    gl[4 * q + e] = __float_as_uint(l);
                 }
             }
-            // A buffer t & 1 was last read by MMA(t - 2)
-            if (t >= 2 && !mbar_wait(sm_addr(&S.empty[(t - 2) % kUdNST]), (uint32_t)(((t - 2) / kUdNST) & 1), a.wait_ns))
-                err = true;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t acol = tbase + lane_off + kColA + 64u * (t & 1) + 16u * half;
-            tmem_st16(acol, ghi);
-            tmem_st16(acol + 32u, glo);
+            // A buffer and accumulator t & 1 were last used by tile t - 2
+            if (t >= 2) drain(t - 2);
+            const uint32_t acol = tbase + lane_off + kUdColA + 96u * (t & 1) + 16u * half;
+            tmem_st16(acol, gh);
+            tmem_st16(acol + 32u, gm);
+            tmem_st16(acol + 64u, gl);
             // the B stores are generic-proxy writes that the tensor core reads
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -213,18 +259,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_ud_kernel(const UdArgs a) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) xc[c] = xn[c];
         }
-        // the accumulator is complete once the last tile's MMAs are
-        uint32_t v[16];
-        if (ntile > 0) {
-            if (!mbar_wait(sm_addr(&S.empty[(ntile - 1) % kUdNST]), (uint32_t)(((ntile - 1) / kUdNST) & 1), a.wait_ns))
-                err = true;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            tmem_ld16(tbase + lane_off + kColD + 16u * half, v);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) v[c] = 0u;
-        }
-        const int c0 = a.r0 + 16 * half;
+        for (int m = (ntile >= 2 ? ntile - 2 : 0); m < ntile; ++m) drain(m);
         if (valid) {
             const int i = it.row0 + row;
             if (!DOWN) {
@@ -235,7 +270,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_ud_kernel(const UdArgs a) {
                 for (int c = 0; c < 16; ++c) qs[c] = c0 + c < a.nrhs ? a.X[es + c0 + c] : 0.f;
 #pragma unroll
                 for (int c = 0; c < 16; ++c)
-                    if (c0 + c < a.nrhs) a.X[ed + c0 + c] = qs[c] + __uint_as_float(v[c]);
+                    if (c0 + c < a.nrhs) a.X[ed + c0 + c] = qs[c] + acc[c];
             } else {
                 // u_R += T^* uhat
                 const int64_t ed = (u.off + a.pos[u.off + k + i]) * a.nrhs;
@@ -244,17 +279,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_ud_kernel(const UdArgs a) {
                 for (int c = 0; c < 16; ++c) ur[c] = c0 + c < a.nrhs ? a.X[ed + c0 + c] : 0.f;
 #pragma unroll
                 for (int c = 0; c < 16; ++c)
-                    if (c0 + c < a.nrhs) a.X[ed + c0 + c] = ur[c] + __uint_as_float(v[c]);
-            }
-        }
-        if (DOWN && it.row0 == 0) {
-            // u_S += uhat (this pass's columns), once per box
-            for (int g = tid; g < k * 32; g += kTcCompute) {
-                const int i = g >> 5, c = a.r0 + (g & 31);
-                if (c < a.nrhs) {
-                    const int64_t es = (u.off + a.pos[u.off + i]) * a.nrhs + c;
-                    a.X[es] = a.X[es] + a.X[(u.dst + i) * a.nrhs + c];
-                }
+                    if (c0 + c < a.nrhs) a.X[ed + c0 + c] = ur[c] + acc[c];
             }
         }
     }

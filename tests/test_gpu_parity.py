@@ -119,6 +119,28 @@ def test_tensor_core_helmholtz_many_rhs(nrhs, b):
         assert relerr(vtc[:, r], v64[:, r]) < 1e-5, r
 
 
+@pytest.mark.parametrize("updown_tc", [False, True])
+def test_tensor_core_updown_accuracy(updown_tc):
+    """FP32_TC on a deep tree (five levels, items of two row blocks, inner
+    sizes up to 1,200), with the upward / downward skeleton GEMMs on the CUDA
+    cores (default) or on the tensor cores (skel_options.updown_tc): every
+    column within 2e-6 of the FP64 apply (the FP32 CUDA-core apply: about
+    2e-7), and the transposed apply too."""
+    x = W.points_uniform(150000, 3, 37)
+    fmm = SkelFMM(x, "laplace3d", 1e-6, 32, nrhs_max=32, updown_tc=updown_tc)
+    q = torch.from_numpy(W.charges_normal(x.shape[0], 32, 38)).cuda()
+    u64 = fmm.apply(q, "fp64").cpu().numpy()
+    utc = fmm.apply(q.float(), "fp32_tc").cpu().numpy()
+    u32 = fmm.apply(q[:, :2].float().contiguous(), "fp32").cpu().numpy()
+    fmm.device_status()
+    e32 = max(relerr(u32[:, r], u64[:, r]) for r in range(2))
+    etc = max(relerr(utc[:, r], u64[:, r]) for r in range(32))
+    print(f"updown_tc {updown_tc}: fp32 vs fp64 {e32:.2e}, fp32_tc vs fp64 {etc:.2e}")
+    assert etc < 2e-6
+    vtc = fmm.apply_transpose(q.float(), "fp32_tc").cpu().numpy()
+    assert max(relerr(vtc[:, r], u64[:, r]) for r in (0, 31)) < 2e-6   # Laplace: A~^T = A~
+
+
 def test_transpose_matches_oracle(oracle_case):
     kind, x, sk, fmm = oracle_case
     q = _charges(kind, x.shape[0], 4, 12)
