@@ -160,20 +160,20 @@ def kernel_source_sha(kernel: str = "") -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, precision: str):
-    """DRAM bytes per launch of `kernel` from a committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def ncu_traffic(kernel: str, precision: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
     sha = kernel_source_sha(kernel)
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
     pat = re.compile(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+kernel:\s*(\S+)\s+precision:\s*(\S+)\s+"
-                     r"source_sha:\s*([0-9a-f]+)")
+                     r"source_sha:\s*([0-9a-f]+)\s+workload:\s*(\S+)")
     for f in sorted(os.listdir(d)):
         if not f.endswith((".md", ".txt")):
             continue
         for m in pat.finditer(open(os.path.join(d, f)).read()):
-            if m.group(2) == kernel and m.group(3) == precision and m.group(4) == sha:
+            if (m.group(2), m.group(3), m.group(4), m.group(5)) == (kernel, precision, sha, workload):
                 return float(m.group(1))
     return None
 
@@ -214,7 +214,7 @@ def oracle_direct_sample(kind, x, q0, targets, kappa=0.0):
     return u, time.perf_counter() - t0, direct.num_threads()
 
 
-def roofline(info, phases, clk, prec, pairs, kind="laplace3d"):
+def roofline(info, phases, clk, prec, pairs, kind="laplace3d", workload=""):
     """The dominant kernel against its roofline: the main translation kernel,
     timed by the plan's own CUDA events on the launching stream inside the
     timed region (skel_set_profiling); the CUDA-core launch for the small
@@ -239,7 +239,7 @@ def roofline(info, phases, clk, prec, pairs, kind="laplace3d"):
     peak = SM_COUNT * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e9
     peaks, peaks_kind = measured_peaks()
     roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(kname, prec),
+            "frac": achieved / peak, "traffic": ncu_traffic(kname, prec, workload),
             "peak_basis": f"{SM_COUNT} SMs x {MUFU_PER_SM_CLK} MUFU ops/clk x median SM clock under load "
                           f"({sm_mhz:.0f} MHz), one MUFU op per kernel evaluation",
             "per_launch_ms": near_ms_per_launch, "launches_per_step": n_near,
@@ -261,7 +261,7 @@ def roofline(info, phases, clk, prec, pairs, kind="laplace3d"):
         # beside the figure
         kname = "tc_stored_kernel"
         alg_bytes = 4 * info["pairs_tc"] + info["n_index"] * 32 * 4
-        traffic = ncu_traffic(kname, prec)
+        traffic = ncu_traffic(kname, prec, workload)
         roof.update({"kernel": kname, "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
                      "achieved": alg_bytes / (near_ms_per_launch * 1e-3) / 1e9,
                      "traffic": traffic,
@@ -285,7 +285,7 @@ def roofline(info, phases, clk, prec, pairs, kind="laplace3d"):
         # kept value (skel_info pairs_stored), not per evaluation
         kname = "tc_sym_kernel"
         alg_bytes = 4 * info["pairs_stored"] + info["n_index"] * 32 * 4
-        traffic = ncu_traffic(kname, prec)
+        traffic = ncu_traffic(kname, prec, workload)
         roof.update({"kernel": kname, "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
                      "achieved": alg_bytes / (near_ms_per_launch * 1e-3) / 1e9,
                      "traffic": traffic,
@@ -490,7 +490,7 @@ def run_curves(args):
             n_eval += len(tg)
             got = U[r, off[i]:off[i + 1]].double().cpu().numpy()[tg]
             errs[f"set{i}_rhs{r}"] = float(np.abs(got - ref).max() / np.abs(ref).max())
-    roof = roofline(info, phases, clk, prec, info["pairs_direct"] + info["pairs_far"])
+    roof = roofline(info, phases, clk, prec, info["pairs_direct"] + info["pairs_far"], "laplace2d", cs.name)
     line = {
         "metric": f"Mpts·RHS/s, {cs.name} batched apply (one merged plan, CUDA graph)", "value": value,
         "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fwd,
@@ -688,7 +688,7 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    roof = roofline(info, phases, clk, prec, pairs, wl.kernel)
+    roof = roofline(info, phases, clk, prec, pairs, wl.kernel, wl.name)
     _, peaks_kind = measured_peaks()
     metric = METRIC if args.workload == "laplace3d" else f"Mpts·RHS/s, {wl0.name} apply: {prec} vs plain FP64"
     line = {
