@@ -1,7 +1,8 @@
 // Upward and downward passes of Algorithm 2 on the tensor cores (FP32_TC,
 // real kernels): the skeleton GEMMs qhat_S = q_S + T q_R and u_R += T^* uhat
-// of a level as 3-pass TF32 MMAs (tcgen05, kind::tf32) over 32 right-hand
-// sides at a time.
+// of a level as split-TF32 MMAs (tcgen05, kind::tf32) over 32 right-hand
+// sides at a time. Opt-in (skel_options.updown_tc): see the accuracy note
+// below.
 //
 // Work item: one box of the level and up to 128 of its output rows (upward:
 // skeleton rows i < k; downward: redundant rows j < |I_B| - k). The inner
@@ -17,12 +18,14 @@
 // columns, three parts, in the shared-memory layout of the MMA) from the
 // entries; the MMA warp forms each tile's product in one of two tensor-memory
 // accumulators and the compute warps add the tiles in FP32 registers.
-// Accuracy: the skeleton sums cancel (T mixes signs), so the two-part split of
-// the translations (3 products, each exact to about 2^-22) measured 5x the
-// FP32 error here. x = hi + mid + lo with hi = tf32(x), mid = tf32(x - hi)
-// (both rounded to nearest) and lo = x - hi - mid (at most 2 significant bits,
-// exact in TF32), and the 6 products hh, hm, mh, hl, lh, mm (24 MMAs per
-// tile) leave out terms below 2^-33 of the product. The epilogue writes
+// Split: x = hi + mid + lo with hi = tf32(x), mid = tf32(x - hi) (both
+// rounded to nearest) and lo = x - hi - mid (at most 2 significant bits,
+// exact in TF32); the 6 products hh, hm, mh, hl, lh, mm (24 MMAs per tile)
+// leave out terms below 2^-33 of the product. Accuracy: the skeleton sums
+// cancel (T mixes signs), and the tensor core's accumulation is less accurate
+// than FP32 FMAs on them: relative error 1.3e-6 instead of 7.8e-7 at
+// N = 2^20, tol 1e-6, with this split as with the translations' two-part
+// one, so the error comes from the accumulation. The epilogue writes
 // qhat_S = q_S + D into the parent's slot (upward) or adds D to u_R
 // (downward); the downward items of row 0 also add uhat to u_S.
 //
