@@ -410,11 +410,24 @@ int skel_test_withhold_tile(skel_handle h, double wait_limit_ms);
 int skel_test_fail_alloc(int countdown);
 
 /*
+ * skel_test_set_updown — force the launch shape of every level's FP32
+ * upward and downward pass on h (what skel_autotune otherwise picks per
+ * level): code 0 = the default rule, 1 / 2 / 4 / 8 = the plain kernel with
+ * that many warps per CTA, 17 / 18 / 20 / 24 = the asynchronous-copy kernel
+ * with 1 / 2 / 4 / 8 warps. Every shape gives the same result bit for bit,
+ * which tests check with it.
+ * Errors: SKEL_ERR_ARG (NULL handle, other codes), SKEL_ERR_STATE (host-only
+ * plan).
+ */
+int skel_test_set_updown(skel_handle h, int code);
+
+/*
  * skel_autotune — pick, by measurement on this plan and device, the variants
  * the FP32 applies of nrhs right-hand sides will use: per tree level and
  * direction the launch shape of the up/down kernel (1, 2, 4 or 8 warps per
- * CTA sharing a 32-row block; every shape adds the same partial sums in the
- * same order), the pipeline depth of the on-the-fly tensor-core kernel (4, 6
+ * CTA sharing a 32-row block, with the blocks staged through registers or by
+ * asynchronous copies; every shape adds the same partial sums in the same
+ * order), the pipeline depth of the on-the-fly tensor-core kernel (4, 6
  * or 8 bulk-copy stages; same arithmetic), and for the tensor-core
  * translations (real kernels, nrhs >= 4) whether the
  * kernel values are evaluated on the fly or read from a store (the choice

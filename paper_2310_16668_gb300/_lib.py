@@ -22,7 +22,8 @@ SYMBOLS = ("skel_build", "skel_apply", "skel_apply_transpose", "skel_free", "ske
            "skel_last_error", "skel_plan_get_dims", "skel_plan_export", "skel_plan_import",
            "skel_neighbors_export", "skel_set_profiling", "skel_last_timings",
            "skel_device_status", "skel_direct_noalloc", "skel_apply_batch", "skel_autotune",
-           "skel_build_batch", "skel_test_withhold_tile", "skel_test_fail_alloc", "skel_merge")
+           "skel_build_batch", "skel_test_withhold_tile", "skel_test_fail_alloc", "skel_merge",
+           "skel_test_set_updown")
 
 
 class SkelKernel(ctypes.Structure):
@@ -108,6 +109,7 @@ def load() -> ctypes.CDLL:
     lib.skel_build_batch.argtypes = [I, P, P, I, SkelKernel, D, I, ctypes.POINTER(SkelOptions), P]
     lib.skel_test_withhold_tile.argtypes = [P, D]
     lib.skel_test_fail_alloc.argtypes = [I]
+    lib.skel_test_set_updown.argtypes = [P, I]
     lib.skel_merge.argtypes = [P, I, ctypes.POINTER(SkelOptions), ctypes.POINTER(P)]
     for name in SYMBOLS:
         if name not in ("skel_free", "skel_last_error"):

@@ -42,6 +42,7 @@
 #include "tc_kernels.cuh"
 #include "tc_complex.cuh"
 #include "tc_updown.cuh"
+#include "updown_async.cuh"
 
 namespace skel {
 
@@ -183,7 +184,25 @@ void ud_attributes_once() {
     if (done) return;
     ud_set_attributes<S, false>();
     ud_set_attributes<S, true>();
+    if constexpr (std::is_same<S, float>::value) {
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(4)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(4)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(8)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(8)));
+    }
     done = true;
+}
+
+// launch-shape codes of the FP32 up/down passes: 1, 2, 4, 8 = updown_kernel
+// with that many warps per CTA (one 32-row block); kUdAsync + NW =
+// updown_rows_kernel with NW warps owning 32 NW rows (same result bit for bit)
+constexpr int kUdAsync = 16;
+
+template <bool DOWN, int NW>
+void ud_rows_launch(unsigned nbox, int nout, int nrhs, const UpBox* up, const int32_t* pos, const float* T, float* X,
+                    cudaStream_t st) {
+    const dim3 grid(nbox, std::max(1u, ceil_div(nout, 32 * NW)), ceil_div(nrhs, kGT));
+    updown_rows_kernel<DOWN, NW><<<grid, 32 * NW, ud_rows_smem(NW), st>>>(up, pos, T, X, nrhs);
 }
 
 // one level of the upward or downward pass on the tensor cores (FP32_TC,
@@ -233,8 +252,24 @@ void up_down(bool down, const DevicePlan* dp, int l, const S* T, S* X, int nrhs,
         if (l < (int)t.size() && t[l] > 0) W = t[l];
     }
     if (W == 0) W = ud_default_warps((ninner + kGT - 1) / kGT);
-    W = std::min(W, ud_streams<S>());
     const UpBox* up = dp->up + b0;
+    if constexpr (std::is_same<S, float>::value) {
+        if (W > kUdAsync) {
+            const unsigned nb = (unsigned)(b1 - b0);
+            switch (W - kUdAsync) {
+                case 1: down ? ud_rows_launch<true, 1>(nb, nout, nrhs, up, dp->pos, T, X, st)
+                             : ud_rows_launch<false, 1>(nb, nout, nrhs, up, dp->pos, T, X, st); break;
+                case 2: down ? ud_rows_launch<true, 2>(nb, nout, nrhs, up, dp->pos, T, X, st)
+                             : ud_rows_launch<false, 2>(nb, nout, nrhs, up, dp->pos, T, X, st); break;
+                case 4: down ? ud_rows_launch<true, 4>(nb, nout, nrhs, up, dp->pos, T, X, st)
+                             : ud_rows_launch<false, 4>(nb, nout, nrhs, up, dp->pos, T, X, st); break;
+                default: down ? ud_rows_launch<true, 8>(nb, nout, nrhs, up, dp->pos, T, X, st)
+                              : ud_rows_launch<false, 8>(nb, nout, nrhs, up, dp->pos, T, X, st); break;
+            }
+            return;
+        }
+    }
+    W = std::min(W, ud_streams<S>());
     switch (W) {
         case 1: down ? ud_launch<S, true, 1>(grid, up, dp->pos, T, X, nrhs, conj_op, st)
                      : ud_launch<S, false, 1>(grid, up, dp->pos, T, X, nrhs, conj_op, st); break;
@@ -1060,7 +1095,7 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
                 const int def = ud_default_warps((ninner + kGT - 1) / kGT);
                 double best_ms = 1e30, def_ms = 0;
                 int best = def;
-                for (int W : {1, 2, 4, 8}) {
+                for (int W : {1, 2, 4, 8, kUdAsync + 1, kUdAsync + 2, kUdAsync + 4, kUdAsync + 8}) {
                     const double ms = time_ms([&] { up_down<float>(down != 0, dp, l, T, (float*)(down ? b->U : b->Q),
                                                                    nrhs, down != 0, st, W); }, 5);
                     if (W == def) def_ms = ms;

@@ -760,6 +760,20 @@ int skel_test_fail_alloc(int countdown) {
     });
 }
 
+int skel_test_set_updown(skel_handle h, int code) {
+    return guarded([&] {
+        if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");
+        if (!h->dev) throw Error(SKEL_ERR_STATE, "plan was built host-only");
+        static const int ok[] = {0, 1, 2, 4, 8, 17, 18, 20, 24};
+        bool valid = false;
+        for (int c : ok) valid |= c == code;
+        if (!valid) throw Error(SKEL_ERR_ARG, "code must be 0, 1, 2, 4, 8, 17, 18, 20 or 24");
+        const int nl = (int)h->dev->up_level_ptr.size() - 1;
+        h->dev->ud_warps_up.assign(std::max(nl, 0), (int8_t)code);
+        h->dev->ud_warps_down.assign(std::max(nl, 0), (int8_t)code);
+    });
+}
+
 int skel_autotune(skel_handle h, int nrhs, int allow_store, void* stream, skel_tuning* out) {
     return guarded([&] {
         if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");

@@ -1,0 +1,171 @@
+// Upward / downward passes (FP32), the CTA-wide form: a CTA owns 32 NW
+// output rows (NW warps, 32 rows each, lane = right-hand side) x 32
+// right-hand sides of one box and streams the inner index in chunks of 32
+// through a three-stage pipeline of asynchronous copies that all its threads
+// issue: per chunk the A block (32 inner x 32 NW rows, zero-filled past the
+// box) and the chunk's 32 rows of X (shared by the warps). The chunks are
+// taken in stream order (stream s: chunks s, s + NS, ...), each stream summed
+// on its own and the streams added in order, which is exactly the arithmetic
+// of updown_kernel with one warp per CTA: every launch shape of both kernels
+// gives the same bits, so the autotuner may pick any of them per level. The
+// entry indices of the chunk after next are loaded while the current chunk's
+// copies are waited for.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "skel_kernels.cuh"
+
+namespace skel {
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
+}
+
+constexpr int kUdrStages = 3;
+// dynamic shared memory: per stage the A block (32 x 32 NW) and the B block (32 x 32)
+__host__ __device__ constexpr int ud_rows_smem(int NW) {
+    return kUdrStages * (NW + 1) * kGT * kGT * (int)sizeof(float);
+}
+
+template <bool DOWN, int NW>
+__global__ void __launch_bounds__(32 * NW) updown_rows_kernel(const UpBox* __restrict__ up,
+                                                              const int32_t* __restrict__ pos,
+                                                              const float* __restrict__ T, float* X, int nrhs) {
+    constexpr int NS = ud_streams<float>();
+    constexpr int ROWS = 32 * NW;
+    constexpr int STAGE = (NW + 1) * kGT * kGT;           // floats per stage: A then B
+    static_assert(NW == 1 || NW == 2 || NW == 4 || NW == 8, "warps per CTA");
+    extern __shared__ __align__(16) unsigned char udr_raw[];
+    float* sm = reinterpret_cast<float*>(udr_raw);
+    const UpBox u = up[blockIdx.x];
+    const int k = u.k, r = u.n - u.k;
+    const int nout = DOWN ? r : k, ninner = DOWN ? k : r;
+    const int row0 = blockIdx.y * ROWS, c0 = blockIdx.z * kGT;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int col = c0 + lane;
+    const bool colok = col < nrhs;
+    if (DOWN && blockIdx.y == 0 && colok) {              // u_S += uhat, this CTA's columns
+        for (int i0 = warp; i0 < k; i0 += 8 * NW) {
+            float uh[8], us[8];
+            int64_t at[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = i0 + q * NW;
+                at[q] = -1;
+                if (i < k) {
+                    at[q] = (u.off + pos[u.off + i]) * nrhs + col;
+                    uh[q] = X[(u.dst + i) * nrhs + col];
+                    us[q] = X[at[q]];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (at[q] >= 0) X[at[q]] = us[q] + uh[q];
+        }
+    }
+    if (row0 >= nout) return;
+    const int nch = (ninner + kGT - 1) / kGT;
+    const int nsum = nch < NS ? nch : NS;
+    const bool arow = row0 + tid < nout;                  // this thread's A row (copies)
+    // the entry of B row `lane` of chunk ch (lanes past the chunk: 0, unused)
+    auto entry = [&](int ch) -> int64_t {
+        const int j0 = ch * kGT, jn = min(kGT, ninner - j0);
+        if (lane >= jn) return 0;
+        return DOWN ? (u.dst + j0 + lane) : (u.off + pos[u.off + k + j0 + lane]);
+    };
+    // the copies of chunk ch into stage buf: A (inner jj, row tid), B rows jj = warp, warp + NW, ...
+    auto issue = [&](int ch, int64_t ri, float* buf) {
+        const int j0 = ch * kGT, jn = min(kGT, ninner - j0);
+        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(buf);
+#pragma unroll 8
+        for (int jj = 0; jj < kGT; ++jj) {
+            const bool av = jj < jn && arow;
+            const float* ga = av ? T + u.T_off + row0 + tid + (int64_t)(j0 + jj) * nout : T;
+            cp_async4(sa + (uint32_t)(jj * ROWS + tid) * 4u, ga, av ? 4u : 0u);
+        }
+#pragma unroll
+        for (int m = 0; m < kGT / NW; ++m) {
+            const int jj = warp + m * NW;
+            const int64_t rj = __shfl_sync(0xffffffffu, ri, jj);
+            const bool bv = jj < jn && colok;
+            const float* gb = bv ? X + rj * nrhs + col : X;
+            cp_async4(sa + (uint32_t)(kGT * ROWS + jj * kGT + lane) * 4u, gb, bv ? 4u : 0u);
+        }
+    };
+    // chunks in stream order: (stream, chunk) -> the next one
+    auto advance = [&](int& s, int& ch) {
+        if (ch + NS < nch) ch += NS;
+        else ch = ++s;
+    };
+    float acc[kGT], tot[kGT];
+#pragma unroll
+    for (int i = 0; i < kGT; ++i) acc[i] = tot[i] = 0.f;
+    if (nch > 0) {
+        // issue pointer (stream, chunk) and the entries of its chunk
+        int is = 0, ic = 0;
+        int64_t ri = entry(0);
+        for (int p = 0; p < kUdrStages - 1; ++p) {
+            if (is < nsum) {
+                issue(ic, ri, sm + p * STAGE);
+                advance(is, ic);
+                ri = is < nsum ? entry(ic) : 0;
+            }
+            cp_async_commit();
+        }
+        int cs = 0, cc = 0;                              // compute pointer
+        for (int t = 0; t < nch; ++t) {
+            if (is < nsum) {
+                issue(ic, ri, sm + ((t + kUdrStages - 1) % kUdrStages) * STAGE);
+                advance(is, ic);
+                ri = is < nsum ? entry(ic) : 0;
+            }
+            cp_async_commit();
+            cp_async_wait<kUdrStages - 1>();
+            __syncthreads();
+            const float* As = sm + (t % kUdrStages) * STAGE;
+            const float* Bs = As + kGT * ROWS;
+#pragma unroll 4
+            for (int jj = 0; jj < kGT; ++jj) ud_rows<float>(acc, As + jj * ROWS + warp * kGT, Bs[jj * kGT + lane]);
+            if (!(cc + NS < nch)) {                      // the stream's last chunk
+#pragma unroll
+                for (int i = 0; i < kGT; ++i) {
+                    tot[i] = cs == 0 ? acc[i] : tot[i] + acc[i];
+                    acc[i] = 0.f;
+                }
+            }
+            advance(cs, cc);
+            __syncthreads();                             // before this stage is filled again
+        }
+    }
+    if (!colok) return;
+    // this warp's 32 rows in two batches of 16: every old value of a batch
+    // is loaded before its stores
+#pragma unroll
+    for (int q0 = 0; q0 < kGT; q0 += 16) {
+        float old[16];
+        int64_t dst[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int orow = row0 + warp * kGT + q0 + q;
+            dst[q] = -1;
+            if (orow < nout) {
+                const int64_t src = DOWN ? (u.off + pos[u.off + k + orow]) * nrhs + col
+                                         : (u.off + pos[u.off + orow]) * nrhs + col;
+                dst[q] = DOWN ? src : (u.dst + orow) * nrhs + col;
+                old[q] = X[src];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (dst[q] >= 0) X[dst[q]] = old[q] + tot[q0 + q];
+    }
+}
+
+}  // namespace skel

@@ -151,6 +151,8 @@ def test_argument_errors():
     assert lib.skel_test_fail_alloc(0) == 0                               # off
     assert lib.skel_test_withhold_tile(None, 5.0) == -1
     assert lib.skel_test_withhold_tile(f._h, 5.0) == -6                   # host-only plan
+    assert lib.skel_test_set_updown(None, 0) == -1
+    assert lib.skel_test_set_updown(f._h, 0) == -6                       # host-only plan
 
 
 def test_single_leaf_root_plan():

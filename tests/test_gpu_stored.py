@@ -136,3 +136,23 @@ def test_autotune_keeps_results(kind, dim):
     else:
         assert torch.equal(tc2, tc0)
     assert rep2["n_updown"] == rep["n_updown"]
+
+
+def test_updown_launch_shapes_same_bits():
+    """Every launch shape of the FP32 upward / downward passes (plain kernel
+    with 1, 2, 4, 8 warps per CTA; asynchronous-copy kernel with 1, 2, 4, 8)
+    gives the default's result bit for bit, in FP32 and FP32_TC, plain and
+    transposed, on a deep adaptive tree with ragged boxes."""
+    from paper_2310_16668_gb300 import _lib
+    lib = _lib.load()
+    x = clustered(12000, 3, 41)
+    f = SkelFMM(x, "laplace3d", 1e-6, 16, nrhs_max=40)
+    q = torch.from_numpy(W.charges_normal(x.shape[0], 40, 42)).cuda().float()
+    ref = {(p, t): (f.apply_transpose if t else f.apply)(q, p) for p in ("fp32", "fp32_tc") for t in (False, True)}
+    for code in (1, 2, 4, 8, 17, 18, 20, 24):
+        _lib.check(lib.skel_test_set_updown(f._h, code))
+        for (p, t), r in ref.items():
+            got = (f.apply_transpose if t else f.apply)(q, p)
+            f.device_status()
+            assert torch.equal(got, r), (code, p, t)
+    _lib.check(lib.skel_test_set_updown(f._h, 0))
