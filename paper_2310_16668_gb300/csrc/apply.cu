@@ -185,10 +185,14 @@ void ud_attributes_once() {
     ud_set_attributes<S, false>();
     ud_set_attributes<S, true>();
     if constexpr (std::is_same<S, float>::value) {
-        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(4)));
-        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(4)));
-        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(8)));
-        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(8)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<false, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(4)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<true, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(4)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<false, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(8)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<true, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(8)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<false, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(4)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<true, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(4)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<false, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(8)));
+        CUDA_CHECK(cudaFuncSetAttribute(updown_rows_kernel<true, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ud_rows_smem(8)));
     }
     done = true;
 }
@@ -199,10 +203,17 @@ void ud_attributes_once() {
 constexpr int kUdAsync = 16;
 
 template <bool DOWN, int NW>
-void ud_rows_launch(unsigned nbox, int nout, int nrhs, const UpBox* up, const int32_t* pos, const float* T, float* X,
+void ud_rows_launch(const DevicePlan* dp, int64_t b0, unsigned nbox, int nout, int nrhs, const float* T, float* X,
                     cudaStream_t st) {
     const dim3 grid(nbox, std::max(1u, ceil_div(nout, 32 * NW)), ceil_div(nrhs, kGT));
-    updown_rows_kernel<DOWN, NW><<<grid, 32 * NW, ud_rows_smem(NW), st>>>(up, pos, T, X, nrhs);
+    const UpBox* up = dp->up + b0;
+    if (nrhs % 4 == 0 && dp->ud_tp) {
+        const float* Tp = DOWN ? dp->ud_ttp : dp->ud_tp;
+        const int64_t* off = (DOWN ? dp->ud_ttp_off : dp->ud_tp_off) + b0;
+        updown_rows_kernel<DOWN, NW, true><<<grid, 32 * NW, ud_rows_smem(NW), st>>>(up, dp->pos, Tp, off, X, nrhs);
+    } else {
+        updown_rows_kernel<DOWN, NW, false><<<grid, 32 * NW, ud_rows_smem(NW), st>>>(up, dp->pos, T, nullptr, X, nrhs);
+    }
 }
 
 // one level of the upward or downward pass on the tensor cores (FP32_TC,
@@ -257,14 +268,14 @@ void up_down(bool down, const DevicePlan* dp, int l, const S* T, S* X, int nrhs,
         if (W > kUdAsync) {
             const unsigned nb = (unsigned)(b1 - b0);
             switch (W - kUdAsync) {
-                case 1: down ? ud_rows_launch<true, 1>(nb, nout, nrhs, up, dp->pos, T, X, st)
-                             : ud_rows_launch<false, 1>(nb, nout, nrhs, up, dp->pos, T, X, st); break;
-                case 2: down ? ud_rows_launch<true, 2>(nb, nout, nrhs, up, dp->pos, T, X, st)
-                             : ud_rows_launch<false, 2>(nb, nout, nrhs, up, dp->pos, T, X, st); break;
-                case 4: down ? ud_rows_launch<true, 4>(nb, nout, nrhs, up, dp->pos, T, X, st)
-                             : ud_rows_launch<false, 4>(nb, nout, nrhs, up, dp->pos, T, X, st); break;
-                default: down ? ud_rows_launch<true, 8>(nb, nout, nrhs, up, dp->pos, T, X, st)
-                              : ud_rows_launch<false, 8>(nb, nout, nrhs, up, dp->pos, T, X, st); break;
+                case 1: down ? ud_rows_launch<true, 1>(dp, b0, nb, nout, nrhs, T, X, st)
+                             : ud_rows_launch<false, 1>(dp, b0, nb, nout, nrhs, T, X, st); break;
+                case 2: down ? ud_rows_launch<true, 2>(dp, b0, nb, nout, nrhs, T, X, st)
+                             : ud_rows_launch<false, 2>(dp, b0, nb, nout, nrhs, T, X, st); break;
+                case 4: down ? ud_rows_launch<true, 4>(dp, b0, nb, nout, nrhs, T, X, st)
+                             : ud_rows_launch<false, 4>(dp, b0, nb, nout, nrhs, T, X, st); break;
+                default: down ? ud_rows_launch<true, 8>(dp, b0, nb, nout, nrhs, T, X, st)
+                              : ud_rows_launch<false, 8>(dp, b0, nb, nout, nrhs, T, X, st); break;
             }
             return;
         }
@@ -889,6 +900,27 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, i
             if (fused > 0) dp->eop2 = upload(eop2, dp->bytes);
         }
         dp->up = upload(up, dp->bytes);
+        if (!dp->cplx) {
+            // padded FP32 copies of T for the vectorised up/down copies
+            std::vector<float> tp, ttp;
+            std::vector<int64_t> tpo(up.size()), ttpo(up.size());
+            for (size_t b = 0; b < up.size(); ++b) {
+                const UpBox& ub = up[b];
+                const int k = ub.k, r = ub.n - ub.k, ldk = (k + 3) & ~3, ldr = (r + 3) & ~3;
+                tpo[b] = (int64_t)tp.size();
+                tp.resize(tp.size() + (size_t)ldk * r, 0.f);
+                for (int j = 0; j < r; ++j)
+                    for (int i = 0; i < k; ++i) tp[tpo[b] + i + (size_t)j * ldk] = (float)lay.T[ub.T_off + i + (int64_t)j * k];
+                ttpo[b] = (int64_t)ttp.size();
+                ttp.resize(ttp.size() + (size_t)ldr * k, 0.f);
+                for (int i = 0; i < k; ++i)
+                    for (int j = 0; j < r; ++j) ttp[ttpo[b] + j + (size_t)i * ldr] = (float)lay.T[ub.T_off + i + (int64_t)j * k];
+            }
+            dp->ud_tp = upload(tp, dp->bytes);
+            dp->ud_ttp = upload(ttp, dp->bytes);
+            dp->ud_tp_off = upload(tpo, dp->bytes);
+            dp->ud_ttp_off = upload(ttpo, dp->bytes);
+        }
         if (!dp->cplx && updown_tc) {
             for (int down = 0; down < 2; ++down) {
                 std::vector<UdItem> items;
@@ -981,7 +1013,7 @@ void device_plan_destroy(DevicePlan* dp) {
                     dp->tc_items, dp->tc_part_ptr, dp->tc_part_idx, dp->status,
                     dp->chunk_start, dp->chunk_cnt, dp->chunk_center, dp->tc_b, dp->tc_a, dp->tc_abase,
                     dp->tc_qmask, dp->tc_refs, dp->tc_isym, dp->ud_items_up, dp->ud_items_down,
-                    dp->ud_a_up, dp->ud_a_down};
+                    dp->ud_a_up, dp->ud_a_down, dp->ud_tp, dp->ud_ttp, dp->ud_tp_off, dp->ud_ttp_off};
     for (void* p : ptrs) cudaFree(p);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);

@@ -77,6 +77,13 @@ struct DevicePlan {
     int tcs_stages = 4;                    // stages per CTA of the per-tile stored kernel (4 or 8)
     // tensor-core upward / downward passes (FP32_TC, real kernels): per
     // direction the work items (UdItem) grouped by level and their A blobs
+    // FP32 T of the up/down boxes with columns padded to a multiple of 4
+    // floats, 16-byte aligned per box (upward: k x (n - k), downward: the
+    // transpose), and per box its first float (real kernels)
+    float* ud_tp = nullptr;
+    float* ud_ttp = nullptr;
+    int64_t* ud_tp_off = nullptr;
+    int64_t* ud_ttp_off = nullptr;
     void* ud_items_up = nullptr;
     void* ud_items_down = nullptr;
     float* ud_a_up = nullptr;

@@ -9,7 +9,10 @@
 // of updown_kernel with one warp per CTA: every launch shape of both kernels
 // gives the same bits, so the autotuner may pick any of them per level. The
 // entry indices of the chunk after next are loaded while the current chunk's
-// copies are waited for.
+// copies are waited for. VEC: 16-byte copies, from a copy of T whose columns
+// are padded to a multiple of 4 floats (zeros) and start 16-byte aligned
+// (toff: per box, its first float), and B rows of 32 columns (nrhs a
+// multiple of 4); else 4-byte copies from T itself.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,6 +26,9 @@ namespace skel {
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
@@ -34,10 +40,11 @@ __host__ __device__ constexpr int ud_rows_smem(int NW) {
     return kUdrStages * (NW + 1) * kGT * kGT * (int)sizeof(float);
 }
 
-template <bool DOWN, int NW>
+template <bool DOWN, int NW, bool VEC>
 __global__ void __launch_bounds__(32 * NW) updown_rows_kernel(const UpBox* __restrict__ up,
                                                               const int32_t* __restrict__ pos,
-                                                              const float* __restrict__ T, float* X, int nrhs) {
+                                                              const float* __restrict__ T,
+                                                              const int64_t* __restrict__ toff, float* X, int nrhs) {
     constexpr int NS = ud_streams<float>();
     constexpr int ROWS = 32 * NW;
     constexpr int STAGE = (NW + 1) * kGT * kGT;           // floats per stage: A then B
@@ -80,14 +87,34 @@ __global__ void __launch_bounds__(32 * NW) updown_rows_kernel(const UpBox* __res
         if (lane >= jn) return 0;
         return DOWN ? (u.dst + j0 + lane) : (u.off + pos[u.off + k + j0 + lane]);
     };
+    const int ld = VEC ? (nout + 3) & ~3 : nout;         // column stride of this box's block
+    const int64_t t0 = VEC ? toff[blockIdx.x] : u.T_off;
     // the copies of chunk ch into stage buf: A (inner jj, row tid), B rows jj = warp, warp + NW, ...
     auto issue = [&](int ch, int64_t ri, float* buf) {
         const int j0 = ch * kGT, jn = min(kGT, ninner - j0);
         const uint32_t sa = (uint32_t)__cvta_generic_to_shared(buf);
+        if constexpr (VEC) {
+            // A: 32 columns x ROWS / 4 segments of 4 rows; B: 32 rows x 8 segments
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int idx = tid + m * ROWS, jj = idx / (ROWS / 4), r4 = (idx % (ROWS / 4)) * 4;
+                const bool av = jj < jn && row0 + r4 < ld;
+                const float* ga = av ? T + t0 + row0 + r4 + (int64_t)(j0 + jj) * ld : T;
+                cp_async16(sa + (uint32_t)(jj * ROWS + r4) * 4u, ga, av ? 16u : 0u);
+            }
+            for (int idx = tid; idx < kGT * 8; idx += ROWS) {
+                const int jj = idx >> 3, c = c0 + (idx & 7) * 4;
+                const int64_t rj = __shfl_sync(0xffffffffu, ri, jj);
+                const int nb = jj < jn ? max(0, min(16, (nrhs - c) * 4)) : 0;
+                const float* gb = nb > 0 ? X + rj * nrhs + c : X;
+                cp_async16(sa + (uint32_t)(kGT * ROWS + jj * kGT + (idx & 7) * 4) * 4u, gb, (uint32_t)nb);
+            }
+            return;
+        }
 #pragma unroll 8
         for (int jj = 0; jj < kGT; ++jj) {
             const bool av = jj < jn && arow;
-            const float* ga = av ? T + u.T_off + row0 + tid + (int64_t)(j0 + jj) * nout : T;
+            const float* ga = av ? T + t0 + row0 + tid + (int64_t)(j0 + jj) * ld : T;
             cp_async4(sa + (uint32_t)(jj * ROWS + tid) * 4u, ga, av ? 4u : 0u);
         }
 #pragma unroll
