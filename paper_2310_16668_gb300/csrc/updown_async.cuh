@@ -1,7 +1,7 @@
 // Upward / downward passes (FP32), the CTA-wide form: a CTA owns 32 NW
 // output rows (NW warps, 32 rows each, lane = right-hand side) x 32
 // right-hand sides of one box and streams the inner index in chunks of 32
-// through a three-stage pipeline of asynchronous copies that all its threads
+// through a two-stage pipeline of asynchronous copies that all its threads
 // issue: per chunk the A block (32 inner x 32 NW rows, zero-filled past the
 // box) and the chunk's 32 rows of X (shared by the warps). The chunks are
 // taken in stream order (stream s: chunks s, s + NS, ...), each stream summed
@@ -34,7 +34,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
 }
 
-constexpr int kUdrStages = 3;
+constexpr int kUdrStages = 2;
 // dynamic shared memory: per stage the A block (32 x 32 NW) and the B block (32 x 32)
 __host__ __device__ constexpr int ud_rows_smem(int NW) {
     return kUdrStages * (NW + 1) * kGT * kGT * (int)sizeof(float);
