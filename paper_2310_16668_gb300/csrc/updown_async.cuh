@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(32 * NW) updown_rows_kernel(const UpBox* __res
         if (ch + NS < nch) ch += NS;
         else ch = ++s;
     };
-    float acc[kGT], tot[kGT];
+    const int rg = lane & 7, cg = lane >> 3;             // compute: 4 rows x 8 columns per thread
+    float acc[kGT], tot[kGT];                            // element (r, c) at 8 r + c
 #pragma unroll
     for (int i = 0; i < kGT; ++i) acc[i] = tot[i] = 0.f;
     if (nch > 0) {
@@ -156,10 +157,27 @@ __global__ void __launch_bounds__(32 * NW) updown_rows_kernel(const UpBox* __res
             cp_async_commit();
             cp_async_wait<kUdrStages - 1>();
             __syncthreads();
-            const float* As = sm + (t % kUdrStages) * STAGE;
-            const float* Bs = As + kGT * ROWS;
+            const float* As = sm + (t % kUdrStages) * STAGE + warp * kGT + 4 * rg;
+            const float* Bs = sm + (t % kUdrStages) * STAGE + kGT * ROWS + 8 * cg;
+            // thread (rg, cg): rows 4 rg .. + 3 of the warp's 32, columns
+            // 8 cg .. + 7; each element gets the same FMA chain as in
+            // updown_kernel (one FMA per inner index, in order)
 #pragma unroll 4
-            for (int jj = 0; jj < kGT; ++jj) ud_rows<float>(acc, As + jj * ROWS + warp * kGT, Bs[jj * kGT + lane]);
+            for (int jj = 0; jj < kGT; ++jj) {
+                const float4 a = *reinterpret_cast<const float4*>(As + jj * ROWS);
+                const float4 b0 = *reinterpret_cast<const float4*>(Bs + jj * kGT);
+                const float4 b1 = *reinterpret_cast<const float4*>(Bs + jj * kGT + 4);
+                const float av[4] = {a.x, a.y, a.z, a.w};
+                const float2 bp[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                                      make_float2(b1.z, b1.w)};
+                float2* acc2 = reinterpret_cast<float2*>(acc);
+#pragma unroll
+                for (int r4 = 0; r4 < 4; ++r4) {
+                    const float2 a2 = make_float2(av[r4], av[r4]);
+#pragma unroll
+                    for (int c2 = 0; c2 < 4; ++c2) acc2[r4 * 4 + c2] = __ffma2_rn(a2, bp[c2], acc2[r4 * 4 + c2]);
+                }
+            }
             if (!(cc + NS < nch)) {                      // the stream's last chunk
 #pragma unroll
                 for (int i = 0; i < kGT; ++i) {
@@ -171,28 +189,29 @@ __global__ void __launch_bounds__(32 * NW) updown_rows_kernel(const UpBox* __res
             __syncthreads();                             // before this stage is filled again
         }
     }
-    if (!colok) return;
-    // this warp's 32 rows in two batches of 16: every old value of a batch
-    // is loaded before its stores
+    // this thread's 4 rows x 8 columns: every old value is loaded before the stores
+    const int cb = c0 + 8 * cg;
+    int64_t src[4], dst[4];
 #pragma unroll
-    for (int q0 = 0; q0 < kGT; q0 += 16) {
-        float old[16];
-        int64_t dst[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int orow = row0 + warp * kGT + q0 + q;
-            dst[q] = -1;
-            if (orow < nout) {
-                const int64_t src = DOWN ? (u.off + pos[u.off + k + orow]) * nrhs + col
-                                         : (u.off + pos[u.off + orow]) * nrhs + col;
-                dst[q] = DOWN ? src : (u.dst + orow) * nrhs + col;
-                old[q] = X[src];
-            }
+    for (int r4 = 0; r4 < 4; ++r4) {
+        const int orow = row0 + warp * kGT + 4 * rg + r4;
+        dst[r4] = -1;
+        if (orow < nout && cb < nrhs) {
+            src[r4] = DOWN ? (u.off + pos[u.off + k + orow]) * nrhs : (u.off + pos[u.off + orow]) * nrhs;
+            dst[r4] = DOWN ? src[r4] : (u.dst + orow) * nrhs;
         }
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-            if (dst[q] >= 0) X[dst[q]] = old[q] + tot[q0 + q];
     }
+    float old[kGT];
+#pragma unroll
+    for (int r4 = 0; r4 < 4; ++r4)
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            old[8 * r4 + c] = (dst[r4] >= 0 && cb + c < nrhs) ? X[src[r4] + cb + c] : 0.f;
+#pragma unroll
+    for (int r4 = 0; r4 < 4; ++r4)
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (dst[r4] >= 0 && cb + c < nrhs) X[dst[r4] + cb + c] = old[8 * r4 + c] + tot[8 * r4 + c];
 }
 
 }  // namespace skel
