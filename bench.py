@@ -79,6 +79,9 @@ def parse_args():
                         "kernel tiles, chosen by measurement); none: the default rules, tiles on the fly")
     p.add_argument("--updown-tc", action="store_true",
                    help="upward / downward skeleton GEMMs on the tensor cores (skel_options.updown_tc)")
+    p.add_argument("--updown-shape", type=int, default=None,
+                   help="force the FP32 up/down launch shape on every level (skel_test_set_updown code: 1, 2, 4, 8 "
+                        "plain kernel warps; 17, 18, 20, 24 the CTA-wide kernel); same result, for profiling")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -565,6 +568,9 @@ def run_ours(args):
             tuning["t_tune_s"] = time.perf_counter() - t0
         except Exception as e:                          # keep the untuned plan
             tuning = {"error": str(e)}
+    if args.updown_shape is not None:
+        from paper_2310_16668_gb300 import _lib
+        _lib.check(_lib.load().skel_test_set_updown(fmm._h, args.updown_shape))
     info = fmm.info()
     pairs = info["pairs_direct"] + info["pairs_far"]
 
