@@ -87,9 +87,11 @@ typedef struct {
                              the on-the-fly apply up to FP32 rounding of those values.
                          0 = none. Real kernels only (ignored otherwise).
                          SKEL_ERR_OOM if the values do not fit.                         */
-    int store_stages; /* per-tile store: bulk-copy stages per CTA of its apply kernel,
-                         4 (two CTAs per SM) or 8 (one CTA per SM); 0 = 4. Same result
-                         either way; skel_autotune may change it.                       */
+    int store_stages; /* per-tile store: the form of its apply kernel: 4 bulk-copy
+                         stages per CTA (two CTAs per SM), 8 (one CTA per SM), or 5 =
+                         split rings (5 slots of kernel values released when read,
+                         3 of B operand released by the MMAs); 0 = 4. Same result
+                         every way; skel_autotune may change it.                        */
     int updown_tc;    /* 1 = FP32_TC applies of a real kernel also run the upward and
                          downward skeleton GEMMs on the tensor cores (three-part TF32
                          split, 6 products); the plan keeps T in tile order (about the
@@ -456,8 +458,8 @@ typedef struct {
     int    tc_stages;         /* pipeline depth (bulk-copy stages) chosen for the on-the-fly
                                  tensor-core kernel: 4, 6 or 8 (0: not tuned)                  */
     double ms_sym;            /* one tensor-core pass reading the symmetric store (-1: not timed) */
-    int    tcs_stages;        /* stages per CTA chosen for the per-tile stored kernel: 4 (two CTAs
-                                 per SM) or 8 (one CTA per SM); 0: not tuned                     */
+    int    tcs_stages;        /* form chosen for the per-tile stored kernel (store_stages: 4, 5
+                                 or 8); 0: not tuned                                             */
 } skel_tuning;
 int skel_autotune(skel_handle h, int nrhs, int allow_store, void* stream, skel_tuning* out);
 

@@ -39,8 +39,8 @@ class SkelFMM:
     applies read them instead of evaluating the kernel: 1 (or True) every
     tile's values (same result bit for bit), 2 the symmetric store (each
     block two tiles share held once; same result up to FP32 rounding).
-    ``store_stages`` (4 or 8, 0 = 4): bulk-copy stages per CTA of the
-    per-tile store's kernel (same result; the autotuner may change it).
+    ``store_stages`` (4, 5 or 8, 0 = 4): the per-tile store kernel's form
+    (skel_options.store_stages; same result; the autotuner may change it).
     ``updown_tc``: FP32_TC applies also run the upward / downward skeleton
     GEMMs on the tensor cores (less accurate than the CUDA-core default on
     these cancelling sums; see skel_options.updown_tc).

@@ -41,6 +41,7 @@
 #include "skel_kernels.cuh"
 #include "tc_kernels.cuh"
 #include "tc_complex.cuh"
+#include "tc_stored_ring.cuh"
 #include "tc_updown.cuh"
 #include "updown_async.cuh"
 
@@ -374,6 +375,8 @@ void set_tc_attributes() {
     CUDA_CHECK(cudaFuncSetAttribute(tc_stored_kernel<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcs_smem_request<8>()));
     CUDA_CHECK(cudaFuncSetAttribute(tc_sym_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTsySmemRequest));
     CUDA_CHECK(cudaFuncSetAttribute(tc_sym_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTsySmemRequest));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_stored_ring_kernel<0, 5, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcr_smem_request<5, 3>()));
+    CUDA_CHECK(cudaFuncSetAttribute(tc_stored_ring_kernel<1, 5, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcr_smem_request<5, 3>()));
     CUDA_CHECK(cudaFuncSetAttribute(tc_cnear_kernel<kNSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTccSmemRequest));
     done = true;
 }
@@ -445,7 +448,10 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
         } else if (stored) {
             // stages per CTA: the autotuner's choice (same arithmetic)
             const unsigned g = (unsigned)dp->n_tc;
-            if (dp->tcs_stages == 8) {
+            if (dp->tcs_stages == 5) {
+                kidx == 0 ? tc_stored_ring_kernel<0, 5, 3><<<g, kTcThreads, tcr_smem_request<5, 3>(), st>>>(t)
+                          : tc_stored_ring_kernel<1, 5, 3><<<g, kTcThreads, tcr_smem_request<5, 3>(), st>>>(t);
+            } else if (dp->tcs_stages == 8) {
                 kidx == 0 ? tc_stored_kernel<0, 8><<<g, kTcThreads, tcs_smem_request<8>(), st>>>(t)
                           : tc_stored_kernel<1, 8><<<g, kTcThreads, tcs_smem_request<8>(), st>>>(t);
             } else {
@@ -846,7 +852,7 @@ void build_ud_items(bool down, const std::vector<UpBox>& up, const std::vector<i
 DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, int store_tiles, int store_stages,
                                bool updown_tc) {
     DevicePlan* dp = new DevicePlan();
-    dp->tcs_stages = store_stages == 8 ? 8 : 4;
+    dp->tcs_stages = store_stages == 8 || store_stages == 5 ? store_stages : 4;
     try {
         CUDA_CHECK(cudaGetDevice(&dp->device));
         dp->dim = p.tree.dim;
@@ -1175,13 +1181,19 @@ TuneReport device_autotune(DevicePlan* dp, int nrhs, bool allow_store, void* str
                 }
                 double ms = time_ms(tc, 3);
                 if (mode == 1) {
-                    // the per-tile store's stages per CTA: 4 (two CTAs per SM) or 8 (one)
-                    const int keep_stages = dp->tcs_stages;
-                    dp->tcs_stages = keep_stages == 8 ? 4 : 8;
-                    const double ms2 = time_ms(tc, 3);
-                    if (ms2 < ms) ms = ms2;
-                    else dp->tcs_stages = keep_stages;
-                    rep.tcs_stages = dp->tcs_stages;
+                    // the per-tile store's kernel form: 4 stages (two CTAs per
+                    // SM), 8 (one), or 5 value + 3 operand slots (split rings)
+                    int best_stages = dp->tcs_stages;
+                    for (int ns : {4, 8, 5}) {
+                        if (ns == best_stages) continue;
+                        const int keep_stages = dp->tcs_stages;
+                        dp->tcs_stages = ns;
+                        const double ms2 = time_ms(tc, 3);
+                        if (ms2 < ms) ms = ms2, best_stages = ns;
+                        dp->tcs_stages = keep_stages;
+                    }
+                    dp->tcs_stages = best_stages;
+                    rep.tcs_stages = best_stages;
                 }
                 (mode == 2 ? rep.ms_sym : rep.ms_stored) = ms;
                 if (ms < best) best = ms, best_mode = mode;

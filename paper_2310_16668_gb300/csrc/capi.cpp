@@ -92,8 +92,8 @@ void finalize(skel_plan* h, const skel_options* opts) {
     h->n_mix_items = (int64_t)lay.mix_items.size();
     h->pairs_tc = lay.pairs_tc;
     if (opts && (opts->store_tiles < 0 || opts->store_tiles > 2)) throw Error(SKEL_ERR_ARG, "store_tiles must be 0, 1 or 2");
-    if (opts && opts->store_stages != 0 && opts->store_stages != 4 && opts->store_stages != 8)
-        throw Error(SKEL_ERR_ARG, "store_stages must be 0, 4 or 8");
+    if (opts && opts->store_stages != 0 && opts->store_stages != 4 && opts->store_stages != 5 && opts->store_stages != 8)
+        throw Error(SKEL_ERR_ARG, "store_stages must be 0, 4, 5 or 8");
     if (!h->host_only)
         h->dev = skel::device_plan_create(h->plan, lay, h->nrhs_max, opts ? opts->store_tiles : 0,
                                           opts && opts->store_stages ? opts->store_stages : 4,
@@ -435,8 +435,9 @@ int skel_merge(const skel_handle* hs, int nsets, const skel_options* opts, skel_
             h->host_only = opts && opts->host_only;
             if (opts && (opts->store_tiles < 0 || opts->store_tiles > 2))
                 throw Error(SKEL_ERR_ARG, "store_tiles must be 0, 1 or 2");
-            if (opts && opts->store_stages != 0 && opts->store_stages != 4 && opts->store_stages != 8)
-                throw Error(SKEL_ERR_ARG, "store_stages must be 0, 4 or 8");
+            if (opts && opts->store_stages != 0 && opts->store_stages != 4 && opts->store_stages != 5 &&
+                opts->store_stages != 8)
+                throw Error(SKEL_ERR_ARG, "store_stages must be 0, 4, 5 or 8");
             if (!h->host_only)
                 h->dev = skel::device_plan_create(h->plan, m, h->nrhs_max, opts ? opts->store_tiles : 0,
                                                   opts && opts->store_stages ? opts->store_stages : 4,

@@ -37,12 +37,14 @@ def _gpu():
     _lib.load().skel_test_fail_alloc(0)
 
 
-@pytest.mark.parametrize("kind,stored", [("laplace3d", 0), ("laplace3d", 1), ("laplace3d", 2), ("helmholtz3d", 0)])
-def test_bounded_wait_runs_out(kind, stored):
+@pytest.mark.parametrize("kind,stored,stages", [("laplace3d", 0, 0), ("laplace3d", 1, 4), ("laplace3d", 1, 5),
+                                                ("laplace3d", 2, 0), ("helmholtz3d", 0, 0)])
+def test_bounded_wait_runs_out(kind, stored, stages):
     """On every tensor-core kernel: on the fly, per-tile store, symmetric
     store, and the complex (3D Helmholtz) kernel."""
     x = W.points_uniform(20000, 3, 61)
-    fmm = SkelFMM(x, kind, 1e-6, 64, nrhs_max=32, store_tiles=stored, kappa=25.0 if kind == "helmholtz3d" else 0.0)
+    fmm = SkelFMM(x, kind, 1e-6, 64, nrhs_max=32, store_tiles=stored, store_stages=stages,
+                  kappa=25.0 if kind == "helmholtz3d" else 0.0)
     assert fmm.info()["n_tc_items"] > 0 and fmm.info()["store_mode"] == stored
     if kind == "helmholtz3d":
         q = torch.from_numpy(W.charges_complex(x.shape[0], 32, 62)).cuda().to(torch.complex64)
