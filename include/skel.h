@@ -174,10 +174,12 @@ int skel_build_batch(int nsets, const double* const* points, const int64_t* n, i
  * skel_apply — u = A~ q by Algorithm 2 on the GPU.
  *   q, u       n x nrhs (see conventions); device pointers (the common case:
  *              asynchronous on `stream`, no allocation, CUDA-graph
- *              capturable) or host pointers (then staged through device
- *              buffers that the handle allocates on first use, and the call
- *              synchronises `stream` before returning). q and u must not
- *              overlap; u is overwritten.
+ *              capturable) or host pointers: page-locked host memory
+ *              (cudaHostAlloc, cudaHostRegister) is read and written in place
+ *              by the apply's permutation kernels, other host memory is
+ *              staged through device buffers that the handle allocates on
+ *              first use; either way the call synchronises `stream` before
+ *              returning. q and u must not overlap; u is overwritten.
  *   nrhs       1 <= nrhs <= opts.nrhs_max
  *   precision  SKEL_FP64 | SKEL_FP32 | SKEL_FP32_TC
  *   stream     a cudaStream_t, or NULL for the legacy default stream

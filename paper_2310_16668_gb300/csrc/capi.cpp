@@ -114,6 +114,17 @@ bool is_device_ptr(const void* p) {
     return w == 1;
 }
 
+// the device address of page-locked host memory (cudaHostAlloc /
+// cudaHostRegister; with unified addressing the same pointer), else null
+const void* mapped_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int do_apply(skel_handle h, const void* q, void* u, int nrhs, int precision, void* stream, bool transpose) {
     return guarded([&] {
         if (!h) throw Error(SKEL_ERR_ARG, "handle is NULL");
@@ -130,10 +141,19 @@ int do_apply(skel_handle h, const void* q, void* u, int nrhs, int precision, voi
         const size_t bytes = elem * (size_t)dp->N * nrhs;
         if (q == u || ((const char*)q < (const char*)u + bytes && (const char*)u < (const char*)q + bytes))
             throw Error(SKEL_ERR_ARG, "q and u overlap");
-        const bool qd = is_device_ptr(q), ud = is_device_ptr(u);
+        bool qd = is_device_ptr(q), ud = is_device_ptr(u);
+        const bool host_call = !qd || !ud;
         cudaStream_t st = (cudaStream_t)stream;
         const void* qq = q;
         void* uu = u;
+        // page-locked host buffers are read and written in place by the
+        // permutation kernels (over the host link): no staging copy
+        if (!qd) {
+            if (const void* m = mapped_host(q)) qq = m, qd = true;
+        }
+        if (!ud) {
+            if (const void* m = mapped_host(u)) uu = const_cast<void*>(m), ud = true;
+        }
         if (!qd || !ud) {
             if (dp->stage_bytes < bytes) {
                 cudaFree(dp->stage_in);
@@ -162,7 +182,7 @@ int do_apply(skel_handle h, const void* q, void* u, int nrhs, int precision, voi
             if (cudaMemcpyAsync(u, uu, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
                 throw Error(SKEL_ERR_CUDA, "device-to-host copy failed");
         }
-        if (!qd || !ud) {
+        if (host_call) {
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) throw Error(SKEL_ERR_CUDA, std::string("apply: ") + cudaGetErrorString(e));
         }

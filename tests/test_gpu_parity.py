@@ -152,11 +152,23 @@ def test_transpose_matches_oracle(oracle_case):
 
 
 def test_host_pointers_match_device(oracle_case):
+    """Host buffers give the device result bit for bit: pageable ones are
+    staged by the C-ABI, page-locked ones read and written in place by the
+    permutation kernels (1 and 32 right-hand sides: both permutation forms)."""
     kind, x, sk, fmm = oracle_case
     q = _charges(kind, x.shape[0], 1, 13)[:, 0]
     u_host = fmm.apply(q, "fp64")                       # numpy in, numpy out: staged by the C-ABI
     u_dev = fmm.apply(torch.from_numpy(q).cuda(), "fp64").cpu().numpy()
     assert np.array_equal(u_host, u_dev)
+    for nrhs in (1, 32):
+        qn = torch.from_numpy(np.ascontiguousarray(_charges(kind, x.shape[0], nrhs, 14).T))
+        qp = qn.pin_memory()
+        up = torch.empty_like(qp).pin_memory()
+        fmm.apply_into(qp.t(), up.t(), nrhs, "fp64")
+        ud = torch.empty_like(qn).cuda()
+        fmm.apply_into(qn.cuda().t(), ud.t(), nrhs, "fp64")
+        torch.cuda.synchronize()
+        assert torch.equal(up, ud.cpu())
 
 
 @pytest.mark.parametrize("kind,dim,b,tol", [("laplace3d", 3, 32, 1e-6), ("laplace2d", 2, 32, 1e-8),
