@@ -204,16 +204,21 @@ void ud_attributes_once() {
 constexpr int kUdAsync = 16;
 
 template <bool DOWN, int NW>
-void ud_rows_launch(const DevicePlan* dp, int64_t b0, unsigned nbox, int nout, int nrhs, const float* T, float* X,
-                    cudaStream_t st) {
-    const dim3 grid(nbox, std::max(1u, ceil_div(nout, 32 * NW)), ceil_div(nrhs, kGT));
-    const UpBox* up = dp->up + b0;
+void ud_rows_launch(const DevicePlan* dp, int l, int nrhs, const float* T, float* X, cudaStream_t st) {
+    constexpr int wi = NW == 1 ? 0 : NW == 2 ? 1 : NW == 4 ? 2 : 3;
+    const std::vector<int64_t>& ptr = dp->ud_work_ptr[DOWN ? 1 : 0][wi];
+    const int64_t w0 = ptr[l], w1 = ptr[l + 1];
+    if (w1 <= w0) return;
+    const dim3 grid((unsigned)(w1 - w0), 1, ceil_div(nrhs, kGT));
+    const int2* work = dp->ud_work[DOWN ? 1 : 0][wi] + w0;
     if (nrhs % 4 == 0 && dp->ud_tp) {
         const float* Tp = DOWN ? dp->ud_ttp : dp->ud_tp;
-        const int64_t* off = (DOWN ? dp->ud_ttp_off : dp->ud_tp_off) + b0;
-        updown_rows_kernel<DOWN, NW, true><<<grid, 32 * NW, ud_rows_smem(NW), st>>>(up, dp->pos, Tp, off, X, nrhs);
+        const int64_t* off = DOWN ? dp->ud_ttp_off : dp->ud_tp_off;
+        updown_rows_kernel<DOWN, NW, true><<<grid, 32 * NW, ud_rows_smem(NW), st>>>(dp->up, work, dp->pos, Tp, off, X,
+                                                                                     nrhs);
     } else {
-        updown_rows_kernel<DOWN, NW, false><<<grid, 32 * NW, ud_rows_smem(NW), st>>>(up, dp->pos, T, nullptr, X, nrhs);
+        updown_rows_kernel<DOWN, NW, false><<<grid, 32 * NW, ud_rows_smem(NW), st>>>(dp->up, work, dp->pos, T, nullptr,
+                                                                                      X, nrhs);
     }
 }
 
@@ -267,16 +272,15 @@ void up_down(bool down, const DevicePlan* dp, int l, const S* T, S* X, int nrhs,
     const UpBox* up = dp->up + b0;
     if constexpr (std::is_same<S, float>::value) {
         if (W > kUdAsync) {
-            const unsigned nb = (unsigned)(b1 - b0);
             switch (W - kUdAsync) {
-                case 1: down ? ud_rows_launch<true, 1>(dp, b0, nb, nout, nrhs, T, X, st)
-                             : ud_rows_launch<false, 1>(dp, b0, nb, nout, nrhs, T, X, st); break;
-                case 2: down ? ud_rows_launch<true, 2>(dp, b0, nb, nout, nrhs, T, X, st)
-                             : ud_rows_launch<false, 2>(dp, b0, nb, nout, nrhs, T, X, st); break;
-                case 4: down ? ud_rows_launch<true, 4>(dp, b0, nb, nout, nrhs, T, X, st)
-                             : ud_rows_launch<false, 4>(dp, b0, nb, nout, nrhs, T, X, st); break;
-                default: down ? ud_rows_launch<true, 8>(dp, b0, nb, nout, nrhs, T, X, st)
-                              : ud_rows_launch<false, 8>(dp, b0, nb, nout, nrhs, T, X, st); break;
+                case 1: down ? ud_rows_launch<true, 1>(dp, l, nrhs, T, X, st)
+                             : ud_rows_launch<false, 1>(dp, l, nrhs, T, X, st); break;
+                case 2: down ? ud_rows_launch<true, 2>(dp, l, nrhs, T, X, st)
+                             : ud_rows_launch<false, 2>(dp, l, nrhs, T, X, st); break;
+                case 4: down ? ud_rows_launch<true, 4>(dp, l, nrhs, T, X, st)
+                             : ud_rows_launch<false, 4>(dp, l, nrhs, T, X, st); break;
+                default: down ? ud_rows_launch<true, 8>(dp, l, nrhs, T, X, st)
+                              : ud_rows_launch<false, 8>(dp, l, nrhs, T, X, st); break;
             }
             return;
         }
@@ -922,6 +926,24 @@ DevicePlan* device_plan_create(const Plan& p, const Layout& lay, int nrhs_max, i
                 for (int i = 0; i < k; ++i)
                     for (int j = 0; j < r; ++j) ttp[ttpo[b] + j + (size_t)i * ldr] = (float)lay.T[ub.T_off + i + (int64_t)j * k];
             }
+            // work lists of the CTA-wide kernel, per direction and rows per CTA
+            for (int dir = 0; dir < 2; ++dir)
+                for (int wi = 0; wi < 4; ++wi) {
+                    const int rows = 32 << wi;
+                    std::vector<int2> w;
+                    std::vector<int64_t>& wp = dp->ud_work_ptr[dir][wi];
+                    wp.assign(dp->up_level_ptr.size(), 0);
+                    for (size_t l = 0; l + 1 < dp->up_level_ptr.size(); ++l) {
+                        wp[l] = (int64_t)w.size();
+                        for (int64_t b = dp->up_level_ptr[l]; b < dp->up_level_ptr[l + 1]; ++b) {
+                            const int nout = dir ? up[b].n - up[b].k : up[b].k;
+                            const int nblk = std::max(dir ? 1 : 0, (nout + rows - 1) / rows);
+                            for (int i = 0; i < nblk; ++i) w.push_back(make_int2((int)b, i * rows));
+                        }
+                    }
+                    wp.back() = (int64_t)w.size();
+                    dp->ud_work[dir][wi] = upload(w, dp->bytes);
+                }
             dp->ud_tp = upload(tp, dp->bytes);
             dp->ud_ttp = upload(ttp, dp->bytes);
             dp->ud_tp_off = upload(tpo, dp->bytes);
@@ -1021,6 +1043,8 @@ void device_plan_destroy(DevicePlan* dp) {
                     dp->tc_qmask, dp->tc_refs, dp->tc_isym, dp->ud_items_up, dp->ud_items_down,
                     dp->ud_a_up, dp->ud_a_down, dp->ud_tp, dp->ud_ttp, dp->ud_tp_off, dp->ud_ttp_off};
     for (void* p : ptrs) cudaFree(p);
+    for (int dir = 0; dir < 2; ++dir)
+        for (int wi = 0; wi < 4; ++wi) cudaFree(dp->ud_work[dir][wi]);
     for (void* e : dp->events)
         if (e) cudaEventDestroy((cudaEvent_t)e);
     free_buffers(dp->p64);

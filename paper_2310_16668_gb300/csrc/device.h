@@ -84,6 +84,10 @@ struct DevicePlan {
     float* ud_ttp = nullptr;
     int64_t* ud_tp_off = nullptr;
     int64_t* ud_ttp_off = nullptr;
+    // work lists of the CTA-wide up/down kernel: per direction (0 up, 1 down)
+    // and rows per CTA (32 << i), (box, first row) pairs grouped by level
+    int2* ud_work[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+    std::vector<int64_t> ud_work_ptr[2][4];
     void* ud_items_up = nullptr;
     void* ud_items_down = nullptr;
     float* ud_a_up = nullptr;

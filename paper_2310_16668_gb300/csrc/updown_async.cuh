@@ -40,8 +40,14 @@ __host__ __device__ constexpr int ud_rows_smem(int NW) {
     return kUdrStages * (NW + 1) * kGT * kGT * (int)sizeof(float);
 }
 
+// The CTAs come from a work list of (box, first output row) pairs, one per
+// 32 NW rows of each box of the level (a downward box without redundant rows
+// keeps one, for its u_S += uhat): in adaptive trees the boxes of a level
+// differ widely in size, and a grid sized by the largest would launch
+// mostly empty CTAs.
 template <bool DOWN, int NW, bool VEC>
 __global__ void __launch_bounds__(32 * NW) updown_rows_kernel(const UpBox* __restrict__ up,
+                                                              const int2* __restrict__ work,
                                                               const int32_t* __restrict__ pos,
                                                               const float* __restrict__ T,
                                                               const int64_t* __restrict__ toff, float* X, int nrhs) {
@@ -51,14 +57,15 @@ __global__ void __launch_bounds__(32 * NW) updown_rows_kernel(const UpBox* __res
     static_assert(NW == 1 || NW == 2 || NW == 4 || NW == 8, "warps per CTA");
     extern __shared__ __align__(16) unsigned char udr_raw[];
     float* sm = reinterpret_cast<float*>(udr_raw);
-    const UpBox u = up[blockIdx.x];
+    const int2 wi = work[blockIdx.x];
+    const UpBox u = up[wi.x];
     const int k = u.k, r = u.n - u.k;
     const int nout = DOWN ? r : k, ninner = DOWN ? k : r;
-    const int row0 = blockIdx.y * ROWS, c0 = blockIdx.z * kGT;
+    const int row0 = wi.y, c0 = blockIdx.z * kGT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int col = c0 + lane;
     const bool colok = col < nrhs;
-    if (DOWN && blockIdx.y == 0 && colok) {              // u_S += uhat, this CTA's columns
+    if (DOWN && row0 == 0 && colok) {                    // u_S += uhat, this CTA's columns
         for (int i0 = warp; i0 < k; i0 += 8 * NW) {
             float uh[8], us[8];
             int64_t at[8];
@@ -88,7 +95,7 @@ __global__ void __launch_bounds__(32 * NW) updown_rows_kernel(const UpBox* __res
         return DOWN ? (u.dst + j0 + lane) : (u.off + pos[u.off + k + j0 + lane]);
     };
     const int ld = VEC ? (nout + 3) & ~3 : nout;         // column stride of this box's block
-    const int64_t t0 = VEC ? toff[blockIdx.x] : u.T_off;
+    const int64_t t0 = VEC ? toff[wi.x] : u.T_off;
     // the copies of chunk ch into stage buf: A (inner jj, row tid), B rows jj = warp, warp + NW, ...
     auto issue = [&](int ch, int64_t ri, float* buf) {
         const int j0 = ch * kGT, jn = min(kGT, ninner - j0);
