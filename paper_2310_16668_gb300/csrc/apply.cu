@@ -432,49 +432,48 @@ int run_tc(DevicePlan* dp, DeviceBuffers* b, int nrhs, cudaStream_t st, int& tc_
             tc_cnear_kernel<kNSC><<<(unsigned)dp->n_tc, kThreadsC, kTccSmemRequest, st>>>(t);
             CUDA_CHECK(cudaGetLastError());
         }
-        dp->test_withhold = false;
-        return launches;
-    }
-    for (int r0 = 0; r0 < nrhs; r0 += kTcN, ++launches, ++tc_launches) {
-        t.r0 = r0;
-        t.withhold_item = (dp->test_withhold && r0 == 0) ? 0 : -1;
-        // the pass's B operand blocks, then the translations
-        tc_bprep_kernel<false><<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q,
-                                                               nrhs, r0, (const float4*)b->X,
-                                                               (const float4*)b->Xlo,
-                                                               (const float4*)dp->chunk_center, dp->tc_b);
-        CUDA_CHECK(cudaGetLastError());
-        ++launches;
-        if (r0 == 0) mark(dp, kMainEvent, st);
-        if (stored && dp->store_mode == 2) {
-            if (kidx == 0) tc_sym_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTsySmemRequest, st>>>(t);
-            else tc_sym_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTsySmemRequest, st>>>(t);
-        } else if (stored) {
-            // stages per CTA: the autotuner's choice (same arithmetic)
-            const unsigned g = (unsigned)dp->n_tc;
-            if (dp->tcs_stages == 5) {
-                kidx == 0 ? tc_stored_ring_kernel<0, 5, 3><<<g, kTcThreads, tcr_smem_request<5, 3>(), st>>>(t)
-                          : tc_stored_ring_kernel<1, 5, 3><<<g, kTcThreads, tcr_smem_request<5, 3>(), st>>>(t);
-            } else if (dp->tcs_stages == 8) {
-                kidx == 0 ? tc_stored_kernel<0, 8><<<g, kTcThreads, tcs_smem_request<8>(), st>>>(t)
-                          : tc_stored_kernel<1, 8><<<g, kTcThreads, tcs_smem_request<8>(), st>>>(t);
+    } else {
+        for (int r0 = 0; r0 < nrhs; r0 += kTcN, ++launches, ++tc_launches) {
+            t.r0 = r0;
+            t.withhold_item = (dp->test_withhold && r0 == 0) ? 0 : -1;
+            // the pass's B operand blocks, then the translations
+            tc_bprep_kernel<false><<<(unsigned)dp->n_chunks, 256, 0, st>>>(dp->chunk_start, dp->chunk_cnt, (const float*)b->Q,
+                                                                   nrhs, r0, (const float4*)b->X,
+                                                                   (const float4*)b->Xlo,
+                                                                   (const float4*)dp->chunk_center, dp->tc_b);
+            CUDA_CHECK(cudaGetLastError());
+            ++launches;
+            if (r0 == 0) mark(dp, kMainEvent, st);
+            if (stored && dp->store_mode == 2) {
+                if (kidx == 0) tc_sym_kernel<0><<<(unsigned)dp->n_tc, kTcThreads, kTsySmemRequest, st>>>(t);
+                else tc_sym_kernel<1><<<(unsigned)dp->n_tc, kTcThreads, kTsySmemRequest, st>>>(t);
+            } else if (stored) {
+                // stages per CTA: the autotuner's choice (same arithmetic)
+                const unsigned g = (unsigned)dp->n_tc;
+                if (dp->tcs_stages == 5) {
+                    kidx == 0 ? tc_stored_ring_kernel<0, 5, 3><<<g, kTcThreads, tcr_smem_request<5, 3>(), st>>>(t)
+                              : tc_stored_ring_kernel<1, 5, 3><<<g, kTcThreads, tcr_smem_request<5, 3>(), st>>>(t);
+                } else if (dp->tcs_stages == 8) {
+                    kidx == 0 ? tc_stored_kernel<0, 8><<<g, kTcThreads, tcs_smem_request<8>(), st>>>(t)
+                              : tc_stored_kernel<1, 8><<<g, kTcThreads, tcs_smem_request<8>(), st>>>(t);
+                } else {
+                    kidx == 0 ? tc_stored_kernel<0, 4><<<g, kTcThreads, tcs_smem_request<4>(), st>>>(t)
+                              : tc_stored_kernel<1, 4><<<g, kTcThreads, tcs_smem_request<4>(), st>>>(t);
+                }
             } else {
-                kidx == 0 ? tc_stored_kernel<0, 4><<<g, kTcThreads, tcs_smem_request<4>(), st>>>(t)
-                          : tc_stored_kernel<1, 4><<<g, kTcThreads, tcs_smem_request<4>(), st>>>(t);
+                // pipeline depth: the autotuner's choice (same arithmetic for every depth)
+                const unsigned g = (unsigned)dp->n_tc;
+                switch (dp->tc_stages) {
+                    case 4: kidx == 0 ? tc_near_kernel<0, kRecNone, 4><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
+                                      : tc_near_kernel<1, kRecNone, 4><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
+                    case 8: kidx == 0 ? tc_near_kernel<0, kRecNone, 8><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
+                                      : tc_near_kernel<1, kRecNone, 8><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
+                    default: kidx == 0 ? tc_near_kernel<0, kRecNone, 6><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
+                                       : tc_near_kernel<1, kRecNone, 6><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
+                }
             }
-        } else {
-            // pipeline depth: the autotuner's choice (same arithmetic for every depth)
-            const unsigned g = (unsigned)dp->n_tc;
-            switch (dp->tc_stages) {
-                case 4: kidx == 0 ? tc_near_kernel<0, kRecNone, 4><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
-                                  : tc_near_kernel<1, kRecNone, 4><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
-                case 8: kidx == 0 ? tc_near_kernel<0, kRecNone, 8><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
-                                  : tc_near_kernel<1, kRecNone, 8><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
-                default: kidx == 0 ? tc_near_kernel<0, kRecNone, 6><<<g, kTcThreads, kTcSmemRequest, st>>>(t)
-                                   : tc_near_kernel<1, kRecNone, 6><<<g, kTcThreads, kTcSmemRequest, st>>>(t); break;
-            }
+            CUDA_CHECK(cudaGetLastError());
         }
-        CUDA_CHECK(cudaGetLastError());
     }
     dp->test_withhold = false;
     return launches;

@@ -1,6 +1,6 @@
 // Upward / downward passes (FP32), the CTA-wide form: a CTA owns 32 NW
-// output rows (NW warps, 32 rows each, lane = right-hand side) x 32
-// right-hand sides of one box and streams the inner index in chunks of 32
+// output rows (NW warps, 32 rows each; a thread holds 4 rows x 8 right-hand
+// sides) x 32 right-hand sides of one box and streams the inner index in chunks of 32
 // through a two-stage pipeline of asynchronous copies that all its threads
 // issue: per chunk the A block (32 inner x 32 NW rows, zero-filled past the
 // box) and the chunk's 32 rows of X (shared by the warps). The chunks are
@@ -116,21 +116,21 @@ __global__ void __launch_bounds__(32 * NW) updown_rows_kernel(const UpBox* __res
                 const float* gb = nb > 0 ? X + rj * nrhs + c : X;
                 cp_async16(sa + (uint32_t)(kGT * ROWS + jj * kGT + (idx & 7) * 4) * 4u, gb, (uint32_t)nb);
             }
-            return;
-        }
+        } else {
 #pragma unroll 8
-        for (int jj = 0; jj < kGT; ++jj) {
-            const bool av = jj < jn && arow;
-            const float* ga = av ? T + t0 + row0 + tid + (int64_t)(j0 + jj) * ld : T;
-            cp_async4(sa + (uint32_t)(jj * ROWS + tid) * 4u, ga, av ? 4u : 0u);
-        }
+            for (int jj = 0; jj < kGT; ++jj) {
+                const bool av = jj < jn && arow;
+                const float* ga = av ? T + t0 + row0 + tid + (int64_t)(j0 + jj) * ld : T;
+                cp_async4(sa + (uint32_t)(jj * ROWS + tid) * 4u, ga, av ? 4u : 0u);
+            }
 #pragma unroll
-        for (int m = 0; m < kGT / NW; ++m) {
-            const int jj = warp + m * NW;
-            const int64_t rj = __shfl_sync(0xffffffffu, ri, jj);
-            const bool bv = jj < jn && colok;
-            const float* gb = bv ? X + rj * nrhs + col : X;
-            cp_async4(sa + (uint32_t)(kGT * ROWS + jj * kGT + lane) * 4u, gb, bv ? 4u : 0u);
+            for (int m = 0; m < kGT / NW; ++m) {
+                const int jj = warp + m * NW;
+                const int64_t rj = __shfl_sync(0xffffffffu, ri, jj);
+                const bool bv = jj < jn && colok;
+                const float* gb = bv ? X + rj * nrhs + col : X;
+                cp_async4(sa + (uint32_t)(kGT * ROWS + jj * kGT + lane) * 4u, gb, bv ? 4u : 0u);
+            }
         }
     };
     // chunks in stream order: (stream, chunk) -> the next one
