@@ -149,11 +149,14 @@ def test_updown_launch_shapes_same_bits():
     x = clustered(12000, 3, 41)
     f = SkelFMM(x, "laplace3d", 1e-6, 16, nrhs_max=40)
     q = torch.from_numpy(W.charges_normal(x.shape[0], 40, 42)).cuda().float()
+    q3 = q[:, :3].contiguous()                           # nrhs not a multiple of 4: 4-byte copies
     ref = {(p, t): (f.apply_transpose if t else f.apply)(q, p) for p in ("fp32", "fp32_tc") for t in (False, True)}
+    ref3 = f.apply(q3, "fp32")
     for code in (1, 2, 4, 8, 17, 18, 20, 24):
         _lib.check(lib.skel_test_set_updown(f._h, code))
         for (p, t), r in ref.items():
             got = (f.apply_transpose if t else f.apply)(q, p)
             f.device_status()
             assert torch.equal(got, r), (code, p, t)
+        assert torch.equal(f.apply(q3, "fp32"), ref3), code
     _lib.check(lib.skel_test_set_updown(f._h, 0))
